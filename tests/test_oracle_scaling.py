@@ -155,3 +155,31 @@ def test_all_ones_closed_form(orc, k, s):
     assert k * 2 ** (2 * (expect + s)) < c["P"] / 2
     C = synthetic.colmajor_view(orc.dgemm(A, B, m, n, k, N))
     assert np.all(C == k * alpha * alpha)
+
+
+@pytest.mark.parametrize("N", [8, 14, 20])
+def test_log2_margin_of_proposed_mu(orc, N):
+    """eq. (proposed-mu) keeps a 4u_32 margin on log2: e <= floor(P' - 0.5 (log2 a_norm + 4u_32))
+    with the exact log2.  Norms are scanned float by float across the point where the margin
+    decides the floor, so dropping the margin (or rounding t the wrong way) fails here."""
+    getcontext().prec = 60
+    c = orc.constants(N)
+    pp = Fraction(c["pprime"])
+    ln2 = Decimal(2).ln()
+    hit = 0
+    for s in range(-40, 41):
+        w = pp - Fraction(s, 2)
+        frac = w - math.floor(w)
+        if not (Fraction(1, 64) < frac < Fraction(1, 2)):
+            continue
+        x0 = np.float32(2.0 ** (2 * float(frac)))
+        for step in range(-48, 49):
+            xf = float(np.float32(x0) + np.float32(step) * np.spacing(np.float32(x0)))
+            a_norm = math.ldexp(xf, s)
+            e = orc.alg2_shift(a_norm, c["pprime"])
+            lg = Decimal(xf).ln() / ln2 + s
+            limit = math.floor(Decimal(c["pprime"]) - Decimal("0.5") * (lg + Decimal(2) ** -22))
+            assert e <= limit
+            assert e >= limit - 1
+            hit += math.floor(Decimal(c["pprime"]) - Decimal("0.5") * lg) != limit
+    assert hit > 0      # the scan reached points where only the margin moves the floor
