@@ -1,0 +1,410 @@
+"""Benchmark of the emulated DGEMM (Ozaki scheme II, fast mode, Algorithm 2 scaling) on GB300.
+
+Workload: square FP64 GEMM m = n = k = 16384, entries (rand - 0.5) exp(phi randn) with phi = 1
+(the paper's generator, eq. random-matrix-generation), N = 14 moduli.  One step = one
+ozaki2_dgemm call: scaling, conversion, residue GEMMs, CRT.  Metric: effective TFLOPS =
+2 m n k / t (eq. tflops).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+For N > 1 (torchrun) every rank runs its own independent problem on its own GPU (weak scaling);
+the only cross-rank traffic is the timing reduction.  --impl reference times the CPU oracle on a
+bounded block of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIZE = 16384
+PHI = 1.0
+NUM_MODULI = 14
+METRIC = "Ozaki-II DGEMM effective TFLOPS at stated error vs cuBLAS DGEMM; p50/p99 lat"
+WORKLOAD = f"square FP64 GEMM m=n=k={SIZE}, phi={PHI}, N={NUM_MODULI} moduli"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), "measured"
+    except Exception:
+        return 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() and args.impl != "reference" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------- oracle arm
+def oracle_block_tflops(A_h, B_h, m, n, k, N, rows: int, cols: int):
+    """Time the CPU oracle on a rows x cols block of C (full k), return (TFLOPS, seconds)."""
+    import numpy as np
+
+    import oracle
+
+    I = np.linspace(0, m - 1, rows).astype(np.int32)
+    J = np.linspace(0, n - 1, cols).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.dgemm_block(A_h, B_h, m, n, k, N, I, J)
+    dt = time.perf_counter() - t0
+    return 2.0 * rows * cols * k / dt / 1e12, dt
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the oracle as it stands, on host cores, bounded blocks of the workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synthetic
+
+    oracle.build()
+    m = n = k = SIZE
+    rows = cols = args.ref_block
+    # The oracle needs only the sampled rows of A and columns of B; the rest is never read, so
+    # draw just those lines from the paper's generator (independent streams per line).
+    I = np.linspace(0, m - 1, rows).astype(np.int32)
+    J = np.linspace(0, n - 1, cols).astype(np.int32)
+    A_rows = synthetic.paper_matrix(rows, k, PHI, synthetic.seed_for(2, 1, 1))  # rows x k block
+    B_cols = synthetic.paper_matrix(k, cols, PHI, synthetic.seed_for(2, 1, 2))
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.dgemm_block(A_rows, B_cols, rows, cols, k, NUM_MODULI, np.arange(rows),
+                           np.arange(cols))
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    flops = 2.0 * rows * cols * k
+    value = flops * len(times) / total / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (int64 residue products, 256-bit CRT)",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{rows}x{cols} block"},
+        "cpu_baseline": {"value": value, "unit": "TFLOPS", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{rows}x{cols} block of C (full k={k}) per step"},
+        "e2e": {"value": value, "unit": "TFLOPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    del I, J
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- GPU arm
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import synthetic
+    from paper_2606_29129_gb300 import ozaki2 as oz
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m = n = k = args.size
+    N = args.moduli
+    seed_a = synthetic.seed_for(2, 1, 1) + 100 * rank
+    seed_b = synthetic.seed_for(2, 1, 2) + 100 * rank
+    A = synthetic.paper_matrix_torch(m, k, PHI, seed_a, device=dev)   # column-major m x k
+    B = synthetic.paper_matrix_torch(k, n, PHI, seed_b, device=dev)   # column-major k x n
+    C = torch.empty((n, m), dtype=torch.float64, device=dev)
+    h = oz.Handle()
+    h.set_timing(True)
+
+    def step():
+        rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N, h)
+        if rc:
+            raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if h.status():
+        raise RuntimeError("device status flags raised during warm-up")
+
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stage_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            stage_ms.append(h.timing())   # waits for this step's events
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    total_ms = t0.elapsed_time(t1)
+    step_ms = sorted(a.elapsed_time(b) for a, b in ev)
+    total_ms = max_over_ranks(total_ms, world)
+    flops_step = 2.0 * m * n * k
+    value = flops_step * world * args.steps / (total_ms * 1e-3) / 1e12
+    status = h.status()
+
+    # dominant kernel: the residue GEMMs (tensor-bound), timed live by the library's events
+    gemm_ms = statistics.mean(s[2] for s in stage_ms)
+    gemm_flops = 2.0 * N * m * n * k
+    burst, sustained, src = peaks()
+    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
+                "frac": achieved / sustained if sustained else None,
+                "traffic": args.gemm_traffic,
+                "peak_source": f"bf16_tflops_sustained ({src}); kernel timed inside the step",
+                "kernel": "residue_gemm_kernel (tcgen05 kind::f16, bf16 residues)"}
+    stages = {name: statistics.mean(s[i] for s in stage_ms)
+              for i, name in enumerate(["scale", "convert", "residue_gemm", "crt"])}
+
+    extra = {}
+    if rank == 0:
+        extra = accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np)
+    e2e = measure_e2e(args, oz, h, A, B, m, n, k, N, torch) if rank == 0 else None
+    if rank != 0:
+        return
+    clk = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 emulated (bf16-held int8 residues on tcgen05, fp32 exact accumulate)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "phi": PHI, "num_moduli": N,
+                   "parallelism": f"replicas x{world} (independent problems)",
+                   "l2": "inputs larger than L2 (A, B, C: 6 GiB)"},
+        "latency_ms": {"p50": step_ms[len(step_ms) // 2],
+                       "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
+                       "min": step_ms[0], "max": step_ms[-1]},
+        "stages_ms": stages,
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": 6 * args.steps,
+        "device_status": status,
+        "e2e": e2e,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np):
+    """Max relative error vs the double-double reference on a sampled block, the same for
+    cuBLAS DGEMM (timed on the same inputs), and the oracle's CPU throughput on a block."""
+    import oracle
+
+    out = {}
+    oracle.build()
+    A_h = A.cpu().numpy()
+    B_h = B.cpu().numpy()
+    C_h = C.cpu().numpy()
+    rng = np.random.default_rng(1)
+    I = np.sort(rng.choice(m, size=args.err_block, replace=False)).astype(np.int32)
+    J = np.sort(rng.choice(n, size=args.err_block, replace=False)).astype(np.int32)
+    hi, lo = oracle.dd_block(A_h, B_h, k, I, J)
+    err, zeros = oracle.max_rel_error(C_h[np.ix_(J, I)], hi, lo)
+    # cuBLAS DGEMM (native FP64) on the same inputs: C^T = B^T A^T in row-major terms
+    At = A.view(k, m)    # row-major (k, m) = A^T
+    Bt = B.view(n, k)    # row-major (n, k) = B^T
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Cd = torch.matmul(Bt, At)   # (n, m) row-major = C column-major
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.cublas_reps):
+        torch.matmul(Bt, At, out=Cd)
+    e.record()
+    torch.cuda.synchronize()
+    cub_ms = s.elapsed_time(e) / args.cublas_reps
+    cub_err, _ = oracle.max_rel_error(Cd.cpu().numpy()[np.ix_(J, I)], hi, lo)
+    out["accuracy"] = {"max_rel_err": err, "zero_reference_entries": zeros,
+                       "sample": f"{len(I)}x{len(J)} random block vs double-double"}
+    out["cublas_dgemm"] = {"tflops": 2.0 * m * n * k / (cub_ms * 1e-3) / 1e12, "ms": cub_ms,
+                           "max_rel_err": cub_err}
+    if not args.no_cpu_baseline:
+        tf, dt = oracle_block_tflops(A_h, B_h, m, n, k, N, args.cpu_block, args.cpu_block)
+        out["cpu_baseline"] = {"value": tf, "unit": "TFLOPS", "cores": oracle.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"{args.cpu_block}x{args.cpu_block} block of C "
+                                         f"(full k={k}), {dt:.1f} s"}
+    return out
+
+
+def measure_e2e(args, oz, h, A, B, m, n, k, N, torch):
+    """The same metric through ozaki2_dgemm with host buffers: pinned H2D of A and B, the call,
+    D2H of C, all inside the timed region."""
+    A_h = torch.empty(A.shape, dtype=torch.float64, pin_memory=True)
+    B_h = torch.empty(B.shape, dtype=torch.float64, pin_memory=True)
+    C_h = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
+    A_h.copy_(A)
+    B_h.copy_(B)
+    dA = torch.empty_like(A)
+    dB = torch.empty_like(B)
+    dC = torch.empty((n, m), dtype=torch.float64, device=A.device)
+    h.set_timing(False)
+
+    def step():
+        dA.copy_(A_h, non_blocking=True)
+        dB.copy_(B_h, non_blocking=True)
+        rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, dC, m, N, h)
+        if rc:
+            raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+        C_h.copy_(dC, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    reps = max(1, min(args.steps, 3))
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        step()
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / reps
+    h.set_timing(True)
+    return {"value": 2.0 * m * n * k / (ms * 1e-3) / 1e12, "unit": "TFLOPS",
+            "h2d_bytes_per_step": A.numel() * 8 + B.numel() * 8,
+            "d2h_bytes_per_step": m * n * 8, "ms_per_step": ms}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=SIZE)
+    ap.add_argument("--moduli", type=int, default=NUM_MODULI)
+    ap.add_argument("--err-block", type=int, default=96)
+    ap.add_argument("--cpu-block", type=int, default=256)
+    ap.add_argument("--ref-block", type=int, default=192)
+    ap.add_argument("--cublas-reps", type=int, default=1)
+    ap.add_argument("--gemm-traffic", type=float, default=None,
+                    help="DRAM bytes per residue-GEMM launch from an ncu capture, if current")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warm-up raised to 3 steps")
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * ozaki2.h -- C ABI of the GB300 (sm_103a) Ozaki scheme II DGEMM emulation.
+ *
+ * Method: Ozaki scheme II (Section 2.2 of Kawakami & Takahashi, "Improved Scaling for Fast Mode
+ * of Ozaki Scheme II") in fast mode with the paper's scale-invariant scaling (Section 4,
+ * eq. (proposed-mu)/(proposed-nu), Algorithm 2).  C = alpha op(A) op(B) + beta C is computed as
+ *   Step 1  moduli p_1..p_N (the first N of eq. (moduli)), P, P_i, q_i;
+ *   Step 2  shifts e_i = log2 mu_i, f_j = log2 nu_j (Algorithm 2), a' = trunc(2^e a);
+ *   Step 3  N exact residue GEMMs rmod(A',p_l) rmod(B',p_l), CRT (eqs. os2-C', os2-C'');
+ *   Step 4  C = diag(mu)^-1 C'' diag(nu)^-1.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are column-major (BLAS).  op(X) = X for trans 'N'/'n', X^T for 'T'/'t'/'C'/'c'.
+ *  - All matrix, shift, plane and residue pointers are DEVICE pointers owned by the caller.  The
+ *    library never frees them and never keeps them after the queued work has run.  Every GPU
+ *    entry point is asynchronous on the handle's stream: keep buffers alive until that stream
+ *    is synchronised.  A and B are only read.  C is read only when beta != 0.
+ *  - handle == NULL selects a process-wide default handle (created on first use, stream 0).
+ *  - Return value: OZAKI2_SUCCESS (0); -i when argument i (1-based, as in BLAS xerbla) is
+ *    invalid; a positive OZAKI2_ERROR_* code otherwise.  Errors raised inside kernels are
+ *    reported as flags by ozaki2_get_status.
+ *  - There is no CPU fallback: without an sm_103 device every GPU entry point returns
+ *    OZAKI2_ERROR_NO_DEVICE.
+ */
+#ifndef OZAKI2_H
+#define OZAKI2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------------- */
+#define OZAKI2_SUCCESS 0
+#define OZAKI2_ERROR_CUDA 1       /* a CUDA runtime call or a kernel launch failed */
+#define OZAKI2_ERROR_ALLOC 2      /* the handle could not allocate its workspace */
+#define OZAKI2_ERROR_WORKSPACE 3  /* a workspace set with ozaki2_set_workspace is too small */
+#define OZAKI2_ERROR_NO_DEVICE 4  /* the current device is not an sm_103 GPU */
+#define OZAKI2_ERROR_DRIVER 5     /* the driver's tensor-map encoder is unavailable or failed */
+
+/* ---- device status flags (ozaki2_get_status) ------------------------------------------- */
+#define OZAKI2_STATUS_NONFINITE 1u /* a row of op(A) or column of op(B) had a non-finite squared
+                                      norm (Inf/NaN input or overflow); its outputs are NaN */
+#define OZAKI2_STATUS_TIMEOUT 2u   /* a bounded wait inside the residue GEMM expired; the
+                                      outputs of that call are undefined */
+#define OZAKI2_STATUS_RANGE 4u     /* a scaled entry trunc(2^e a) exceeded the range the shifts
+                                      allow (only reachable with caller-supplied shifts) */
+
+/* Layout constants of the residue planes (see ozaki2_convert_a / ozaki2_residue_gemm). */
+#define OZAKI2_ROWS_ALIGN_A 128   /* rows_pad of A planes must be a multiple of this */
+#define OZAKI2_ROWS_ALIGN_B 256   /* rows_pad of B planes must be a multiple of this */
+#define OZAKI2_K_ALIGN 64         /* k_pad must be a multiple of this */
+#define OZAKI2_MAX_MODULI 20
+#define OZAKI2_MIN_MODULI 2
+#define OZAKI2_SHIFT_NONFINITE INT32_MIN /* shift written for a line with a non-finite norm */
+
+typedef struct ozaki2_context* ozaki2_handle_t;
+
+/* ---- handle ------------------------------------------------------------------------------ */
+/* Create a handle bound to the current CUDA device (stream 0, internal workspace).
+ * Allocates a few bytes of device memory for status flags.  Errors: OZAKI2_ERROR_NO_DEVICE,
+ * OZAKI2_ERROR_CUDA; -1 if handle is NULL. */
+int ozaki2_create(ozaki2_handle_t* handle);
+
+/* Destroy a handle; synchronises its stream, frees its internal workspace (never a workspace
+ * given with ozaki2_set_workspace). */
+int ozaki2_destroy(ozaki2_handle_t handle);
+
+/* Set the cudaStream_t (passed as void*) on which the handle queues work. */
+int ozaki2_set_stream(ozaki2_handle_t handle, void* stream);
+
+/* Give the handle a caller-owned device workspace of `bytes` bytes (256-byte aligned), or
+ * NULL/0 to return to the internal, growable workspace.  The caller keeps it alive while work
+ * that uses it is queued. */
+int ozaki2_set_workspace(ozaki2_handle_t handle, void* workspace, size_t bytes);
+
+/* Workspace bytes that ozaki2_dgemm needs for op(A) m x k, op(B) k x n and N moduli:
+ * shifts, bf16 residue planes of A and B, and int8 product residues.  0 on invalid sizes. */
+size_t ozaki2_workspace_size(int m, int n, int k, int num_moduli);
+
+/* Synchronise the handle's stream, then return and clear the OR of the status flags raised by
+ * the kernels queued since the last call.  *flags receives OZAKI2_STATUS_* bits. */
+int ozaki2_get_status(ozaki2_handle_t handle, unsigned* flags);
+
+/* Stage timing: with on = 1 the handle records CUDA events on its stream around the stages of
+ * each later ozaki2_dgemm_h / ozaki2_dgemm call (scaling of A and B, conversion of A and B,
+ * residue GEMMs, CRT); on = 0 stops.  Costs four event records per call. */
+int ozaki2_set_timing(ozaki2_handle_t handle, int on);
+
+/* Milliseconds of each stage of the most recent timed ozaki2_dgemm call on this handle:
+ * ms[0] scaling, ms[1] conversion, ms[2] residue GEMMs, ms[3] CRT (host array of 4 floats).
+ * Waits for that call's events.  Returns OZAKI2_ERROR_CUDA if no timed call was made. */
+int ozaki2_get_timing(ozaki2_handle_t handle, float* ms);
+
+/* Human-readable text of a return code. */
+const char* ozaki2_error_string(int code);
+
+/* ---- Step 1: constants (host only) -------------------------------------------------------- */
+/* Step 1 (Section 2.2) and P'_prop (Section 4): writes the first num_moduli moduli of
+ * eq. (moduli), q_l = (P/p_l)^{-1} mod p_l, and P'_prop = single-down(log2(P-1)/2 - 0.5).
+ * moduli and inverses are host arrays of num_moduli ints; pprime a host float. */
+int ozaki2_constants(int num_moduli, int* moduli, int* inverses, float* pprime);
+
+/* ---- the whole path ----------------------------------------------------------------------- */
+/* Emulated DGEMM: C = alpha op(A) op(B) + beta C through Steps 1-4 with N = num_moduli moduli
+ * (2..20).  op(A) is m x k, op(B) k x n, C is m x n with ldc >= max(1, m).  Quick returns:
+ * m = 0 or n = 0 does nothing; k = 0 or alpha = 0 computes C = beta C (C = 0 when beta = 0).
+ * Uses the default handle.  Argument numbers for errors: transA 1, transB 2, m 3, n 4, k 5,
+ * alpha 6, A 7, lda 8, B 9, ldb 10, beta 11, C 12, ldc 13, num_moduli 14. */
+int ozaki2_dgemm(char transA, char transB, int m, int n, int k, double alpha, const double* A,
+                 int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                 int num_moduli);
+
+/* Same as ozaki2_dgemm on an explicit handle (argument numbers shift by one). */
+int ozaki2_dgemm_h(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
+                   double alpha, const double* A, int lda, const double* B, int ldb,
+                   double beta, double* C, int ldc, int num_moduli);
+
+/* ---- the stages, one entry point each ------------------------------------------------------ */
+/* Step 2 scaling (Algorithm 2, eq. (proposed-mu)): shifts[i] = log2(mu_i) for the m rows of
+ * op(A) (m x k, lda).  The squared norm is accumulated in order h = 1..k with one fused
+ * multiply-add rounded upward per term.  A zero row gets 0; a row with a non-finite squared
+ * norm gets OZAKI2_SHIFT_NONFINITE and raises OZAKI2_STATUS_NONFINITE.  shifts: device int[m].
+ * Arguments: handle 1, transA 2, m 3, k 4, A 5, lda 6, num_moduli 7, shifts 8. */
+int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
+                   int num_moduli, int* shifts);
+
+/* Step 2 scaling for the n columns of op(B) (k x n, ldb): shifts[j] = log2(nu_j)
+ * (eq. (proposed-nu)).  Same conventions as ozaki2_scale_a. */
+int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const double* B, int ldb,
+                   int num_moduli, int* shifts);
+
+/* Step 2 conversion (a' = trunc(2^{e_i} a_ih)) and the residues of eq. (os2-C'):
+ * planes[l][i][h] = rmod(a'_ih, p_l) stored as bfloat16 (every residue is an integer in
+ * [-128, 127], exact in bf16), layout l*rows_pad*k_pad + i*k_pad + h (K contiguous).  Rows
+ * i >= m and columns h >= k of each plane are written as zero.  rows_pad >= m must be a
+ * multiple of OZAKI2_ROWS_ALIGN_A, k_pad >= k a multiple of OZAKI2_K_ALIGN.  The residue of
+ * the even modulus 256 uses the representative in [-128, 127].  A line with shift
+ * OZAKI2_SHIFT_NONFINITE gets zero residues.  Arguments: handle 1, transA 2, m 3, k 4, A 5,
+ * lda 6, shifts 7, num_moduli 8, planes 9, rows_pad 10, k_pad 11. */
+int ozaki2_convert_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
+                     const int* shifts, int num_moduli, void* planes, int rows_pad, int k_pad);
+
+/* Same for the columns of op(B): planes[l][j][h] = rmod(trunc(2^{f_j} b_hj), p_l), layout
+ * l*rows_pad*k_pad + j*k_pad + h; rows_pad >= n a multiple of OZAKI2_ROWS_ALIGN_B. */
+int ozaki2_convert_b(ozaki2_handle_t handle, char transB, int k, int n, const double* B, int ldb,
+                     const int* shifts, int num_moduli, void* planes, int rows_pad, int k_pad);
+
+/* Step 3 residue GEMMs (eq. (os2-C')): for every modulus l,
+ *   residues[l][i][j] = rmod(sum_h A_l[i][h] B_l[j][h], p_l)
+ * exactly, for all i < m_pad, j < n_pad (layout l*m_pad*n_pad + i*n_pad + j, int8, values in
+ * [-128, 127]).  planes_a / planes_b are bf16 planes as written by ozaki2_convert_a/_b with
+ * rows_pad = m_pad / n_pad and the same k_pad; their entries must be integers in
+ * [-128, 127].  Runs on tcgen05 tensor cores (bf16 operands, FP32 accumulation kept exact by
+ * reducing modulo p_l every <= 960 products).  Pointers 16-byte aligned.  Arguments: handle 1,
+ * num_moduli 2, m_pad 3, n_pad 4, k_pad 5, planes_a 6, planes_b 7, residues 8. */
+int ozaki2_residue_gemm(ozaki2_handle_t handle, int num_moduli, int m_pad, int n_pad, int k_pad,
+                        const void* planes_a, const void* planes_b, int8_t* residues);
+
+/* Steps 3-4 (eqs. os2-C', os2-C'' and the rescaling): from product residues
+ * residues[l*plane_stride + i*ldr + j] (any representative in [-128, 127]) computes
+ * C'' = rmod(sum_l P_l q_l c_l, P) exactly, rounds it to the nearest double, multiplies by
+ * 2^-(shifts_a[i] + shifts_b[j]) and writes C[i + j*ldc] = alpha*y (+ beta*C when beta != 0),
+ * for i < m, j < n.  A sentinel shift gives NaN.  Arguments: handle 1, num_moduli 2, m 3, n 4,
+ * residues 5, ldr 6, plane_stride 7, shifts_a 8, shifts_b 9, alpha 10, beta 11, C 12, ldc 13. */
+int ozaki2_crt(ozaki2_handle_t handle, int num_moduli, int m, int n, const int8_t* residues,
+               int ldr, long long plane_stride, const int* shifts_a, const int* shifts_b,
+               double alpha, double beta, double* C, int ldc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OZAKI2_H */

@@ -1,0 +1,454 @@
+// api.cu -- the C ABI of include/ozaki2.h: handles, workspace, argument checks, the stage entry
+// points and the composed emulated DGEMM (Steps 1-4 of Ozaki scheme II, Section 2.2, with the
+// scaling of Section 4).
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "ozaki2_internal.h"
+
+struct ozaki2_context {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = 0;
+    unsigned* d_status = nullptr;  // device word of OZAKI2_STATUS_* flags
+    void* ws = nullptr;            // workspace (owned unless user_ws)
+    size_t ws_bytes = 0;
+    bool user_ws = false;
+    int chunk_k = 960;             // products accumulated between modular reductions
+    bool timing = false;           // record stage events in ozaki2_dgemm
+    bool timed_call = false;       // a timed call has been queued
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+using namespace ozaki2;
+
+bool is_trans_char(char c) {
+    return c == 'N' || c == 'n' || c == 'T' || c == 't' || c == 'C' || c == 'c';
+}
+bool is_notrans(char c) { return c == 'N' || c == 'n'; }
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+int check_device(int* dev_out, int* sms_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return OZAKI2_ERROR_NO_DEVICE;
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+        return OZAKI2_ERROR_NO_DEVICE;
+    if (major != 10 || minor != 3) return OZAKI2_ERROR_NO_DEVICE;  // built for sm_103a only
+    if (sms_out) cudaDeviceGetAttribute(sms_out, cudaDevAttrMultiProcessorCount, dev);
+    if (dev_out) *dev_out = dev;
+    return OZAKI2_SUCCESS;
+}
+
+int init_context(ozaki2_context* ctx) {
+    int rc = check_device(&ctx->device, &ctx->num_sms);
+    if (rc) return rc;
+    if (cudaMalloc(&ctx->d_status, 256) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if (cudaMemset(ctx->d_status, 0, 256) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    return OZAKI2_SUCCESS;
+}
+
+ozaki2_context* g_default = nullptr;
+int g_default_rc = OZAKI2_SUCCESS;
+std::once_flag g_default_once;
+
+// handle == NULL -> the process-wide default handle.
+int resolve(ozaki2_handle_t h, ozaki2_context** out) {
+    if (h) {
+        *out = h;
+        return OZAKI2_SUCCESS;
+    }
+    std::call_once(g_default_once, [] {
+        g_default = new ozaki2_context();
+        g_default_rc = init_context(g_default);
+    });
+    *out = g_default;
+    return g_default_rc;
+}
+
+// Make sure the handle has at least `bytes` of workspace.
+int ensure_workspace(ozaki2_context* ctx, size_t bytes) {
+    if (ctx->ws_bytes >= bytes) return OZAKI2_SUCCESS;
+    if (ctx->user_ws) return OZAKI2_ERROR_WORKSPACE;
+    if (ctx->ws) {
+        // work queued on other streams may still use the old buffer
+        if (cudaDeviceSynchronize() != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return OZAKI2_ERROR_ALLOC;
+    }
+    ctx->ws_bytes = bytes;
+    return OZAKI2_SUCCESS;
+}
+
+struct Layout {
+    int64_t m_pad, n_pad, k_pad;
+    size_t off_e, off_f, off_pa, off_pb, off_res, total;
+};
+
+Layout make_layout(int m, int n, int k, int N) {
+    Layout L;
+    L.m_pad = round_up(m > 0 ? m : 1, OZAKI2_ROWS_ALIGN_A);
+    L.n_pad = round_up(n > 0 ? n : 1, OZAKI2_ROWS_ALIGN_B);
+    L.k_pad = round_up(k > 0 ? k : 1, OZAKI2_K_ALIGN);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (size_t)round_up((int64_t)bytes, 256);
+        return o;
+    };
+    L.off_e = take(sizeof(int) * (size_t)L.m_pad);
+    L.off_f = take(sizeof(int) * (size_t)L.n_pad);
+    L.off_pa = take((size_t)2 * N * L.m_pad * L.k_pad);
+    L.off_pb = take((size_t)2 * N * L.n_pad * L.k_pad);
+    L.off_res = take((size_t)N * L.m_pad * L.n_pad);
+    L.total = off;
+    return L;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA; }
+
+// Strides of the lines of op(A) (rows) and op(B) (columns) of a column-major matrix.
+void rows_of_op(char trans, int64_t ld, int64_t* line_stride, int64_t* elem_stride) {
+    if (is_notrans(trans)) { *line_stride = 1; *elem_stride = ld; }
+    else { *line_stride = ld; *elem_stride = 1; }
+}
+void cols_of_op(char trans, int64_t ld, int64_t* line_stride, int64_t* elem_stride) {
+    if (is_notrans(trans)) { *line_stride = ld; *elem_stride = 1; }
+    else { *line_stride = 1; *elem_stride = ld; }
+}
+
+int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m, int n, int k,
+               double alpha, const double* A, int lda, const double* B, int ldb, double beta,
+               double* C, int ldc, int N) {
+    if (!is_trans_char(transA)) return -(argbase + 1);
+    if (!is_trans_char(transB)) return -(argbase + 2);
+    if (m < 0) return -(argbase + 3);
+    if (n < 0) return -(argbase + 4);
+    if (k < 0) return -(argbase + 5);
+    const int arows = is_notrans(transA) ? m : k;
+    const int brows = is_notrans(transB) ? k : n;
+    if (lda < (arows > 1 ? arows : 1)) return -(argbase + 8);
+    if (ldb < (brows > 1 ? brows : 1)) return -(argbase + 10);
+    if (ldc < (m > 1 ? m : 1)) return -(argbase + 13);
+    if (N < OZAKI2_MIN_MODULI || N > OZAKI2_MAX_MODULI) return -(argbase + 14);
+    if (m > 0 && k > 0 && !A) return -(argbase + 7);
+    if (k > 0 && n > 0 && !B) return -(argbase + 9);
+    if (m > 0 && n > 0 && !C) return -(argbase + 12);
+    if (m == 0 || n == 0) return OZAKI2_SUCCESS;
+    if (k == 0 || alpha == 0.0) return cuda_rc(launch_scale_c(m, n, beta, C, ldc, ctx->stream));
+
+    const ModTables* T = mod_tables(N);
+    const Layout L = make_layout(m, n, k, N);
+    int rc = ensure_workspace(ctx, L.total);
+    if (rc) return rc;
+    char* ws = static_cast<char*>(ctx->ws);
+    int* e = reinterpret_cast<int*>(ws + L.off_e);
+    int* f = reinterpret_cast<int*>(ws + L.off_f);
+    void* pa = ws + L.off_pa;
+    void* pb = ws + L.off_pb;
+    int8_t* res = reinterpret_cast<int8_t*>(ws + L.off_res);
+    cudaStream_t st = ctx->stream;
+
+    auto mark = [&](int i) {
+        if (ctx->timing) cudaEventRecord(ctx->ev[i], st);
+    };
+    int64_t als, aes, bls, bes;
+    rows_of_op(transA, lda, &als, &aes);
+    cols_of_op(transB, ldb, &bls, &bes);
+    mark(0);
+    if ((rc = cuda_rc(launch_scale(A, als, aes, m, k, T->pprime, e, ctx->d_status, st)))) return rc;
+    if ((rc = cuda_rc(launch_scale(B, bls, bes, n, k, T->pprime, f, ctx->d_status, st)))) return rc;
+    mark(1);
+    if ((rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, (int)L.m_pad,
+                                     (int)L.k_pad, ctx->d_status, st))))
+        return rc;
+    if ((rc = cuda_rc(launch_convert(B, bls, bes, n, k, f, T->conv, pb, (int)L.n_pad,
+                                     (int)L.k_pad, ctx->d_status, st))))
+        return rc;
+    mark(2);
+    if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, pa, pb, res,
+                                  T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k, st)))
+        return rc;
+    mark(3);
+    rc = cuda_rc(launch_crt(res, L.n_pad, L.m_pad * L.n_pad, m, n, e, f, alpha, beta, C, ldc, *T,
+                            ctx->d_status, st));
+    mark(4);
+    if (ctx->timing) ctx->timed_call = true;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ozaki2_create(ozaki2_handle_t* handle) {
+    if (!handle) return -1;
+    *handle = nullptr;
+    auto* ctx = new ozaki2_context();
+    int rc = init_context(ctx);
+    if (rc) {
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        delete ctx;
+        return rc;
+    }
+    *handle = ctx;
+    return OZAKI2_SUCCESS;
+}
+
+int ozaki2_destroy(ozaki2_handle_t handle) {
+    if (!handle) return -1;
+    cudaStreamSynchronize(handle->stream);
+    if (handle->ws && !handle->user_ws) cudaFree(handle->ws);
+    if (handle->d_status) cudaFree(handle->d_status);
+    for (auto& e : handle->ev)
+        if (e) cudaEventDestroy(e);
+    delete handle;
+    return OZAKI2_SUCCESS;
+}
+
+int ozaki2_set_stream(ozaki2_handle_t handle, void* stream) {
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return OZAKI2_SUCCESS;
+}
+
+int ozaki2_set_workspace(ozaki2_handle_t handle, void* workspace, size_t bytes) {
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return -2;
+    if (ctx->ws && !ctx->user_ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+    }
+    ctx->ws = workspace;
+    ctx->ws_bytes = workspace ? bytes : 0;
+    ctx->user_ws = workspace != nullptr;
+    return OZAKI2_SUCCESS;
+}
+
+size_t ozaki2_workspace_size(int m, int n, int k, int num_moduli) {
+    if (m < 0 || n < 0 || k < 0 || num_moduli < OZAKI2_MIN_MODULI ||
+        num_moduli > OZAKI2_MAX_MODULI)
+        return 0;
+    return make_layout(m, n, k, num_moduli).total;
+}
+
+int ozaki2_get_status(ozaki2_handle_t handle, unsigned* flags) {
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    if (!flags) return -2;
+    unsigned v = 0;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if (cudaMemcpy(&v, ctx->d_status, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    if (cudaMemset(ctx->d_status, 0, sizeof(v)) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    *flags = v;
+    return OZAKI2_SUCCESS;
+}
+
+int ozaki2_set_timing(ozaki2_handle_t handle, int on) {
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    if (on && !ctx->ev[0]) {
+        for (auto& e : ctx->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    }
+    ctx->timing = on != 0;
+    return OZAKI2_SUCCESS;
+}
+
+int ozaki2_get_timing(ozaki2_handle_t handle, float* ms) {
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    if (!ms) return -2;
+    if (!ctx->timed_call) return OZAKI2_ERROR_CUDA;
+    if (cudaEventSynchronize(ctx->ev[4]) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    for (int i = 0; i < 4; ++i)
+        if (cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+    return OZAKI2_SUCCESS;
+}
+
+const char* ozaki2_error_string(int code) {
+    if (code < 0) return "invalid argument";
+    switch (code) {
+        case OZAKI2_SUCCESS: return "success";
+        case OZAKI2_ERROR_CUDA: return "CUDA runtime error";
+        case OZAKI2_ERROR_ALLOC: return "workspace allocation failed";
+        case OZAKI2_ERROR_WORKSPACE: return "user workspace too small";
+        case OZAKI2_ERROR_NO_DEVICE: return "no sm_103 GPU available";
+        case OZAKI2_ERROR_DRIVER: return "tensor map encoder unavailable or failed";
+        default: return "unknown error";
+    }
+}
+
+int ozaki2_constants(int num_moduli, int* moduli, int* inverses, float* pprime) {
+    const ModTables* T = mod_tables(num_moduli);
+    if (!T) return -1;
+    if (!moduli) return -2;
+    if (!inverses) return -3;
+    if (!pprime) return -4;
+    for (int l = 0; l < num_moduli; ++l) {
+        moduli[l] = T->moduli[l];
+        inverses[l] = T->inverses[l];
+    }
+    *pprime = T->pprime;
+    return OZAKI2_SUCCESS;
+}
+
+int ozaki2_dgemm(char transA, char transB, int m, int n, int k, double alpha, const double* A,
+                 int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                 int num_moduli) {
+    ozaki2_context* ctx;
+    int rc = resolve(nullptr, &ctx);
+    if (rc) return rc;
+    return dgemm_impl(ctx, 0, transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                      num_moduli);
+}
+
+int ozaki2_dgemm_h(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
+                   double alpha, const double* A, int lda, const double* B, int ldb,
+                   double beta, double* C, int ldc, int num_moduli) {
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    return dgemm_impl(ctx, 1, transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                      num_moduli);
+}
+
+int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
+                   int num_moduli, int* shifts) {
+    if (!is_trans_char(transA)) return -2;
+    if (m < 0) return -3;
+    if (k < 0) return -4;
+    const int rows = is_notrans(transA) ? m : k;
+    if (lda < (rows > 1 ? rows : 1)) return -6;
+    const ModTables* T = mod_tables(num_moduli);
+    if (!T) return -7;
+    if (m > 0 && k > 0 && !A) return -5;
+    if (m > 0 && !shifts) return -8;
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    int64_t ls, es;
+    rows_of_op(transA, lda, &ls, &es);
+    return cuda_rc(launch_scale(A, ls, es, m, k, T->pprime, shifts, ctx->d_status, ctx->stream));
+}
+
+int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const double* B, int ldb,
+                   int num_moduli, int* shifts) {
+    if (!is_trans_char(transB)) return -2;
+    if (k < 0) return -3;
+    if (n < 0) return -4;
+    const int rows = is_notrans(transB) ? k : n;
+    if (ldb < (rows > 1 ? rows : 1)) return -6;
+    const ModTables* T = mod_tables(num_moduli);
+    if (!T) return -7;
+    if (n > 0 && k > 0 && !B) return -5;
+    if (n > 0 && !shifts) return -8;
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    int64_t ls, es;
+    cols_of_op(transB, ldb, &ls, &es);
+    return cuda_rc(launch_scale(B, ls, es, n, k, T->pprime, shifts, ctx->d_status, ctx->stream));
+}
+
+static int convert_common(ozaki2_handle_t handle, bool is_a, char trans, int lines, int len,
+                          const double* X, int ld, const int* shifts, int num_moduli,
+                          void* planes, int rows_pad, int k_pad) {
+    const int rows = is_a ? (is_notrans(trans) ? lines : len) : (is_notrans(trans) ? len : lines);
+    if (ld < (rows > 1 ? rows : 1)) return -6;
+    if (!mod_tables(num_moduli)) return -8;
+    if (lines > 0 && len > 0 && !X) return -5;
+    if (lines > 0 && !shifts) return -7;
+    const int align = is_a ? OZAKI2_ROWS_ALIGN_A : OZAKI2_ROWS_ALIGN_B;
+    if (rows_pad < lines || rows_pad % align) return -10;
+    if (k_pad < len || k_pad % OZAKI2_K_ALIGN) return -11;
+    if (!planes || (reinterpret_cast<uintptr_t>(planes) & 15u)) return -9;
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    int64_t ls, es;
+    if (is_a) rows_of_op(trans, ld, &ls, &es);
+    else cols_of_op(trans, ld, &ls, &es);
+    return cuda_rc(launch_convert(X, ls, es, lines, len, shifts, mod_tables(num_moduli)->conv,
+                                  planes, rows_pad, k_pad, ctx->d_status, ctx->stream));
+}
+
+int ozaki2_convert_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
+                     const int* shifts, int num_moduli, void* planes, int rows_pad, int k_pad) {
+    if (!is_trans_char(transA)) return -2;
+    if (m < 0) return -3;
+    if (k < 0) return -4;
+    return convert_common(handle, true, transA, m, k, A, lda, shifts, num_moduli, planes,
+                          rows_pad, k_pad);
+}
+
+int ozaki2_convert_b(ozaki2_handle_t handle, char transB, int k, int n, const double* B, int ldb,
+                     const int* shifts, int num_moduli, void* planes, int rows_pad, int k_pad) {
+    if (!is_trans_char(transB)) return -2;
+    if (k < 0) return -3;
+    if (n < 0) return -4;
+    return convert_common(handle, false, transB, n, k, B, ldb, shifts, num_moduli, planes,
+                          rows_pad, k_pad);
+}
+
+int ozaki2_residue_gemm(ozaki2_handle_t handle, int num_moduli, int m_pad, int n_pad, int k_pad,
+                        const void* planes_a, const void* planes_b, int8_t* residues) {
+    const ModTables* T = mod_tables(num_moduli);
+    if (!T) return -2;
+    if (m_pad < 0 || m_pad % OZAKI2_ROWS_ALIGN_A) return -3;
+    if (n_pad < 0 || n_pad % OZAKI2_ROWS_ALIGN_B) return -4;
+    if (k_pad < 0 || k_pad % OZAKI2_K_ALIGN) return -5;
+    const bool work = m_pad > 0 && n_pad > 0;
+    if (work && k_pad > 0 && (!planes_a || (reinterpret_cast<uintptr_t>(planes_a) & 15u))) return -6;
+    if (work && k_pad > 0 && (!planes_b || (reinterpret_cast<uintptr_t>(planes_b) & 15u))) return -7;
+    if (work && (!residues || (reinterpret_cast<uintptr_t>(residues) & 15u))) return -8;
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    return launch_residue_gemm(num_moduli, m_pad, n_pad, k_pad, planes_a, planes_b, residues,
+                               T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k, ctx->stream);
+}
+
+int ozaki2_crt(ozaki2_handle_t handle, int num_moduli, int m, int n, const int8_t* residues,
+               int ldr, long long plane_stride, const int* shifts_a, const int* shifts_b,
+               double alpha, double beta, double* C, int ldc) {
+    const ModTables* T = mod_tables(num_moduli);
+    if (!T) return -2;
+    if (m < 0) return -3;
+    if (n < 0) return -4;
+    if (ldr < (n > 1 ? n : 1)) return -6;
+    if (plane_stride < (long long)m * ldr) return -7;
+    if (ldc < (m > 1 ? m : 1)) return -13;
+    if (m > 0 && n > 0) {
+        if (!residues) return -5;
+        if (!shifts_a) return -8;
+        if (!shifts_b) return -9;
+        if (!C) return -12;
+    }
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    return cuda_rc(launch_crt(residues, ldr, plane_stride, m, n, shifts_a, shifts_b, alpha, beta,
+                              C, ldc, *T, ctx->d_status, ctx->stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,242 @@
+// crt.cu -- Steps 3-4 of Ozaki scheme II: CRT reconstruction (eqs. os2-C', os2-C'') and the
+// rescaling C = diag(mu)^-1 C'' diag(nu)^-1, then C = alpha C (+ beta C_in).
+//
+// GB300 design: FP64 throughput is a small fraction of the integer rate on this part, so the
+// reconstruction is exact multi-word integer arithmetic instead of split FP64 constants:
+//   w_l  = q_l c_l mod p_l                       (in [0, p_l))
+//   X    = sum_l P_l w_l                         (P_l = P/p_l, W 32-bit words, 64-bit column sums)
+//   Q    = round(sum_l w_l / p_l) = round(X / P) (single-precision estimate)
+//   C''  = X - Q P                               (exact; corrected by +-P if the estimate sat
+//                                                 within 0.01 of a half-integer)
+// Since P_l q_l w_l == P_l q_l c_l (mod P), C'' = rmod(sum_l P_l q_l c_l, P) of eq. (os2-C'').
+// C'' is rounded to the nearest double (ties to even) with the unscaling 2^-(e_i + f_j) folded
+// into the exponent; results outside the normal range take a two-multiply path that rounds once.
+//
+// Memory: reads N bytes of product residues per entry, writes 8 bytes (reads 8 more if beta != 0).
+#include "ozaki2_internal.h"
+
+namespace ozaki2 {
+namespace {
+
+constexpr int TI = 32, TJ = 32;  // tile of the output: 32 rows x 32 columns, 256 threads
+
+// y * 2^s rounded to nearest once, for any s (x is a normal double).
+__device__ double scale_pow2_rn(double x, int s) {
+    if (s > 0) {
+        while (s > 1000) { x = __dmul_rn(x, 0x1p1000); s -= 1000; }
+        return __dmul_rn(x, __longlong_as_double((long long)(s + 1023) << 52));
+    }
+    // bring x to [1, 2) exactly, then one rounding multiply by 2^(e + s) split as 2^(t) 2^-600
+    int e = ilogb(x);
+    double m = __dmul_rn(x, __longlong_as_double((long long)(1023 - e) << 52));
+    int t = e + s;  // final exponent
+    if (t >= -1022) return __dmul_rn(m, __longlong_as_double((long long)(t + 1023) << 52));
+    if (t < -1022 - 600) return __dmul_rn(m, 0.0);  // far below the smallest subnormal: +-0
+    double m2 = __dmul_rn(m, __longlong_as_double((long long)(t + 600 + 1023) << 52));  // exact
+    return __dmul_rn(m2, 0x1p-600);
+}
+
+template <int W>
+__device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int64_t plane, int ea,
+                                           int fb, const CrtTables& t) {
+    if (ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE) return __longlong_as_double(0x7FF8000000000000ll);
+    uint64_t acc[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) acc[j] = 0;
+    float qf = 0.0f;
+    for (int l = 0; l < t.N; ++l) {
+        const int c = res[(int64_t)l * plane];
+        const uint32_t v = (uint32_t)(c + 128) * t.q[l] + t.off[l];   // = q_l c (mod p_l), < 2^16
+        const uint32_t qq = __umulhi(v, t.barrett[l]);
+        uint32_t w = v - qq * t.p[l];
+        if (w >= t.p[l]) w -= t.p[l];
+        qf = fmaf((float)w, t.inv_p[l], qf);
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.Pl[l][j] * w;
+    }
+    // carry-propagate X into 32-bit words
+    uint32_t X[W];
+    uint64_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const uint64_t s = acc[j] + carry;
+        X[j] = (uint32_t)s;
+        carry = s >> 32;
+    }
+    const float qr = rintf(qf);
+    int Q = (int)qr;
+    // Y = X - Q P, two's complement over W words
+    uint32_t Y[W];
+    uint64_t qpc = 0;
+    int64_t borrow = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const uint64_t prod = (uint64_t)(uint32_t)Q * t.P[j] + qpc;
+        qpc = prod >> 32;
+        const int64_t d = (int64_t)X[j] - (int64_t)(uint32_t)prod - borrow;
+        Y[j] = (uint32_t)d;
+        borrow = d < 0 ? 1 : 0;
+    }
+    if (fabsf(qf - qr) > 0.49f) {
+        // The estimate may be one off: make -P/2 <= Y < P/2 exactly.
+        const bool neg = (Y[W - 1] >> 31) != 0;
+        // compare |Y| with P/2
+        uint32_t mag[W];
+        uint32_t cb = 1;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const uint32_t v = neg ? ~Y[j] : Y[j];
+            const uint64_t s = (uint64_t)v + (neg ? cb : 0u);
+            mag[j] = (uint32_t)s;
+            cb = (uint32_t)(s >> 32);
+        }
+        int cmp = 0;  // sign of |Y| - P/2
+#pragma unroll
+        for (int j = W - 1; j >= 0; --j)
+            if (cmp == 0 && mag[j] != t.halfP[j]) cmp = mag[j] > t.halfP[j] ? 1 : -1;
+        const bool too_high = !neg && cmp >= 0;  // Y >= P/2
+        const bool too_low = neg && cmp > 0;     // Y < -P/2
+        if (too_high || too_low) {
+            uint64_t c2 = 0;
+            int64_t b2 = 0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                if (too_high) {
+                    const int64_t d = (int64_t)Y[j] - (int64_t)t.P[j] - b2;
+                    Y[j] = (uint32_t)d;
+                    b2 = d < 0 ? 1 : 0;
+                } else {
+                    const uint64_t s = (uint64_t)Y[j] + t.P[j] + c2;
+                    Y[j] = (uint32_t)s;
+                    c2 = s >> 32;
+                }
+            }
+        }
+    }
+    // |Y| and sign
+    const bool neg = (Y[W - 1] >> 31) != 0;
+    uint32_t cb = 1;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const uint32_t v = neg ? ~Y[j] : Y[j];
+        const uint64_t s = (uint64_t)v + (neg ? cb : 0u);
+        Y[j] = (uint32_t)s;
+        cb = (uint32_t)(s >> 32);
+    }
+    // leading word and the 96-bit window below the leading bit
+    int top = -1;
+    uint32_t w0 = 0, w1 = 0, w2 = 0, low_or = 0;
+#pragma unroll
+    for (int j = W - 1; j >= 0; --j)
+        if (top < 0 && Y[j] != 0) top = j;
+    if (top < 0) return 0.0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        if (j == top) w0 = Y[j];
+        if (j == top - 1) w1 = Y[j];
+        if (j == top - 2) w2 = Y[j];
+        if (j < top - 2) low_or |= Y[j];
+    }
+    const int lz = __clz(w0);
+    int msb = 32 * top + 31 - lz;
+    uint64_t win = ((uint64_t)w0 << 32) | w1;
+    bool sticky = low_or != 0;
+    if (lz) {
+        win = (win << lz) | (w2 >> (32 - lz));
+        sticky = sticky || ((w2 << lz) != 0);
+    } else {
+        sticky = sticky || (w2 != 0);
+    }
+    uint64_t m53 = win >> 11;
+    const uint32_t rem = (uint32_t)(win & 0x7FF);
+    if (rem > 0x400 || (rem == 0x400 && (sticky || (m53 & 1)))) {
+        ++m53;
+        if (m53 >> 53) {
+            m53 >>= 1;
+            ++msb;
+        }
+    }
+    const uint64_t sign = neg ? (1ull << 63) : 0ull;
+    const int E = msb - (ea + fb);  // unbiased exponent of C'' 2^-(e+f)
+    if (E >= -1022 && E <= 1023)
+        return __longlong_as_double((long long)(sign | ((uint64_t)(E + 1023) << 52) |
+                                                (m53 & ((1ull << 52) - 1))));
+    const double x = __longlong_as_double(
+        (long long)(sign | ((uint64_t)(msb + 1023) << 52) | (m53 & ((1ull << 52) - 1))));
+    return scale_pow2_rn(x, -(ea + fb));
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res, int64_t ldr,
+                                                  int64_t plane, int m, int n,
+                                                  const int* __restrict__ sa,
+                                                  const int* __restrict__ sb, double alpha,
+                                                  double beta, double* __restrict__ C,
+                                                  int64_t ldc, const CrtTables t) {
+    __shared__ double tile[TJ][TI + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = blockIdx.y * TI, j0 = blockIdx.x * TJ;
+    const int j = j0 + lane;
+    const int fb = j < n ? sb[j] : 0;
+#pragma unroll
+    for (int r = 0; r < TI / 8; ++r) {
+        const int il = warp + 8 * r;
+        const int i = i0 + il;
+        double y = 0.0;
+        if (i < m && j < n) y = crt_entry<W>(res + (int64_t)i * ldr + j, plane, sa[i], fb, t);
+        tile[lane][il] = y;
+    }
+    __syncthreads();
+    const bool plain = (alpha == 1.0 && beta == 0.0);
+#pragma unroll
+    for (int r = 0; r < TJ / 8; ++r) {
+        const int jl = warp + 8 * r;
+        const int jj = j0 + jl, ii = i0 + lane;
+        if (ii < m && jj < n) {
+            double* out = C + ii + (int64_t)jj * ldc;
+            const double y = tile[jl][lane];
+            double v = plain ? y : __dmul_rn(alpha, y);
+            if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, *out));
+            *out = v;
+        }
+    }
+}
+
+__global__ void scale_c_kernel(int m, int n, double beta, double* C, int64_t ldc) {
+    const int64_t total = (int64_t)m * n;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = g / m, i = g - j * m;
+        double* p = C + i + j * ldc;
+        *p = beta == 0.0 ? 0.0 : __dmul_rn(beta, *p);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
+                       const int* sa, const int* sb, double alpha, double beta, double* C,
+                       int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream) {
+    (void)status;
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    dim3 grid((n + TJ - 1) / TJ, (m + TI - 1) / TI);
+    switch (t.words) {
+        case 2: crt_kernel<2><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
+        case 3: crt_kernel<3><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
+        case 4: crt_kernel<4><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
+        case 5: crt_kernel<5><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
+        default: crt_kernel<6><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_c(int m, int n, double beta, double* C, int64_t ldc,
+                           cudaStream_t stream) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const int64_t total = (int64_t)m * n;
+    const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    scale_c_kernel<<<grid, 256, 0, stream>>>(m, n, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace ozaki2

@@ -1,0 +1,81 @@
+// ozaki2_internal.h -- internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "ozaki2.h"
+
+namespace ozaki2 {
+
+constexpr int kMaxModuli = OZAKI2_MAX_MODULI;
+constexpr int kMaxWords = 6;  // 32-bit words of sum_l P_l w_l < N P for N <= 20 (161 bits)
+
+// Per-N tables derived from Step 1 (Section 2.2) on the host, passed to kernels by value.
+struct ConvertTables {
+    int N;
+    int limbs;                      // 18-bit limbs needed for |a'| < 2^(P'_prop + 1)
+    uint32_t p[kMaxModuli];
+    uint32_t barrett[kMaxModuli];   // floor(2^32 / p)
+    uint32_t pow18[kMaxModuli][5];  // 2^(18 j) mod p
+};
+
+struct CrtTables {
+    int N;
+    uint32_t p[kMaxModuli];
+    uint32_t barrett[kMaxModuli];   // floor(2^32 / p)
+    uint32_t q[kMaxModuli];         // q_l = (P/p_l)^{-1} mod p_l
+    uint32_t off[kMaxModuli];       // (-128 q_l) mod p_l, so (c + 128) q_l + off = q_l c (mod p_l)
+    float inv_p[kMaxModuli];        // 1/p_l rounded to single
+    uint32_t Pl[kMaxModuli][kMaxWords];  // P_l = P/p_l, little-endian 32-bit words
+    uint32_t P[kMaxWords];
+    uint32_t halfP[kMaxWords];      // P/2 (P is even: 256 is always a modulus)
+};
+
+struct EpilogueTables {
+    int N;
+    float p[kMaxModuli];
+    float inv_p[kMaxModuli];
+    float hi[kMaxModuli];  // largest symmetric representative: (p-1)/2, or 127 for 256
+    float lo[kMaxModuli];  // smallest: -(p-1)/2, or -128 for 256
+};
+
+struct ModTables {
+    int N;
+    int moduli[kMaxModuli];
+    int inverses[kMaxModuli];
+    float pprime;           // P'_prop
+    int words;              // 32-bit words used by the CRT accumulator
+    ConvertTables conv;
+    CrtTables crt;
+    EpilogueTables epi;
+};
+
+// Tables for 2 <= N <= 20 (cached, thread safe).  Returns nullptr for other N.
+const ModTables* mod_tables(int N);
+
+// ---- launchers (asynchronous on `stream`) ----------------------------------------------------
+// Shifts for `lines` lines of length `len`.  Element h of line i is at
+//   X[i * line_stride + h * elem_stride]  with either line_stride == 1 (lines adjacent) or
+//   elem_stride == 1 (each line contiguous).
+cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
+                         int len, float pprime, int* shifts, unsigned* status,
+                         cudaStream_t stream);
+
+cudaError_t launch_convert(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
+                           int len, const int* shifts, const ConvertTables& t, void* planes,
+                           int rows_pad, int k_pad, unsigned* status, cudaStream_t stream);
+
+int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
+                        const void* planes_b, int8_t* out, const EpilogueTables& t,
+                        unsigned* status, int num_sms, int chunk_k, cudaStream_t stream);
+
+cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
+                       const int* sa, const int* sb, double alpha, double beta, double* C,
+                       int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream);
+
+cudaError_t launch_scale_c(int m, int n, double beta, double* C, int64_t ldc,
+                           cudaStream_t stream);
+
+}  // namespace ozaki2

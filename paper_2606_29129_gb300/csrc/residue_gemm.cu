@@ -1,0 +1,490 @@
+// residue_gemm.cu -- Step 3 of Ozaki scheme II: the N residue GEMMs of eq. (os2-C'),
+// G_l = rmod(A', p_l) rmod(B', p_l), reduced modulo p_l in the epilogue.
+//
+// GB300 design.  sm_103a has no integer tcgen05 MMA, so the residues (integers in [-128, 127])
+// are stored as bf16, where they are exact, and multiplied on the 5th-generation tensor cores
+// with tcgen05.mma kind::f16 into FP32 accumulators in tensor memory (TMEM).  Every product has
+// magnitude <= 2^14, so an FP32 accumulator holding a value below 2^24 in magnitude is exact.
+// The K loop is cut into chunks of at most 960 (15 x 64); after each chunk the epilogue warps
+// reduce the accumulator modulo p_l in place (tcgen05.ld -> r = x - p*rint(x/p) -> tcgen05.st),
+// keeping |acc| <= ~0.52 p + 960 * 2^14 < 2^24.  The last chunk's drain produces the symmetric
+// residue c_l = rmod(G_l, p_l) as int8.
+//
+// Pipeline (one CTA per SM, persistent over (modulus, m-tile, n-tile) work):
+//   warp 0   TMA producer: 128x64 A and 256x64 B bf16 tiles, 128-byte swizzle, 4 stages.
+//   warp 1   TMEM allocator and MMA issuer (one thread): 4 x (M=128, N=256, K=16) per stage.
+//   warps 4-7 epilogue: TMEM lanes 32*(warp%4).. ; in-place reductions and the final drain.
+// Two TMEM accumulators (2 x 256 columns) hold two tiles whose K chunks are interleaved, so the
+// in-place reduction of one tile overlaps the MMAs of the other.
+//
+// Every mbarrier wait is bounded (globaltimer); on expiry the kernel raises
+// OZAKI2_STATUS_TIMEOUT, stops all roles, waits (bounded) for its TMA copies and MMAs, frees
+// TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "ozaki2_internal.h"
+
+namespace ozaki2 {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, UMMA_K = 16;
+constexpr int A_BYTES = BM * BK * 2;           // 16 KiB
+constexpr int B_BYTES = BN * BK * 2;           // 32 KiB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 2 * BN;              // two fp32 accumulators of 128 x 256
+constexpr int NUM_THREADS = 256;
+constexpr int EPI_WARP0 = 4;
+constexpr int NUM_BARRIERS = 2 * STAGES + 5;   // full, empty, acc_full[2], acc_empty[2], drain
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARRIERS * 8 + 16;
+constexpr int GROUP_M = 16;                    // m-tiles per group in the tile order (L2 reuse)
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+// Instruction descriptor of tcgen05.mma kind::f16: D fp32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct GemmArgs {
+    int tiles_m, tiles_n, total_tiles, k_blocks, chunk_blocks, nchunks;
+    int8_t* out;
+    int64_t out_ld, out_plane;
+    unsigned* status;
+    EpilogueTables ep;
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of `bar` with the given parity.  Returns false (and stops the CTA) when
+// the CTA was told to abort or the wait exceeded kTimeoutNs.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                          unsigned* status, unsigned long long limit_ns = kTimeoutNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > limit_ns) {
+                atomicOr(status, OZAKI2_STATUS_TIMEOUT);
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor of a K-major tile written by TMA with 128-byte swizzle: rows of
+// 128 bytes, 8-row swizzle atoms 1024 bytes apart (stride byte offset), version bits 46-47 = 1,
+// swizzle mode 2 (128 B) at bits 61-63.  The leading byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+        "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+        "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Tile t -> (modulus l, m-tile, n-tile).  Within a modulus, groups of GROUP_M m-tiles sweep the
+// n-tiles so that CTAs running at the same time share A and B panels in L2.
+__device__ __forceinline__ void decode_tile(int tile, const GemmArgs& a, int& l, int& mt,
+                                            int& nt) {
+    const int per_plane = a.tiles_m * a.tiles_n;
+    l = tile / per_plane;
+    const int idx = tile - l * per_plane;
+    const int per_group = GROUP_M * a.tiles_n;
+    const int g = idx / per_group;
+    const int first_m = g * GROUP_M;
+    const int gsize = min(a.tiles_m - first_m, GROUP_M);
+    const int r = idx - g * per_group;
+    mt = first_m + r % gsize;
+    nt = r / gsize;
+}
+
+// ---------------------------------------------------------------- the kernel
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    residue_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB, const GemmArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    uint8_t* smem = smem_raw + pad;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + STAGES;
+    uint64_t* acc_full = bars + 2 * STAGES;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(tmem_slot)),
+            "r"(TMEM_COLS)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int my_tiles = blockIdx.x < args.total_tiles
+                             ? (args.total_tiles - 1 - blockIdx.x) / gridDim.x + 1
+                             : 0;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------ TMA producer
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t armed_parity[STAGES];
+        bool armed[STAGES];
+        for (int s = 0; s < STAGES; ++s) armed[s] = false, armed_parity[s] = 0;
+        bool ok = true;
+        for (int pair = 0; ok && 2 * pair < my_tiles; ++pair) {
+            const int npair = min(2, my_tiles - 2 * pair);
+            for (int c = 0; ok && c < args.nchunks; ++c) {
+                for (int s = 0; ok && s < npair; ++s) {
+                    const int tile = blockIdx.x + (2 * pair + s) * gridDim.x;
+                    int l, mt, nt;
+                    decode_tile(tile, args, l, mt, nt);
+                    const int kb0 = c * args.chunk_blocks;
+                    const int kb1 = min(kb0 + args.chunk_blocks, args.k_blocks);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, args.status)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
+                        tma_load_3d(sA + stage * A_BYTES, &tmA, &full[stage], kb * BK, mt * BM, l);
+                        tma_load_3d(sB + stage * B_BYTES, &tmB, &full[stage], kb * BK, nt * BN, l);
+                        armed[stage] = true;
+                        armed_parity[stage] = phase;
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok) {  // let every copy this thread started land before the CTA exits
+            volatile int no_abort = 0;
+            for (int s = 0; s < STAGES; ++s)
+                if (armed[s])
+                    mbar_wait(&full[s], armed_parity[s], &no_abort, args.status, 100000000ull);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t acc_cnt[2] = {0, 0};
+        bool ok = true, issued = false;
+        for (int pair = 0; ok && 2 * pair < my_tiles; ++pair) {
+            const int npair = min(2, my_tiles - 2 * pair);
+            for (int c = 0; ok && c < args.nchunks; ++c) {
+                for (int s = 0; ok && s < npair; ++s) {
+                    if (!mbar_wait(&acc_empty[s], (acc_cnt[s] & 1) ^ 1, abort_flag, args.status)) {
+                        ok = false;
+                        break;
+                    }
+                    ++acc_cnt[s];
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(s * BN);
+                    const int kb0 = c * args.chunk_blocks;
+                    const int kb1 = min(kb0 + args.chunk_blocks, args.k_blocks);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, args.status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(sA + stage * A_BYTES);
+                        const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                            const uint32_t acc = (c > 0 || kb > kb0 || kk > 0) ? 1u : 0u;
+                            umma_bf16(d_tmem, sw128_desc(a0 + kk * UMMA_K * 2),
+                                      sw128_desc(b0 + kk * UMMA_K * 2), acc);
+                        }
+                        issued = true;
+                        umma_commit(&empty[stage]);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                    if (ok) umma_commit(&acc_full[s]);
+                }
+            }
+        }
+        if (!ok && issued) {  // make sure the MMAs already issued have finished
+            volatile int no_abort = 0;
+            umma_commit(drain);
+            mbar_wait(drain, 0, &no_abort, args.status, 100000000ull);
+        }
+    } else if (warp >= EPI_WARP0) {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        uint32_t acc_cnt[2] = {0, 0};
+        bool ok = true;
+        for (int pair = 0; ok && 2 * pair < my_tiles; ++pair) {
+            const int npair = min(2, my_tiles - 2 * pair);
+            for (int c = 0; ok && c < args.nchunks; ++c) {
+                for (int s = 0; ok && s < npair; ++s) {
+                    const int tile = blockIdx.x + (2 * pair + s) * gridDim.x;
+                    int l, mt, nt;
+                    decode_tile(tile, args, l, mt, nt);
+                    bool got = true;
+                    if (lane == 0)
+                        got = mbar_wait(&acc_full[s], acc_cnt[s] & 1, abort_flag, args.status);
+                    got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                    if (!got) {
+                        ok = false;
+                        break;
+                    }
+                    ++acc_cnt[s];
+                    tc_fence_after();
+                    const uint32_t taddr = tmem_base + lane_base + (uint32_t)(s * BN);
+                    const float p = args.ep.p[l], inv = args.ep.inv_p[l];
+                    if (c + 1 < args.nchunks) {
+                        // in-place reduction modulo p: |r| <= ~0.52 p
+#pragma unroll 1
+                        for (int col = 0; col < BN; col += 32) {
+                            uint32_t v[32];
+                            tmem_ld32(taddr + col, v);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const float x = __uint_as_float(v[j]);
+                                v[j] = __float_as_uint(fmaf(-rintf(x * inv), p, x));
+                            }
+                            tmem_st32(taddr + col, v);
+                        }
+                        tmem_wait_st();
+                    } else {
+                        // final drain: symmetric residue as int8
+                        const float hi = args.ep.hi[l], lo = args.ep.lo[l];
+                        const int64_t row = (int64_t)mt * BM + q * 32 + lane;
+                        int8_t* dst = args.out + (int64_t)l * args.out_plane + row * args.out_ld +
+                                      (int64_t)nt * BN;
+#pragma unroll 1
+                        for (int col = 0; col < BN; col += 32) {
+                            uint32_t v[32];
+                            tmem_ld32(taddr + col, v);
+                            uint32_t packed[8];
+#pragma unroll
+                            for (int w = 0; w < 8; ++w) {
+                                uint32_t word = 0;
+#pragma unroll
+                                for (int b = 0; b < 4; ++b) {
+                                    const float x = __uint_as_float(v[4 * w + b]);
+                                    float r = fmaf(-rintf(x * inv), p, x);
+                                    r = r > hi ? r - p : r;
+                                    r = r < lo ? r + p : r;
+                                    word |= ((uint32_t)__float2int_rn(r) & 0xFFu) << (8 * b);
+                                }
+                                packed[w] = word;
+                            }
+                            uint4* o = reinterpret_cast<uint4*>(dst + col);
+                            o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                            o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[s]);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();  // lane 0 ran the MMA loop alone; the dealloc is warp-collective
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3-D map over residue planes [N][rows_pad][k_pad] (bf16, K contiguous), box 64 x box_rows x 1.
+bool encode_planes(CUtensorMap* map, const void* base, int N, int rows_pad, int k_pad,
+                   int box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)N};
+    cuuint64_t strides[2] = {(cuuint64_t)k_pad * 2, (cuuint64_t)rows_pad * (cuuint64_t)k_pad * 2};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
+                        const void* planes_b, int8_t* out, const EpilogueTables& t,
+                        unsigned* status, int num_sms, int chunk_k, cudaStream_t stream) {
+    if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
+    CUtensorMap ta, tb;
+    if (!encode_planes(&ta, planes_a, num_moduli, m_pad, k_pad, BM) ||
+        !encode_planes(&tb, planes_b, num_moduli, n_pad, k_pad, BN))
+        return OZAKI2_ERROR_DRIVER;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(residue_gemm_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+
+    GemmArgs a;
+    a.tiles_m = m_pad / BM;
+    a.tiles_n = n_pad / BN;
+    a.total_tiles = a.tiles_m * a.tiles_n * num_moduli;
+    a.k_blocks = k_pad / BK;
+    int cb = chunk_k / BK;
+    if (cb < 1) cb = 1;
+    if (cb > 15) cb = 15;  // <= 960 products between reductions keeps fp32 exact
+    a.chunk_blocks = cb;
+    a.nchunks = a.k_blocks > 0 ? (a.k_blocks + cb - 1) / cb : 0;
+    a.out = out;
+    a.out_ld = n_pad;
+    a.out_plane = (int64_t)m_pad * n_pad;
+    a.status = status;
+    a.ep = t;
+    if (a.k_blocks == 0) {  // empty inner dimension: every product residue is zero
+        cudaError_t e = cudaMemsetAsync(out, 0, (size_t)num_moduli * m_pad * n_pad, stream);
+        return e == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
+    }
+    const int grid = a.total_tiles < num_sms ? a.total_tiles : num_sms;
+    residue_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, stream>>>(ta, tb, a);
+    return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
+}
+
+}  // namespace ozaki2

@@ -1,0 +1,220 @@
+"""GPU parity of the whole emulated DGEMM (ozaki2_dgemm through the C ABI) against the oracle.
+
+Bit-exact comparison of C for every shape, transpose, moduli count and alpha/beta case; the
+all-ones worked example of Section 3.1 (exact result); scale invariance (Section 4); quick
+returns and argument errors; and, at the full benchmark size, every shift plus a sampled block
+of C covering every output tile.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+import _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def oz():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the gpu-marked tests")
+    from paper_2606_29129_gb300 import ozaki2
+
+    return ozaki2
+
+
+def make(m, n, k, phi, seed, transA="N", transB="N"):
+    A = synthetic.paper_matrix(m, k, phi, seed) if transA == "N" else \
+        synthetic.paper_matrix(k, m, phi, seed)
+    B = synthetic.paper_matrix(k, n, phi, seed + 1) if transB == "N" else \
+        synthetic.paper_matrix(n, k, phi, seed + 1)
+    return A, B
+
+
+def test_config1_256_cubed(oz, orc):
+    """m = n = k = 256, phi = 1, N = 14 (the small configuration), against the oracle."""
+    m = n = k = 256
+    A, B = make(m, n, k, 1.0, synthetic.seed_for(1, 0, 1))
+    C = _gpu.dgemm(oz, A, B, m, n, k, 14)
+    assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 14))
+    # rigorous truncation bound per entry (a' = mu a - d, |d| < 1; one rounding of C''):
+    # |C - AB| <= 2^-f_j sum|a_i.| + 2^-e_i sum|b_.j| + k 2^-(e_i+f_j) + 2^-53 |C|
+    hi, lo = orc.dd_block(A, B, k, list(range(m)), list(range(n)))
+    e, _ = orc.shifts_a(A, m, k, 14)
+    f, _ = orc.shifts_b(B, k, n, 14)
+    ra = np.abs(synthetic.colmajor_view(A)).sum(axis=1)          # (m,)
+    cb = np.abs(synthetic.colmajor_view(B)).sum(axis=0)          # (n,)
+    ei, fj = 2.0 ** -e.astype(np.float64), 2.0 ** -f.astype(np.float64)
+    bound = (ra[None, :] * fj[:, None] + cb[:, None] * ei[None, :] + k * fj[:, None] * ei[None, :]
+             + np.abs(C) * 2.0**-53) * 1.001                      # storage (n, m)
+    assert np.all(np.abs((C - hi) - lo) <= bound)
+    err, _ = orc.max_rel_error(C, hi, lo)
+    assert err < 1e-9
+
+
+SHAPES = [(1, 1, 1), (3, 5, 7), (129, 257, 1025), (300, 200, 64), (128, 256, 960),
+          (127, 255, 961), (40, 600, 33)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("trans", ["NN", "TN", "NT", "TT"])
+def test_shapes_and_transposes(oz, orc, shape, trans):
+    m, n, k = shape
+    tA, tB = trans
+    A, B = make(m, n, k, 2.0, sum(shape), tA, tB)
+    C = _gpu.dgemm(oz, A, B, m, n, k, 14, tA, tB)
+    assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 14, tA, tB))
+
+
+@pytest.mark.parametrize("N", [2, 5, 8, 11, 14, 16, 17, 18, 20])
+@pytest.mark.parametrize("phi", [0.5, 4.0])
+def test_moduli_counts(oz, orc, N, phi):
+    m, n, k = 150, 130, 700
+    A, B = make(m, n, k, phi, N)
+    C = _gpu.dgemm(oz, A, B, m, n, k, N)
+    assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, N))
+
+
+def test_alpha_beta(oz, orc):
+    m, n, k = 70, 90, 110
+    A, B = make(m, n, k, 1.0, 3)
+    Cin = synthetic.paper_matrix(m, n, 1.0, 9)
+    for alpha, beta in [(1.0, 0.0), (-2.5, 0.0), (1.0, 1.0), (0.3, -0.7)]:
+        C = _gpu.dgemm(oz, A, B, m, n, k, 14, alpha=alpha, beta=beta, Cin=Cin)
+        ref = orc.dgemm(A, B, m, n, k, 14, alpha=alpha, beta=beta, Cin=Cin)
+        assert _gpu.same_bits(C, ref), (alpha, beta)
+    nan_in = np.full_like(Cin, np.nan)    # beta = 0 never reads C
+    C = _gpu.dgemm(oz, A, B, m, n, k, 14, beta=0.0, Cin=nan_in)
+    assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 14))
+
+
+def test_quick_returns(oz):
+    import torch
+
+    m, n = 5, 4
+    Cin = synthetic.paper_matrix(m, n, 1.0, 1)
+    C = _gpu.dgemm(oz, np.zeros((0, m)), np.zeros((n, 0)), m, n, 0, 14, alpha=2.0, beta=0.5,
+                   Cin=Cin, lda=m, ldb=1)
+    assert np.array_equal(C, 0.5 * Cin)
+    A, B = make(m, n, 3, 1.0, 2)
+    C = _gpu.dgemm(oz, A, B, m, n, 3, 14, alpha=0.0, beta=0.0, Cin=Cin)
+    assert np.all(C == 0.0)
+    # m = 0: nothing happens, nothing is read
+    _gpu.ok(oz.ozaki2_dgemm("N", "N", 0, n, 3, 1.0, None, 1, _gpu.dev(B), 3, 0.0, None, 1, 14))
+    torch.cuda.synchronize()
+
+
+def test_argument_errors(oz):
+    import torch
+
+    A = torch.zeros(64, dtype=torch.float64, device="cuda")
+    call = lambda *a: oz.ozaki2_dgemm(*a)  # noqa: E731
+    assert call("X", "N", 4, 4, 4, 1.0, A, 4, A, 4, 0.0, A, 4, 14) == -2
+    assert call("N", "Q", 4, 4, 4, 1.0, A, 4, A, 4, 0.0, A, 4, 14) == -3
+    assert call("N", "N", -1, 4, 4, 1.0, A, 4, A, 4, 0.0, A, 4, 14) == -4
+    assert call("N", "N", 4, 4, 4, 1.0, A, 3, A, 4, 0.0, A, 4, 14) == -9
+    assert call("N", "N", 4, 4, 4, 1.0, A, 4, A, 3, 0.0, A, 4, 14) == -11
+    assert call("N", "N", 4, 4, 4, 1.0, A, 4, A, 4, 0.0, A, 3, 14) == -14
+    assert call("N", "N", 4, 4, 4, 1.0, A, 4, A, 4, 0.0, A, 4, 1) == -15
+    assert call("N", "N", 4, 4, 4, 1.0, A, 4, A, 4, 0.0, A, 4, 21) == -15
+    assert call("N", "N", 4, 4, 4, 1.0, None, 4, A, 4, 0.0, A, 4, 14) == -8
+
+
+def test_user_workspace(oz, orc):
+    import torch
+
+    m, n, k = 64, 80, 96
+    A, B = make(m, n, k, 1.0, 5)
+    h = oz.Handle()
+    need = oz.ozaki2_workspace_size(m, n, k, 14)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    h.set_workspace(ws, need)
+    C = _gpu.dgemm(oz, A, B, m, n, k, 14, handle=h)
+    assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 14))
+    small = torch.empty(need // 2, dtype=torch.uint8, device="cuda")
+    h.set_workspace(small, need // 2)
+    Cd = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, _gpu.dev(A), m, _gpu.dev(B), k, 0.0, Cd, m, 14,
+                         h)
+    assert rc == 3   # OZAKI2_ERROR_WORKSPACE
+
+
+@pytest.mark.parametrize("k", [1024, 16384])
+@pytest.mark.parametrize("s", [-10, -2, 0, 10])
+def test_all_ones_exact(oz, k, s):
+    """All-ones example (Section 3.1), N = 20: the proposed scaling never breaks the CRT and the
+    product is exactly k alpha^2, like cuBLAS (Fig. 3 caption)."""
+    m, n = 64, 48
+    alpha = 2.0**s
+    A = synthetic.ones_matrix(m, k, alpha)
+    B = synthetic.ones_matrix(k, n, alpha)
+    C = _gpu.dgemm(oz, A, B, m, n, k, 20)
+    assert np.all(C == k * alpha * alpha)
+
+
+@pytest.mark.parametrize("s", [40, -40])
+def test_scale_invariance(oz, orc, s):
+    m, n, k = 100, 90, 500
+    A, B = make(m, n, k, 2.0, 17)
+    C0 = _gpu.dgemm(oz, A, B, m, n, k, 14)
+    C1 = _gpu.dgemm(oz, A * 2.0**s, B * 2.0**s, m, n, k, 14)
+    assert np.array_equal(C1, C0 * 2.0 ** (2 * s))
+
+
+def test_nonfinite_inputs(oz, orc):
+    m, n, k = 30, 20, 40
+    A, B = make(m, n, k, 1.0, 23)
+    A[4, 7] = np.nan      # row 7 of A
+    B[2, 3] = np.inf      # column 2 of B
+    h = oz.Handle()
+    C = _gpu.dgemm(oz, A, B, m, n, k, 14, handle=h)
+    assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 14))
+    assert np.isnan(C[:, 7]).all() and np.isnan(C[2, :]).all()
+    assert h.status() & oz.STATUS_NONFINITE
+
+
+def test_torch_convenience(oz, orc):
+    import torch
+
+    from paper_2606_29129_gb300 import dgemm
+
+    m, n, k = 33, 44, 55
+    A = torch.randn(m, k, dtype=torch.float64, device="cuda")
+    B = torch.randn(k, n, dtype=torch.float64, device="cuda")
+    C = dgemm(A, B, num_moduli=16)
+    # row-major (m, k) storage is the column-major k x m matrix A^T, so op = 'T' recovers A
+    ref = orc.dgemm(A.cpu().numpy(), B.cpu().numpy(), m, n, k, 16, "T", "T", lda=k, ldb=n)
+    assert _gpu.same_bits(C.cpu().numpy().T, ref)
+
+
+@pytest.mark.parametrize("size", [8192, 16384])
+def test_full_size_sampled(oz, orc, size):
+    """The benchmark's problem (square, phi = 1, N = 14, one ozaki2_dgemm call): every row and
+    column shift equals the oracle's, and a block of C with one row in every 128-row tile and
+    one column in every 256-column tile is bit-identical to the oracle's."""
+    import torch
+
+    m = n = k = size
+    N = 14
+    A = synthetic.paper_matrix_torch(m, k, 1.0, synthetic.seed_for(2, 1, 1))
+    B = synthetic.paper_matrix_torch(k, n, 1.0, synthetic.seed_for(2, 1, 2))
+    C = torch.empty((n, m), dtype=torch.float64, device="cuda")
+    _gpu.ok(oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N))
+    e = torch.empty(m, dtype=torch.int32, device="cuda")
+    f = torch.empty(n, dtype=torch.int32, device="cuda")
+    _gpu.ok(oz.ozaki2_scale_a("N", m, k, A, m, N, e))
+    _gpu.ok(oz.ozaki2_scale_b("N", k, n, B, k, N, f))
+    torch.cuda.synchronize()
+    A_h, B_h = A.cpu().numpy(), B.cpu().numpy()
+    e_ref, _ = orc.shifts_a(A_h, m, k, N)
+    f_ref, _ = orc.shifts_b(B_h, k, n, N)
+    assert np.array_equal(e.cpu().numpy(), e_ref)
+    assert np.array_equal(f.cpu().numpy(), f_ref)
+    rng = np.random.default_rng(size)
+    I = np.arange(0, m, 128) + rng.integers(0, 128, size=m // 128)
+    J = np.arange(0, n, 256) + rng.integers(0, 256, size=n // 256)
+    blk = orc.dgemm_block(A_h, B_h, m, n, k, N, I, J, e=e_ref, f=f_ref)
+    got = C.cpu().numpy()[np.ix_(J, I)]
+    assert _gpu.same_bits(got, blk)

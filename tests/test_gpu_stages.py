@@ -1,0 +1,237 @@
+"""GPU parity of each stage of the path against the oracle, through the C ABI, bit for bit.
+
+Stages: scaling (Algorithm 2), conversion to residues (Step 2), residue GEMMs (eq. os2-C'),
+CRT and rescaling (eqs. os2-C'', Step 4).  Each stage is fed the same inputs as the oracle; the
+later stages are fed oracle-made or synthetic inputs so that each is checked on its own.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic
+import _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def oz():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the gpu-marked tests")
+    from paper_2606_29129_gb300 import ozaki2
+
+    return ozaki2
+
+
+SHAPES = [(1, 1), (17, 7), (129, 1023), (300, 1025), (64, 2000), (257, 64)]
+
+
+@pytest.mark.parametrize("trans", ["N", "T"])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("phi", [0.5, 4.0])
+def test_scale_matches_oracle(oz, orc, trans, shape, phi):
+    lines, k = shape
+    N = 14
+    seed = 31 * lines + k
+    if trans == "N":
+        A = synthetic.paper_matrix(lines, k, phi, seed)
+    else:
+        A = synthetic.paper_matrix(k, lines, phi, seed)
+    e_ref, _ = orc.shifts_a(A, lines, k, N, trans=trans)
+    assert np.array_equal(_gpu.shifts_a(oz, A, lines, k, N, trans), e_ref)
+    # the same storage read as op(B) columns (transposed meaning of trans)
+    tb = "T" if trans == "N" else "N"
+    f_ref, _ = orc.shifts_b(A, k, lines, N, trans=tb)
+    assert np.array_equal(_gpu.shifts_b(oz, A, k, lines, N, tb), f_ref)
+    assert np.array_equal(f_ref, e_ref)
+
+
+@pytest.mark.parametrize("N", [2, 8, 20])
+@pytest.mark.parametrize("alpha", [2.0**40, 2.0**-40, 3.7e20, 3.7e-20, 1e-160])
+def test_scale_extreme_magnitudes(oz, orc, N, alpha):
+    m, k = 96, 333
+    A = synthetic.paper_matrix(m, k, 2.0, 5) * alpha
+    A[:, 3] = 0.0
+    e_ref, _ = orc.shifts_a(A, m, k, N)
+    assert np.array_equal(_gpu.shifts_a(oz, A, m, k, N), e_ref)
+
+
+def test_scale_log2_argument_sweep(oz, orc):
+    """2^23 one-element rows whose squared norms sweep every single-precision mantissa in
+    [1, 2): the GPU's logarithm step and the oracle's agree on all of them."""
+    m = 1 << 23
+    x = 1.0 + np.arange(m, dtype=np.float64) * 2.0**-23
+    A = np.sqrt(x).reshape(1, m)     # column-major m x 1, lda = m
+    for N in (14, 20):
+        e_ref, _ = orc.shifts_a(A, m, 1, N)
+        assert np.array_equal(_gpu.shifts_a(oz, A, m, 1, N), e_ref)
+
+
+def test_scale_nonfinite_flag(oz, orc):
+    m, k = 40, 50
+    A = synthetic.paper_matrix(m, k, 1.0, 8)
+    A[3, 5] = np.nan     # row 5
+    A[7, 9] = np.inf     # row 9
+    A[:, 11] = 1e200     # row 11: squared norm overflows
+    h = oz.Handle()
+    import torch
+
+    out = torch.zeros(m, dtype=torch.int32, device="cuda")
+    _gpu.ok(oz.ozaki2_scale_a("N", m, k, _gpu.dev(A), m, 14, out, handle=h))
+    e = out.cpu().numpy()
+    e_ref, _ = orc.shifts_a(A, m, k, 14)
+    assert np.array_equal(e, e_ref)
+    assert set(np.nonzero(e == oz.SHIFT_NONFINITE)[0]) == {5, 9, 11}
+    assert h.status() & oz.STATUS_NONFINITE
+    assert h.status() == 0   # reading clears the flags
+
+
+@pytest.mark.parametrize("trans", ["N", "T"])
+@pytest.mark.parametrize("shape", [(1, 1), (31, 65), (129, 1023), (200, 77)])
+@pytest.mark.parametrize("N", [2, 14, 17, 20])
+def test_convert_a_matches_oracle(oz, orc, trans, shape, N):
+    m, k = shape
+    phi = 4.0
+    A = synthetic.paper_matrix(m, k, phi, 3 * m + k) if trans == "N" else \
+        synthetic.paper_matrix(k, m, phi, 3 * m + k)
+    e, _ = orc.shifts_a(A, m, k, N, trans=trans)
+    R_ref = orc.residues_a(A, m, k, e, N, trans=trans)
+    P = _gpu.planes_a(oz, A, m, k, e, N, trans)
+    assert np.array_equal(P[:, :m, :k], R_ref)
+    assert not P[:, m:, :].any() and not P[:, :, k:].any()   # padding is zero
+
+
+@pytest.mark.parametrize("trans", ["N", "T"])
+@pytest.mark.parametrize("N", [8, 14, 20])
+def test_convert_b_matches_oracle(oz, orc, trans, N):
+    k, n = 300, 270
+    B = synthetic.paper_matrix(k, n, 2.0, 77) if trans == "N" else \
+        synthetic.paper_matrix(n, k, 2.0, 77)
+    f, _ = orc.shifts_b(B, k, n, N, trans=trans)
+    R_ref = orc.residues_b(B, k, n, f, N, trans=trans)
+    P = _gpu.planes_b(oz, B, k, n, f, N, trans)
+    assert np.array_equal(P[:, :n, :k], R_ref)
+    assert not P[:, n:, :].any() and not P[:, :, k:].any()
+
+
+def test_convert_special_values(oz, orc):
+    """Subnormals, signed zeros, a zero row, a sentinel row and wide magnitudes."""
+    m, k, N = 8, 64, 20
+    A = synthetic.paper_matrix(m, k, 4.0, 9)
+    A[:, 0] = 0.0
+    A[0, 1] = 5e-324
+    A[1, 1] = -0.0
+    A[2, 1] = -2.5e-310
+    A[:, 2] *= 1e-300
+    e, _ = orc.shifts_a(A, m, k, N)
+    e[3] = oz.SHIFT_NONFINITE
+    R_ref = orc.residues_a(A, m, k, e, N)
+    assert not R_ref[:, 3, :].any()
+    P = _gpu.planes_a(oz, A, m, k, e, N)
+    assert np.array_equal(P[:, :m, :k], R_ref)
+
+
+def random_residues(rng, N, rows, kk, p, fill_k=None):
+    R = np.zeros((N, rows, kk), np.int64)
+    for l in range(N):
+        lo, hi = (-128, 127) if p[l] == 256 else (-(p[l] - 1) // 2, (p[l] - 1) // 2)
+        R[l] = rng.integers(lo, hi + 1, size=(rows, kk))
+    if fill_k is not None:
+        R[:, :, fill_k:] = 0
+    return R
+
+
+@pytest.mark.parametrize("dims", [(128, 256, 64), (256, 512, 1024), (384, 256, 3008),
+                                  (128, 256, 16384)])
+@pytest.mark.parametrize("N", [2, 14, 20])
+def test_residue_gemm_matches_oracle(oz, orc, dims, N):
+    mp, npad, kp = dims
+    rng = np.random.default_rng(mp + npad + kp + N)
+    p = orc.constants(N)["p"]
+    RA = random_residues(rng, N, mp, kp)
+    RB = random_residues(rng, N, npad, kp)
+    c = _gpu.residue_gemm(oz, RA, RB)
+    rows = np.arange(0, mp, 7 if kp > 4096 else 1)
+    c_ref = orc.residue_products(RA[:, rows].astype(np.int8), RB.astype(np.int8))
+    assert np.array_equal(c[:, rows], c_ref)
+
+
+@pytest.mark.parametrize("kp", [960, 1024, 1088, 2048, 65536])
+def test_residue_gemm_accumulation_extremes(oz, orc, kp):
+    """Worst-case magnitudes for the FP32 accumulator: every product (-128)^2 = 2^14 on the
+    modulus 256, and +-127 patterns on the others, across reduction-chunk boundaries."""
+    N, mp, npad = 3, 128, 256
+    RA = np.zeros((N, mp, kp), np.int64)
+    RB = np.zeros((N, npad, kp), np.int64)
+    RA[0] = -128
+    RB[0] = -128
+    RB[0, 1::2] = 127            # odd columns: -128 * 127 products
+    RA[1] = 127
+    RB[1] = 127
+    RB[1, ::3] = -127
+    sgn = np.where(np.arange(kp) % 2 == 0, 1, -1)
+    RA[2] = 126 * sgn
+    RB[2] = 126
+    c = _gpu.residue_gemm(oz, RA, RB)
+    c_ref = orc.residue_products(RA[:, :16].astype(np.int8), RB.astype(np.int8))
+    assert np.array_equal(c[:, :16], c_ref)
+    assert np.array_equal(c[:, 16:], np.broadcast_to(c[:, :1], c[:, 16:].shape))
+
+
+def test_residue_gemm_many_tiles(oz, orc):
+    """More tiles than SMs: the persistent loop, tile pairs and the tile order."""
+    N, mp, npad, kp = 14, 2048, 2048, 192
+    rng = np.random.default_rng(4)
+    p = orc.constants(N)["p"]
+    RA = random_residues(rng, N, mp, kp)
+    RB = random_residues(rng, N, npad, kp)
+    c = _gpu.residue_gemm(oz, RA, RB)
+    rows = np.arange(3, mp, 61)
+    c_ref = orc.residue_products(RA[:, rows].astype(np.int8), RB.astype(np.int8))
+    assert np.array_equal(c[:, rows], c_ref)
+
+
+@pytest.mark.parametrize("N", [2, 8, 14, 16, 17, 20])
+def test_crt_matches_oracle(oz, orc, N):
+    m, n = 100, 70
+    rng = np.random.default_rng(N)
+    mp, npad = 128, 256
+    c = rng.integers(-128, 128, size=(N, mp, npad)).astype(np.int8)
+    e = rng.integers(-60, 60, size=m).astype(np.int32)
+    f = rng.integers(-60, 60, size=n).astype(np.int32)
+    C_ref = orc.crt(np.ascontiguousarray(c[:, :m, :n]), e, f)
+    assert _gpu.same_bits(_gpu.crt(oz, c, e, f, m, n), C_ref)
+    Cin = synthetic.paper_matrix(m, n, 1.0, 5)
+    C_ref = orc.crt(np.ascontiguousarray(c[:, :m, :n]), e, f, alpha=-1.5, beta=0.25, Cin=Cin)
+    assert _gpu.same_bits(_gpu.crt(oz, c, e, f, m, n, -1.5, 0.25, Cin), C_ref)
+
+
+@pytest.mark.parametrize("N", [2, 14, 20])
+def test_crt_extreme_integers_and_exponents(oz, orc, N):
+    """Residues of chosen integers at the ends of the symmetric range (where the quotient
+    estimate sits next to a half-integer), ties of the final rounding, and shifts that push
+    results into the subnormal range or past overflow; sentinel shifts give NaN."""
+    P = orc.constants(N)["P"]
+    half = (P - 1) // 2
+    xs = [0, 1, -1, half, -half, half - 1, -(half - 1), half // 3, -(half // 7),
+          2**53 + 1, (2**53 + 1) * 2**20 + 2**19, -(2**60 + 2**7 + 1)]
+    rng = np.random.default_rng(N)
+    xs += [int(v) for v in rng.integers(-2**62, 2**62, size=20)]
+    xs = [x for x in xs if abs(x) <= half]
+    m, n = len(xs), 6
+    res = orc.int_residues(xs, N)                          # (m, N)
+    c = np.zeros((N, 128, 256), np.int8)
+    for j in range(n):
+        c[:, :m, j] = res.T
+    e = np.zeros(m, np.int32)
+    f = np.array([0, 1100, -900, 1074, -1023, 0], np.int32)
+    e[-1] = oz.SHIFT_NONFINITE
+    C_ref = orc.crt(np.ascontiguousarray(c[:, :m, :n]), e, f)
+    C = _gpu.crt(oz, c, e, f, m, n)
+    assert _gpu.same_bits(C, C_ref)
+    for i, x in enumerate(xs[:-1]):
+        assert C[0, i] == float(x)
+    assert np.isnan(C[:, m - 1]).all()
