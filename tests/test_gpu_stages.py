@@ -151,8 +151,8 @@ def test_residue_gemm_matches_oracle(oz, orc, dims, N):
     mp, npad, kp = dims
     rng = np.random.default_rng(mp + npad + kp + N)
     p = orc.constants(N)["p"]
-    RA = random_residues(rng, N, mp, kp)
-    RB = random_residues(rng, N, npad, kp)
+    RA = random_residues(rng, N, mp, kp, p)
+    RB = random_residues(rng, N, npad, kp, p)
     c = _gpu.residue_gemm(oz, RA, RB)
     rows = np.arange(0, mp, 7 if kp > 4096 else 1)
     c_ref = orc.residue_products(RA[:, rows].astype(np.int8), RB.astype(np.int8))
@@ -186,8 +186,8 @@ def test_residue_gemm_many_tiles(oz, orc):
     N, mp, npad, kp = 14, 2048, 2048, 192
     rng = np.random.default_rng(4)
     p = orc.constants(N)["p"]
-    RA = random_residues(rng, N, mp, kp)
-    RB = random_residues(rng, N, npad, kp)
+    RA = random_residues(rng, N, mp, kp, p)
+    RB = random_residues(rng, N, npad, kp, p)
     c = _gpu.residue_gemm(oz, RA, RB)
     rows = np.arange(3, mp, 61)
     c_ref = orc.residue_products(RA[:, rows].astype(np.int8), RB.astype(np.int8))
