@@ -39,6 +39,7 @@ extern "C" {
 #define OZAKI2_ERROR_WORKSPACE 3  /* a workspace set with ozaki2_set_workspace is too small */
 #define OZAKI2_ERROR_NO_DEVICE 4  /* the current device is not an sm_103 GPU */
 #define OZAKI2_ERROR_DRIVER 5     /* the driver's tensor-map encoder is unavailable or failed */
+#define OZAKI2_ERROR_TOO_LARGE 6  /* the problem does not fit ozaki2_dgemm_noalloc's scratch */
 
 /* ---- device status flags (ozaki2_get_status) ------------------------------------------- */
 #define OZAKI2_STATUS_NONFINITE 1u /* a row of op(A) or column of op(B) had a non-finite squared
@@ -168,6 +169,39 @@ int ozaki2_residue_gemm(ozaki2_handle_t handle, int num_moduli, int m_pad, int n
 int ozaki2_crt(ozaki2_handle_t handle, int num_moduli, int m, int n, const int8_t* residues,
                int ldr, long long plane_stride, const int* shifts_a, const int* shifts_b,
                double alpha, double beta, double* C, int ldc);
+
+/* ---- the whole path without allocation --------------------------------------------------- */
+/* Size of the device array that ozaki2_dgemm_noalloc keeps its intermediates in (8 MiB). */
+#define OZAKI2_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* The emulated DGEMM of ozaki2_dgemm for callers that may not allocate device memory at call
+ * time: code whose device memory is budgeted once at start-up (a solver or a serving loop that
+ * reserves its memory up front, where a later cudaMalloc can fail, fragment the pool or stall
+ * on the implicit device synchronisation that cudaFree brings), or code called back from a host
+ * framework that forbids allocation.  The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * It allocates nothing: no cudaMalloc or cudaFree, no handle, no allocating library routine.
+ * Its intermediates (shifts, residue planes, product residues, a status word) live in one
+ * file-scope device array of OZAKI2_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the
+ * library holds until the process exits.  The caller passes the inputs and the output as for
+ * ozaki2_dgemm, plus the cudaStream_t (as void*) to queue on.
+ *
+ * Limit: the problem must fit the array, i.e. the workspace of ozaki2_dgemm plus 256 bytes
+ * (ozaki2_workspace_size(m, n, k, N) + 256) must not exceed OZAKI2_NOALLOC_SCRATCH_BYTES;
+ * m = n = k = 256 fits for every N <= 20.  Larger problems return OZAKI2_ERROR_TOO_LARGE and
+ * touch nothing.
+ *
+ * Set-up: the first call made with a given device current looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture.
+ * Sharing: every call uses the same array and it keeps the last call's contents, so calls that
+ * overlap on the GPU (other streams, other threads) race and must be serialised by the caller.
+ * The status word is cleared at the start of each call; device-side status flags are not
+ * reported by this entry point (non-finite lines still produce NaN outputs).
+ * Argument numbers for errors: as ozaki2_dgemm, stream 15. */
+int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int k, double alpha,
+                         const double* A, int lda, const double* B, int ldb, double beta,
+                         double* C, int ldc, int num_moduli, void* stream);
 
 #ifdef __cplusplus
 }

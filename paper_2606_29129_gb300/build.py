@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libozaki2.so")
-SOURCES = ["api.cu", "tables.cu", "scale.cu", "convert.cu", "residue_gemm.cu", "crt.cu"]
+SOURCES = ["api.cu", "tables.cu", "scale.cu", "convert.cu", "residue_gemm.cu", "crt.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

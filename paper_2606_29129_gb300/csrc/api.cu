@@ -294,6 +294,7 @@ const char* ozaki2_error_string(int code) {
         case OZAKI2_ERROR_WORKSPACE: return "user workspace too small";
         case OZAKI2_ERROR_NO_DEVICE: return "no sm_103 GPU available";
         case OZAKI2_ERROR_DRIVER: return "tensor map encoder unavailable or failed";
+        case OZAKI2_ERROR_TOO_LARGE: return "problem exceeds the static scratch of ozaki2_dgemm_noalloc";
         default: return "unknown error";
     }
 }

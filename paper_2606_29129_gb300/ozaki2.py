@@ -23,6 +23,8 @@ ROWS_ALIGN_A = 128
 ROWS_ALIGN_B = 256
 K_ALIGN = 64
 SHIFT_NONFINITE = -(2**31)
+ERROR_TOO_LARGE = 6
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 _lib = None
 _lock = threading.Lock()
@@ -64,6 +66,8 @@ def lib() -> ctypes.CDLL:
             "ozaki2_convert_b": [vp, ch, i32, i32, vp, i32, vp, i32, vp, i32, i32],
             "ozaki2_residue_gemm": [vp, i32, i32, i32, i32, vp, vp, vp],
             "ozaki2_crt": [vp, i32, i32, i32, vp, i32, i64, vp, vp, f64, f64, vp, i32],
+            "ozaki2_dgemm_noalloc": [ch, ch, i32, i32, i32, f64, vp, i32, vp, i32, f64, vp, i32,
+                                     i32, vp],
             "ozaki2_set_timing": [vp, i32],
             "ozaki2_get_timing": [vp, ctypes.POINTER(ctypes.c_float)],
         }
