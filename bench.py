@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 SIZE = 16384
 PHI = 1.0
-NUM_MODULI = 14
+NUM_MODULI = 16
 METRIC = "Ozaki-II DGEMM effective TFLOPS at stated error vs cuBLAS DGEMM; p50/p99 lat"
 WORKLOAD = f"square FP64 GEMM m=n=k={SIZE}, phi={PHI}, N={NUM_MODULI} moduli"
 
@@ -376,6 +376,53 @@ def measure_e2e(args, oz, h, A, B, m, n, k, N, torch):
             "d2h_bytes_per_step": m * n * 8, "ms_per_step": ms}
 
 
+def run_sweep(args):
+    """Accuracy sweep: max relative error vs the double-double reference for N = 8..20, phi in
+    {0.5, 1, 2} and the copies scaled by 2^+-40 and 3.7e+-20, beside cuBLAS DGEMM on the same
+    inputs.  One JSON line per (size, phi, alpha)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synthetic
+    from paper_2606_29129_gb300 import ozaki2 as oz
+
+    oracle.build()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for size in args.sweep_sizes:
+        m = n = k = size
+        for pi, phi in enumerate((0.5, 1.0, 2.0)):
+            A0 = synthetic.paper_matrix_torch(m, k, phi, synthetic.seed_for(2, pi, 1))
+            B0 = synthetic.paper_matrix_torch(k, n, phi, synthetic.seed_for(2, pi, 2))
+            rng = np.random.default_rng(size + pi)
+            I = np.sort(rng.choice(m, size=args.err_block, replace=False)).astype(np.int32)
+            J = np.sort(rng.choice(n, size=args.err_block, replace=False)).astype(np.int32)
+            for alpha in (1.0, 2.0**40, 2.0**-40, 3.7e20, 3.7e-20):
+                A = A0 * alpha
+                B = B0 * alpha
+                A_h, B_h = A.cpu().numpy(), B.cpu().numpy()
+                hi, lo = oracle.dd_block(A_h, B_h, k, I, J)
+                C = torch.empty((n, m), dtype=torch.float64, device="cuda")
+                errs = {}
+                for N in range(8, 21):
+                    rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N)
+                    if rc:
+                        raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+                    torch.cuda.synchronize()
+                    errs[N] = oracle.max_rel_error(C.cpu().numpy()[np.ix_(J, I)], hi, lo)[0]
+                Cd = torch.matmul(B.view(n, k), A.view(k, m))
+                torch.cuda.synchronize()
+                cub = oracle.max_rel_error(Cd.cpu().numpy()[np.ix_(J, I)], hi, lo)[0]
+                default = next((N for N in range(8, 21) if errs[N] <= cub), None)
+                print(json.dumps({"size": size, "phi": phi, "alpha": alpha,
+                                  "sample": f"{len(I)}x{len(J)}", "max_rel_err": errs,
+                                  "cublas_dgemm": cub, "smallest_N_not_worse": default}),
+                      flush=True)
+                del A, B, C, Cd
+            del A0, B0
+            torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,7 +438,13 @@ def main():
     ap.add_argument("--gemm-traffic", type=float, default=None,
                     help="DRAM bytes per residue-GEMM launch from an ncu capture, if current")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="accuracy sweep over N, phi and alpha instead of the benchmark")
+    ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[8192, 16384])
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
         args.warmup = 3

@@ -2,13 +2,14 @@
 // residues rmod(a', p_l) of eq. (os2-C') for every modulus, written as bf16 residue planes with
 // K contiguous (the operand layout of the residue GEMM).
 //
-// Integer-only arithmetic: the double's mantissa M (53 bits) and the exponent give
-// |a'| = floor(M 2^sh), held as up to five 18-bit limbs d_j (|a'| < 2^(P'_prop+1) <= 2^79).
-// For each modulus, x = sum_j d_j (2^(18 j) mod p) < 2^28 and one Barrett step gives |a'| mod p.
-// The sign is applied and the symmetric representative taken ((p-1)/2 bound for odd p,
-// [-128, 127] for 256); the small integer is exact in bf16.
+// Integer-only arithmetic.  The double's 53-bit mantissa M and its exponent give
+// |a'| = floor(M 2^sh) < 2^(bits(P)/2), held as L 21-bit limbs d_j (L = 3 for N <= 14, 4 up to
+// N = 20).  For an odd modulus, x = sum_j d_j (2^(21 j) mod p) < 2^31 and one Barrett step gives
+// |a'| mod p; the symmetric representative is negated for negative a'.  For p = 256 the residue
+// is the low byte of +-|a'| read as a signed byte ([-128, 127]).  Each small integer is exact in
+// bf16.  Kernels are instantiated per N so every per-modulus constant is an immediate operand.
 //
-// Traffic per element: 8 bytes read, 2N bytes written; HBM-bound for N <= ~14, ALU-heavy above.
+// Traffic per element: 8 bytes read, 2N bytes written.
 #include <cuda_bf16.h>
 
 #include "ozaki2_internal.h"
@@ -16,16 +17,27 @@
 namespace ozaki2 {
 namespace {
 
-constexpr uint32_t kMask18 = (1u << 18) - 1;
+constexpr uint32_t kMask21 = (1u << 21) - 1;
+
+// bits(P) for N moduli, N = 2..20 (P = product of the first N moduli of eq. (moduli)).
+__host__ __device__ constexpr int p_bits(int N) {
+    constexpr int b[21] = {0, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80,
+                           88, 95, 103, 111, 118, 126, 133, 141, 148, 156};
+    return b[N];
+}
+// 21-bit limbs covering |a'| <= sqrt((P-1)/2) < 2^(bits(P)/2), with one bit to spare.
+__host__ __device__ constexpr int limbs_for(int N) { return (p_bits(N) / 2 + 2 + 20) / 21; }
 
 struct Scaled {
-    uint32_t d[5];
+    uint32_t d[4];
+    uint32_t low;  // low 32 bits of |a'|
     bool neg;
 };
 
-// |trunc(a 2^e)| as 18-bit limbs.  Flags OZAKI2_STATUS_RANGE when the value needs more than
-// 18*limbs bits (only possible with shifts that break the bound of eq. (proposed-condition)).
-__device__ __forceinline__ Scaled split_scaled(double a, int e, int limbs, unsigned* status) {
+// |trunc(a 2^e)| as 21-bit limbs.  Flags OZAKI2_STATUS_RANGE when the value needs more than
+// 21*L bits (only possible with shifts that break the bound of eq. (proposed-condition)).
+template <int L>
+__device__ __forceinline__ Scaled split_scaled(double a, int e, unsigned* status) {
     Scaled r;
     const uint64_t bits = (uint64_t)__double_as_longlong(a);
     r.neg = (bits >> 63) != 0;
@@ -34,11 +46,10 @@ __device__ __forceinline__ Scaled split_scaled(double a, int e, int limbs, unsig
     if (E) M |= 1ull << 52; else E = 1;
     int sh = E - 1075 + e;
     uint64_t lo = 0, hi = 0;
-    const int max_sh = 18 * limbs - 53;
-    if (M != 0 && sh > max_sh) {
-        // bits of |a'| = (64 - clz(M)) + sh must fit in 18*limbs
-        if (sh > 18 * limbs - (64 - __clzll((long long)M))) atomicOr(status, OZAKI2_STATUS_RANGE);
-        sh = min(sh, 37);
+    if (M != 0 && sh > 21 * L - 53) {
+        // bits of |a'| = (64 - clz(M)) + sh must fit in 21 L
+        if (sh > 21 * L - (64 - __clzll((long long)M))) atomicOr(status, OZAKI2_STATUS_RANGE);
+        sh = min(sh, 21 * L - 53 + 11);
     }
     if (sh >= 0) {
         lo = M << sh;
@@ -46,48 +57,56 @@ __device__ __forceinline__ Scaled split_scaled(double a, int e, int limbs, unsig
     } else if (sh > -64) {
         lo = M >> (-sh);
     }
-    r.d[0] = (uint32_t)lo & kMask18;
-    r.d[1] = (uint32_t)(lo >> 18) & kMask18;
-    r.d[2] = (uint32_t)(lo >> 36) & kMask18;
-    r.d[3] = (uint32_t)((lo >> 54) | (hi << 10)) & kMask18;
-    r.d[4] = (uint32_t)(hi >> 8) & kMask18;
+    r.low = (uint32_t)lo;
+    r.d[0] = (uint32_t)lo & kMask21;
+    r.d[1] = (uint32_t)(lo >> 21) & kMask21;
+    r.d[2] = (uint32_t)(lo >> 42) & kMask21;
+    r.d[3] = (uint32_t)((lo >> 63) | (hi << 1)) & kMask21;
     return r;
 }
 
-// Symmetric residue of +-|a'| modulo p as a bf16 bit pattern in the upper 16 bits of a float.
+// bf16 bits (in the upper half of a float) of the small integer s.
+__device__ __forceinline__ uint32_t small_int_bits(int s) {
+    return __float_as_uint(__int_as_float(0x4B400000 + s) - 12582912.0f);
+}
+
+// Symmetric residue of +-|a'| modulo the l-th modulus, as bf16 bits.
+template <int L>
 __device__ __forceinline__ uint32_t residue_bits(const Scaled& v, const ConvertTables& t, int l) {
+    if (l == 0) {  // p = 256: the low byte of a' in two's complement
+        const uint32_t b = (v.neg ? 0u - v.low : v.low) & 0xFFu;
+        return small_int_bits((int)(int8_t)(uint8_t)b);
+    }
     const uint32_t p = t.p[l];
     uint32_t x = v.d[0];
 #pragma unroll
-    for (int j = 1; j < 5; ++j)
-        if (j < t.limbs) x += v.d[j] * t.pow18[l][j];
-    const uint32_t q = __umulhi(x, t.barrett[l]);
-    uint32_t r = x - q * p;
+    for (int j = 1; j < L; ++j) x += v.d[j] * t.pow21[l][j];
+    uint32_t r = x - __umulhi(x, t.barrett[l]) * p;
     if (r >= p) r -= p;
-    if (v.neg && r) r = p - r;
-    const int s = (2 * r >= p) ? (int)r - (int)p : (int)r;
-    // exact float of a small integer: 1.5*2^23 + s, minus 1.5*2^23
-    const float f = __int_as_float(0x4B400000 + s) - 12582912.0f;
-    return __float_as_uint(f);
+    int s = (2 * r > p) ? (int)r - (int)p : (int)r;   // odd p: [-(p-1)/2, (p-1)/2]
+    s = v.neg ? -s : s;
+    return small_int_bits(s);
 }
 
 // Writes the residues of 8 consecutive elements of one line into the N planes.
+template <int N>
 __device__ __forceinline__ void store_residues8(const double (&v)[8], int e, bool live,
                                                 const ConvertTables& t, __nv_bfloat16* planes,
                                                 int64_t plane_elems, int64_t offset,
                                                 unsigned* status) {
+    constexpr int L = limbs_for(N);
     Scaled sc[8];
-    const bool nonfinite = (e == OZAKI2_SHIFT_NONFINITE) || !live;
+    const bool zero = (e == OZAKI2_SHIFT_NONFINITE) || !live;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        sc[u] = nonfinite ? Scaled{{0, 0, 0, 0, 0}, false} : split_scaled(v[u], e, t.limbs, status);
-    }
-    for (int l = 0; l < t.N; ++l) {
+    for (int u = 0; u < 8; ++u)
+        sc[u] = zero ? Scaled{{0, 0, 0, 0}, 0, false} : split_scaled<L>(v[u], e, status);
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
         uint32_t w[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t a = residue_bits(sc[2 * u], t, l);
-            const uint32_t b = residue_bits(sc[2 * u + 1], t, l);
+            const uint32_t a = residue_bits<L>(sc[2 * u], t, l);
+            const uint32_t b = residue_bits<L>(sc[2 * u + 1], t, l);
             w[u] = __byte_perm(a, b, 0x7632);  // upper halves: a -> bits 0..15, b -> 16..31
         }
         *reinterpret_cast<uint4*>(planes + (int64_t)l * plane_elems + offset) =
@@ -95,7 +114,9 @@ __device__ __forceinline__ void store_residues8(const double (&v)[8], int e, boo
     }
 }
 
-// Lines contiguous (elem_stride == 1): thread = (line, group of 8 elements).
+// Lines contiguous (elem_stride == 1): thread = (line, group of 8 elements); a warp covers 256
+// consecutive elements of one line, so loads and stores are both contiguous.
+template <int N>
 __global__ void __launch_bounds__(256) convert_contiguous_kernel(
     const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
@@ -103,6 +124,7 @@ __global__ void __launch_bounds__(256) convert_contiguous_kernel(
     const int groups = k_pad / 8;
     const int64_t total = (int64_t)rows_pad * groups;
     const int64_t plane_elems = (int64_t)rows_pad * k_pad;
+    const bool vec = ((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(g / groups);
@@ -110,19 +132,31 @@ __global__ void __launch_bounds__(256) convert_contiguous_kernel(
         const bool row_live = i < lines;
         double v[8];
         const double* src = X + (int64_t)i * ld + h0;
+        if (row_live && vec && h0 + 8 <= len) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = (row_live && h0 + u < len) ? __ldg(src + u) : 0.0;
+            for (int u = 0; u < 4; ++u) {
+                const double2 d = __ldg(reinterpret_cast<const double2*>(src) + u);
+                v[2 * u] = d.x;
+                v[2 * u + 1] = d.y;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (row_live && h0 + u < len) ? __ldg(src + u) : 0.0;
+        }
         const int e = row_live ? shifts[i] : 0;
-        store_residues8(v, e, row_live, t, planes, plane_elems, (int64_t)i * k_pad + h0, status);
+        store_residues8<N>(v, e, row_live, t, planes, plane_elems, (int64_t)i * k_pad + h0,
+                           status);
     }
 }
 
-// Lines adjacent (line_stride == 1): a block converts a tile of 32 lines x 64 elements.  The tile
-// is read with coalesced loads along the lines (32 consecutive doubles per warp and element),
-// transposed through shared memory, and each thread writes 8 consecutive elements of one line.
-constexpr int kTileLines = 32;
+// Lines adjacent (line_stride == 1): a block converts a tile of 64 lines x 64 elements.  The tile
+// is read with coalesced loads along the lines (a warp reads 32 consecutive doubles), transposed
+// through shared memory, and each group of 8 lanes writes one line's 64 elements (128 bytes per
+// plane) as 8 contiguous 16-byte stores.
+constexpr int kTileLines = 64;
 constexpr int kTileK = 64;
 
+template <int N>
 __global__ void __launch_bounds__(256) convert_adjacent_kernel(
     const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
@@ -130,31 +164,66 @@ __global__ void __launch_bounds__(256) convert_adjacent_kernel(
     __shared__ double tile[kTileK][kTileLines + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t plane_elems = (int64_t)rows_pad * k_pad;
-    const int tiles_l = rows_pad / kTileLines;
+    const int tiles_l = (rows_pad + kTileLines - 1) / kTileLines;
     const int tiles_k = k_pad / kTileK;
     const int64_t ntiles = (int64_t)tiles_l * tiles_k;
     for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
         const int tl = (int)(tt % tiles_l);
         const int tk = (int)(tt / tiles_l);
         const int line0 = tl * kTileLines, h0 = tk * kTileK;
-        const int line = line0 + lane;
+        // load: warp w reads rows h = w, w+8, ... of the tile, two 32-line halves each
 #pragma unroll
         for (int r = 0; r < kTileK / 8; ++r) {
             const int hh = warp + 8 * r;
             const int h = h0 + hh;
-            tile[hh][lane] = (line < lines && h < len) ? __ldg(X + line + (int64_t)h * ld) : 0.0;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int line = line0 + 32 * half + lane;
+                tile[hh][32 * half + lane] =
+                    (line < lines && h < len) ? __ldg(X + line + (int64_t)h * ld) : 0.0;
+            }
         }
         __syncthreads();
-        // warp w converts elements h0 + 8w .. h0 + 8w + 7 of line line0 + lane
-        double v[8];
+        // convert: 256 threads x 2 = 64 lines x 8 groups of 8 elements
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = tile[8 * warp + u][lane];
-        const bool live = line < lines;
-        const int e = live ? shifts[line] : 0;
-        store_residues8(v, e, live, t, planes, plane_elems, (int64_t)line * k_pad + h0 + 8 * warp,
-                        status);
+        for (int rep = 0; rep < 2; ++rep) {
+            const int item = threadIdx.x + 256 * rep;
+            const int ll = item >> 3, hg = item & 7;
+            const int line = line0 + ll;
+            if (line < rows_pad) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = tile[8 * hg + u][ll];
+                const bool live = line < lines;
+                const int e = live ? shifts[line] : 0;
+                store_residues8<N>(v, e, live, t, planes, plane_elems,
+                                   (int64_t)line * k_pad + h0 + 8 * hg, status);
+            }
+        }
         __syncthreads();
     }
+}
+
+template <int N>
+cudaError_t launch_convert_n(const double* X, int64_t line_stride, int64_t elem_stride,
+                             int lines, int len, const int* shifts, const ConvertTables& t,
+                             __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
+                             int sms, cudaStream_t stream) {
+    if (elem_stride != 1) {  // then line_stride == 1: lines adjacent
+        const int64_t ntiles =
+            (int64_t)((rows_pad + kTileLines - 1) / kTileLines) * (k_pad / kTileK);
+        const int grid = (int)(ntiles < (int64_t)sms * 8 ? ntiles : (int64_t)sms * 8);
+        convert_adjacent_kernel<N><<<grid, 256, 0, stream>>>(X, elem_stride, lines, len, shifts,
+                                                             t, out, rows_pad, k_pad, status);
+    } else {
+        const int64_t total = (int64_t)rows_pad * (k_pad / 8);
+        const int64_t blocks = (total + 255) / 256;
+        const int grid = (int)(blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8);
+        convert_contiguous_kernel<N><<<grid, 256, 0, stream>>>(X, line_stride, lines, len,
+                                                               shifts, t, out, rows_pad, k_pad,
+                                                               status);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -167,18 +236,21 @@ cudaError_t launch_convert(const double* X, int64_t line_stride, int64_t elem_st
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     auto* out = static_cast<__nv_bfloat16*>(planes);
-    if (elem_stride != 1) {  // then line_stride == 1: lines adjacent
-        const int64_t ntiles = (int64_t)(rows_pad / kTileLines) * (k_pad / kTileK);
-        const int grid = (int)(ntiles < (int64_t)sms * 8 ? ntiles : (int64_t)sms * 8);
-        convert_adjacent_kernel<<<grid, 256, 0, stream>>>(X, elem_stride, lines, len, shifts, t,
-                                                          out, rows_pad, k_pad, status);
-    } else {
-        const int64_t total = (int64_t)rows_pad * (k_pad / 8);
-        const int grid = (int)((total + 255) / 256 < (int64_t)sms * 8 ? (total + 255) / 256 : (int64_t)sms * 8);
-        convert_contiguous_kernel<<<grid, 256, 0, stream>>>(X, line_stride, lines, len, shifts,
-                                                            t, out, rows_pad, k_pad, status);
+    switch (t.N) {
+#define OZAKI2_CONVERT_CASE(NN)                                                              \
+    case NN:                                                                                 \
+        return launch_convert_n<NN>(X, line_stride, elem_stride, lines, len, shifts, t, out, \
+                                    rows_pad, k_pad, status, sms, stream);
+        OZAKI2_CONVERT_CASE(2) OZAKI2_CONVERT_CASE(3) OZAKI2_CONVERT_CASE(4)
+        OZAKI2_CONVERT_CASE(5) OZAKI2_CONVERT_CASE(6) OZAKI2_CONVERT_CASE(7)
+        OZAKI2_CONVERT_CASE(8) OZAKI2_CONVERT_CASE(9) OZAKI2_CONVERT_CASE(10)
+        OZAKI2_CONVERT_CASE(11) OZAKI2_CONVERT_CASE(12) OZAKI2_CONVERT_CASE(13)
+        OZAKI2_CONVERT_CASE(14) OZAKI2_CONVERT_CASE(15) OZAKI2_CONVERT_CASE(16)
+        OZAKI2_CONVERT_CASE(17) OZAKI2_CONVERT_CASE(18) OZAKI2_CONVERT_CASE(19)
+        OZAKI2_CONVERT_CASE(20)
+#undef OZAKI2_CONVERT_CASE
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace ozaki2

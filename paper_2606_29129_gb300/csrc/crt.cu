@@ -5,9 +5,12 @@
 // reconstruction is exact multi-word integer arithmetic instead of split FP64 constants:
 //   w_l  = q_l c_l mod p_l                       (in [0, p_l))
 //   X    = sum_l P_l w_l                         (P_l = P/p_l, W 32-bit words, 64-bit column sums)
-//   Q    = round(sum_l w_l / p_l) = round(X / P) (single-precision estimate)
+//   Q    = round(sum_l w_l / p_l) = round(X / P) (48-bit fixed-point estimate)
 //   C''  = X - Q P                               (exact; corrected by +-P if the estimate sat
-//                                                 within 0.01 of a half-integer)
+//                                                 within 2^-10 of a half-integer)
+// The moduli are taken in groups of three (v_g = sum w_l coef_l < 3 prod_g < 2^26), so X needs
+// one 64-bit multiply-add per group and word instead of one per modulus and word; the kernel
+// is instantiated per N so every table entry is a compile-time constant-bank operand.
 // Since P_l q_l w_l == P_l q_l c_l (mod P), C'' = rmod(sum_l P_l q_l c_l, P) of eq. (os2-C'').
 // C'' is rounded to the nearest double (ties to even) with the unscaling 2^-(e_i + f_j) folded
 // into the exponent; results outside the normal range take a two-multiply path that rounds once.
@@ -36,25 +39,39 @@ __device__ double scale_pow2_rn(double x, int s) {
     return __dmul_rn(m2, 0x1p-600);
 }
 
-template <int W>
+// Words of X = sum_l P_l w_l < N P for N moduli (the same count the host tables use).
+__host__ __device__ constexpr int crt_words(int N) {
+    // bits(P) for N = 2..20: 16 24 32 40 48 56 64 72 80 88 95 103 111 118 126 133 141 148 156
+    return N <= 4 ? 2 : N <= 8 ? 3 : N <= 12 ? 4 : N <= 16 ? 5 : 6;
+}
+
+template <int N>
 __device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int64_t plane, int ea,
                                            int fb, const CrtTables& t) {
-    if (ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE) return __longlong_as_double(0x7FF8000000000000ll);
+    constexpr int W = crt_words(N);
+    constexpr int G = (N + 2) / 3;
+    if (ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE)
+        return __longlong_as_double(0x7FF8000000000000ll);
+    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^48 X / P (fixed point)
     uint64_t acc[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) acc[j] = 0;
-    float qf = 0.0f;
-    for (int l = 0; l < t.N; ++l) {
-        const int c = res[(int64_t)l * plane];
-        const uint32_t v = (uint32_t)(c + 128) * t.q[l] + t.off[l];   // = q_l c (mod p_l), < 2^16
-        const uint32_t qq = __umulhi(v, t.barrett[l]);
-        uint32_t w = v - qq * t.p[l];
-        if (w >= t.p[l]) w -= t.p[l];
-        qf = fmaf((float)w, t.inv_p[l], qf);
+    uint64_t S = 0;
 #pragma unroll
-        for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.Pl[l][j] * w;
+    for (int g = 0; g < G; ++g) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int l = 3 * g; l < 3 * g + 3 && l < N; ++l) {
+            const int c = res[(int64_t)l * plane];
+            const uint32_t x = (uint32_t)(c + 128) * t.q[l] + t.off[l];   // = q_l c (mod p_l)
+            uint32_t w = x - __umulhi(x, t.barrett[l]) * t.p[l];
+            if (w >= t.p[l]) w -= t.p[l];
+            v += w * t.coef[l];
+        }
+        S += (uint64_t)v * t.R48[g];
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.PG[g][j] * v;
     }
-    // carry-propagate X into 32-bit words
     uint32_t X[W];
     uint64_t carry = 0;
 #pragma unroll
@@ -63,24 +80,24 @@ __device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int6
         X[j] = (uint32_t)s;
         carry = s >> 32;
     }
-    const float qr = rintf(qf);
-    int Q = (int)qr;
-    // Y = X - Q P, two's complement over W words
+    // Q = round(X / P) from the fixed-point estimate; |S/2^48 - X/P| < 2^-20
+    const uint64_t frac = S & ((1ull << 48) - 1);
+    const uint32_t Q = (uint32_t)((S + (1ull << 47)) >> 48);
     uint32_t Y[W];
     uint64_t qpc = 0;
     int64_t borrow = 0;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-        const uint64_t prod = (uint64_t)(uint32_t)Q * t.P[j] + qpc;
+        const uint64_t prod = (uint64_t)Q * t.P[j] + qpc;
         qpc = prod >> 32;
         const int64_t d = (int64_t)X[j] - (int64_t)(uint32_t)prod - borrow;
         Y[j] = (uint32_t)d;
         borrow = d < 0 ? 1 : 0;
     }
-    if (fabsf(qf - qr) > 0.49f) {
-        // The estimate may be one off: make -P/2 <= Y < P/2 exactly.
+    const uint64_t half = 1ull << 47;
+    if ((frac > half ? frac - half : half - frac) < (1ull << 38)) {
+        // The estimate sits within 2^-10 of a half-integer: make -P/2 <= Y < P/2 exactly.
         const bool neg = (Y[W - 1] >> 31) != 0;
-        // compare |Y| with P/2
         uint32_t mag[W];
         uint32_t cb = 1;
 #pragma unroll
@@ -166,7 +183,7 @@ __device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int6
     return scale_pow2_rn(x, -(ea + fb));
 }
 
-template <int W>
+template <int N>
 __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res, int64_t ldr,
                                                   int64_t plane, int m, int n,
                                                   const int* __restrict__ sa,
@@ -183,7 +200,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res
         const int il = warp + 8 * r;
         const int i = i0 + il;
         double y = 0.0;
-        if (i < m && j < n) y = crt_entry<W>(res + (int64_t)i * ldr + j, plane, sa[i], fb, t);
+        if (i < m && j < n) y = crt_entry<N>(res + (int64_t)i * ldr + j, plane, sa[i], fb, t);
         tile[lane][il] = y;
     }
     __syncthreads();
@@ -220,13 +237,20 @@ cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int
     (void)status;
     if (m <= 0 || n <= 0) return cudaSuccess;
     dim3 grid((n + TJ - 1) / TJ, (m + TI - 1) / TI);
-    switch (t.words) {
-        case 2: crt_kernel<2><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
-        case 3: crt_kernel<3><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
-        case 4: crt_kernel<4><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
-        case 5: crt_kernel<5><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
-        default: crt_kernel<6><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t.crt); break;
+#define OZAKI2_CRT_CASE(NN)                                                                      \
+    case NN:                                                                                     \
+        crt_kernel<NN><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, \
+                                                 ldc, t.crt);                                    \
+        break;
+    switch (t.N) {
+        OZAKI2_CRT_CASE(2) OZAKI2_CRT_CASE(3) OZAKI2_CRT_CASE(4) OZAKI2_CRT_CASE(5)
+        OZAKI2_CRT_CASE(6) OZAKI2_CRT_CASE(7) OZAKI2_CRT_CASE(8) OZAKI2_CRT_CASE(9)
+        OZAKI2_CRT_CASE(10) OZAKI2_CRT_CASE(11) OZAKI2_CRT_CASE(12) OZAKI2_CRT_CASE(13)
+        OZAKI2_CRT_CASE(14) OZAKI2_CRT_CASE(15) OZAKI2_CRT_CASE(16) OZAKI2_CRT_CASE(17)
+        OZAKI2_CRT_CASE(18) OZAKI2_CRT_CASE(19) OZAKI2_CRT_CASE(20)
+        default: return cudaErrorInvalidValue;
     }
+#undef OZAKI2_CRT_CASE
     return cudaGetLastError();
 }
 

@@ -15,10 +15,9 @@ constexpr int kMaxWords = 6;  // 32-bit words of sum_l P_l w_l < N P for N <= 20
 // Per-N tables derived from Step 1 (Section 2.2) on the host, passed to kernels by value.
 struct ConvertTables {
     int N;
-    int limbs;                      // 18-bit limbs needed for |a'| < 2^(P'_prop + 1)
     uint32_t p[kMaxModuli];
     uint32_t barrett[kMaxModuli];   // floor(2^32 / p)
-    uint32_t pow18[kMaxModuli][5];  // 2^(18 j) mod p
+    uint32_t pow21[kMaxModuli][4];  // 2^(21 j) mod p
 };
 
 struct CrtTables {
@@ -31,6 +30,13 @@ struct CrtTables {
     uint32_t Pl[kMaxModuli][kMaxWords];  // P_l = P/p_l, little-endian 32-bit words
     uint32_t P[kMaxWords];
     uint32_t halfP[kMaxWords];      // P/2 (P is even: 256 is always a modulus)
+    // Moduli grouped in threes, g = 0.. : group g holds moduli 3g, 3g+1, 3g+2 (fewer at the end).
+    // With w_l in [0, p_l), v_g = sum_{l in g} w_l coef_l where coef_l is the product of the
+    // other moduli of the group, so v_g / prod_g = sum_{l in g} w_l / p_l and
+    // X = sum_l P_l w_l = sum_g PG_g v_g with PG_g = P / prod_g.
+    uint32_t coef[kMaxModuli];
+    uint32_t PG[(kMaxModuli + 2) / 3][kMaxWords];
+    unsigned long long R48[(kMaxModuli + 2) / 3];  // round(2^48 / prod_g)
 };
 
 struct EpilogueTables {

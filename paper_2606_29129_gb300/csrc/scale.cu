@@ -37,60 +37,89 @@ __device__ int alg2_shift(double a_norm, float pprime, unsigned* status) {
     return (int)floor(__dsub_rd((double)w, (double)t));
 }
 
-// Lines adjacent in memory (line_stride == 1): thread i walks line i; a warp reads 32
-// consecutive doubles per step, so every load is coalesced.
-__global__ void __launch_bounds__(128) scale_adjacent_kernel(const double* __restrict__ X,
-                                                             int64_t ld, int lines, int len,
-                                                             float pprime, int* shifts,
-                                                             unsigned* status) {
+// Lines adjacent in memory (line_stride == 1): thread i walks line i in order; a warp reads 32
+// consecutive doubles per step, so every load is coalesced.  Loads run two batches of 16 ahead
+// of the dependent FMA chain so that enough bytes are in flight with one thread per line.
+constexpr int kBatch = 16;
+
+__global__ void __launch_bounds__(32) scale_adjacent_kernel(const double* __restrict__ X,
+                                                            int64_t ld, int lines, int len,
+                                                            float pprime, int* shifts,
+                                                            unsigned* status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= lines) return;
     const double* p = X + i;
     double s = 0.0;
-    int h = 0;
-    for (; h + 8 <= len; h += 8) {
-        double v[8];
+    const int full = len / kBatch * kBatch;
+    double a[kBatch], b[kBatch];
+    if (full > 0) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldg(p + (int64_t)(h + u) * ld);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s = __fma_ru(v[u], v[u], s);
+        for (int u = 0; u < kBatch; ++u) a[u] = __ldg(p + (int64_t)u * ld);
     }
-    for (; h < len; ++h) {
+    for (int h = 0; h < full; h += 2 * kBatch) {
+        const bool has_b = h + kBatch < full;
+        if (has_b) {
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) b[u] = __ldg(p + (int64_t)(h + kBatch + u) * ld);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) s = __fma_ru(a[u], a[u], s);
+        if (!has_b) break;
+        if (h + 2 * kBatch < full) {
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                a[u] = __ldg(p + (int64_t)(h + 2 * kBatch + u) * ld);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) s = __fma_ru(b[u], b[u], s);
+    }
+    for (int h = full; h < len; ++h) {
         const double v = __ldg(p + (int64_t)h * ld);
         s = __fma_ru(v, v, s);
     }
     shifts[i] = alg2_shift(s, pprime, status);
 }
 
-// Contiguous lines (elem_stride == 1): a block of 64 threads owns 64 lines.  Tiles of 32
-// elements per line are staged through shared memory with coalesced loads (one warp reads one
-// line's 32 consecutive doubles), then each thread sums its own line in order.
-constexpr int kLinesPerBlock = 64;
+// Contiguous lines (elem_stride == 1): each warp owns 32 lines.  Tiles of 32 elements per line
+// are read with one coalesced 256-byte load per line, the next tile is held in registers while
+// the current one (in shared memory) is summed, each lane walking its own line in order.
+constexpr int kWarpsPerBlock = 4;
 constexpr int kTileLen = 32;
 
-__global__ void __launch_bounds__(kLinesPerBlock) scale_contiguous_kernel(
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) scale_contiguous_kernel(
     const double* __restrict__ X, int64_t ld, int lines, int len, float pprime, int* shifts,
     unsigned* status) {
-    __shared__ double tile[kLinesPerBlock][kTileLen + 1];
+    __shared__ double tile[kWarpsPerBlock][32][kTileLen + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int line0 = blockIdx.x * kLinesPerBlock;
-    const int nlines = min(kLinesPerBlock, lines - line0);
+    const int line0 = (blockIdx.x * kWarpsPerBlock + warp) * 32;
+    if (line0 >= lines) return;
+    const int nl = min(32, lines - line0);
+    double (*t)[kTileLen + 1] = tile[warp];
+    double reg[32];
+    auto load = [&](int h0) {
+        const int cnt = min(kTileLen, len - h0);
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            reg[r] = (r < nl && lane < cnt) ? __ldg(X + (int64_t)(line0 + r) * ld + h0 + lane)
+                                            : 0.0;
+    };
     double s = 0.0;
+    if (len > 0) load(0);
     for (int h0 = 0; h0 < len; h0 += kTileLen) {
         const int cnt = min(kTileLen, len - h0);
-        for (int r = warp; r < nlines; r += kLinesPerBlock / 32) {
-            if (lane < cnt) tile[r][lane] = __ldg(X + (int64_t)(line0 + r) * ld + h0 + lane);
-        }
-        __syncthreads();
-        if (threadIdx.x < nlines) {
+#pragma unroll
+        for (int r = 0; r < 32; ++r) t[r][lane] = reg[r];
+        __syncwarp();
+        if (h0 + kTileLen < len) load(h0 + kTileLen);
+        if (lane < nl) {
             for (int u = 0; u < cnt; ++u) {
-                const double v = tile[threadIdx.x][u];
+                const double v = t[lane][u];
                 s = __fma_ru(v, v, s);
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
-    if (threadIdx.x < nlines) shifts[line0 + threadIdx.x] = alg2_shift(s, pprime, status);
+    if (lane < nl) shifts[line0 + lane] = alg2_shift(s, pprime, status);
 }
 
 }  // namespace
@@ -100,13 +129,12 @@ cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stri
                          cudaStream_t stream) {
     if (lines <= 0) return cudaSuccess;
     if (elem_stride != 1 || line_stride == 1) {  // lines adjacent
-        const int threads = 128;
-        scale_adjacent_kernel<<<(lines + threads - 1) / threads, threads, 0, stream>>>(
-            X, elem_stride, lines, len, pprime, shifts, status);
+        scale_adjacent_kernel<<<(lines + 31) / 32, 32, 0, stream>>>(X, elem_stride, lines, len,
+                                                                    pprime, shifts, status);
     } else {
-        scale_contiguous_kernel<<<(lines + kLinesPerBlock - 1) / kLinesPerBlock, kLinesPerBlock,
-                                  0, stream>>>(X, line_stride, lines, len, pprime, shifts,
-                                               status);
+        const int per_block = 32 * kWarpsPerBlock;
+        scale_contiguous_kernel<<<(lines + per_block - 1) / per_block, per_block, 0, stream>>>(
+            X, line_stride, lines, len, pprime, shifts, status);
     }
     return cudaGetLastError();
 }

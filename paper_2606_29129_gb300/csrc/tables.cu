@@ -77,11 +77,6 @@ void build(int N, ModTables& t) {
     const int pbits = bit_length(P);
     t.words = (pbits + 5 + 31) / 32;  // sum_l P_l w_l < N P < 2^(pbits + 5)
 
-    // |a'| <= sqrt((P-1)/2) < 2^(P'_prop + 1): 18-bit limbs covering that many bits
-    int abits = (int)ceil((double)t.pprime + 1.0) + 1;
-    t.conv.limbs = (abits + 17) / 18;
-    if (t.conv.limbs > 5) t.conv.limbs = 5;
-
     t.conv.N = t.crt.N = t.epi.N = N;
     for (int l = 0; l < N; ++l) {
         const uint32_t p = (uint32_t)kModuli[l];
@@ -94,10 +89,10 @@ void build(int N, ModTables& t) {
 
         t.conv.p[l] = p;
         t.conv.barrett[l] = (uint32_t)((1ull << 32) / p);
-        for (int j = 0; j < 5; ++j) {
+        for (int j = 0; j < 4; ++j) {
             uint64_t v = 1;
-            for (int b = 0; b < 18 * j; ++b) v = (v * 2) % p;
-            t.conv.pow18[l][j] = (uint32_t)v;
+            for (int b = 0; b < 21 * j; ++b) v = (v * 2) % p;
+            t.conv.pow21[l][j] = (uint32_t)v;
         }
 
         t.crt.p[l] = p;
@@ -111,6 +106,18 @@ void build(int N, ModTables& t) {
         t.epi.inv_p[l] = 1.0f / (float)p;
         t.epi.hi[l] = (p % 2) ? (float)((p - 1) / 2) : (float)(p / 2 - 1);
         t.epi.lo[l] = (p % 2) ? -(float)((p - 1) / 2) : -(float)(p / 2);
+    }
+    for (int g = 0; 3 * g < N; ++g) {
+        const int l0 = 3 * g, l1 = (3 * g + 3 < N) ? 3 * g + 3 : N;
+        uint64_t prod = 1;
+        for (int l = l0; l < l1; ++l) prod *= (uint64_t)kModuli[l];
+        for (int l = l0; l < l1; ++l) t.crt.coef[l] = (uint32_t)(prod / (uint64_t)kModuli[l]);
+        Words PG{1};
+        for (int j = 0; j < N; ++j)
+            if (j < l0 || j >= l1) mul_small(PG, (uint32_t)kModuli[j]);
+        for (int w = 0; w < kMaxWords; ++w) t.crt.PG[g][w] = w < (int)PG.size() ? PG[w] : 0u;
+        t.crt.R48[g] = (unsigned long long)(((unsigned __int128)1 << 48) / prod +
+                                            ((((unsigned __int128)1 << 48) % prod) * 2 >= prod));
     }
     for (int w = 0; w < kMaxWords; ++w) {
         t.crt.P[w] = w < (int)P.size() ? P[w] : 0u;
