@@ -57,6 +57,14 @@ extern "C" {
 #define OZAKI2_MIN_MODULI 2
 #define OZAKI2_SHIFT_NONFINITE INT32_MIN /* shift written for a line with a non-finite norm */
 
+/* Options (ozaki2_set_option). */
+#define OZAKI2_OPT_GEMM_VARIANT 1 /* residue-GEMM kernel: one of OZAKI2_GEMM_* (default AUTO) */
+#define OZAKI2_OPT_CHUNK_K 2      /* products accumulated between modular reductions in the residue
+                                     GEMM: a multiple of 64 in [64, 960] (default 960) */
+#define OZAKI2_GEMM_AUTO 0        /* two-SM tiles when m_pad >= 256, else one-SM tiles */
+#define OZAKI2_GEMM_SINGLE 1      /* 128 x 256 tiles, one CTA per SM (tcgen05 cta_group::1) */
+#define OZAKI2_GEMM_PAIR 2        /* 256 x 256 tiles on SM pairs (tcgen05 cta_group::2) */
+
 typedef struct ozaki2_context* ozaki2_handle_t;
 
 /* ---- handle ------------------------------------------------------------------------------ */
@@ -76,6 +84,10 @@ int ozaki2_set_stream(ozaki2_handle_t handle, void* stream);
  * NULL/0 to return to the internal, growable workspace.  The caller keeps it alive while work
  * that uses it is queued. */
 int ozaki2_set_workspace(ozaki2_handle_t handle, void* workspace, size_t bytes);
+
+/* Set an OZAKI2_OPT_* option of the handle.  Returns -2 for an unknown option, -3 for a value
+ * out of range.  Results do not depend on the options; only the kernels used do. */
+int ozaki2_set_option(ozaki2_handle_t handle, int option, int value);
 
 /* Workspace bytes that ozaki2_dgemm needs for op(A) m x k, op(B) k x n and N moduli:
  * shifts, bf16 residue planes of A and B, and int8 product residues.  0 on invalid sizes. */

@@ -17,6 +17,7 @@ struct ozaki2_context {
     size_t ws_bytes = 0;
     bool user_ws = false;
     int chunk_k = 960;             // products accumulated between modular reductions
+    int gemm_variant = OZAKI2_GEMM_AUTO;
     bool timing = false;           // record stage events in ozaki2_dgemm
     bool timed_call = false;       // a timed call has been queued
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -177,7 +178,8 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
         return rc;
     mark(2);
     if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, pa, pb, res,
-                                  T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k, st)))
+                                  T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
+                                  ctx->gemm_variant, st)))
         return rc;
     mark(3);
     rc = cuda_rc(launch_crt(res, L.n_pad, L.m_pad * L.n_pad, m, n, e, f, alpha, beta, C, ldc, *T,
@@ -222,6 +224,24 @@ int ozaki2_set_stream(ozaki2_handle_t handle, void* stream) {
     if (rc) return rc;
     ctx->stream = static_cast<cudaStream_t>(stream);
     return OZAKI2_SUCCESS;
+}
+
+int ozaki2_set_option(ozaki2_handle_t handle, int option, int value) {
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    switch (option) {
+        case OZAKI2_OPT_GEMM_VARIANT:
+            if (value < OZAKI2_GEMM_AUTO || value > OZAKI2_GEMM_PAIR) return -3;
+            ctx->gemm_variant = value;
+            return OZAKI2_SUCCESS;
+        case OZAKI2_OPT_CHUNK_K:
+            if (value < 64 || value > 960 || value % 64) return -3;
+            ctx->chunk_k = value;
+            return OZAKI2_SUCCESS;
+        default:
+            return -2;
+    }
 }
 
 int ozaki2_set_workspace(ozaki2_handle_t handle, void* workspace, size_t bytes) {
@@ -426,7 +446,8 @@ int ozaki2_residue_gemm(ozaki2_handle_t handle, int num_moduli, int m_pad, int n
     int rc = resolve(handle, &ctx);
     if (rc) return rc;
     return launch_residue_gemm(num_moduli, m_pad, n_pad, k_pad, planes_a, planes_b, residues,
-                               T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k, ctx->stream);
+                               T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
+                               ctx->gemm_variant, ctx->stream);
 }
 
 int ozaki2_crt(ozaki2_handle_t handle, int num_moduli, int m, int n, const int8_t* residues,

@@ -75,7 +75,8 @@ cudaError_t launch_convert(const double* X, int64_t line_stride, int64_t elem_st
 
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
                         const void* planes_b, int8_t* out, const EpilogueTables& t,
-                        unsigned* status, int num_sms, int chunk_k, cudaStream_t stream);
+                        unsigned* status, int num_sms, int chunk_k, int variant,
+                        cudaStream_t stream);
 
 cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
                        const int* sa, const int* sb, double alpha, double beta, double* C,

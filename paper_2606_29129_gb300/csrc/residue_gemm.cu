@@ -50,6 +50,7 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
 
 struct GemmArgs {
     int tiles_m, tiles_n, total_tiles, k_blocks, chunk_blocks, nchunks;
+    int m_rows;  // rows of the A planes / product residues (m_pad)
     int8_t* out;
     int64_t out_ld, out_plane;
     unsigned* status;
@@ -168,6 +169,62 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 }
 __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// ---- cluster (2-SM) helpers
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Address of the same shared-memory object in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
+}
+// TMA load whose completion is signalled on an mbarrier in either CTA of the pair.
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster_addr, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::"
+        "bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar_cluster_addr)
+        : "memory");
+}
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                               uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Arrive (once MMAs issued so far complete) on the mbarrier at this offset in both CTAs.
+__device__ __forceinline__ void umma_commit_pair_both(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(smem_u32(bar)), "h"((uint16_t)3)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair_local(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void spin_ns(unsigned long long ns) {
+    const uint64_t t0 = global_ns();
+    while (global_ns() - t0 < ns) {
+    }
 }
 
 // Tile t -> (modulus l, m-tile, n-tile).  Within a modulus, groups of GROUP_M m-tiles sweep the
@@ -413,6 +470,258 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------- the 2-SM kernel
+// A cluster of two CTAs on a pair of SMs computes a 256 x 256 tile with tcgen05.mma
+// cta_group::2 (M = 256, N = 256, K = 16).  Each CTA loads its own 128 rows of A and its 128-row
+// half of B per stage (32 KiB, 6 stages), so each SM takes in two thirds of the bytes per FLOP of
+// the 1-SM kernel.  The even CTA (the leader) issues the MMAs; each CTA's TMEM holds its own 128
+// rows x 256 columns of the accumulators, which its own epilogue warps reduce and drain exactly as
+// in the 1-SM kernel.  Synchronisation across the pair: TMA completions of both CTAs land on the
+// leader's full barriers; MMA commits are multicast to both CTAs' empty and acc_full barriers;
+// the peer's epilogue warps arrive remotely on the leader's acc_empty barriers.
+namespace pair {
+constexpr int BM = 256, BN = 256, HALF = 128, STAGES = 6;
+constexpr int A_BYTES = HALF * BK * 2;          // 16 KiB
+constexpr int B_BYTES = HALF * BK * 2;          // 16 KiB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 2 * BN;
+constexpr int NUM_BARRIERS = 2 * STAGES + 5;
+constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARRIERS * 8 + 16;
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+}  // namespace pair
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    residue_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
+                             const __grid_constant__ CUtensorMap tmB, const GemmArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    uint8_t* smem = smem_raw + pad;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + pair::STAGES * pair::A_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + pair::STAGES * pair::B_BYTES);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + pair::STAGES;
+    uint64_t* acc_full = bars + 2 * pair::STAGES;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int cluster = (int)(blockIdx.x >> 1), nclusters = (int)(gridDim.x >> 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < pair::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 8);   // 4 epilogue warps in each CTA of the pair
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {  // collective over the pair: one warp in each CTA
+        asm volatile(
+            "tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(tmem_slot)),
+            "r"(pair::TMEM_COLS)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int my_tiles = cluster < args.total_tiles
+                             ? (args.total_tiles - 1 - cluster) / nclusters + 1
+                             : 0;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------------------------ TMA producer (both CTAs)
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true, started = false;
+        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
+            const int npair = min(2, my_tiles - 2 * pr);
+            for (int c = 0; ok && c < args.nchunks; ++c) {
+                for (int s = 0; ok && s < npair; ++s) {
+                    const int tile = cluster + (2 * pr + s) * nclusters;
+                    int l, mt, nt;
+                    decode_tile(tile, args, l, mt, nt);
+                    const int kb0 = c * args.chunk_blocks;
+                    const int kb1 = min(kb0 + args.chunk_blocks, args.k_blocks);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, args.status)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fb = map_to_rank(smem_u32(&full[stage]), 0);
+                        if (leader) mbar_arrive_expect_tx(&full[stage], 2 * pair::STAGE_BYTES);
+                        tma_load_3d_pair(sA + stage * pair::A_BYTES, &tmA, fb, kb * BK,
+                                         mt * pair::BM + (int)rank * pair::HALF, l);
+                        tma_load_3d_pair(sB + stage * pair::B_BYTES, &tmB, fb, kb * BK,
+                                         nt * pair::BN + (int)rank * pair::HALF, l);
+                        started = true;
+                        if (++stage == pair::STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok && started) spin_ns(2000000ull);  // let copies already issued land
+    } else if (warp == 1 && lane == 0 && leader) {
+        // ------------------------------------------------------------ MMA issuer (leader)
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t acc_cnt[2] = {0, 0};
+        bool ok = true, issued = false;
+        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
+            const int npair = min(2, my_tiles - 2 * pr);
+            for (int c = 0; ok && c < args.nchunks; ++c) {
+                for (int s = 0; ok && s < npair; ++s) {
+                    if (!mbar_wait(&acc_empty[s], (acc_cnt[s] & 1) ^ 1, abort_flag, args.status)) {
+                        ok = false;
+                        break;
+                    }
+                    ++acc_cnt[s];
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + (uint32_t)(s * pair::BN);
+                    const int kb0 = c * args.chunk_blocks;
+                    const int kb1 = min(kb0 + args.chunk_blocks, args.k_blocks);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, args.status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(sA + stage * pair::A_BYTES);
+                        const uint32_t b0 = smem_u32(sB + stage * pair::B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                            const uint32_t acc = (c > 0 || kb > kb0 || kk > 0) ? 1u : 0u;
+                            umma_bf16_pair(d_tmem, sw128_desc(a0 + kk * UMMA_K * 2),
+                                           sw128_desc(b0 + kk * UMMA_K * 2), pair::IDESC, acc);
+                        }
+                        issued = true;
+                        umma_commit_pair_both(&empty[stage]);
+                        if (++stage == pair::STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                    if (ok) umma_commit_pair_both(&acc_full[s]);
+                }
+            }
+        }
+        if (!ok && issued) {  // make sure the MMAs already issued have finished
+            volatile int no_abort = 0;
+            umma_commit_pair_local(drain);
+            mbar_wait(drain, 0, &no_abort, args.status, 100000000ull);
+        }
+    } else if (warp >= EPI_WARP0) {
+        // ------------------------------------------------------------ epilogue (both CTAs)
+        const int q = warp & 3;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        uint32_t acc_cnt[2] = {0, 0};
+        const uint32_t empty_remote[2] = {map_to_rank(smem_u32(&acc_empty[0]), 0),
+                                          map_to_rank(smem_u32(&acc_empty[1]), 0)};
+        bool ok = true;
+        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
+            const int npair = min(2, my_tiles - 2 * pr);
+            for (int c = 0; ok && c < args.nchunks; ++c) {
+                for (int s = 0; ok && s < npair; ++s) {
+                    const int tile = cluster + (2 * pr + s) * nclusters;
+                    int l, mt, nt;
+                    decode_tile(tile, args, l, mt, nt);
+                    bool got = true;
+                    if (lane == 0)
+                        got = mbar_wait(&acc_full[s], acc_cnt[s] & 1, abort_flag, args.status);
+                    got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                    if (!got) {
+                        ok = false;
+                        break;
+                    }
+                    ++acc_cnt[s];
+                    tc_fence_after();
+                    const uint32_t taddr = tmem_base + lane_base + (uint32_t)(s * pair::BN);
+                    const float p = args.ep.p[l], inv = args.ep.inv_p[l];
+                    if (c + 1 < args.nchunks) {
+#pragma unroll 1
+                        for (int col = 0; col < pair::BN; col += 32) {
+                            uint32_t v[32];
+                            tmem_ld32(taddr + col, v);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const float x = __uint_as_float(v[j]);
+                                v[j] = __float_as_uint(fmaf(-rintf(x * inv), p, x));
+                            }
+                            tmem_st32(taddr + col, v);
+                        }
+                        tmem_wait_st();
+                    } else {
+                        const float hi = args.ep.hi[l], lo = args.ep.lo[l];
+                        const int64_t row = (int64_t)mt * pair::BM + (int64_t)rank * pair::HALF + q * 32 + lane;
+                        const bool live = row < args.m_rows;
+                        int8_t* dst = args.out + (int64_t)l * args.out_plane +
+                                      (live ? row : 0) * args.out_ld + (int64_t)nt * pair::BN;
+#pragma unroll 1
+                        for (int col = 0; col < pair::BN; col += 32) {
+                            uint32_t v[32];
+                            tmem_ld32(taddr + col, v);
+                            uint32_t packed[8];
+#pragma unroll
+                            for (int w = 0; w < 8; ++w) {
+                                uint32_t word = 0;
+#pragma unroll
+                                for (int b = 0; b < 4; ++b) {
+                                    const float x = __uint_as_float(v[4 * w + b]);
+                                    float r = fmaf(-rintf(x * inv), p, x);
+                                    r = r > hi ? r - p : r;
+                                    r = r < lo ? r + p : r;
+                                    word |= ((uint32_t)__float2int_rn(r) & 0xFFu) << (8 * b);
+                                }
+                                packed[w] = word;
+                            }
+                            if (live) {
+                                uint4* o = reinterpret_cast<uint4*>(dst + col);
+                                o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                                o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (leader) mbar_arrive(&acc_empty[s]);
+                        else mbar_arrive_cluster(empty_remote[s]);
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(pair::TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -448,9 +757,67 @@ bool encode_planes(CUtensorMap* map, const void* base, int N, int rows_pad, int 
 
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
                         const void* planes_b, int8_t* out, const EpilogueTables& t,
-                        unsigned* status, int num_sms, int chunk_k, cudaStream_t stream) {
+                        unsigned* status, int num_sms, int chunk_k, int variant,
+                        cudaStream_t stream) {
     if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
+    int cb = chunk_k / BK;
+    if (cb < 1) cb = 1;
+    if (cb > 15) cb = 15;  // <= 960 products between reductions keeps fp32 exact
+    GemmArgs a;
+    a.k_blocks = k_pad / BK;
+    a.chunk_blocks = cb;
+    a.nchunks = a.k_blocks > 0 ? (a.k_blocks + cb - 1) / cb : 0;
+    a.m_rows = m_pad;
+    a.out = out;
+    a.out_ld = n_pad;
+    a.out_plane = (int64_t)m_pad * n_pad;
+    a.status = status;
+    a.ep = t;
+    if (a.k_blocks == 0) {  // empty inner dimension: every product residue is zero
+        cudaError_t e = cudaMemsetAsync(out, 0, (size_t)num_moduli * m_pad * n_pad, stream);
+        return e == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
+    }
+    const bool use_pair = variant == OZAKI2_GEMM_PAIR || (variant == OZAKI2_GEMM_AUTO && m_pad >= 256);
     CUtensorMap ta, tb;
+    if (use_pair) {
+        if (!encode_planes(&ta, planes_a, num_moduli, m_pad, k_pad, pair::HALF) ||
+            !encode_planes(&tb, planes_b, num_moduli, n_pad, k_pad, pair::HALF))
+            return OZAKI2_ERROR_DRIVER;
+        static std::once_flag attr_once;
+        static cudaError_t attr_err = cudaSuccess;
+        std::call_once(attr_once, [] {
+            attr_err = cudaFuncSetAttribute(residue_gemm_pair_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)pair::SMEM_BYTES);
+        });
+        if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        a.tiles_m = (m_pad + pair::BM - 1) / pair::BM;
+        a.tiles_n = n_pad / pair::BN;
+        a.total_tiles = a.tiles_m * a.tiles_n * num_moduli;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(NUM_THREADS);
+        cfg.dynamicSmemBytes = pair::SMEM_BYTES;
+        cfg.stream = stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int max_clusters = num_sms / 2;
+        cfg.gridDim = dim3(2 * max_clusters);
+        int q = 0;
+        if (cudaOccupancyMaxActiveClusters(&q, residue_gemm_pair_kernel, &cfg) == cudaSuccess &&
+            q > 0 && q < max_clusters)
+            max_clusters = q;
+        cudaGetLastError();
+        const int clusters = a.total_tiles < max_clusters ? a.total_tiles : max_clusters;
+        cfg.gridDim = dim3(2 * clusters);
+        if (cudaLaunchKernelEx(&cfg, residue_gemm_pair_kernel, ta, tb, a) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+        return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
+    }
     if (!encode_planes(&ta, planes_a, num_moduli, m_pad, k_pad, BM) ||
         !encode_planes(&tb, planes_b, num_moduli, n_pad, k_pad, BN))
         return OZAKI2_ERROR_DRIVER;
@@ -462,26 +829,9 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const v
                                         (int)SMEM_BYTES);
     });
     if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
-
-    GemmArgs a;
     a.tiles_m = m_pad / BM;
     a.tiles_n = n_pad / BN;
     a.total_tiles = a.tiles_m * a.tiles_n * num_moduli;
-    a.k_blocks = k_pad / BK;
-    int cb = chunk_k / BK;
-    if (cb < 1) cb = 1;
-    if (cb > 15) cb = 15;  // <= 960 products between reductions keeps fp32 exact
-    a.chunk_blocks = cb;
-    a.nchunks = a.k_blocks > 0 ? (a.k_blocks + cb - 1) / cb : 0;
-    a.out = out;
-    a.out_ld = n_pad;
-    a.out_plane = (int64_t)m_pad * n_pad;
-    a.status = status;
-    a.ep = t;
-    if (a.k_blocks == 0) {  // empty inner dimension: every product residue is zero
-        cudaError_t e = cudaMemsetAsync(out, 0, (size_t)num_moduli * m_pad * n_pad, stream);
-        return e == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
-    }
     const int grid = a.total_tiles < num_sms ? a.total_tiles : num_sms;
     residue_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, stream>>>(ta, tb, a);
     return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;

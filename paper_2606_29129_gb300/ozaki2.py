@@ -24,6 +24,9 @@ ROWS_ALIGN_B = 256
 K_ALIGN = 64
 SHIFT_NONFINITE = -(2**31)
 ERROR_TOO_LARGE = 6
+OPT_GEMM_VARIANT = 1
+OPT_CHUNK_K = 2
+GEMM_AUTO, GEMM_SINGLE, GEMM_PAIR = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 _lib = None
@@ -69,6 +72,7 @@ def lib() -> ctypes.CDLL:
             "ozaki2_dgemm_noalloc": [ch, ch, i32, i32, i32, f64, vp, i32, vp, i32, f64, vp, i32,
                                      i32, vp],
             "ozaki2_set_timing": [vp, i32],
+            "ozaki2_set_option": [vp, i32, i32],
             "ozaki2_get_timing": [vp, ctypes.POINTER(ctypes.c_float)],
         }
         for name, args in sig.items():
@@ -136,6 +140,9 @@ class Handle:
 
     def set_workspace(self, buf, nbytes: int):
         _check("ozaki2_set_workspace", lib().ozaki2_set_workspace(self.h, _ptr(buf), nbytes))
+
+    def set_option(self, option: int, value: int):
+        _check("ozaki2_set_option", lib().ozaki2_set_option(self.h, option, value))
 
     def set_timing(self, on: bool = True):
         _check("ozaki2_set_timing", lib().ozaki2_set_timing(self.h, 1 if on else 0))

@@ -63,16 +63,21 @@ def planes_b(oz, B_np, k, n, f, N, trans="N", ldb=None):
     return planes.float().cpu().numpy().astype(np.int64)
 
 
-def residue_gemm(oz, RA, RB):
-    """RA (N, m_pad, k_pad), RB (N, n_pad, k_pad) integer arrays -> int8 (N, m_pad, n_pad)."""
+def residue_gemm(oz, RA, RB, variant=None):
+    """RA (N, m_pad, k_pad), RB (N, n_pad, k_pad) integer arrays -> int8 (N, m_pad, n_pad).
+    variant: None (automatic) or one of oz.GEMM_SINGLE / oz.GEMM_PAIR."""
     import torch
 
+    h = None
+    if variant is not None:
+        h = oz.Handle()
+        h.set_option(oz.OPT_GEMM_VARIANT, variant)
     N, mp, kp = RA.shape
     npad = RB.shape[1]
     pa = torch.from_numpy(np.ascontiguousarray(RA, dtype=np.float32)).to(torch.bfloat16).cuda()
     pb = torch.from_numpy(np.ascontiguousarray(RB, dtype=np.float32)).to(torch.bfloat16).cuda()
     out = torch.full((N, mp, npad), 99, dtype=torch.int8, device="cuda")
-    ok(oz.ozaki2_residue_gemm(N, mp, npad, kp, pa, pb, out), "residue_gemm")
+    ok(oz.ozaki2_residue_gemm(N, mp, npad, kp, pa, pb, out, handle=h), "residue_gemm")
     torch.cuda.synchronize()
     return out.cpu().numpy()
 
@@ -90,11 +95,14 @@ def crt(oz, c, e, f, m, n, alpha=1.0, beta=0.0, Cin=None):
 
 
 def dgemm(oz, A_np, B_np, m, n, k, N, transA="N", transB="N", alpha=1.0, beta=0.0, Cin=None,
-          lda=None, ldb=None, handle=None):
+          lda=None, ldb=None, handle=None, variant=None):
     import torch
 
     lda = lda if lda is not None else A_np.shape[-1]
     ldb = ldb if ldb is not None else B_np.shape[-1]
+    if variant is not None:
+        handle = handle or oz.Handle()
+        handle.set_option(oz.OPT_GEMM_VARIANT, variant)
     C = torch.zeros((max(n, 1), max(m, 1)), dtype=torch.float64, device="cuda") if Cin is None \
         else dev(Cin)
     A = dev(A_np) if A_np.size else torch.zeros(1, dtype=torch.float64, device="cuda")

@@ -68,6 +68,18 @@ def test_shapes_and_transposes(oz, orc, shape, trans):
     assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 14, tA, tB))
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("chunk", [64, 512, 960])
+def test_gemm_variants_and_chunks(oz, orc, variant, chunk):
+    """Both residue-GEMM kernels and several reduction chunk lengths give the same bits."""
+    m, n, k = 300, 520, 1500
+    A, B = make(m, n, k, 1.0, 61)
+    h = oz.Handle()
+    h.set_option(oz.OPT_CHUNK_K, chunk)
+    C = _gpu.dgemm(oz, A, B, m, n, k, 16, handle=h, variant=variant)
+    assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 16))
+
+
 @pytest.mark.parametrize("N", [2, 5, 8, 11, 14, 16, 17, 18, 20])
 @pytest.mark.parametrize("phi", [0.5, 4.0])
 def test_moduli_counts(oz, orc, N, phi):

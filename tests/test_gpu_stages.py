@@ -144,23 +144,32 @@ def random_residues(rng, N, rows, kk, p, fill_k=None):
     return R
 
 
+VARIANTS = ["single", "pair"]
+
+
+def variant_code(oz, name):
+    return {"single": oz.GEMM_SINGLE, "pair": oz.GEMM_PAIR}[name]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("dims", [(128, 256, 64), (256, 512, 1024), (384, 256, 3008),
-                                  (128, 256, 16384)])
+                                  (128, 256, 16384), (640, 768, 320)])
 @pytest.mark.parametrize("N", [2, 14, 20])
-def test_residue_gemm_matches_oracle(oz, orc, dims, N):
+def test_residue_gemm_matches_oracle(oz, orc, dims, N, variant):
     mp, npad, kp = dims
     rng = np.random.default_rng(mp + npad + kp + N)
     p = orc.constants(N)["p"]
     RA = random_residues(rng, N, mp, kp, p)
     RB = random_residues(rng, N, npad, kp, p)
-    c = _gpu.residue_gemm(oz, RA, RB)
+    c = _gpu.residue_gemm(oz, RA, RB, variant_code(oz, variant))
     rows = np.arange(0, mp, 7 if kp > 4096 else 1)
     c_ref = orc.residue_products(RA[:, rows].astype(np.int8), RB.astype(np.int8))
     assert np.array_equal(c[:, rows], c_ref)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("kp", [960, 1024, 1088, 2048, 65536])
-def test_residue_gemm_accumulation_extremes(oz, orc, kp):
+def test_residue_gemm_accumulation_extremes(oz, orc, kp, variant):
     """Worst-case magnitudes for the FP32 accumulator: every product (-128)^2 = 2^14 on the
     modulus 256, and +-127 patterns on the others, across reduction-chunk boundaries."""
     N, mp, npad = 3, 128, 256
@@ -175,20 +184,21 @@ def test_residue_gemm_accumulation_extremes(oz, orc, kp):
     sgn = np.where(np.arange(kp) % 2 == 0, 1, -1)
     RA[2] = 126 * sgn
     RB[2] = 126
-    c = _gpu.residue_gemm(oz, RA, RB)
+    c = _gpu.residue_gemm(oz, RA, RB, variant_code(oz, variant))
     c_ref = orc.residue_products(RA[:, :16].astype(np.int8), RB.astype(np.int8))
     assert np.array_equal(c[:, :16], c_ref)
     assert np.array_equal(c[:, 16:], np.broadcast_to(c[:, :1], c[:, 16:].shape))
 
 
-def test_residue_gemm_many_tiles(oz, orc):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_residue_gemm_many_tiles(oz, orc, variant):
     """More tiles than SMs: the persistent loop, tile pairs and the tile order."""
     N, mp, npad, kp = 14, 2048, 2048, 192
     rng = np.random.default_rng(4)
     p = orc.constants(N)["p"]
     RA = random_residues(rng, N, mp, kp, p)
     RB = random_residues(rng, N, npad, kp, p)
-    c = _gpu.residue_gemm(oz, RA, RB)
+    c = _gpu.residue_gemm(oz, RA, RB, variant_code(oz, variant))
     rows = np.arange(3, mp, 61)
     c_ref = orc.residue_products(RA[:, rows].astype(np.int8), RB.astype(np.int8))
     assert np.array_equal(c[:, rows], c_ref)
