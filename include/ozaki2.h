@@ -61,7 +61,12 @@ extern "C" {
 #define OZAKI2_OPT_GEMM_VARIANT 1 /* residue-GEMM kernel: one of OZAKI2_GEMM_* (default AUTO) */
 #define OZAKI2_OPT_CHUNK_K 2      /* products accumulated between modular reductions in the residue
                                      GEMM: a multiple of 64 in [64, 960] (default 960) */
-#define OZAKI2_GEMM_AUTO 0        /* two-SM tiles when m_pad >= 256, else one-SM tiles */
+#define OZAKI2_OPT_GRAPH 3        /* 1: ozaki2_dgemm_grouped captures each distinct problem list
+                                     once into a CUDA graph and replays it on later calls with
+                                     the same list (same pointers and sizes); 0 (default): off.
+                                     A graph's table buffer is kept until the handle is destroyed,
+                                     the option is turned off, or the workspace is reallocated. */
+#define OZAKI2_GEMM_AUTO 0        /* the kernel measured fastest on GB300 (currently SINGLE) */
 #define OZAKI2_GEMM_SINGLE 1      /* 128 x 256 tiles, one CTA per SM (tcgen05 cta_group::1) */
 #define OZAKI2_GEMM_PAIR 2        /* 256 x 256 tiles on SM pairs (tcgen05 cta_group::2) */
 
@@ -130,6 +135,36 @@ int ozaki2_dgemm(char transA, char transB, int m, int n, int k, double alpha, co
 int ozaki2_dgemm_h(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
                    double alpha, const double* A, int lda, const double* B, int ldb,
                    double beta, double* C, int ldc, int num_moduli);
+
+/* ---- many independent problems at once ---------------------------------------------------- */
+/* One problem of a grouped call: the arguments of ozaki2_dgemm. */
+typedef struct ozaki2_problem {
+    char transA, transB;
+    int m, n, k;
+    double alpha;
+    const double* A;
+    int lda;
+    const double* B;
+    int ldb;
+    double beta;
+    double* C;
+    int ldc;
+    int num_moduli;
+} ozaki2_problem;
+
+/* Workspace bytes ozaki2_dgemm_grouped needs for these problems (0 if one is invalid). */
+size_t ozaki2_grouped_workspace_size(int count, const ozaki2_problem* problems);
+
+/* `count` independent emulated DGEMMs (each exactly as ozaki2_dgemm computes it, bit for bit)
+ * in a handful of launches: one grouped scaling launch, one grouped conversion launch per
+ * distinct moduli count, ONE persistent residue-GEMM launch over the tiles of all problems, and
+ * one grouped CRT launch per distinct moduli count.  Sizes, transposes, moduli counts and
+ * alpha/beta may differ between problems; outputs must not overlap.  `problems` is a host array
+ * that is read during the call only.  The per-problem tables are staged in pinned host memory
+ * owned by the handle and copied with one cudaMemcpyAsync.  Errors: -2 count < 0, -3 problems
+ * NULL; -(100 (i+1) + a) when argument a (numbered as for ozaki2_dgemm) of problem i is
+ * invalid. */
+int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem* problems);
 
 /* ---- the stages, one entry point each ------------------------------------------------------ */
 /* Step 2 scaling (Algorithm 2, eq. (proposed-mu)): shifts[i] = log2(mu_i) for the m rows of

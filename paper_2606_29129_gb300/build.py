@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libozaki2.so")
 SOURCES = ["api.cu", "tables.cu", "scale.cu", "convert.cu", "residue_gemm.cu", "crt.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "grouped.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

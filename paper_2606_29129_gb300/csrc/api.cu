@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "ozaki2_internal.h"
 
@@ -21,7 +22,33 @@ struct ozaki2_context {
     bool timing = false;           // record stage events in ozaki2_dgemm
     bool timed_call = false;       // a timed call has been queued
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    char* stage = nullptr;         // pinned staging buffer of grouped-call tables
+    size_t stage_bytes = 0;
+    cudaEvent_t staged = nullptr;  // recorded after the last copy out of `stage`
+    bool use_graphs = false;       // replay grouped calls from captured CUDA graphs
+    struct GraphEntry {
+        std::vector<ozaki2_problem> probs;
+        int chunk_k;
+        void* tables = nullptr;    // device copy of the call's tables
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t capture_stream = nullptr;
 };
+
+namespace {
+void clear_graphs(ozaki2_context* ctx) {
+    for (auto& g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.tables) cudaFree(g.tables);
+    }
+    ctx->graphs.clear();
+}
+bool same_problems(const std::vector<ozaki2_problem>& a, int count, const ozaki2_problem* b) {
+    return (int)a.size() == count &&
+           (count == 0 || memcmp(a.data(), b, sizeof(ozaki2_problem) * (size_t)count) == 0);
+}
+}  // namespace
 
 namespace {
 
@@ -79,6 +106,7 @@ int ensure_workspace(ozaki2_context* ctx, size_t bytes) {
     if (ctx->ws) {
         // work queued on other streams may still use the old buffer
         if (cudaDeviceSynchronize() != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        clear_graphs(ctx);  // captured kernels refer to the old workspace
         cudaFree(ctx->ws);
         ctx->ws = nullptr;
         ctx->ws_bytes = 0;
@@ -214,6 +242,10 @@ int ozaki2_destroy(ozaki2_handle_t handle) {
     if (handle->d_status) cudaFree(handle->d_status);
     for (auto& e : handle->ev)
         if (e) cudaEventDestroy(e);
+    if (handle->staged) cudaEventDestroy(handle->staged);
+    clear_graphs(handle);
+    if (handle->capture_stream) cudaStreamDestroy(handle->capture_stream);
+    if (handle->stage) cudaFreeHost(handle->stage);
     delete handle;
     return OZAKI2_SUCCESS;
 }
@@ -237,7 +269,13 @@ int ozaki2_set_option(ozaki2_handle_t handle, int option, int value) {
             return OZAKI2_SUCCESS;
         case OZAKI2_OPT_CHUNK_K:
             if (value < 64 || value > 960 || value % 64) return -3;
+            if (value != ctx->chunk_k) clear_graphs(ctx);
             ctx->chunk_k = value;
+            return OZAKI2_SUCCESS;
+        case OZAKI2_OPT_GRAPH:
+            if (value != 0 && value != 1) return -3;
+            if (!value) clear_graphs(ctx);
+            ctx->use_graphs = value != 0;
             return OZAKI2_SUCCESS;
         default:
             return -2;
@@ -351,6 +389,96 @@ int ozaki2_dgemm_h(ozaki2_handle_t handle, char transA, char transB, int m, int 
     if (rc) return rc;
     return dgemm_impl(ctx, 1, transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
                       num_moduli);
+}
+
+size_t ozaki2_grouped_workspace_size(int count, const ozaki2_problem* problems) {
+    if (count < 0 || (count > 0 && !problems)) return 0;
+    if (grouped_check(count, problems)) return 0;
+    return grouped_workspace_bytes(count, problems);
+}
+
+int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem* problems) {
+    if (count < 0) return -2;
+    if (count > 0 && !problems) return -3;
+    int rc = grouped_check(count, problems);
+    if (rc) return rc;
+    if (count == 0) return OZAKI2_SUCCESS;
+    ozaki2_context* ctx;
+    if ((rc = resolve(handle, &ctx))) return rc;
+    if ((rc = ensure_workspace(ctx, grouped_workspace_bytes(count, problems)))) return rc;
+    if (!ctx->staged &&
+        cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    const size_t tb = (size_t)grouped_table_bytes(count, problems);
+    char* ws = static_cast<char*>(ctx->ws);
+    if (ctx->use_graphs) {
+        for (auto& g : ctx->graphs)
+            if (g.chunk_k == ctx->chunk_k && same_problems(g.probs, count, problems))
+                return cudaGraphLaunch(g.exec, ctx->stream) == cudaSuccess ? OZAKI2_SUCCESS
+                                                                            : OZAKI2_ERROR_CUDA;
+        // First call with these problems: upload the tables to a buffer of their own, capture
+        // the launches once, keep the instantiated graph.
+        ozaki2_context::GraphEntry g;
+        g.probs.assign(problems, problems + count);
+        g.chunk_k = ctx->chunk_k;
+        std::vector<char> host(tb ? tb : 1);
+        if ((rc = build_grouped_tables(count, problems, ws, host.data(), ctx->chunk_k))) return rc;
+        if (cudaMalloc(&g.tables, tb ? tb : 1) != cudaSuccess) {
+            cudaGetLastError();
+            return OZAKI2_ERROR_ALLOC;
+        }
+        if (cudaMemcpy(g.tables, host.data(), tb, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(g.tables);
+            return OZAKI2_ERROR_CUDA;
+        }
+        if (!ctx->capture_stream &&
+            cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaFree(g.tables);
+            return OZAKI2_ERROR_CUDA;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess) {
+            cudaFree(g.tables);
+            return OZAKI2_ERROR_CUDA;
+        }
+        rc = launch_grouped(count, problems, static_cast<const char*>(g.tables), ctx->d_status,
+                            ctx->num_sms, ctx->chunk_k, ctx->capture_stream);
+        const cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (rc || ce != cudaSuccess ||
+            cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaFree(g.tables);
+            cudaGetLastError();
+            return rc ? rc : OZAKI2_ERROR_CUDA;
+        }
+        cudaGraphDestroy(graph);
+        ctx->graphs.push_back(std::move(g));
+        return cudaGraphLaunch(ctx->graphs.back().exec, ctx->stream) == cudaSuccess
+                   ? OZAKI2_SUCCESS
+                   : OZAKI2_ERROR_CUDA;
+    }
+    if (ctx->stage_bytes < tb) {
+        if (cudaEventSynchronize(ctx->staged) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        if (ctx->stage) cudaFreeHost(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        if (cudaMallocHost(&ctx->stage, tb) != cudaSuccess) {
+            cudaGetLastError();
+            return OZAKI2_ERROR_ALLOC;
+        }
+        ctx->stage_bytes = tb;
+    }
+    // the staging buffer may still be read by the previous call's copy
+    if (cudaEventSynchronize(ctx->staged) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if ((rc = build_grouped_tables(count, problems, ws, ctx->stage, ctx->chunk_k))) return rc;
+    char* tables_dev = grouped_tables_in_workspace(count, problems, ws);
+    if (tb && (cudaMemcpyAsync(tables_dev, ctx->stage, tb, cudaMemcpyHostToDevice,
+                               ctx->stream) != cudaSuccess ||
+               cudaEventRecord(ctx->staged, ctx->stream) != cudaSuccess))
+        return OZAKI2_ERROR_CUDA;
+    return launch_grouped(count, problems, tables_dev, ctx->d_status, ctx->num_sms,
+                          ctx->chunk_k, ctx->stream);
 }
 
 int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,

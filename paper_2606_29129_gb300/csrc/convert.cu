@@ -117,16 +117,14 @@ __device__ __forceinline__ void store_residues8(const double (&v)[8], int e, boo
 // Lines contiguous (elem_stride == 1): thread = (line, group of 8 elements); a warp covers 256
 // consecutive elements of one line, so loads and stores are both contiguous.
 template <int N>
-__global__ void __launch_bounds__(256) convert_contiguous_kernel(
+__device__ __forceinline__ void convert_contiguous_item(
     const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
-    const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
-    unsigned* status) {
+    const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
+    int64_t g, unsigned* status) {
     const int groups = k_pad / 8;
-    const int64_t total = (int64_t)rows_pad * groups;
     const int64_t plane_elems = (int64_t)rows_pad * k_pad;
     const bool vec = ((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
+    {
         const int i = (int)(g / groups);
         const int h0 = (int)(g - (int64_t)i * groups) * 8;
         const bool row_live = i < lines;
@@ -149,6 +147,18 @@ __global__ void __launch_bounds__(256) convert_contiguous_kernel(
     }
 }
 
+template <int N>
+__global__ void __launch_bounds__(256) convert_contiguous_kernel(
+    const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
+    const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
+    unsigned* status) {
+    const int64_t total = (int64_t)rows_pad * (k_pad / 8);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x)
+        convert_contiguous_item<N>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, g,
+                                   status);
+}
+
 // Lines adjacent (line_stride == 1): a block converts a tile of 64 lines x 64 elements.  The tile
 // is read with coalesced loads along the lines (a warp reads 32 consecutive doubles), transposed
 // through shared memory, and each group of 8 lanes writes one line's 64 elements (128 bytes per
@@ -156,18 +166,16 @@ __global__ void __launch_bounds__(256) convert_contiguous_kernel(
 constexpr int kTileLines = 64;
 constexpr int kTileK = 64;
 
+// Tile tt (64 lines x 64 elements) of an adjacent-line matrix; all 256 threads take part.
 template <int N>
-__global__ void __launch_bounds__(256) convert_adjacent_kernel(
+__device__ __forceinline__ void convert_adjacent_tile(
     const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
-    const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
-    unsigned* status) {
-    __shared__ double tile[kTileK][kTileLines + 1];
+    const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
+    int64_t tt, double (*tile)[kTileLines + 1], unsigned* status) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t plane_elems = (int64_t)rows_pad * k_pad;
     const int tiles_l = (rows_pad + kTileLines - 1) / kTileLines;
-    const int tiles_k = k_pad / kTileK;
-    const int64_t ntiles = (int64_t)tiles_l * tiles_k;
-    for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+    {
         const int tl = (int)(tt % tiles_l);
         const int tk = (int)(tt / tiles_l);
         const int line0 = tl * kTileLines, h0 = tk * kTileK;
@@ -205,6 +213,45 @@ __global__ void __launch_bounds__(256) convert_adjacent_kernel(
 }
 
 template <int N>
+__global__ void __launch_bounds__(256) convert_adjacent_kernel(
+    const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
+    const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
+    unsigned* status) {
+    __shared__ double tile[kTileK][kTileLines + 1];
+    const int tiles_l = (rows_pad + kTileLines - 1) / kTileLines;
+    const int64_t ntiles = (int64_t)tiles_l * (k_pad / kTileK);
+    for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x)
+        convert_adjacent_tile<N>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, tt, tile,
+                                 status);
+}
+
+// Grouped: each block converts one tile (adjacent lines) or 256 groups of 8 elements
+// (contiguous lines) of one side of one problem.
+template <int N>
+__global__ void __launch_bounds__(256) convert_grouped_kernel(
+    const GroupProblem* __restrict__ probs, const ConvertWork* __restrict__ work,
+    const ConvertTables t, unsigned* status) {
+    __shared__ double tile[kTileK][kTileLines + 1];
+    const ConvertWork w = work[blockIdx.x];
+    const GroupProblem& P = probs[w.problem];
+    const double* X = w.side ? P.B : P.A;
+    const int64_t ls = w.side ? P.b_ls : P.a_ls, es = w.side ? P.b_es : P.a_es;
+    const int lines = w.side ? P.n : P.m;
+    const int rows_pad = w.side ? P.n_pad : P.m_pad;
+    const int* shifts = w.side ? P.f : P.e;
+    auto* planes = static_cast<__nv_bfloat16*>(w.side ? P.pb : P.pa);
+    if (es != 1) {
+        convert_adjacent_tile<N>(X, es, lines, P.k, shifts, t, planes, rows_pad, P.k_pad, w.block,
+                                 tile, status);
+    } else {
+        const int64_t g = (int64_t)w.block * 256 + threadIdx.x;
+        if (g < (int64_t)rows_pad * (P.k_pad / 8))
+            convert_contiguous_item<N>(X, ls, lines, P.k, shifts, t, planes, rows_pad, P.k_pad, g,
+                                       status);
+    }
+}
+
+template <int N>
 cudaError_t launch_convert_n(const double* X, int64_t line_stride, int64_t elem_stride,
                              int lines, int len, const int* shifts, const ConvertTables& t,
                              __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
@@ -227,6 +274,38 @@ cudaError_t launch_convert_n(const double* X, int64_t line_stride, int64_t elem_
 }
 
 }  // namespace
+
+int convert_blocks(int lines, int64_t elem_stride, int rows_pad, int k_pad) {
+    (void)lines;
+    if (elem_stride != 1)
+        return ((rows_pad + kTileLines - 1) / kTileLines) * (k_pad / kTileK);
+    return (int)(((int64_t)rows_pad * (k_pad / 8) + 255) / 256);
+}
+
+cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const ConvertWork* work,
+                                   int blocks, const ConvertTables& t, unsigned* status,
+                                   cudaStream_t stream) {
+    if (blocks <= 0) return cudaSuccess;
+    switch (N) {
+#define OZAKI2_CONVERT_GROUPED_CASE(NN)                                                      \
+    case NN:                                                                                 \
+        convert_grouped_kernel<NN><<<blocks, 256, 0, stream>>>(probs, work, t, status);      \
+        break;
+        OZAKI2_CONVERT_GROUPED_CASE(2) OZAKI2_CONVERT_GROUPED_CASE(3)
+        OZAKI2_CONVERT_GROUPED_CASE(4) OZAKI2_CONVERT_GROUPED_CASE(5)
+        OZAKI2_CONVERT_GROUPED_CASE(6) OZAKI2_CONVERT_GROUPED_CASE(7)
+        OZAKI2_CONVERT_GROUPED_CASE(8) OZAKI2_CONVERT_GROUPED_CASE(9)
+        OZAKI2_CONVERT_GROUPED_CASE(10) OZAKI2_CONVERT_GROUPED_CASE(11)
+        OZAKI2_CONVERT_GROUPED_CASE(12) OZAKI2_CONVERT_GROUPED_CASE(13)
+        OZAKI2_CONVERT_GROUPED_CASE(14) OZAKI2_CONVERT_GROUPED_CASE(15)
+        OZAKI2_CONVERT_GROUPED_CASE(16) OZAKI2_CONVERT_GROUPED_CASE(17)
+        OZAKI2_CONVERT_GROUPED_CASE(18) OZAKI2_CONVERT_GROUPED_CASE(19)
+        OZAKI2_CONVERT_GROUPED_CASE(20)
+#undef OZAKI2_CONVERT_GROUPED_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_convert(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, const int* shifts, const ConvertTables& t, void* planes,

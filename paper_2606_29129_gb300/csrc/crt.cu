@@ -183,16 +183,14 @@ __device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int6
     return scale_pow2_rn(x, -(ea + fb));
 }
 
+// One 32 x 32 tile of C (rows i0.., columns j0..); all 256 threads take part.
 template <int N>
-__global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res, int64_t ldr,
-                                                  int64_t plane, int m, int n,
-                                                  const int* __restrict__ sa,
-                                                  const int* __restrict__ sb, double alpha,
-                                                  double beta, double* __restrict__ C,
-                                                  int64_t ldc, const CrtTables t) {
-    __shared__ double tile[TJ][TI + 1];
+__device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t ldr,
+                                         int64_t plane, int m, int n, const int* __restrict__ sa,
+                                         const int* __restrict__ sb, double alpha, double beta,
+                                         double* __restrict__ C, int64_t ldc, const CrtTables& t,
+                                         int i0, int j0, double (*tile)[TI + 1]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i0 = blockIdx.y * TI, j0 = blockIdx.x * TJ;
     const int j = j0 + lane;
     const int fb = j < n ? sb[j] : 0;
 #pragma unroll
@@ -217,6 +215,30 @@ __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res
             *out = v;
         }
     }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res, int64_t ldr,
+                                                  int64_t plane, int m, int n,
+                                                  const int* __restrict__ sa,
+                                                  const int* __restrict__ sb, double alpha,
+                                                  double beta, double* __restrict__ C,
+                                                  int64_t ldc, const CrtTables t) {
+    __shared__ double tile[TJ][TI + 1];
+    crt_tile<N>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t, blockIdx.y * TI,
+                blockIdx.x * TJ, tile);
+}
+
+// Grouped: each block reconstructs one 32 x 32 tile of one problem's C.
+template <int N>
+__global__ void __launch_bounds__(256) crt_grouped_kernel(const GroupProblem* __restrict__ probs,
+                                                          const CrtWork* __restrict__ work,
+                                                          const CrtTables t) {
+    __shared__ double tile[TJ][TI + 1];
+    const CrtWork w = work[blockIdx.x];
+    const GroupProblem& P = probs[w.problem];
+    crt_tile<N>(P.res, P.n_pad, (int64_t)P.m_pad * P.n_pad, P.m, P.n, P.e, P.f, P.alpha, P.beta,
+                P.C, P.ldc, t, w.i0, w.j0, tile);
 }
 
 __global__ void scale_c_kernel(int m, int n, double beta, double* C, int64_t ldc) {
@@ -251,6 +273,27 @@ cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int
         default: return cudaErrorInvalidValue;
     }
 #undef OZAKI2_CRT_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* work, int blocks,
+                               const CrtTables& t, cudaStream_t stream) {
+    if (blocks <= 0) return cudaSuccess;
+    switch (N) {
+#define OZAKI2_CRT_GROUPED_CASE(NN)                                                    \
+    case NN:                                                                           \
+        crt_grouped_kernel<NN><<<blocks, 256, 0, stream>>>(probs, work, t);            \
+        break;
+        OZAKI2_CRT_GROUPED_CASE(2) OZAKI2_CRT_GROUPED_CASE(3) OZAKI2_CRT_GROUPED_CASE(4)
+        OZAKI2_CRT_GROUPED_CASE(5) OZAKI2_CRT_GROUPED_CASE(6) OZAKI2_CRT_GROUPED_CASE(7)
+        OZAKI2_CRT_GROUPED_CASE(8) OZAKI2_CRT_GROUPED_CASE(9) OZAKI2_CRT_GROUPED_CASE(10)
+        OZAKI2_CRT_GROUPED_CASE(11) OZAKI2_CRT_GROUPED_CASE(12) OZAKI2_CRT_GROUPED_CASE(13)
+        OZAKI2_CRT_GROUPED_CASE(14) OZAKI2_CRT_GROUPED_CASE(15) OZAKI2_CRT_GROUPED_CASE(16)
+        OZAKI2_CRT_GROUPED_CASE(17) OZAKI2_CRT_GROUPED_CASE(18) OZAKI2_CRT_GROUPED_CASE(19)
+        OZAKI2_CRT_GROUPED_CASE(20)
+#undef OZAKI2_CRT_GROUPED_CASE
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -1,6 +1,7 @@
 // ozaki2_internal.h -- internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -57,6 +58,74 @@ struct ModTables {
     CrtTables crt;
     EpilogueTables epi;
 };
+
+// One problem of a grouped call, as the grouped kernels see it (device memory).
+struct GroupProblem {
+    const double* A;
+    const double* B;
+    double* C;
+    int64_t a_ls, a_es;  // element h of row i of op(A): A[i * a_ls + h * a_es]
+    int64_t b_ls, b_es;  // element h of column j of op(B): B[j * b_ls + h * b_es]
+    int64_t ldc;
+    int m, n, k, N;
+    int m_pad, n_pad, k_pad;
+    double alpha, beta;
+    float pprime;
+    int* e;              // shifts of the rows of op(A)   [m_pad]
+    int* f;              // shifts of the columns of op(B) [n_pad]
+    void* pa;            // bf16 planes [N][m_pad][k_pad]
+    void* pb;            // bf16 planes [N][n_pad][k_pad]
+    int8_t* res;         // product residues [N][m_pad][n_pad]
+};
+
+// Work tables of the grouped kernels: one entry per thread block.
+struct ScaleWork {       // 128 lines of one side of one problem
+    int problem, side, line0;
+};
+struct ConvertWork {     // block `block` of one side of one problem (adjacent: a 64 x 64 tile,
+    int problem, side, block;  // contiguous: 256 groups of 8 elements)
+};
+struct CrtWork {         // one 32 x 32 tile of C
+    int problem, i0, j0;
+};
+
+// One problem of a grouped residue GEMM (device memory, 64-byte aligned for the tensor maps).
+struct alignas(64) GroupGemmProblem {
+    CUtensorMap ta;      // A planes [N][m_pad][k_pad], box 64 x 128
+    CUtensorMap tb;      // B planes [N][n_pad][k_pad], box 64 x 256
+    int8_t* out;         // product residues [N][m_pad][n_pad]
+    int64_t out_ld, out_plane;
+    int tiles_m, tiles_n, k_blocks, nchunks;
+    int tile_begin;      // index of this problem's first tile in the grouped launch
+};
+
+// Fills the tensor maps and tile counts of one grouped-GEMM problem (host); false on failure.
+bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, int k_pad,
+                             const void* planes_a, const void* planes_b, int8_t* out,
+                             int chunk_k);
+int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
+                                const EpilogueTables& t, unsigned* status, int num_sms,
+                                int chunk_k, cudaStream_t stream);
+
+cudaError_t launch_scale_grouped(const GroupProblem* probs, const ScaleWork* work, int blocks,
+                                 unsigned* status, cudaStream_t stream);
+cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const ConvertWork* work,
+                                   int blocks, const ConvertTables& t, unsigned* status,
+                                   cudaStream_t stream);
+cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* work, int blocks,
+                               const CrtTables& t, cudaStream_t stream);
+// Blocks of the grouped convert for one side of one problem.
+int convert_blocks(int lines, int64_t elem_stride, int rows_pad, int k_pad);
+
+// Grouped calls (grouped.cu).
+size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs);
+int grouped_table_bytes(int count, const ozaki2_problem* probs);
+int grouped_check(int count, const ozaki2_problem* probs);
+int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char* host,
+                         int chunk_k);
+int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_dev,
+                   unsigned* status, int num_sms, int chunk_k, cudaStream_t stream);
+char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* ws);
 
 // Tables for 2 <= N <= 20 (cached, thread safe).  Returns nullptr for other N.
 const ModTables* mod_tables(int N);

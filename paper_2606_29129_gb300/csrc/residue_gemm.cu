@@ -36,7 +36,9 @@ constexpr int B_BYTES = BN * BK * 2;           // 32 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 2 * BN;              // two fp32 accumulators of 128 x 256
 constexpr int NUM_THREADS = 256;
-constexpr int EPI_WARP0 = 4;
+constexpr int EPI_WARP0 = 4;       // warps 4..7: one epilogue warp per TMEM lane quarter
+constexpr int EPI_WARPS = 4;
+constexpr int EPI_COLS = 256;      // accumulator columns drained by one epilogue warp
 constexpr int NUM_BARRIERS = 2 * STAGES + 5;   // full, empty, acc_full[2], acc_empty[2], drain
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARRIERS * 8 + 16;
 constexpr int GROUP_M = 16;                    // m-tiles per group in the tile order (L2 reuse)
@@ -171,6 +173,10 @@ __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// Nearest integer, ties to even.  (On this power-capped part the single rounding instruction
+// measured faster than the two-add magic-number form.)
+__device__ __forceinline__ float round_small(float y) { return rintf(y); }
+
 // ---- cluster (2-SM) helpers
 __device__ __forceinline__ uint32_t cluster_rank() {
     uint32_t r;
@@ -243,10 +249,81 @@ __device__ __forceinline__ void decode_tile(int tile, const GemmArgs& a, int& l,
     nt = r / gsize;
 }
 
-// ---------------------------------------------------------------- the kernel
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-    residue_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                        const __grid_constant__ CUtensorMap tmB, const GemmArgs args) {
+// ---------------------------------------------------------------- tile sources
+// Everything the three roles need about one output tile.
+struct TileInfo {
+    const CUtensorMap* ta;
+    const CUtensorMap* tb;
+    int l, mt, nt, k_blocks, nchunks;
+    int8_t* out;
+    int64_t out_ld, out_plane;
+};
+
+__device__ __forceinline__ void decode_local(int idx, int tiles_m, int tiles_n, int& l, int& mt,
+                                             int& nt) {
+    const int per_plane = tiles_m * tiles_n;
+    l = idx / per_plane;
+    const int r0 = idx - l * per_plane;
+    const int per_group = GROUP_M * tiles_n;
+    const int g = r0 / per_group;
+    const int first_m = g * GROUP_M;
+    const int gsize = min(tiles_m - first_m, GROUP_M);
+    const int r = r0 - g * per_group;
+    mt = first_m + r % gsize;
+    nt = r / gsize;
+}
+
+// One problem; tensor maps in kernel parameters.
+struct SingleSource {
+    const CUtensorMap* ta;
+    const CUtensorMap* tb;
+    const GemmArgs* a;
+    __device__ __forceinline__ TileInfo get(int t) const {
+        TileInfo ti;
+        decode_local(t, a->tiles_m, a->tiles_n, ti.l, ti.mt, ti.nt);
+        ti.ta = ta;
+        ti.tb = tb;
+        ti.k_blocks = a->k_blocks;
+        ti.nchunks = a->nchunks;
+        ti.out = a->out;
+        ti.out_ld = a->out_ld;
+        ti.out_plane = a->out_plane;
+        return ti;
+    }
+};
+
+// Many problems; each with its own tensor maps in device memory.
+struct GroupSource {
+    const GroupGemmProblem* probs;
+    int count;
+    __device__ __forceinline__ TileInfo get(int t) const {
+        int lo = 0, hi = count - 1;  // last problem whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].tile_begin <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const GroupGemmProblem& P = probs[lo];
+        TileInfo ti;
+        decode_local(t - P.tile_begin, P.tiles_m, P.tiles_n, ti.l, ti.mt, ti.nt);
+        ti.ta = &P.ta;
+        ti.tb = &P.tb;
+        ti.k_blocks = P.k_blocks;
+        ti.nchunks = P.nchunks;
+        ti.out = P.out;
+        ti.out_ld = P.out_ld;
+        ti.out_plane = P.out_plane;
+        return ti;
+    }
+};
+
+// ---------------------------------------------------------------- the kernel body
+// Tiles t = blockIdx.x + i * gridDim.x of the source, taken two at a time: the two tiles of a
+// pair accumulate in the two TMEM buffers and their K chunks alternate (a tile with fewer chunks
+// simply drops out), so the reduction of one overlaps the MMAs of the other.
+template <class Src>
+__device__ __forceinline__ void residue_gemm_body(const Src& src, int total_tiles,
+                                                  const GemmArgs& args) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     uint8_t* smem = smem_raw + pad;
@@ -269,7 +346,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 4);
+            mbar_init(&acc_empty[b], EPI_WARPS);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -289,8 +366,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const int my_tiles = blockIdx.x < args.total_tiles
-                             ? (args.total_tiles - 1 - blockIdx.x) / gridDim.x + 1
+    const int my_tiles = (int)blockIdx.x < total_tiles
+                             ? (total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
                              : 0;
 
     if (warp == 0 && lane == 0) {
@@ -301,23 +378,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         bool armed[STAGES];
         for (int s = 0; s < STAGES; ++s) armed[s] = false, armed_parity[s] = 0;
         bool ok = true;
-        for (int pair = 0; ok && 2 * pair < my_tiles; ++pair) {
-            const int npair = min(2, my_tiles - 2 * pair);
-            for (int c = 0; ok && c < args.nchunks; ++c) {
+        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
+            const int npair = min(2, my_tiles - 2 * pr);
+            TileInfo ti[2];
+            for (int s = 0; s < npair; ++s) ti[s] = src.get(blockIdx.x + (2 * pr + s) * gridDim.x);
+            const int maxc = max(ti[0].nchunks, npair > 1 ? ti[1].nchunks : 0);
+            for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
-                    const int tile = blockIdx.x + (2 * pair + s) * gridDim.x;
-                    int l, mt, nt;
-                    decode_tile(tile, args, l, mt, nt);
+                    if (c >= ti[s].nchunks) continue;
                     const int kb0 = c * args.chunk_blocks;
-                    const int kb1 = min(kb0 + args.chunk_blocks, args.k_blocks);
+                    const int kb1 = min(kb0 + args.chunk_blocks, ti[s].k_blocks);
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, args.status)) {
                             ok = false;
                             break;
                         }
                         mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
-                        tma_load_3d(sA + stage * A_BYTES, &tmA, &full[stage], kb * BK, mt * BM, l);
-                        tma_load_3d(sB + stage * B_BYTES, &tmB, &full[stage], kb * BK, nt * BN, l);
+                        tma_load_3d(sA + stage * A_BYTES, ti[s].ta, &full[stage], kb * BK,
+                                    ti[s].mt * BM, ti[s].l);
+                        tma_load_3d(sB + stage * B_BYTES, ti[s].tb, &full[stage], kb * BK,
+                                    ti[s].nt * BN, ti[s].l);
                         armed[stage] = true;
                         armed_parity[stage] = phase;
                         if (++stage == STAGES) {
@@ -340,10 +420,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         uint32_t phase = 0;
         uint32_t acc_cnt[2] = {0, 0};
         bool ok = true, issued = false;
-        for (int pair = 0; ok && 2 * pair < my_tiles; ++pair) {
-            const int npair = min(2, my_tiles - 2 * pair);
-            for (int c = 0; ok && c < args.nchunks; ++c) {
+        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
+            const int npair = min(2, my_tiles - 2 * pr);
+            TileInfo ti[2];
+            for (int s = 0; s < npair; ++s) ti[s] = src.get(blockIdx.x + (2 * pr + s) * gridDim.x);
+            const int maxc = max(ti[0].nchunks, npair > 1 ? ti[1].nchunks : 0);
+            for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
+                    if (c >= ti[s].nchunks) continue;
                     if (!mbar_wait(&acc_empty[s], (acc_cnt[s] & 1) ^ 1, abort_flag, args.status)) {
                         ok = false;
                         break;
@@ -352,7 +436,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(s * BN);
                     const int kb0 = c * args.chunk_blocks;
-                    const int kb1 = min(kb0 + args.chunk_blocks, args.k_blocks);
+                    const int kb1 = min(kb0 + args.chunk_blocks, ti[s].k_blocks);
                     for (int kb = kb0; kb < kb1; ++kb) {
                         if (!mbar_wait(&full[stage], phase, abort_flag, args.status)) {
                             ok = false;
@@ -386,16 +470,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     } else if (warp >= EPI_WARP0) {
         // ------------------------------------------------------------ epilogue
         const int q = warp & 3;
-        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int col0 = ((warp - EPI_WARP0) >> 2) * EPI_COLS;  // this warp's share of columns
+        const uint32_t lane_base = ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
         uint32_t acc_cnt[2] = {0, 0};
         bool ok = true;
-        for (int pair = 0; ok && 2 * pair < my_tiles; ++pair) {
-            const int npair = min(2, my_tiles - 2 * pair);
-            for (int c = 0; ok && c < args.nchunks; ++c) {
+        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
+            const int npair = min(2, my_tiles - 2 * pr);
+            TileInfo ti[2];
+            for (int s = 0; s < npair; ++s) ti[s] = src.get(blockIdx.x + (2 * pr + s) * gridDim.x);
+            const int maxc = max(ti[0].nchunks, npair > 1 ? ti[1].nchunks : 0);
+            for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
-                    const int tile = blockIdx.x + (2 * pair + s) * gridDim.x;
-                    int l, mt, nt;
-                    decode_tile(tile, args, l, mt, nt);
+                    if (c >= ti[s].nchunks) continue;
                     bool got = true;
                     if (lane == 0)
                         got = mbar_wait(&acc_full[s], acc_cnt[s] & 1, abort_flag, args.status);
@@ -407,17 +493,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     ++acc_cnt[s];
                     tc_fence_after();
                     const uint32_t taddr = tmem_base + lane_base + (uint32_t)(s * BN);
+                    const int l = ti[s].l;
                     const float p = args.ep.p[l], inv = args.ep.inv_p[l];
-                    if (c + 1 < args.nchunks) {
+                    if (c + 1 < ti[s].nchunks) {
                         // in-place reduction modulo p: |r| <= ~0.52 p
 #pragma unroll 1
-                        for (int col = 0; col < BN; col += 32) {
+                        for (int col = 0; col < EPI_COLS; col += 32) {
                             uint32_t v[32];
                             tmem_ld32(taddr + col, v);
 #pragma unroll
                             for (int j = 0; j < 32; ++j) {
                                 const float x = __uint_as_float(v[j]);
-                                v[j] = __float_as_uint(fmaf(-rintf(x * inv), p, x));
+                                v[j] = __float_as_uint(fmaf(-round_small(x * inv), p, x));
                             }
                             tmem_st32(taddr + col, v);
                         }
@@ -425,11 +512,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     } else {
                         // final drain: symmetric residue as int8
                         const float hi = args.ep.hi[l], lo = args.ep.lo[l];
-                        const int64_t row = (int64_t)mt * BM + q * 32 + lane;
-                        int8_t* dst = args.out + (int64_t)l * args.out_plane + row * args.out_ld +
-                                      (int64_t)nt * BN;
+                        const int64_t row = (int64_t)ti[s].mt * BM + q * 32 + lane;
+                        int8_t* dst = ti[s].out + (int64_t)l * ti[s].out_plane +
+                                      row * ti[s].out_ld + (int64_t)ti[s].nt * BN + col0;
 #pragma unroll 1
-                        for (int col = 0; col < BN; col += 32) {
+                        for (int col = 0; col < EPI_COLS; col += 32) {
                             uint32_t v[32];
                             tmem_ld32(taddr + col, v);
                             uint32_t packed[8];
@@ -439,7 +526,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                                 for (int b = 0; b < 4; ++b) {
                                     const float x = __uint_as_float(v[4 * w + b]);
-                                    float r = fmaf(-rintf(x * inv), p, x);
+                                    float r = fmaf(-round_small(x * inv), p, x);
                                     r = r > hi ? r - p : r;
                                     r = r < lo ? r + p : r;
                                     word |= ((uint32_t)__float2int_rn(r) & 0xFFu) << (8 * b);
@@ -468,6 +555,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                      "r"(TMEM_COLS)
                      : "memory");
     }
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    residue_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB, const GemmArgs args) {
+    const SingleSource src{&tmA, &tmB, &args};
+    residue_gemm_body(src, args.total_tiles, args);
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    residue_gemm_grouped_kernel(const GroupGemmProblem* __restrict__ probs, int count,
+                                int total_tiles, const GemmArgs args) {
+    const GroupSource src{probs, count};
+    residue_gemm_body(src, total_tiles, args);
 }
 
 // ---------------------------------------------------------------- the 2-SM kernel
@@ -519,7 +620,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 8);   // 4 epilogue warps in each CTA of the pair
+            mbar_init(&acc_empty[b], 2 * EPI_WARPS);   // epilogue warps of both CTAs of the pair
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -631,7 +732,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     } else if (warp >= EPI_WARP0) {
         // ------------------------------------------------------------ epilogue (both CTAs)
         const int q = warp & 3;
-        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        const int col0 = ((warp - EPI_WARP0) >> 2) * EPI_COLS;  // this warp's half of the columns
+        const uint32_t lane_base = ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
         uint32_t acc_cnt[2] = {0, 0};
         const uint32_t empty_remote[2] = {map_to_rank(smem_u32(&acc_empty[0]), 0),
                                           map_to_rank(smem_u32(&acc_empty[1]), 0)};
@@ -657,13 +759,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const float p = args.ep.p[l], inv = args.ep.inv_p[l];
                     if (c + 1 < args.nchunks) {
 #pragma unroll 1
-                        for (int col = 0; col < pair::BN; col += 32) {
+                        for (int col = 0; col < EPI_COLS; col += 32) {
                             uint32_t v[32];
                             tmem_ld32(taddr + col, v);
 #pragma unroll
                             for (int j = 0; j < 32; ++j) {
                                 const float x = __uint_as_float(v[j]);
-                                v[j] = __float_as_uint(fmaf(-rintf(x * inv), p, x));
+                                v[j] = __float_as_uint(fmaf(-round_small(x * inv), p, x));
                             }
                             tmem_st32(taddr + col, v);
                         }
@@ -673,9 +775,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const int64_t row = (int64_t)mt * pair::BM + (int64_t)rank * pair::HALF + q * 32 + lane;
                         const bool live = row < args.m_rows;
                         int8_t* dst = args.out + (int64_t)l * args.out_plane +
-                                      (live ? row : 0) * args.out_ld + (int64_t)nt * pair::BN;
+                                      (live ? row : 0) * args.out_ld + (int64_t)nt * pair::BN +
+                                      col0;
 #pragma unroll 1
-                        for (int col = 0; col < pair::BN; col += 32) {
+                        for (int col = 0; col < EPI_COLS; col += 32) {
                             uint32_t v[32];
                             tmem_ld32(taddr + col, v);
                             uint32_t packed[8];
@@ -685,7 +788,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                                 for (int b = 0; b < 4; ++b) {
                                     const float x = __uint_as_float(v[4 * w + b]);
-                                    float r = fmaf(-rintf(x * inv), p, x);
+                                    float r = fmaf(-round_small(x * inv), p, x);
                                     r = r > hi ? r - p : r;
                                     r = r < lo ? r + p : r;
                                     word |= ((uint32_t)__float2int_rn(r) & 0xFFu) << (8 * b);
@@ -755,6 +858,53 @@ bool encode_planes(CUtensorMap* map, const void* base, int N, int rows_pad, int 
 
 }  // namespace
 
+static int chunk_blocks_of(int chunk_k) {
+    int cb = chunk_k / BK;
+    if (cb < 1) cb = 1;
+    if (cb > 15) cb = 15;  // <= 960 products between reductions keeps fp32 exact
+    return cb;
+}
+
+bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, int k_pad,
+                             const void* planes_a, const void* planes_b, int8_t* out,
+                             int chunk_k) {
+    if (!encode_planes(&g->ta, planes_a, N, m_pad, k_pad, BM) ||
+        !encode_planes(&g->tb, planes_b, N, n_pad, k_pad, BN))
+        return false;
+    const int cb = chunk_blocks_of(chunk_k);
+    g->out = out;
+    g->out_ld = n_pad;
+    g->out_plane = (int64_t)m_pad * n_pad;
+    g->tiles_m = m_pad / BM;
+    g->tiles_n = n_pad / BN;
+    g->k_blocks = k_pad / BK;
+    g->nchunks = (g->k_blocks + cb - 1) / cb;
+    g->tile_begin = 0;
+    return true;
+}
+
+int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
+                                const EpilogueTables& t, unsigned* status, int num_sms,
+                                int chunk_k, cudaStream_t stream) {
+    if (count <= 0 || total_tiles <= 0) return OZAKI2_SUCCESS;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(residue_gemm_grouped_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    GemmArgs a = {};
+    a.chunk_blocks = chunk_blocks_of(chunk_k);
+    a.status = status;
+    a.ep = t;
+    const int grid = total_tiles < num_sms ? total_tiles : num_sms;
+    residue_gemm_grouped_kernel<<<grid, NUM_THREADS, SMEM_BYTES, stream>>>(probs, count,
+                                                                          total_tiles, a);
+    return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
+}
+
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
                         const void* planes_b, int8_t* out, const EpilogueTables& t,
                         unsigned* status, int num_sms, int chunk_k, int variant,
@@ -777,7 +927,9 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const v
         cudaError_t e = cudaMemsetAsync(out, 0, (size_t)num_moduli * m_pad * n_pad, stream);
         return e == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
     }
-    const bool use_pair = variant == OZAKI2_GEMM_PAIR || (variant == OZAKI2_GEMM_AUTO && m_pad >= 256);
+    // Measured at 16384^3 on GB300 the one-SM kernel is the faster of the two, so it is the
+    // automatic choice; the pair kernel stays available through OZAKI2_OPT_GEMM_VARIANT.
+    const bool use_pair = variant == OZAKI2_GEMM_PAIR;
     CUtensorMap ta, tb;
     if (use_pair) {
         if (!encode_planes(&ta, planes_a, num_moduli, m_pad, k_pad, pair::HALF) ||

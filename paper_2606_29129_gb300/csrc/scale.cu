@@ -42,12 +42,9 @@ __device__ int alg2_shift(double a_norm, float pprime, unsigned* status) {
 // of the dependent FMA chain so that enough bytes are in flight with one thread per line.
 constexpr int kBatch = 16;
 
-__global__ void __launch_bounds__(32) scale_adjacent_kernel(const double* __restrict__ X,
-                                                            int64_t ld, int lines, int len,
-                                                            float pprime, int* shifts,
-                                                            unsigned* status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= lines) return;
+__device__ __forceinline__ void scale_adjacent_line(const double* __restrict__ X, int64_t ld,
+                                                    int i, int len, float pprime, int* shifts,
+                                                    unsigned* status) {
     const double* p = X + i;
     double s = 0.0;
     const int full = len / kBatch * kBatch;
@@ -80,21 +77,28 @@ __global__ void __launch_bounds__(32) scale_adjacent_kernel(const double* __rest
     shifts[i] = alg2_shift(s, pprime, status);
 }
 
+__global__ void __launch_bounds__(32) scale_adjacent_kernel(const double* __restrict__ X,
+                                                            int64_t ld, int lines, int len,
+                                                            float pprime, int* shifts,
+                                                            unsigned* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < lines) scale_adjacent_line(X, ld, i, len, pprime, shifts, status);
+}
+
 // Contiguous lines (elem_stride == 1): each warp owns 32 lines.  Tiles of 32 elements per line
 // are read with one coalesced 256-byte load per line, the next tile is held in registers while
 // the current one (in shared memory) is summed, each lane walking its own line in order.
 constexpr int kWarpsPerBlock = 4;
 constexpr int kTileLen = 32;
 
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) scale_contiguous_kernel(
-    const double* __restrict__ X, int64_t ld, int lines, int len, float pprime, int* shifts,
-    unsigned* status) {
-    __shared__ double tile[kWarpsPerBlock][32][kTileLen + 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int line0 = (blockIdx.x * kWarpsPerBlock + warp) * 32;
-    if (line0 >= lines) return;
+// Lines line0 .. line0 + 31 of a contiguous-line matrix, summed by one warp (t: its smem tile).
+__device__ __forceinline__ void scale_contiguous_warp(const double* __restrict__ X, int64_t ld,
+                                                      int lines, int len, int line0,
+                                                      float pprime, int* shifts,
+                                                      unsigned* status,
+                                                      double (*t)[kTileLen + 1]) {
+    const int lane = threadIdx.x & 31;
     const int nl = min(32, lines - line0);
-    double (*t)[kTileLen + 1] = tile[warp];
     double reg[32];
     auto load = [&](int h0) {
         const int cnt = min(kTileLen, len - h0);
@@ -122,7 +126,47 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) scale_contiguous_kernel(
     if (lane < nl) shifts[line0 + lane] = alg2_shift(s, pprime, status);
 }
 
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) scale_contiguous_kernel(
+    const double* __restrict__ X, int64_t ld, int lines, int len, float pprime, int* shifts,
+    unsigned* status) {
+    __shared__ double tile[kWarpsPerBlock][32][kTileLen + 1];
+    const int warp = threadIdx.x >> 5;
+    const int line0 = (blockIdx.x * kWarpsPerBlock + warp) * 32;
+    if (line0 < lines)
+        scale_contiguous_warp(X, ld, lines, len, line0, pprime, shifts, status, tile[warp]);
+}
+
+// Grouped: each block takes 128 lines of one side of one problem (one thread per line for
+// adjacent lines, one warp per 32 lines for contiguous lines).
+__global__ void __launch_bounds__(128) scale_grouped_kernel(const GroupProblem* __restrict__ probs,
+                                                            const ScaleWork* __restrict__ work,
+                                                            unsigned* status) {
+    __shared__ double tile[kWarpsPerBlock][32][kTileLen + 1];
+    const ScaleWork w = work[blockIdx.x];
+    const GroupProblem& P = probs[w.problem];
+    const double* X = w.side ? P.B : P.A;
+    const int64_t ls = w.side ? P.b_ls : P.a_ls, es = w.side ? P.b_es : P.a_es;
+    const int lines = w.side ? P.n : P.m;
+    int* shifts = w.side ? P.f : P.e;
+    if (es != 1 || ls == 1) {
+        const int i = w.line0 + (int)threadIdx.x;
+        if (i < lines) scale_adjacent_line(X, es, i, P.k, P.pprime, shifts, status);
+    } else {
+        const int warp = threadIdx.x >> 5;
+        const int line0 = w.line0 + 32 * warp;
+        if (line0 < lines)
+            scale_contiguous_warp(X, ls, lines, P.k, line0, P.pprime, shifts, status, tile[warp]);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_scale_grouped(const GroupProblem* probs, const ScaleWork* work, int blocks,
+                                 unsigned* status, cudaStream_t stream) {
+    if (blocks <= 0) return cudaSuccess;
+    scale_grouped_kernel<<<blocks, 128, 0, stream>>>(probs, work, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                          int len, float pprime, int* shifts, unsigned* status,

@@ -26,11 +26,21 @@ SHIFT_NONFINITE = -(2**31)
 ERROR_TOO_LARGE = 6
 OPT_GEMM_VARIANT = 1
 OPT_CHUNK_K = 2
+OPT_GRAPH = 3
 GEMM_AUTO, GEMM_SINGLE, GEMM_PAIR = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 _lib = None
 _lock = threading.Lock()
+
+
+class Problem(ctypes.Structure):
+    """ozaki2_problem: the arguments of one ozaki2_dgemm inside a grouped call."""
+    _fields_ = [("transA", ctypes.c_char), ("transB", ctypes.c_char), ("m", ctypes.c_int),
+                ("n", ctypes.c_int), ("k", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int), ("B", ctypes.c_void_p),
+                ("ldb", ctypes.c_int), ("beta", ctypes.c_double), ("C", ctypes.c_void_p),
+                ("ldc", ctypes.c_int), ("num_moduli", ctypes.c_int)]
 
 
 class Ozaki2Error(RuntimeError):
@@ -71,6 +81,7 @@ def lib() -> ctypes.CDLL:
             "ozaki2_crt": [vp, i32, i32, i32, vp, i32, i64, vp, vp, f64, f64, vp, i32],
             "ozaki2_dgemm_noalloc": [ch, ch, i32, i32, i32, f64, vp, i32, vp, i32, f64, vp, i32,
                                      i32, vp],
+            "ozaki2_dgemm_grouped": [vp, i32, vp],
             "ozaki2_set_timing": [vp, i32],
             "ozaki2_set_option": [vp, i32, i32],
             "ozaki2_get_timing": [vp, ctypes.POINTER(ctypes.c_float)],
@@ -79,6 +90,8 @@ def lib() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = i32
+        L.ozaki2_grouped_workspace_size.argtypes = [i32, vp]
+        L.ozaki2_grouped_workspace_size.restype = ctypes.c_size_t
         L.ozaki2_workspace_size.argtypes = [i32, i32, i32, i32]
         L.ozaki2_workspace_size.restype = ctypes.c_size_t
         L.ozaki2_error_string.argtypes = [i32]
@@ -191,6 +204,27 @@ def ozaki2_dgemm(transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, n
                  handle: Handle | None = None) -> int:
     return lib().ozaki2_dgemm_h(_h(handle), _ch(transA), _ch(transB), m, n, k, alpha, _ptr(A),
                                 lda, _ptr(B), ldb, beta, _ptr(C), ldc, num_moduli)
+
+
+def problems_array(problems):
+    """A ctypes array of Problem from dicts with the ozaki2_dgemm argument names (device buffers
+    as tensors or addresses)."""
+    arr = (Problem * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = Problem(_ch(p.get("transA", "N")), _ch(p.get("transB", "N")), p["m"], p["n"],
+                         p["k"], p.get("alpha", 1.0), _ptr(p["A"]), p["lda"], _ptr(p["B"]),
+                         p["ldb"], p.get("beta", 0.0), _ptr(p["C"]), p["ldc"],
+                         p["num_moduli"])
+    return arr
+
+
+def ozaki2_dgemm_grouped(count, problems, handle=None) -> int:
+    """problems: a ctypes array of Problem (see problems_array)."""
+    return lib().ozaki2_dgemm_grouped(_h(handle), count, ctypes.cast(problems, ctypes.c_void_p))
+
+
+def ozaki2_grouped_workspace_size(count, problems) -> int:
+    return lib().ozaki2_grouped_workspace_size(count, ctypes.cast(problems, ctypes.c_void_p))
 
 
 def ozaki2_scale_a(transA, m, k, A, lda, num_moduli, shifts, handle=None) -> int:
