@@ -339,41 +339,285 @@ def accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np):
 
 
 def measure_e2e(args, oz, h, A, B, m, n, k, N, torch):
-    """The same metric through ozaki2_dgemm with host buffers: pinned H2D of A and B, the call,
-    D2H of C, all inside the timed region."""
+    """The same metric through ozaki2_dgemm with host buffers: every step uploads its A and B
+    from pinned host memory and downloads its C, all inside the timed region.  Steps are
+    pipelined the way a caller would: two sets of device buffers, uploads on one stream,
+    ozaki2_dgemm on the handle's stream, downloads on a third, ordered by events, so the copies
+    of one step overlap the computation of its neighbours."""
     A_h = torch.empty(A.shape, dtype=torch.float64, pin_memory=True)
     B_h = torch.empty(B.shape, dtype=torch.float64, pin_memory=True)
-    C_h = torch.empty((n, m), dtype=torch.float64, pin_memory=True)
+    C_h = [torch.empty((n, m), dtype=torch.float64, pin_memory=True) for _ in range(2)]
     A_h.copy_(A)
     B_h.copy_(B)
-    dA = torch.empty_like(A)
-    dB = torch.empty_like(B)
-    dC = torch.empty((n, m), dtype=torch.float64, device=A.device)
+    dev = A.device
+    dA = [torch.empty_like(A) for _ in range(2)]
+    dB = [torch.empty_like(B) for _ in range(2)]
+    dC = [torch.empty((n, m), dtype=torch.float64, device=dev) for _ in range(2)]
+    s_up = torch.cuda.Stream(device=dev)
+    s_comp = torch.cuda.Stream(device=dev)
+    s_down = torch.cuda.Stream(device=dev)
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    uploaded = [ev(), ev()]
+    computed = [ev(), ev()]
+    downloaded = [ev(), ev()]
+    consumed = [ev(), ev()]   # inputs of buffer set b no longer needed
+    for b in range(2):
+        downloaded[b].record(s_down)
+        consumed[b].record(s_comp)
     h.set_timing(False)
 
-    def step():
-        dA.copy_(A_h, non_blocking=True)
-        dB.copy_(B_h, non_blocking=True)
-        rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, dC, m, N, h)
-        if rc:
-            raise oz.Ozaki2Error("ozaki2_dgemm", rc)
-        C_h.copy_(dC, non_blocking=True)
+    def step(i):
+        b = i % 2
+        with torch.cuda.stream(s_up):
+            s_up.wait_event(consumed[b])
+            dA[b].copy_(A_h, non_blocking=True)
+            dB[b].copy_(B_h, non_blocking=True)
+            uploaded[b].record(s_up)
+        with torch.cuda.stream(s_comp):
+            s_comp.wait_event(uploaded[b])
+            s_comp.wait_event(downloaded[b])
+            rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, dA[b], m, dB[b], k, 0.0, dC[b], m, N,
+                                 h)
+            if rc:
+                raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+            consumed[b].record(s_comp)
+            computed[b].record(s_comp)
+        with torch.cuda.stream(s_down):
+            s_down.wait_event(computed[b])
+            C_h[b].copy_(dC[b], non_blocking=True)
+            downloaded[b].record(s_down)
 
-    step()
+    step(0)
+    step(1)
     torch.cuda.synchronize()
-    reps = max(1, min(args.steps, 3))
-    s = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(reps):
-        step()
-    e.record()
+    reps = max(2, min(args.steps, 6))
+    t0 = time.perf_counter()
+    for i in range(reps):
+        step(i)
     torch.cuda.synchronize()
-    ms = s.elapsed_time(e) / reps
+    ms = (time.perf_counter() - t0) * 1e3 / reps
     h.set_timing(True)
     return {"value": 2.0 * m * n * k / (ms * 1e-3) / 1e12, "unit": "TFLOPS",
             "h2d_bytes_per_step": A.numel() * 8 + B.numel() * 8,
-            "d2h_bytes_per_step": m * n * 8, "ms_per_step": ms}
+            "d2h_bytes_per_step": m * n * 8, "ms_per_step": ms, "steps": reps,
+            "pipelining": "double-buffered: uploads, compute and downloads on three streams",
+            "clock": "host wall clock around the steps, synchronised on both sides"}
+
+
+def batched_problems(count, seed, lo=64, hi=2048, device="cuda"):
+    """The batched workload: `count` problems with m, n, k each log-uniform in [lo, hi], phi in
+    {0.5, 1} alternating, seeded per item; column-major device inputs."""
+    import numpy as np
+
+    import synthetic
+
+    rng = np.random.default_rng(seed)
+    items = []
+    for i in range(count):
+        m, n, k = (int(np.exp(rng.uniform(np.log(lo), np.log(hi + 1)))) for _ in range(3))
+        phi = (0.5, 1.0)[i % 2]
+        A = synthetic.paper_matrix_torch(m, k, phi, 100000 + 2 * i, device=device)
+        B = synthetic.paper_matrix_torch(k, n, phi, 100001 + 2 * i, device=device)
+        items.append(dict(m=m, n=n, k=k, phi=phi, A=A, B=B))
+    return items
+
+
+def run_batched(args):
+    """512 emulated DGEMMs in one grouped call replayed from a CUDA graph, N per item from the
+    accuracy autotuner (smallest N not worse than cuBLAS DGEMM for the item's size class),
+    against a per-request cuBLAS DGEMM loop on the same inputs."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2606_29129_gb300 import autotune
+    from paper_2606_29129_gb300 import ozaki2 as oz
+
+    oracle.build()
+    items = batched_problems(args.batch, seed=4)
+    t0 = time.perf_counter()
+    table = autotune.calibrate(ks=(64, 128, 256, 512, 1024, 2048))
+    calib_s = time.perf_counter() - t0
+    for it in items:
+        it["N"] = autotune.choose_n(table, it["k"])
+        it["C"] = torch.empty((it["n"], it["m"]), dtype=torch.float64, device="cuda")
+    flops = sum(2.0 * it["m"] * it["n"] * it["k"] for it in items)
+    probs = oz.problems_array([dict(m=it["m"], n=it["n"], k=it["k"], A=it["A"], lda=it["m"],
+                                    B=it["B"], ldb=it["k"], C=it["C"], ldc=it["m"],
+                                    num_moduli=it["N"]) for it in items])
+    h = oz.Handle()
+    h.set_option(oz.OPT_GRAPH, 1)
+
+    def grouped():
+        rc = oz.ozaki2_dgemm_grouped(len(items), probs, h)
+        if rc:
+            raise oz.Ozaki2Error("ozaki2_dgemm_grouped", rc)
+
+    def ev_loop(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / reps
+
+    t_grouped = ev_loop(grouped, args.steps)
+    status = h.status()
+    # per-request loops on the same inputs
+    h2 = oz.Handle()
+
+    def per_request_ozaki():
+        for it in items:
+            rc = oz.ozaki2_dgemm("N", "N", it["m"], it["n"], it["k"], 1.0, it["A"], it["m"],
+                                 it["B"], it["k"], 0.0, it["C"], it["m"], it["N"], h2)
+            if rc:
+                raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+
+    def per_request_cublas():
+        for it in items:
+            torch.matmul(it["B"].view(it["n"], it["k"]), it["A"].view(it["k"], it["m"]),
+                         out=it["Cd"])
+
+    for it in items:
+        it["Cd"] = torch.empty((it["n"], it["m"]), dtype=torch.float64, device="cuda")
+    t_loop = ev_loop(per_request_ozaki, max(1, args.steps // 2))
+    torch.backends.cuda.matmul.allow_tf32 = False
+    t_cublas = ev_loop(per_request_cublas, 1)
+    # accuracy: every item against the double-double reference on a sampled block
+    grouped()
+    torch.cuda.synchronize()
+    per_request_cublas()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    worst, worst_cub, worse_than_cublas = 0.0, 0.0, 0
+    for it in items[: args.err_items]:
+        A_h, B_h = it["A"].cpu().numpy(), it["B"].cpu().numpy()
+        I = np.sort(rng.choice(it["m"], size=min(32, it["m"]), replace=False)).astype(np.int32)
+        J = np.sort(rng.choice(it["n"], size=min(32, it["n"]), replace=False)).astype(np.int32)
+        hi, lo = oracle.dd_block(A_h, B_h, it["k"], I, J)
+        e1 = oracle.max_rel_error(it["C"].cpu().numpy()[np.ix_(J, I)], hi, lo)[0]
+        e2 = oracle.max_rel_error(it["Cd"].cpu().numpy()[np.ix_(J, I)], hi, lo)[0]
+        worst, worst_cub = max(worst, e1), max(worst_cub, e2)
+        worse_than_cublas += e1 > e2
+    line = {
+        "mode": "batched", "metric": "batched Ozaki-II DGEMM effective TFLOPS (sum 2mnk / time)",
+        "value": flops / (t_grouped * 1e-3) / 1e12, "unit": "TFLOPS", "n_gpus": 1,
+        "ms_per_batch": t_grouped, "steps": args.steps, "warmup": args.warmup,
+        "config": {"workload": f"{len(items)} problems, m, n, k log-uniform in [64, 2048], "
+                               "phi in {0.5, 1} alternating", "launch": "ozaki2_dgemm_grouped "
+                               "replayed from a CUDA graph", "n_per_item": "autotuned per "
+                               "size class to the accuracy of cuBLAS DGEMM"},
+        "moduli_histogram": {str(N): sum(1 for it in items if it["N"] == N)
+                             for N in sorted({it["N"] for it in items})},
+        "per_request_ozaki2_ms": t_loop, "per_request_cublas_dgemm_ms": t_cublas,
+        "speedup_vs_cublas_loop": t_cublas / t_grouped,
+        "speedup_vs_per_request_ozaki2": t_loop / t_grouped,
+        "accuracy": {"items_checked": min(args.err_items, len(items)),
+                     "max_rel_err": worst, "cublas_max_rel_err": worst_cub,
+                     "items_worse_than_cublas": int(worse_than_cublas),
+                     "sample": "32x32 random block per item vs double-double"},
+        "calibration": {"seconds": calib_s, "table": autotune.table_to_json(table)},
+        "device_status": status,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Serving: a Poisson stream of requests (sizes log-uniform in [64, serve_max], relative-error
+    targets 1e-10 / 1e-13 / 1e-15 in turn, N from the calibration table) through the
+    continuous-batching server; p50/p99 latency and throughput, beside a per-request cuBLAS
+    DGEMM loop over the same stream."""
+    import numpy as np
+    import torch
+
+    import synthetic
+    from paper_2606_29129_gb300 import autotune
+    from paper_2606_29129_gb300.serve import GpuExecutor, Request, Server
+
+    rng = np.random.default_rng(args.serve_seed)
+    pool = []
+    for i in range(args.serve_pool):
+        m, n, k = (int(np.exp(rng.uniform(np.log(64), np.log(args.serve_max + 1))))
+                   for _ in range(3))
+        phi = (0.5, 1.0)[i % 2]
+        A = synthetic.paper_matrix_torch(m, k, phi, 300000 + 2 * i).cpu().pin_memory()
+        B = synthetic.paper_matrix_torch(k, n, phi, 300001 + 2 * i).cpu().pin_memory()
+        pool.append((m, n, k, A, B))
+    targets = (1e-10, 1e-13, 1e-15)
+    t0 = time.perf_counter()
+    table = autotune.calibrate(ks=tuple(e for e in autotune.CLASS_EDGES if e <= args.serve_max))
+    calib_s = time.perf_counter() - t0
+    slot_ws = args.serve_slot_ws_gb << 30
+    budget = args.serve_budget_gb << 30
+    ex = GpuExecutor(slots=args.serve_slots, slot_workspace_bytes=slot_ws)
+    srv = Server(ex, io_budget_bytes=budget - args.serve_slots * slot_ws, max_batch=64,
+                 calibration=table)
+    # arrival times of a Poisson process of rate lam over the stream
+    lam = args.serve_rate
+    count = args.serve_requests
+    gaps = rng.exponential(1.0 / lam, size=count)
+    arrivals = np.cumsum(gaps)
+    picks = rng.integers(0, len(pool), size=count)
+    reqs = []
+    start = time.perf_counter()
+    i = 0
+    while i < count or not srv.idle():
+        now = time.perf_counter() - start
+        while i < count and arrivals[i] <= now:
+            m, n, k, A, B = pool[picks[i]]
+            r = Request(rid=i, m=m, n=n, k=k, target=targets[i % 3], A=A, B=B,
+                        arrival=start + arrivals[i])
+            srv.submit(r)
+            reqs.append(r)
+            i += 1
+        srv.step()
+    makespan = time.perf_counter() - start
+    lat = sorted(r.latency for r in reqs if r.error is None)
+    ok = [r for r in reqs if r.error is None]
+    flops = sum(2.0 * r.m * r.n * r.k for r in ok)
+    # per-request cuBLAS DGEMM loop over the same stream (device-resident inputs, as the
+    # cuBLAS baseline is given every advantage)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    dev_pool = [(A.cuda(), B.cuda()) for (_, _, _, A, B) in pool]
+    cub_ms = []
+    for (m, n, k, _, _), (dA, dB) in zip(pool, dev_pool):
+        out = torch.empty((n, m), dtype=torch.float64, device="cuda")
+        torch.matmul(dB.view(n, k), dA.view(k, m), out=out)
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        torch.matmul(dB.view(n, k), dA.view(k, m), out=out)
+        e.record()
+        torch.cuda.synchronize()
+        cub_ms.append(s.elapsed_time(e))
+    cub_total = sum(cub_ms[picks[r.rid]] for r in ok) / 1e3
+    line = {
+        "mode": "serving", "metric": "served emulated DGEMM p50/p99 latency and throughput",
+        "requests": len(reqs), "completed": len(ok), "rate_per_s": lam,
+        "makespan_s": makespan, "throughput_req_per_s": len(ok) / makespan,
+        "effective_tflops": flops / makespan / 1e12,
+        "latency_ms": {"p50": 1e3 * lat[len(lat) // 2],
+                       "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "max": 1e3 * lat[-1]},
+        "moduli_histogram": {str(N): sum(1 for r in ok if r.num_moduli == N)
+                             for N in sorted({r.num_moduli for r in ok})},
+        "peak_io_gb": srv.peak_io / 2**30, "budget_gb": args.serve_budget_gb,
+        "cublas_dgemm_loop_s": cub_total,
+        "cublas_loop_tflops": flops / cub_total / 1e12,
+        "speedup_vs_cublas_loop": cub_total / makespan,
+        "config": {"sizes": f"m, n, k log-uniform in [64, {args.serve_max}]",
+                   "targets": list(targets), "slots": args.serve_slots,
+                   "slot_workspace_gb": args.serve_slot_ws_gb, "pool": len(pool),
+                   "arrivals": "Poisson"},
+        "calibration_s": calib_s,
+    }
+    print(json.dumps(line), flush=True)
 
 
 def run_sweep(args):
@@ -438,12 +682,32 @@ def main():
     ap.add_argument("--gemm-traffic", type=float, default=None,
                     help="DRAM bytes per residue-GEMM launch from an ncu capture, if current")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="the batched workload (grouped call) instead of the benchmark")
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--err-items", type=int, default=64)
+    ap.add_argument("--serve", action="store_true",
+                    help="the serving workload (Poisson stream) instead of the benchmark")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-max", type=int, default=8192)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-slots", type=int, default=2)
+    ap.add_argument("--serve-slot-ws-gb", type=int, default=20)
+    ap.add_argument("--serve-budget-gb", type=int, default=120)
+    ap.add_argument("--serve-seed", type=int, default=5)
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy sweep over N, phi and alpha instead of the benchmark")
     ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[8192, 16384])
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)
+        return
+    if args.batched:
+        run_batched(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
