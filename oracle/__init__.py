@@ -62,6 +62,13 @@ def lib():
         L.orc_dgemm_block.argtypes = [ch, ch, i32, i32, i32, f64, P, i64, P, i64, f64, P,
                                       i32, i32, P, i32, P, P, P, P]
         L.orc_dd_block.argtypes = [ch, ch, i32, P, i64, P, i64, i32, P, i32, P, P, P]
+        L.orc_fast_delta.restype = f32
+        L.orc_alg1_shift.argtypes = [f64, f64, f32]
+        L.orc_alg1_shift.restype = i32
+        L.orc_shifts_mode.argtypes = [i32, ch, i32, i32, P, i64, i32, i32, P]
+        L.orc_dgemm_mode.argtypes = [ch, ch, i32, i32, i32, f64, P, i64, P, i64, f64, P, i64,
+                                     i32, i32]
+        L.orc_pprime_fast.argtypes = [i32, P]
         _lib = L
     return _lib
 
@@ -203,6 +210,45 @@ def int_residues(values, N: int) -> np.ndarray:
     out = np.zeros((len(values), N), np.int32)
     _ck(lib().orc_words_residues(len(values), _p(w), N, _p(out)))
     return out
+
+
+# ---------------------------------------------------------------- original fast mode
+FAST_MODE = 1      # Algorithm 1 (Section 2.3)
+PROPOSED_MODE = 0  # Algorithm 2 (Section 4)
+
+
+def fast_delta() -> float:
+    return lib().orc_fast_delta()
+
+
+def pprime_fast(N: int) -> float:
+    f = ctypes.c_float()
+    _ck(lib().orc_pprime_fast(N, ctypes.byref(f)))
+    return f.value
+
+
+def alg1_shift(a_norm: float, a_max: float, pprime_f: float) -> int:
+    return lib().orc_alg1_shift(float(a_norm), float(a_max), float(pprime_f))
+
+
+def shifts_mode(X, lines, length, N, mode, side=0, trans="N", ld=None):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    ld = ld if ld is not None else X.shape[-1]
+    out = np.zeros(lines, np.int32)
+    _ck(lib().orc_shifts_mode(side, _b(trans), lines, length, _p(X), ld, N, mode, _p(out)))
+    return out
+
+
+def dgemm_mode(A, B, m, n, k, N, mode, transA="N", transB="N", alpha=1.0, beta=0.0, Cin=None,
+               lda=None, ldb=None) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    lda = lda if lda is not None else A.shape[-1]
+    ldb = ldb if ldb is not None else B.shape[-1]
+    C = np.zeros((n, m), np.float64) if Cin is None else np.array(Cin, dtype=np.float64, copy=True)
+    _ck(lib().orc_dgemm_mode(_b(transA), _b(transB), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta,
+                             _p(C), max(m, 1), N, mode))
+    return C
 
 
 # ---------------------------------------------------------------- whole emulated DGEMM

@@ -271,6 +271,7 @@ typedef struct {
     i256 P;                    /* product of the moduli */
     i256 Pq[ORC_MAX_MODULI];   /* P_i * q_i */
     float pprime;              /* P'_prop */
+    float pprime_fast;         /* P'_fast (original fast mode) */
 } orc_consts;
 
 static int mod_inverse(int a, int m) { /* extended Euclid; a and m coprime */
@@ -310,6 +311,8 @@ static int make_consts(int N, orc_consts* c) {
     /* P'_prop := single-down(log2(P - 1)/2 - 0.5), Section 4 (eq. P-prime-proposed). */
     double lg = u256_log2(i256_sub(c->P, i256_from_u64(1)));
     c->pprime = rd_float(lg / 2.0 - 0.5);
+    /* P'_fast := single-down(log2(P - 1)/2 - 1.5), Section 2.3 (original fast mode). */
+    c->pprime_fast = rd_float(lg / 2.0 - 1.5);
     return 0;
 }
 
@@ -354,6 +357,42 @@ int orc_alg2_shift(double a_norm, float pprime) {
     float t = ru_float(0.5 * (double)lg + 0x1p-23); /* 2u_32 = 2^-23; the sum is exact */
     float w = rd_float((double)pprime - 0.5 * (double)s);
     return (int)floor(sub_rd((double)w, (double)t));
+}
+
+static double mul_ru(double a, double b) { /* a * b rounded toward +inf */
+    int old = fegetround();
+    fesetround(FE_UPWARD);
+    volatile double r = a * b;
+    fesetround(old);
+    return r;
+}
+
+/* delta := single-up(0.5 / (1 - 4u_32)), eq. (delta), Section 2.3. */
+float orc_fast_delta(void) {
+    int old = fegetround();
+    fesetround(FE_UPWARD);
+    volatile double den = 1.0 - 4.0 * 0x1p-24;   /* exact */
+    volatile double q = 0.5 / den;
+    fesetround(old);
+    return ru_float(q);
+}
+
+/* Algorithm 1 (original fast mode), log2(mu_i) from a_norm and a_max:
+ *   s := floor(log2 a_norm)
+ *   t := single-up(delta * (log2f(a_norm / 2^s) + s))
+ *   return floor(P'_fast - max(1, t)) - floor(log2 a_max)
+ * with the same log2 stand-in and readings as Algorithm 2 (argument rounded up to single,
+ * floors taken exactly).  A zero line gets shift 0; a non-finite a_norm is flagged. */
+int orc_alg1_shift(double a_norm, double a_max, float pprime_fast) {
+    if (a_norm == 0.0 || a_max == 0.0) return 0;
+    if (!isfinite(a_norm) || !isfinite(a_max)) return ORC_SHIFT_NONFINITE;
+    int s = ilogb(a_norm);
+    double xprime = scalbn(a_norm, -s);
+    float lg = orc_log2_ru(ru_float(xprime));
+    float delta = orc_fast_delta();
+    float t = ru_float(mul_ru((double)delta, (double)lg + (double)s)); /* lg + s is exact */
+    double mx = t > 1.0f ? (double)t : 1.0;
+    return (int)floor(sub_rd((double)pprime_fast, mx)) - ilogb(a_max);
 }
 
 /* Line accessors.  Matrices are column-major (BLAS).  Row i of op(A) and column j of op(B). */
@@ -427,6 +466,73 @@ int orc_constants(int N, int* p, int* q, float* pprime, uint64_t* P_words, uint6
     }
     for (int w = 0; w < 4; ++w) P_words[w] = c.P.w[w];
     *pprime = c.pprime;
+    return 0;
+}
+
+static double line_max_abs(const double* x, int64_t stride, int64_t len) {
+    double mx = 0.0;
+    for (int64_t h = 0; h < len; ++h) {
+        double a = fabs(x[h * stride]);
+        if (!(a <= mx)) mx = a;   /* NaN propagates */
+    }
+    return mx;
+}
+
+/* Shifts of the rows of op(A) (side 0) or the columns of op(B) (side 1) under a scaling mode:
+ * mode 0 = the proposed scaling (Algorithm 2), mode 1 = the original fast mode (Algorithm 1). */
+int orc_shifts_mode(int side, char trans, int lines, int len, const double* X, int64_t ld, int N,
+                    int mode, int* shifts) {
+    orc_consts c;
+    if (make_consts(N, &c)) return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < lines; ++i) {
+        const double* base; int64_t st;
+        if (side == 0) row_of_opA(trans, X, ld, i, &base, &st);
+        else col_of_opB(trans, X, ld, i, &base, &st);
+        double nr = line_norm_ru(base, st, len);
+        shifts[i] = mode == 1 ? orc_alg1_shift(nr, line_max_abs(base, st, len), c.pprime_fast)
+                              : orc_alg2_shift(nr, c.pprime);
+    }
+    return 0;
+}
+
+int orc_residues_a(char transA, int m, int k, const double* A, int64_t lda, const int* e, int N,
+                   int8_t* R);
+int orc_residues_b(char transB, int k, int n, const double* B, int64_t ldb, const int* f, int N,
+                   int8_t* R);
+int orc_residue_products(int N, int m, int n, int k, const int8_t* RA, const int8_t* RB,
+                         int8_t* cout);
+int orc_crt(int N, int m, int n, const int8_t* cres, const int* e, const int* f, double alpha,
+            double beta, double* C, int64_t ldc);
+
+/* The whole emulated DGEMM under a scaling mode (0 proposed, 1 original fast mode). */
+int orc_dgemm_mode(char transA, char transB, int m, int n, int k, double alpha, const double* A,
+                   int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                   int64_t ldc, int N, int mode) {
+    if (N < 2 || N > ORC_MAX_MODULI || m < 0 || n < 0 || k < 0) return -1;
+    if (m == 0 || n == 0) return 0;
+    int* e = (int*)malloc(sizeof(int) * (size_t)m);
+    int* f = (int*)malloc(sizeof(int) * (size_t)n);
+    int8_t* RA = (int8_t*)malloc((size_t)N * m * (k ? k : 1));
+    int8_t* RB = (int8_t*)malloc((size_t)N * n * (k ? k : 1));
+    int8_t* cr = (int8_t*)malloc((size_t)N * m * n);
+    int rc = -2;
+    if (e && f && RA && RB && cr) {
+        orc_shifts_mode(0, transA, m, k, A, lda, N, mode, e);
+        orc_shifts_mode(1, transB, n, k, B, ldb, N, mode, f);
+        orc_residues_a(transA, m, k, A, lda, e, N, RA);
+        orc_residues_b(transB, k, n, B, ldb, f, N, RB);
+        orc_residue_products(N, m, n, k, RA, RB, cr);
+        rc = orc_crt(N, m, n, cr, e, f, alpha, beta, C, ldc);
+    }
+    free(e); free(f); free(RA); free(RB); free(cr);
+    return rc;
+}
+
+int orc_pprime_fast(int N, float* out) {
+    orc_consts c;
+    if (make_consts(N, &c)) return -1;
+    *out = c.pprime_fast;
     return 0;
 }
 
