@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -560,8 +561,9 @@ def run_serve(args):
     # arrival times of a Poisson process of rate lam over the stream
     lam = args.serve_rate
     count = args.serve_requests
-    gaps = rng.exponential(1.0 / lam, size=count)
-    arrivals = np.cumsum(gaps)
+    # rate 0: every request arrives at once (the server's capacity, not the arrival rate, sets
+    # the makespan)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=count)) if lam > 0 else np.zeros(count)
     picks = rng.integers(0, len(pool), size=count)
     reqs = []
     start = time.perf_counter()
@@ -614,7 +616,7 @@ def run_serve(args):
         "config": {"sizes": f"m, n, k log-uniform in [64, {args.serve_max}]",
                    "targets": list(targets), "slots": args.serve_slots,
                    "slot_workspace_gb": args.serve_slot_ws_gb, "pool": len(pool),
-                   "arrivals": "Poisson"},
+                   "arrivals": "Poisson" if lam > 0 else "all at t = 0"},
         "calibration_s": calib_s,
     }
     print(json.dumps(line), flush=True)
@@ -667,6 +669,110 @@ def run_sweep(args):
             torch.cuda.empty_cache()
 
 
+def run_scaling_study(args):
+    """Figs. 1-3 on the GPU: the original fast mode (Algorithm 1) against the proposed scaling
+    (Algorithm 2), both at N = 20, for A = 2^s A^, B = 2^s B^, s = -10..10.
+
+    Random inputs (eq. random-matrix-generation, phi in {0.5, 1, 2}): per s, the max relative
+    error of each mode against double-double on a sampled block (the block's reference is taken
+    once at s = 0 and scaled by 4^s, exact for powers of two), and the fast mode's max relative
+    difference over the FULL matrix from the proposed N = 20 result (which resolves every error
+    above ~2e-16 and so finds the isolated entries where CRT recovery fails).  cuBLAS DGEMM is
+    measured at s in {-10, 0, 10} (its error does not depend on a power-of-two scale).
+    All-ones inputs: log2 (A'B')_ij from the GPU shifts against log2(P/2) (Fig. 1), and the max
+    relative error of both modes against the exact k 4^s over the full matrix (Fig. 3)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synthetic
+    from paper_2606_29129_gb300 import ozaki2 as oz
+
+    oracle.build()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    N = 20
+    moduli, _, _ = oz.ozaki2_constants(N)
+    log2_half_P = sum(math.log2(p) for p in moduli) - 1.0
+    hf = oz.Handle()
+    hf.set_option(oz.OPT_SCALING, oz.SCALING_FAST)
+    hp = oz.Handle()
+
+    def emulate(A, B, C, m, n, k, h):
+        rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N, h)
+        if rc:
+            raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+
+    def full_rel(C, R):
+        nz = R != 0
+        d = (C - R).abs() / R.abs().where(nz, torch.ones_like(R))
+        return float(d.where(nz, torch.zeros_like(d)).max())
+
+    svals = list(range(-10, 11))
+    for size in args.study_sizes:
+        m = n = k = size
+        Cf = torch.empty((n, m), dtype=torch.float64, device="cuda")
+        Cp = torch.empty_like(Cf)
+        for pi, phi in enumerate((0.5, 1.0, 2.0)):
+            A0 = synthetic.paper_matrix_torch(m, k, phi, synthetic.seed_for(2, pi, 1))
+            B0 = synthetic.paper_matrix_torch(k, n, phi, synthetic.seed_for(2, pi, 2))
+            rng = np.random.default_rng(size + pi)
+            I = np.sort(rng.choice(m, size=args.err_block, replace=False)).astype(np.int32)
+            J = np.sort(rng.choice(n, size=args.err_block, replace=False)).astype(np.int32)
+            hi0, lo0 = oracle.dd_block(A0.cpu().numpy(), B0.cpu().numpy(), k, I, J)
+            Jd, Id = torch.from_numpy(J).long().cuda(), torch.from_numpy(I).long().cuda()
+
+            def block(C):
+                return C[Jd][:, Id].cpu().numpy()
+
+            for s in svals:
+                A, B = A0 * 2.0**s, B0 * 2.0**s
+                hi, lo = hi0 * 4.0**s, lo0 * 4.0**s
+                emulate(A, B, Cf, m, n, k, hf)
+                emulate(A, B, Cp, m, n, k, hp)
+                torch.cuda.synchronize()
+                line = {"study": "fig2", "size": size, "phi": phi, "s": s, "N": N,
+                        "sample": f"{len(I)}x{len(J)}",
+                        "fast_vs_dd_block": oracle.max_rel_error(block(Cf), hi, lo)[0],
+                        "proposed_vs_dd_block": oracle.max_rel_error(block(Cp), hi, lo)[0],
+                        "fast_full_vs_proposed": full_rel(Cf, Cp)}
+                if s in (-10, 0, 10):
+                    Cd = torch.matmul(B.view(n, k), A.view(k, m))
+                    torch.cuda.synchronize()
+                    line["cublas_vs_dd_block"] = oracle.max_rel_error(block(Cd), hi, lo)[0]
+                    del Cd
+                print(json.dumps(line), flush=True)
+                del A, B
+            del A0, B0
+            torch.cuda.empty_cache()
+        ones_A = torch.ones((k, m), dtype=torch.float64, device="cuda")
+        ones_B = torch.ones((n, k), dtype=torch.float64, device="cuda")
+        e = torch.empty(m, dtype=torch.int32, device="cuda")
+        for s in svals:
+            A, B = ones_A * 2.0**s, ones_B * 2.0**s
+            exact = torch.full_like(Cf, k * 4.0**s)
+            emulate(A, B, Cf, m, n, k, hf)
+            emulate(A, B, Cp, m, n, k, hp)
+            rc = oz.ozaki2_scale_a("N", m, k, A, m, N, e, hf)
+            if rc:
+                raise oz.Ozaki2Error("ozaki2_scale_a", rc)
+            torch.cuda.synchronize()
+            ef = int(e[0])
+            rc = oz.ozaki2_scale_a("N", m, k, A, m, N, e, hp)
+            if rc:
+                raise oz.Ozaki2Error("ozaki2_scale_a", rc)
+            torch.cuda.synchronize()
+            ep = int(e[0])
+            print(json.dumps({"study": "fig1_fig3", "size": size, "s": s, "N": N,
+                              "log2_half_P": log2_half_P,
+                              "fast_log2_ApBp": math.log2(k) + 2 * (ef + s),
+                              "proposed_log2_ApBp": math.log2(k) + 2 * (ep + s),
+                              "fast_full_vs_exact": full_rel(Cf, exact),
+                              "proposed_full_vs_exact": full_rel(Cp, exact)}), flush=True)
+            del A, B, exact
+        del ones_A, ones_B, Cf, Cp
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -688,7 +794,8 @@ def main():
     ap.add_argument("--err-items", type=int, default=64)
     ap.add_argument("--serve", action="store_true",
                     help="the serving workload (Poisson stream) instead of the benchmark")
-    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0,
+                    help="Poisson arrival rate per second; 0 = all requests at once")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-max", type=int, default=8192)
     ap.add_argument("--serve-pool", type=int, default=64)
@@ -699,9 +806,15 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy sweep over N, phi and alpha instead of the benchmark")
     ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[8192, 16384])
+    ap.add_argument("--scaling-study", action="store_true",
+                    help="fast mode (Algorithm 1) against the proposed scaling over alpha = 2^s")
+    ap.add_argument("--study-sizes", type=int, nargs="+", default=[1024, 16384])
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)
+        return
+    if args.scaling_study:
+        run_scaling_study(args)
         return
     if args.batched:
         run_batched(args)

@@ -66,6 +66,13 @@ extern "C" {
                                      the same list (same pointers and sizes); 0 (default): off.
                                      A graph's table buffer is kept until the handle is destroyed,
                                      the option is turned off, or the workspace is reallocated. */
+#define OZAKI2_OPT_SCALING 4      /* scaling step: OZAKI2_SCALING_PROPOSED (default) or
+                                     OZAKI2_SCALING_FAST */
+#define OZAKI2_SCALING_PROPOSED 0 /* Algorithm 2 (Section 4): scale-invariant, CRT bound by
+                                     construction */
+#define OZAKI2_SCALING_FAST 1     /* Algorithm 1 (Section 2.3): the original fast mode, kept for
+                                     comparison; its shifts depend on the scale of the input and
+                                     can break the CRT bound (Section 3.1) */
 #define OZAKI2_GEMM_AUTO 0        /* the kernel measured fastest on GB300 (currently SINGLE) */
 #define OZAKI2_GEMM_SINGLE 1      /* 128 x 256 tiles, one CTA per SM (tcgen05 cta_group::1) */
 #define OZAKI2_GEMM_PAIR 2        /* 256 x 256 tiles on SM pairs (tcgen05 cta_group::2) */
@@ -91,7 +98,9 @@ int ozaki2_set_stream(ozaki2_handle_t handle, void* stream);
 int ozaki2_set_workspace(ozaki2_handle_t handle, void* workspace, size_t bytes);
 
 /* Set an OZAKI2_OPT_* option of the handle.  Returns -2 for an unknown option, -3 for a value
- * out of range.  Results do not depend on the options; only the kernels used do. */
+ * out of range.  Results do not depend on the options, except OZAKI2_OPT_SCALING, which selects
+ * the scaling algorithm (and so the shifts and the result) of ozaki2_dgemm, ozaki2_dgemm_h,
+ * ozaki2_dgemm_grouped, ozaki2_scale_a and ozaki2_scale_b on this handle. */
 int ozaki2_set_option(ozaki2_handle_t handle, int option, int value);
 
 /* Workspace bytes that ozaki2_dgemm needs for op(A) m x k, op(B) k x n and N moduli:
@@ -171,6 +180,9 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
  * op(A) (m x k, lda).  The squared norm is accumulated in order h = 1..k with one fused
  * multiply-add rounded upward per term.  A zero row gets 0; a row with a non-finite squared
  * norm gets OZAKI2_SHIFT_NONFINITE and raises OZAKI2_STATUS_NONFINITE.  shifts: device int[m].
+ * With OZAKI2_OPT_SCALING = OZAKI2_SCALING_FAST the shifts are those of Algorithm 1 instead
+ * (eq. (fast-mode-mu): the same norm, plus the row maximum max_h |a_ih|); a row whose norm or
+ * maximum is zero gets 0.
  * Arguments: handle 1, transA 2, m 3, k 4, A 5, lda 6, num_moduli 7, shifts 8. */
 int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
                    int num_moduli, int* shifts);

@@ -19,6 +19,7 @@ struct ozaki2_context {
     bool user_ws = false;
     int chunk_k = 960;             // products accumulated between modular reductions
     int gemm_variant = OZAKI2_GEMM_AUTO;
+    int scaling = OZAKI2_SCALING_PROPOSED;  // Algorithm 2, or Algorithm 1 (original fast mode)
     bool timing = false;           // record stage events in ozaki2_dgemm
     bool timed_call = false;       // a timed call has been queued
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -29,6 +30,7 @@ struct ozaki2_context {
     struct GraphEntry {
         std::vector<ozaki2_problem> probs;
         int chunk_k;
+        int scaling;
         void* tables = nullptr;    // device copy of the call's tables
         cudaGraphExec_t exec = nullptr;
     };
@@ -195,8 +197,13 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     rows_of_op(transA, lda, &als, &aes);
     cols_of_op(transB, ldb, &bls, &bes);
     mark(0);
-    if ((rc = cuda_rc(launch_scale(A, als, aes, m, k, T->pprime, e, ctx->d_status, st)))) return rc;
-    if ((rc = cuda_rc(launch_scale(B, bls, bes, n, k, T->pprime, f, ctx->d_status, st)))) return rc;
+    const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
+    if ((rc = cuda_rc(launch_scale(A, als, aes, m, k, pp, e, ctx->d_status, st, ctx->scaling,
+                                   T->delta))))
+        return rc;
+    if ((rc = cuda_rc(launch_scale(B, bls, bes, n, k, pp, f, ctx->d_status, st, ctx->scaling,
+                                   T->delta))))
+        return rc;
     mark(1);
     if ((rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, (int)L.m_pad,
                                      (int)L.k_pad, ctx->d_status, st))))
@@ -276,6 +283,10 @@ int ozaki2_set_option(ozaki2_handle_t handle, int option, int value) {
             if (value != 0 && value != 1) return -3;
             if (!value) clear_graphs(ctx);
             ctx->use_graphs = value != 0;
+            return OZAKI2_SUCCESS;
+        case OZAKI2_OPT_SCALING:
+            if (value != OZAKI2_SCALING_PROPOSED && value != OZAKI2_SCALING_FAST) return -3;
+            ctx->scaling = value;
             return OZAKI2_SUCCESS;
         default:
             return -2;
@@ -413,7 +424,8 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
     char* ws = static_cast<char*>(ctx->ws);
     if (ctx->use_graphs) {
         for (auto& g : ctx->graphs)
-            if (g.chunk_k == ctx->chunk_k && same_problems(g.probs, count, problems))
+            if (g.chunk_k == ctx->chunk_k && g.scaling == ctx->scaling &&
+                same_problems(g.probs, count, problems))
                 return cudaGraphLaunch(g.exec, ctx->stream) == cudaSuccess ? OZAKI2_SUCCESS
                                                                             : OZAKI2_ERROR_CUDA;
         // First call with these problems: upload the tables to a buffer of their own, capture
@@ -421,8 +433,11 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
         ozaki2_context::GraphEntry g;
         g.probs.assign(problems, problems + count);
         g.chunk_k = ctx->chunk_k;
+        g.scaling = ctx->scaling;
         std::vector<char> host(tb ? tb : 1);
-        if ((rc = build_grouped_tables(count, problems, ws, host.data(), ctx->chunk_k))) return rc;
+        if ((rc = build_grouped_tables(count, problems, ws, host.data(), ctx->chunk_k,
+                                       ctx->scaling)))
+            return rc;
         if (cudaMalloc(&g.tables, tb ? tb : 1) != cudaSuccess) {
             cudaGetLastError();
             return OZAKI2_ERROR_ALLOC;
@@ -471,7 +486,8 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
     }
     // the staging buffer may still be read by the previous call's copy
     if (cudaEventSynchronize(ctx->staged) != cudaSuccess) return OZAKI2_ERROR_CUDA;
-    if ((rc = build_grouped_tables(count, problems, ws, ctx->stage, ctx->chunk_k))) return rc;
+    if ((rc = build_grouped_tables(count, problems, ws, ctx->stage, ctx->chunk_k, ctx->scaling)))
+        return rc;
     char* tables_dev = grouped_tables_in_workspace(count, problems, ws);
     if (tb && (cudaMemcpyAsync(tables_dev, ctx->stage, tb, cudaMemcpyHostToDevice,
                                ctx->stream) != cudaSuccess ||
@@ -497,7 +513,9 @@ int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const doub
     if (rc) return rc;
     int64_t ls, es;
     rows_of_op(transA, lda, &ls, &es);
-    return cuda_rc(launch_scale(A, ls, es, m, k, T->pprime, shifts, ctx->d_status, ctx->stream));
+    const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
+    return cuda_rc(launch_scale(A, ls, es, m, k, pp, shifts, ctx->d_status, ctx->stream,
+                                ctx->scaling, T->delta));
 }
 
 int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const double* B, int ldb,
@@ -516,7 +534,9 @@ int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const doub
     if (rc) return rc;
     int64_t ls, es;
     cols_of_op(transB, ldb, &ls, &es);
-    return cuda_rc(launch_scale(B, ls, es, n, k, T->pprime, shifts, ctx->d_status, ctx->stream));
+    const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
+    return cuda_rc(launch_scale(B, ls, es, n, k, pp, shifts, ctx->d_status, ctx->stream,
+                                ctx->scaling, T->delta));
 }
 
 static int convert_common(ozaki2_handle_t handle, bool is_a, char trans, int lines, int len,

@@ -132,7 +132,7 @@ size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs) {
 // Builds the tables of a grouped call into `host` (grouped_table_bytes bytes).  `ws` is the device
 // workspace holding the problems' intermediates.
 int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char* host,
-                         int chunk_k) {
+                         int chunk_k, int scaling) {
     Plan P;
     make_plan(count, probs, P);
     if (P.idx.empty()) return OZAKI2_SUCCESS;
@@ -169,7 +169,9 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
         g.k_pad = (int)k_pad;
         g.alpha = p.alpha;
         g.beta = p.beta;
-        g.pprime = T->pprime;
+        g.scaling = scaling;
+        g.pprime = scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
+        g.delta = T->delta;
         int64_t o = 0;
         g.e = reinterpret_cast<int*>(base + o);  o += round_up64(4 * m_pad, 256);
         g.f = reinterpret_cast<int*>(base + o);  o += round_up64(4 * n_pad, 256);

@@ -53,6 +53,8 @@ struct ModTables {
     int moduli[kMaxModuli];
     int inverses[kMaxModuli];
     float pprime;           // P'_prop
+    float pprime_fast;      // P'_fast (original fast mode)
+    float delta;            // single-up(0.5 / (1 - 4u_32)), eq. (delta)
     int words;              // 32-bit words used by the CRT accumulator
     ConvertTables conv;
     CrtTables crt;
@@ -70,7 +72,9 @@ struct GroupProblem {
     int m, n, k, N;
     int m_pad, n_pad, k_pad;
     double alpha, beta;
-    float pprime;
+    float pprime;        // P'_prop, or P'_fast in the original fast mode
+    float delta;
+    int scaling;         // OZAKI2_SCALING_*
     int* e;              // shifts of the rows of op(A)   [m_pad]
     int* f;              // shifts of the columns of op(B) [n_pad]
     void* pa;            // bf16 planes [N][m_pad][k_pad]
@@ -122,7 +126,7 @@ size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs);
 int grouped_table_bytes(int count, const ozaki2_problem* probs);
 int grouped_check(int count, const ozaki2_problem* probs);
 int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char* host,
-                         int chunk_k);
+                         int chunk_k, int scaling = OZAKI2_SCALING_PROPOSED);
 int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_dev,
                    unsigned* status, int num_sms, int chunk_k, cudaStream_t stream);
 char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* ws);
@@ -134,9 +138,11 @@ const ModTables* mod_tables(int N);
 // Shifts for `lines` lines of length `len`.  Element h of line i is at
 //   X[i * line_stride + h * elem_stride]  with either line_stride == 1 (lines adjacent) or
 //   elem_stride == 1 (each line contiguous).
+// scaling: OZAKI2_SCALING_PROPOSED (pprime = P'_prop) or OZAKI2_SCALING_FAST (pprime = P'_fast).
 cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                          int len, float pprime, int* shifts, unsigned* status,
-                         cudaStream_t stream);
+                         cudaStream_t stream, int scaling = OZAKI2_SCALING_PROPOSED,
+                         float delta = 0.0f);
 
 cudaError_t launch_convert(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, const int* shifts, const ConvertTables& t, void* planes,

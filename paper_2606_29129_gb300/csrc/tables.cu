@@ -73,6 +73,13 @@ void build(int N, ModTables& t) {
     Words Pm1 = P;
     Pm1[0] -= 1;  // P is a multiple of 256, so no borrow
     t.pprime = round_down_to_float(log2_words(Pm1) / 2.0 - 0.5);
+    t.pprime_fast = round_down_to_float(log2_words(Pm1) / 2.0 - 1.5);
+    {   // delta = single-up(0.5 / (1 - 4u_32)) = 0.5 + 2^-23 + 2^-45 + ... -> 0.5 + 3 * 2^-24
+        const double q = 0.5 / (1.0 - 4.0 * 0x1p-24);
+        float d = (float)q;
+        if ((double)d < q) d = nextafterf(d, INFINITY);
+        t.delta = d;
+    }
 
     const int pbits = bit_length(P);
     t.words = (pbits + 5 + 31) / 32;  // sum_l P_l w_l < N P < 2^(pbits + 5)

@@ -27,6 +27,8 @@ ERROR_TOO_LARGE = 6
 OPT_GEMM_VARIANT = 1
 OPT_CHUNK_K = 2
 OPT_GRAPH = 3
+OPT_SCALING = 4
+SCALING_PROPOSED, SCALING_FAST = 0, 1
 GEMM_AUTO, GEMM_SINGLE, GEMM_PAIR = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 8 << 20
 

@@ -18,22 +18,22 @@ def round_up(v, a):
     return (max(v, 1) + a - 1) // a * a
 
 
-def shifts_a(oz, A_np, m, k, N, trans="N", lda=None):
+def shifts_a(oz, A_np, m, k, N, trans="N", lda=None, handle=None):
     import torch
 
     lda = lda if lda is not None else A_np.shape[-1]
     out = torch.zeros(max(m, 1), dtype=torch.int32, device="cuda")
-    ok(oz.ozaki2_scale_a(trans, m, k, dev(A_np), lda, N, out), "scale_a")
+    ok(oz.ozaki2_scale_a(trans, m, k, dev(A_np), lda, N, out, handle), "scale_a")
     torch.cuda.synchronize()
     return out.cpu().numpy()[:m]
 
 
-def shifts_b(oz, B_np, k, n, N, trans="N", ldb=None):
+def shifts_b(oz, B_np, k, n, N, trans="N", ldb=None, handle=None):
     import torch
 
     ldb = ldb if ldb is not None else B_np.shape[-1]
     out = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
-    ok(oz.ozaki2_scale_b(trans, k, n, dev(B_np), ldb, N, out), "scale_b")
+    ok(oz.ozaki2_scale_b(trans, k, n, dev(B_np), ldb, N, out, handle), "scale_b")
     torch.cuda.synchronize()
     return out.cpu().numpy()[:n]
 

@@ -111,3 +111,26 @@ def test_fast_mode_still_satisfies_its_own_bound_on_random_data(orc):
     for i in range(m):
         for j in range(n):
             assert 2 * sum(abs(Ap[i][h] * Bp[h][j]) for h in range(k)) < P
+
+
+@pytest.mark.parametrize("s", [-3, -2])
+def test_fast_mode_breakdown_on_random_phi_half(orc, s):
+    """Section 3.2, Fig. 2: with phi = 0.5 and m = n = k = 1024 (N = 20) the fast mode breaks
+    down (relative error ~1 on some entries) for alpha <= 2^-3 and not above; the proposed
+    scaling stays at the level of one rounding."""
+    m = n = k = 1024
+    N = 20
+    A = synthetic.paper_matrix(m, k, 0.5, 11) * 2.0**s
+    B = synthetic.paper_matrix(k, n, 0.5, 12) * 2.0**s
+    Cf = orc.dgemm_mode(A, B, m, n, k, N, orc.FAST_MODE)
+    Cp = orc.dgemm_mode(A, B, m, n, k, N, orc.PROPOSED_MODE)
+    diff = np.abs(Cf - Cp)
+    J = np.sort(np.argsort(diff.max(axis=1))[-4:]).astype(np.int32)
+    I = np.sort(np.argsort(diff.max(axis=0))[-4:]).astype(np.int32)
+    hi, lo = orc.dd_block(A, B, k, I, J)
+    err_f, _ = orc.max_rel_error(Cf[np.ix_(J, I)], hi, lo)
+    err_p, _ = orc.max_rel_error(Cp[np.ix_(J, I)], hi, lo)
+    assert err_p < 2e-16
+    assert (err_f > 0.5) == (s <= -3)
+    if s > -3:
+        assert np.all(diff <= 1e-13 * np.abs(Cp))
