@@ -69,6 +69,10 @@ def lib():
         L.orc_dgemm_mode.argtypes = [ch, ch, i32, i32, i32, f64, P, i64, P, i64, f64, P, i64,
                                      i32, i32]
         L.orc_pprime_fast.argtypes = [i32, P]
+        L.orc_accu_shift.argtypes = [i32, i32, i64, f32]
+        L.orc_accu_shift.restype = i32
+        L.orc_accu_bar.argtypes = [i32, ch, i32, i32, P, i64, P, P, P]
+        L.orc_accurate_shifts.argtypes = [ch, ch, i32, i32, i32, P, i64, P, i64, i32, P, P, P, P]
         _lib = L
     return _lib
 
@@ -215,6 +219,8 @@ def int_residues(values, N: int) -> np.ndarray:
 # ---------------------------------------------------------------- original fast mode
 FAST_MODE = 1      # Algorithm 1 (Section 2.3)
 PROPOSED_MODE = 0  # Algorithm 2 (Section 4)
+ACCURATE_MODE = 2  # accurate mode (Section 2.3, eq. mu_accu / nu_accu)
+SHIFT_VANISH = -1100
 
 
 def fast_delta() -> float:
@@ -306,3 +312,35 @@ def max_rel_error(C: np.ndarray, hi: np.ndarray, lo: np.ndarray):
     err = np.abs((C - hi) - lo)
     rel = np.where(nz, err / np.where(nz, np.abs(hi), 1.0), 0.0)
     return float(rel.max(initial=0.0)), int((~nz).sum())
+
+
+# ---------------------------------------------------------------- accurate mode
+def accu_shift(kind: int, E: int, cmax: int, pprime_accu: float) -> int:
+    return lib().orc_accu_shift(kind, E, cmax, pprime_accu)
+
+
+def accu_bar(X, lines, length, side=0, trans="N", ld=None):
+    """(bar uint8 (lines, length), E int32 (lines,), kind int32 (lines,)) of accurate mode."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    ld = ld if ld is not None else X.shape[-1]
+    bar = np.zeros((max(lines, 1), max(length, 1)), np.uint8)
+    E = np.zeros(max(lines, 1), np.int32)
+    kind = np.zeros(max(lines, 1), np.int32)
+    _ck(lib().orc_accu_bar(side, _b(trans), lines, length, _p(X), ld, _p(bar), _p(E), _p(kind)))
+    return bar[:lines, :length], E[:lines], kind[:lines]
+
+
+def accurate_shifts(A, B, m, n, k, N, transA="N", transB="N", lda=None, ldb=None):
+    """(e, f, rowmax, colmax) of accurate mode: shifts of both operands and the row and column
+    maxima of C-bar = A-bar B-bar."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    lda = lda if lda is not None else A.shape[-1]
+    ldb = ldb if ldb is not None else B.shape[-1]
+    e = np.zeros(max(m, 1), np.int32)
+    f = np.zeros(max(n, 1), np.int32)
+    rm = np.zeros(max(m, 1), np.int64)
+    cm = np.zeros(max(n, 1), np.int64)
+    _ck(lib().orc_accurate_shifts(_b(transA), _b(transB), m, n, k, _p(A), lda, _p(B), ldb, N,
+                                  _p(e), _p(f), _p(rm), _p(cm)))
+    return e[:m], f[:n], rm[:m], cm[:n]

@@ -40,6 +40,9 @@
 #pragma STDC FENV_ACCESS ON
 
 #define ORC_MAX_MODULI 20
+/* Accurate mode: a line whose products with every line of the other operand vanish
+ * (max of its row/column of C-bar is 0) gets this shift, which makes every a' zero. */
+#define ORC_SHIFT_VANISH (-1100)
 /* A line whose squared norm is not finite gets this shift; its outputs become NaN. */
 #define ORC_SHIFT_NONFINITE INT32_MIN
 
@@ -505,7 +508,125 @@ int orc_residue_products(int N, int m, int n, int k, const int8_t* RA, const int
 int orc_crt(int N, int m, int n, const int8_t* cres, const int* e, const int* f, double alpha,
             double beta, double* C, int64_t ldc);
 
-/* The whole emulated DGEMM under a scaling mode (0 proposed, 1 original fast mode). */
+/* ---------------------------------------------------------------- accurate mode
+ * Section 2.3: mu'_i = 2^(5 - floor(log2 max_h |a_ih|)),  a-bar_ih = ceil(mu'_i |a_ih|) <= 64,
+ * C-bar = A-bar B-bar (exact integers), and
+ *   log2 mu_i = log2 mu'_i + floor(P'_accu - delta * log2~(max_j c-bar_ij))
+ * with P'_accu = single-down(log2(P - 1)/2 - 0.5) and log2~ of eq. (flog2).
+ * Reading: the paper prints mu'^(-1)_i in eq. (mu_accu), but its own bound chain
+ * 2 mu_i mu'^(-1)_i c-bar_ij nu'^(-1)_j nu_j < P only holds with mu_i = mu'_i 2^(...), which is
+ * the reading taken.  The floor is of the exact value (the double product delta * log2~ of two
+ * singles is exact, and so is the difference).  A line whose max c-bar is 0 contributes
+ * nothing to any product and gets ORC_SHIFT_VANISH; a zero line gets 0; a line with a
+ * non-finite entry gets ORC_SHIFT_NONFINITE and a zero a-bar line. */
+
+/* Exponent E = floor(log2 max |x_h|) of a line and its a-bar entries; returns 0 (zero line),
+ * 1 (finite, nonzero) or -1 (non-finite). */
+static int accu_bar_line(const double* x, int64_t stride, int64_t len, int* E, uint8_t* bar) {
+    double mx = line_max_abs(x, stride, len);
+    if (!(mx <= DBL_MAX)) {
+        for (int64_t h = 0; h < len; ++h) bar[h] = 0;
+        return -1;
+    }
+    if (mx == 0.0) {
+        for (int64_t h = 0; h < len; ++h) bar[h] = 0;
+        *E = 0;
+        return 0;
+    }
+    *E = ilogb(mx);
+    for (int64_t h = 0; h < len; ++h) {
+        double a = fabs(x[h * stride]);
+        if (a == 0.0) { bar[h] = 0; continue; }
+        /* mu' |a| <= 2^5 * 2 = 64; ldexp is exact unless it underflows, and then the exact value
+         * is below 1, whose ceiling is 1 */
+        double v = ceil(ldexp(a, 5 - *E));
+        bar[h] = (uint8_t)(v < 1.0 ? 1.0 : v);
+    }
+    return 1;
+}
+
+/* log2 mu_i from E_i and the maximum of row i of C-bar. */
+int orc_accu_shift(int kind, int E, int64_t cmax, float pprime_accu) {
+    if (kind < 0) return ORC_SHIFT_NONFINITE;
+    if (kind == 0) return 0;
+    if (cmax == 0) return ORC_SHIFT_VANISH;
+    /* eq. (flog2): s = floor(log2 x), x' = x / 2^s in [1, 2) (exact: x < 2^53) */
+    int s = 63 - __builtin_clzll((unsigned long long)cmax);
+    double xprime = ldexp((double)cmax, -s);
+    float lg = ru_float((double)orc_log2_ru(ru_float(xprime)) + (double)s);
+    float delta = orc_fast_delta();
+    double u = (double)delta * (double)lg;             /* exact: 24 x 24 bits */
+    return 5 - E + (int)floor(sub_rd((double)pprime_accu, u));
+}
+
+/* a-bar of the rows of op(A) (side 0) or the columns of op(B) (side 1): bar[i * len + h],
+ * exps[i] = E_i, kinds[i] as accu_bar_line. */
+int orc_accu_bar(int side, char trans, int lines, int len, const double* X, int64_t ld,
+                 uint8_t* bar, int* exps, int* kinds) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < lines; ++i) {
+        const double* base; int64_t st;
+        if (side == 0) row_of_opA(trans, X, ld, i, &base, &st);
+        else col_of_opB(trans, X, ld, i, &base, &st);
+        exps[i] = 0;
+        kinds[i] = accu_bar_line(base, st, len, &exps[i], bar + (int64_t)i * len);
+    }
+    return 0;
+}
+
+/* Shifts of accurate mode for both operands, with the row and column maxima of C-bar. */
+int orc_accurate_shifts(char transA, char transB, int m, int n, int k, const double* A,
+                        int64_t lda, const double* B, int64_t ldb, int N, int* e, int* f,
+                        int64_t* rowmax, int64_t* colmax) {
+    orc_consts c;
+    if (make_consts(N, &c)) return -1;
+    size_t kk = (size_t)(k ? k : 1);
+    uint8_t* Abar = (uint8_t*)malloc((size_t)(m ? m : 1) * kk);
+    uint8_t* Bbar = (uint8_t*)malloc((size_t)(n ? n : 1) * kk);
+    int* EA = (int*)malloc(sizeof(int) * (size_t)(m ? m : 1));
+    int* EB = (int*)malloc(sizeof(int) * (size_t)(n ? n : 1));
+    int* KA = (int*)malloc(sizeof(int) * (size_t)(m ? m : 1));
+    int* KB = (int*)malloc(sizeof(int) * (size_t)(n ? n : 1));
+    if (!Abar || !Bbar || !EA || !EB || !KA || !KB) {
+        free(Abar); free(Bbar); free(EA); free(EB); free(KA); free(KB);
+        return -2;
+    }
+    orc_accu_bar(0, transA, m, k, A, lda, Abar, EA, KA);
+    orc_accu_bar(1, transB, n, k, B, ldb, Bbar, EB, KB);
+    int64_t* Cbar = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m ? m : 1) * (n ? n : 1));
+    if (!Cbar) {
+        free(Abar); free(Bbar); free(EA); free(EB); free(KA); free(KB);
+        return -2;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < m; ++i) {                   /* C-bar = A-bar B-bar, exact */
+        const uint8_t* ar = Abar + (size_t)i * kk;
+        for (int j = 0; j < n; ++j) {
+            const uint8_t* bc = Bbar + (size_t)j * kk;
+            int64_t cbar = 0;
+            for (int h = 0; h < k; ++h) cbar += (int64_t)ar[h] * bc[h];
+            Cbar[(size_t)i * n + j] = cbar;
+        }
+    }
+    for (int i = 0; i < m; ++i) {
+        int64_t r = 0;
+        for (int j = 0; j < n; ++j) r = Cbar[(size_t)i * n + j] > r ? Cbar[(size_t)i * n + j] : r;
+        rowmax[i] = r;
+    }
+    for (int j = 0; j < n; ++j) {
+        int64_t r = 0;
+        for (int i = 0; i < m; ++i) r = Cbar[(size_t)i * n + j] > r ? Cbar[(size_t)i * n + j] : r;
+        colmax[j] = r;
+    }
+    free(Cbar);
+    for (int i = 0; i < m; ++i) e[i] = orc_accu_shift(KA[i], EA[i], rowmax[i], c.pprime);
+    for (int j = 0; j < n; ++j) f[j] = orc_accu_shift(KB[j], EB[j], colmax[j], c.pprime);
+    free(Abar); free(Bbar); free(EA); free(EB); free(KA); free(KB);
+    return 0;
+}
+
+/* The whole emulated DGEMM under a scaling mode (0 proposed, 1 original fast mode,
+ * 2 accurate mode). */
 int orc_dgemm_mode(char transA, char transB, int m, int n, int k, double alpha, const double* A,
                    int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                    int64_t ldc, int N, int mode) {
@@ -518,8 +639,16 @@ int orc_dgemm_mode(char transA, char transB, int m, int n, int k, double alpha, 
     int8_t* cr = (int8_t*)malloc((size_t)N * m * n);
     int rc = -2;
     if (e && f && RA && RB && cr) {
-        orc_shifts_mode(0, transA, m, k, A, lda, N, mode, e);
-        orc_shifts_mode(1, transB, n, k, B, ldb, N, mode, f);
+        if (mode == 2) {
+            int64_t* rmx = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+            int64_t* cmx = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+            if (rmx && cmx)
+                orc_accurate_shifts(transA, transB, m, n, k, A, lda, B, ldb, N, e, f, rmx, cmx);
+            free(rmx); free(cmx);
+        } else {
+            orc_shifts_mode(0, transA, m, k, A, lda, N, mode, e);
+            orc_shifts_mode(1, transB, n, k, B, ldb, N, mode, f);
+        }
         orc_residues_a(transA, m, k, A, lda, e, N, RA);
         orc_residues_b(transB, k, n, B, ldb, f, N, RB);
         orc_residue_products(N, m, n, k, RA, RB, cr);
