@@ -216,6 +216,9 @@ def run_gpu(args, world, rank, local):
     C = torch.empty((n, m), dtype=torch.float64, device=dev)
     h = oz.Handle()
     h.set_timing(True)
+    scaling = {"proposed": oz.SCALING_PROPOSED, "fast": oz.SCALING_FAST,
+               "accurate": oz.SCALING_ACCURATE}[args.scaling]
+    h.set_option(oz.OPT_SCALING, scaling)
 
     def step():
         rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N, h)
@@ -279,7 +282,10 @@ def run_gpu(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 emulated (bf16-held int8 residues on tcgen05, fp32 exact accumulate)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "phi": PHI, "num_moduli": N,
+        "config": {"workload": f"square FP64 GEMM m=n=k={m}, phi={PHI}, N={N} moduli" +
+                   ("" if args.scaling == "proposed" else f", {args.scaling} scaling"),
+                   "m": m, "n": n, "k": k, "phi": PHI,
+                   "num_moduli": N, "scaling": args.scaling,
                    "parallelism": f"replicas x{world} (independent problems)",
                    "l2": "inputs larger than L2 (A, B, C: 6 GiB)"},
         "latency_ms": {"p50": step_ms[len(step_ms) // 2],
@@ -288,7 +294,7 @@ def run_gpu(args, world, rank, local):
         "stages_ms": stages,
         "roofline": roofline,
         "clocks": clk,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": (10 if args.scaling == "accurate" else 6) * args.steps,
         "device_status": status,
         "e2e": e2e,
     }
@@ -781,6 +787,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--moduli", type=int, default=NUM_MODULI)
+    ap.add_argument("--scaling", default="proposed", choices=["proposed", "fast", "accurate"],
+                    help="scaling step: Algorithm 2 (default), Algorithm 1, or accurate mode")
     ap.add_argument("--err-block", type=int, default=96)
     ap.add_argument("--cpu-block", type=int, default=256)
     ap.add_argument("--ref-block", type=int, default=192)

@@ -39,7 +39,9 @@ extern "C" {
 #define OZAKI2_ERROR_WORKSPACE 3  /* a workspace set with ozaki2_set_workspace is too small */
 #define OZAKI2_ERROR_NO_DEVICE 4  /* the current device is not an sm_103 GPU */
 #define OZAKI2_ERROR_DRIVER 5     /* the driver's tensor-map encoder is unavailable or failed */
-#define OZAKI2_ERROR_TOO_LARGE 6  /* the problem does not fit ozaki2_dgemm_noalloc's scratch */
+#define OZAKI2_ERROR_TOO_LARGE 6  /* the problem does not fit ozaki2_dgemm_noalloc's scratch, or
+                                     k > OZAKI2_ACCURATE_MAX_K in accurate mode */
+#define OZAKI2_ERROR_MODE 7       /* the entry point does not apply in the handle's scaling mode */
 
 /* ---- device status flags (ozaki2_get_status) ------------------------------------------- */
 #define OZAKI2_STATUS_NONFINITE 1u /* a row of op(A) or column of op(B) had a non-finite squared
@@ -56,6 +58,10 @@ extern "C" {
 #define OZAKI2_MAX_MODULI 20
 #define OZAKI2_MIN_MODULI 2
 #define OZAKI2_SHIFT_NONFINITE INT32_MIN /* shift written for a line with a non-finite norm */
+#define OZAKI2_SHIFT_VANISH (-1100)      /* accurate mode: shift of a nonzero line whose products
+                                            with every line of the other operand vanish (its row
+                                            or column of C-bar is 0); it makes every a' zero */
+#define OZAKI2_ACCURATE_MAX_K 1048575    /* accurate mode: largest k (C-bar < 2^32) */
 
 /* Options (ozaki2_set_option). */
 #define OZAKI2_OPT_GEMM_VARIANT 1 /* residue-GEMM kernel: one of OZAKI2_GEMM_* (default AUTO) */
@@ -73,6 +79,9 @@ extern "C" {
 #define OZAKI2_SCALING_FAST 1     /* Algorithm 1 (Section 2.3): the original fast mode, kept for
                                      comparison; its shifts depend on the scale of the input and
                                      can break the CRT bound (Section 3.1) */
+#define OZAKI2_SCALING_ACCURATE 2 /* accurate mode (Section 2.3, eq. (mu_accu)/(nu_accu)): shifts
+                                     from the row/column maxima of an auxiliary product
+                                     C-bar = A-bar B-bar of integers <= 64; k <= 2^20 - 1 */
 #define OZAKI2_GEMM_AUTO 0        /* the kernel measured fastest on GB300 (currently SINGLE) */
 #define OZAKI2_GEMM_SINGLE 1      /* 128 x 256 tiles, one CTA per SM (tcgen05 cta_group::1) */
 #define OZAKI2_GEMM_PAIR 2        /* 256 x 256 tiles on SM pairs (tcgen05 cta_group::2) */
@@ -182,7 +191,8 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
  * norm gets OZAKI2_SHIFT_NONFINITE and raises OZAKI2_STATUS_NONFINITE.  shifts: device int[m].
  * With OZAKI2_OPT_SCALING = OZAKI2_SCALING_FAST the shifts are those of Algorithm 1 instead
  * (eq. (fast-mode-mu): the same norm, plus the row maximum max_h |a_ih|); a row whose norm or
- * maximum is zero gets 0.
+ * maximum is zero gets 0.  In OZAKI2_SCALING_ACCURATE mode the shifts depend on both operands:
+ * this entry returns OZAKI2_ERROR_MODE (use ozaki2_scale_accurate).
  * Arguments: handle 1, transA 2, m 3, k 4, A 5, lda 6, num_moduli 7, shifts 8. */
 int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
                    int num_moduli, int* shifts);
@@ -191,6 +201,22 @@ int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const doub
  * (eq. (proposed-nu)).  Same conventions as ozaki2_scale_a. */
 int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const double* B, int ldb,
                    int num_moduli, int* shifts);
+
+/* Both scalings of accurate mode (Section 2.3), which need A and B together: line maxima,
+ * A-bar = ceil(mu' |A|) and B-bar as bf16 planes in the handle's workspace, the auxiliary
+ * product C-bar = A-bar B-bar on the tensor cores (exact), and
+ *   e[i] = log2 mu_i = 5 - E_i + floor(P'_accu - delta log2~(max_j c-bar_ij)),
+ *   f[j] likewise from the column maxima,
+ * with E_i = floor(log2 max_h |a_ih|) and the reading mu_i = mu'_i 2^floor(...) of eq. (mu_accu).
+ * A zero line gets 0, a line with an Inf or NaN gets OZAKI2_SHIFT_NONFINITE (and raises
+ * OZAKI2_STATUS_NONFINITE), a nonzero line whose C-bar row/column is 0 gets OZAKI2_SHIFT_VANISH.
+ * e: device int[m], f: device int[n]; cmax: NULL or device uint32[m + n] that receives the row
+ * maxima of C-bar then the column maxima.  Works in any scaling mode of the handle.
+ * Errors: -2/-3 trans, -4/-5/-6 m/n/k < 0, -7 A NULL, -8 lda, -9 B NULL, -10 ldb, -11 N,
+ * -12 e NULL, -13 f NULL, OZAKI2_ERROR_TOO_LARGE for k > OZAKI2_ACCURATE_MAX_K. */
+int ozaki2_scale_accurate(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
+                          const double* A, int lda, const double* B, int ldb, int num_moduli,
+                          int* e, int* f, unsigned* cmax);
 
 /* Step 2 conversion (a' = trunc(2^{e_i} a_ih)) and the residues of eq. (os2-C'):
  * planes[l][i][h] = rmod(a'_ih, p_l) stored as bfloat16 (every residue is an integer in

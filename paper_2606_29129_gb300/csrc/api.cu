@@ -158,6 +158,31 @@ void cols_of_op(char trans, int64_t ld, int64_t* line_stride, int64_t* elem_stri
     else { *line_stride = 1; *elem_stride = ld; }
 }
 
+// Accurate mode (Section 2.3): line exponents, A-bar and B-bar in the first residue plane of
+// each operand's planes, the maxima of C-bar = A-bar B-bar in the product-residue region (at
+// least 4 (m_pad + n_pad) bytes), and the shifts written over the exponents.
+int accurate_shifts(ozaki2_context* ctx, const double* A, int64_t als, int64_t aes,
+                    const double* B, int64_t bls, int64_t bes, int m, int n, int k,
+                    const Layout& L, const ModTables& T, int* e, int* f, void* pa, void* pb,
+                    void* cmax_region) {
+    cudaStream_t st = ctx->stream;
+    auto* cmax = static_cast<uint32_t*>(cmax_region);
+    int rc;
+    if ((rc = cuda_rc(launch_scale(A, als, aes, m, k, T.pprime, e, ctx->d_status, st,
+                                   OZAKI2_SCALING_ACCURATE, T.delta))) ||
+        (rc = cuda_rc(launch_scale(B, bls, bes, n, k, T.pprime, f, ctx->d_status, st,
+                                   OZAKI2_SCALING_ACCURATE, T.delta))) ||
+        (rc = cuda_rc(launch_convert_bar(A, als, aes, m, k, e, pa, (int)L.m_pad, (int)L.k_pad,
+                                         ctx->d_status, st))) ||
+        (rc = cuda_rc(launch_convert_bar(B, bls, bes, n, k, f, pb, (int)L.n_pad, (int)L.k_pad,
+                                         ctx->d_status, st))))
+        return rc;
+    if ((rc = launch_aux_gemm((int)L.m_pad, (int)L.n_pad, (int)L.k_pad, pa, pb, cmax,
+                              ctx->d_status, ctx->num_sms, st)))
+        return rc;
+    return cuda_rc(launch_accu_shift(e, m, f, n, cmax, (int)L.m_pad, T.pprime, T.delta, st));
+}
+
 int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m, int n, int k,
                double alpha, const double* A, int lda, const double* B, int ldb, double beta,
                double* C, int ldc, int N) {
@@ -177,6 +202,8 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     if (m > 0 && n > 0 && !C) return -(argbase + 12);
     if (m == 0 || n == 0) return OZAKI2_SUCCESS;
     if (k == 0 || alpha == 0.0) return cuda_rc(launch_scale_c(m, n, beta, C, ldc, ctx->stream));
+    if (ctx->scaling == OZAKI2_SCALING_ACCURATE && k > OZAKI2_ACCURATE_MAX_K)
+        return OZAKI2_ERROR_TOO_LARGE;
 
     const ModTables* T = mod_tables(N);
     const Layout L = make_layout(m, n, k, N);
@@ -197,13 +224,19 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     rows_of_op(transA, lda, &als, &aes);
     cols_of_op(transB, ldb, &bls, &bes);
     mark(0);
-    const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
-    if ((rc = cuda_rc(launch_scale(A, als, aes, m, k, pp, e, ctx->d_status, st, ctx->scaling,
-                                   T->delta))))
-        return rc;
-    if ((rc = cuda_rc(launch_scale(B, bls, bes, n, k, pp, f, ctx->d_status, st, ctx->scaling,
-                                   T->delta))))
-        return rc;
+    if (ctx->scaling == OZAKI2_SCALING_ACCURATE) {
+        if ((rc = accurate_shifts(ctx, A, als, aes, B, bls, bes, m, n, k, L, *T, e, f, pa, pb,
+                                  res)))
+            return rc;
+    } else {
+        const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
+        if ((rc = cuda_rc(launch_scale(A, als, aes, m, k, pp, e, ctx->d_status, st,
+                                       ctx->scaling, T->delta))))
+            return rc;
+        if ((rc = cuda_rc(launch_scale(B, bls, bes, n, k, pp, f, ctx->d_status, st,
+                                       ctx->scaling, T->delta))))
+            return rc;
+    }
     mark(1);
     if ((rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, (int)L.m_pad,
                                      (int)L.k_pad, ctx->d_status, st))))
@@ -285,7 +318,9 @@ int ozaki2_set_option(ozaki2_handle_t handle, int option, int value) {
             ctx->use_graphs = value != 0;
             return OZAKI2_SUCCESS;
         case OZAKI2_OPT_SCALING:
-            if (value != OZAKI2_SCALING_PROPOSED && value != OZAKI2_SCALING_FAST) return -3;
+            if (value != OZAKI2_SCALING_PROPOSED && value != OZAKI2_SCALING_FAST &&
+                value != OZAKI2_SCALING_ACCURATE)
+                return -3;
             ctx->scaling = value;
             return OZAKI2_SUCCESS;
         default:
@@ -363,7 +398,10 @@ const char* ozaki2_error_string(int code) {
         case OZAKI2_ERROR_WORKSPACE: return "user workspace too small";
         case OZAKI2_ERROR_NO_DEVICE: return "no sm_103 GPU available";
         case OZAKI2_ERROR_DRIVER: return "tensor map encoder unavailable or failed";
-        case OZAKI2_ERROR_TOO_LARGE: return "problem exceeds the static scratch of ozaki2_dgemm_noalloc";
+        case OZAKI2_ERROR_TOO_LARGE:
+            return "problem exceeds the static scratch of ozaki2_dgemm_noalloc, or k exceeds "
+                   "OZAKI2_ACCURATE_MAX_K in accurate mode";
+        case OZAKI2_ERROR_MODE: return "entry point not available in the handle's scaling mode";
         default: return "unknown error";
     }
 }
@@ -420,7 +458,9 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
     if (!ctx->staged &&
         cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess)
         return OZAKI2_ERROR_CUDA;
-    const size_t tb = (size_t)grouped_table_bytes(count, problems);
+    for (int i = 0; ctx->scaling == OZAKI2_SCALING_ACCURATE && i < count; ++i)
+        if (problems[i].k > OZAKI2_ACCURATE_MAX_K) return OZAKI2_ERROR_TOO_LARGE;
+    const size_t tb = (size_t)grouped_table_bytes(count, problems, ctx->scaling);
     char* ws = static_cast<char*>(ctx->ws);
     if (ctx->use_graphs) {
         for (auto& g : ctx->graphs)
@@ -458,7 +498,7 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
             return OZAKI2_ERROR_CUDA;
         }
         rc = launch_grouped(count, problems, static_cast<const char*>(g.tables), ctx->d_status,
-                            ctx->num_sms, ctx->chunk_k, ctx->capture_stream);
+                            ctx->num_sms, ctx->chunk_k, ctx->capture_stream, ctx->scaling);
         const cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (rc || ce != cudaSuccess ||
             cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
@@ -494,7 +534,7 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
                cudaEventRecord(ctx->staged, ctx->stream) != cudaSuccess))
         return OZAKI2_ERROR_CUDA;
     return launch_grouped(count, problems, tables_dev, ctx->d_status, ctx->num_sms,
-                          ctx->chunk_k, ctx->stream);
+                          ctx->chunk_k, ctx->stream, ctx->scaling);
 }
 
 int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
@@ -513,6 +553,7 @@ int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const doub
     if (rc) return rc;
     int64_t ls, es;
     rows_of_op(transA, lda, &ls, &es);
+    if (ctx->scaling == OZAKI2_SCALING_ACCURATE) return OZAKI2_ERROR_MODE;
     const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
     return cuda_rc(launch_scale(A, ls, es, m, k, pp, shifts, ctx->d_status, ctx->stream,
                                 ctx->scaling, T->delta));
@@ -534,9 +575,66 @@ int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const doub
     if (rc) return rc;
     int64_t ls, es;
     cols_of_op(transB, ldb, &ls, &es);
+    if (ctx->scaling == OZAKI2_SCALING_ACCURATE) return OZAKI2_ERROR_MODE;
     const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
     return cuda_rc(launch_scale(B, ls, es, n, k, pp, shifts, ctx->d_status, ctx->stream,
                                 ctx->scaling, T->delta));
+}
+
+int ozaki2_scale_accurate(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
+                          const double* A, int lda, const double* B, int ldb, int num_moduli,
+                          int* e, int* f, unsigned* cmax) {
+    if (!is_trans_char(transA)) return -2;
+    if (!is_trans_char(transB)) return -3;
+    if (m < 0) return -4;
+    if (n < 0) return -5;
+    if (k < 0) return -6;
+    const int arows = is_notrans(transA) ? m : k;
+    const int brows = is_notrans(transB) ? k : n;
+    if (m > 0 && k > 0 && !A) return -7;
+    if (lda < (arows > 1 ? arows : 1)) return -8;
+    if (k > 0 && n > 0 && !B) return -9;
+    if (ldb < (brows > 1 ? brows : 1)) return -10;
+    const ModTables* T = mod_tables(num_moduli);
+    if (!T) return -11;
+    if (m > 0 && !e) return -12;
+    if (n > 0 && !f) return -13;
+    if (k > OZAKI2_ACCURATE_MAX_K) return OZAKI2_ERROR_TOO_LARGE;
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    if (m == 0 && n == 0) return OZAKI2_SUCCESS;
+    // A-bar, B-bar and the maxima use the layout of a one-modulus product
+    const Layout L = make_layout(m, n, k, 1);
+    if ((rc = ensure_workspace(ctx, L.total))) return rc;
+    char* ws = static_cast<char*>(ctx->ws);
+    int64_t als, aes, bls, bes;
+    rows_of_op(transA, lda, &als, &aes);
+    cols_of_op(transB, ldb, &bls, &bes);
+    if (k == 0) {  // no products: every line is a zero line
+        if (m > 0 && cudaMemsetAsync(e, 0, sizeof(int) * (size_t)m, ctx->stream) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+        if (n > 0 && cudaMemsetAsync(f, 0, sizeof(int) * (size_t)n, ctx->stream) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+        if (cmax &&
+            cudaMemsetAsync(cmax, 0, sizeof(unsigned) * ((size_t)m + n), ctx->stream) !=
+                cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+        return OZAKI2_SUCCESS;
+    }
+    void* region = ws + L.off_res;
+    if ((rc = accurate_shifts(ctx, A, als, aes, B, bls, bes, m, n, k, L, *T, e, f, ws + L.off_pa,
+                              ws + L.off_pb, region)))
+        return rc;
+    if (cmax) {
+        const auto* src = static_cast<const uint32_t*>(region);
+        if ((m > 0 && cudaMemcpyAsync(cmax, src, sizeof(uint32_t) * (size_t)m,
+                                      cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) ||
+            (n > 0 && cudaMemcpyAsync(cmax + m, src + L.m_pad, sizeof(uint32_t) * (size_t)n,
+                                      cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess))
+            return OZAKI2_ERROR_CUDA;
+    }
+    return OZAKI2_SUCCESS;
 }
 
 static int convert_common(ozaki2_handle_t handle, bool is_a, char trans, int lines, int len,

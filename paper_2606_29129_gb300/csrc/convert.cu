@@ -3,9 +3,9 @@
 // K contiguous (the operand layout of the residue GEMM).
 //
 // Integer-only arithmetic.  The double's 53-bit mantissa M and its exponent give
-// |a'| = floor(M 2^sh) < 2^(bits(P)/2), held as L 21-bit limbs d_j (L = 3 for N <= 14, 4 up to
-// N = 20).  For an odd modulus, x = sum_j d_j (2^(21 j) mod p) < 2^31 and one Barrett step gives
-// |a'| mod p; the symmetric representative is negated for negative a'.  For p = 256 the residue
+// |a'| = floor(M 2^sh), held as L 21-bit limbs d_j (L = 1 for N <= 3, 2 up to N = 9, 3 up to
+// N = 14, 4 up to N = 20).  For an odd modulus, x = sum_j d_j (2^(21 j) mod p) < 2^31 and one
+// Barrett step gives |a'| mod p; the symmetric representative is negated for negative a'.  For p = 256 the residue
 // is the low byte of +-|a'| read as a signed byte ([-128, 127]).  Each small integer is exact in
 // bf16.  Kernels are instantiated per N so every per-modulus constant is an immediate operand.
 //
@@ -25,8 +25,10 @@ __host__ __device__ constexpr int p_bits(int N) {
                            88, 95, 103, 111, 118, 126, 133, 141, 148, 156};
     return b[N];
 }
-// 21-bit limbs covering |a'| <= sqrt((P-1)/2) < 2^(bits(P)/2), with one bit to spare.
-__host__ __device__ constexpr int limbs_for(int N) { return (p_bits(N) / 2 + 2 + 20) / 21; }
+// 21-bit limbs covering |a'|.  The proposed and fast scalings keep |a'| <= sqrt((P-1)/2) <
+// 2^(bits(P)/2); accurate mode allows up to 2^6 times more (|a| < 2^(E+1), mu' = 2^(5-E), and
+// the second factor is at most 2^P'), so floor(bits(P)/2) + 6 bits are provided.
+__host__ __device__ constexpr int limbs_for(int N) { return (p_bits(N) / 2 + 6 + 20) / 21; }
 
 struct Scaled {
     uint32_t d[4];
@@ -88,12 +90,35 @@ __device__ __forceinline__ uint32_t residue_bits(const Scaled& v, const ConvertT
     return small_int_bits(s);
 }
 
-// Writes the residues of 8 consecutive elements of one line into the N planes.
+// Accurate mode (Section 2.3): a-bar = ceil(2^(5 - E) |a|) <= 64 with E = floor(log2 max |a|) of
+// the line.  The power-of-two product is exact unless it underflows, and then the exact value
+// lies in (0, 1), whose ceiling is 1.
+__device__ __forceinline__ uint32_t bar_bits(double a, int E) {
+    const double x = fabs(a);
+    if (x == 0.0) return small_int_bits(0);
+    const double c = ceil(scalbn(x, 5 - E));
+    return small_int_bits(c < 1.0 ? 1 : (int)c);
+}
+
+// Writes the residues of 8 consecutive elements of one line into the N planes.  N = 1 is the
+// a-bar plane of accurate mode instead, with e the line's exponent code.
 template <int N>
 __device__ __forceinline__ void store_residues8(const double (&v)[8], int e, bool live,
                                                 const ConvertTables& t, __nv_bfloat16* planes,
                                                 int64_t plane_elems, int64_t offset,
                                                 unsigned* status) {
+    if constexpr (N == 1) {
+        const bool zero = !live || e == OZAKI2_SHIFT_NONFINITE || e == kAccuZeroLine;
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t a = zero ? 0u : bar_bits(v[2 * u], e);
+            const uint32_t b = zero ? 0u : bar_bits(v[2 * u + 1], e);
+            w[u] = __byte_perm(a, b, 0x7632);
+        }
+        *reinterpret_cast<uint4*>(planes + offset) = make_uint4(w[0], w[1], w[2], w[3]);
+        return;
+    }
     constexpr int L = limbs_for(N);
     Scaled sc[8];
     const bool zero = (e == OZAKI2_SHIFT_NONFINITE) || !live;
@@ -282,6 +307,20 @@ int convert_blocks(int lines, int64_t elem_stride, int rows_pad, int k_pad) {
     return (int)(((int64_t)rows_pad * (k_pad / 8) + 255) / 256);
 }
 
+cudaError_t launch_convert_bar(const double* X, int64_t line_stride, int64_t elem_stride,
+                               int lines, int len, const int* codes, void* plane, int rows_pad,
+                               int k_pad, unsigned* status, cudaStream_t stream) {
+    if (rows_pad <= 0 || k_pad <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ConvertTables t = {};
+    t.N = 1;
+    return launch_convert_n<1>(X, line_stride, elem_stride, lines, len, codes, t,
+                               static_cast<__nv_bfloat16*>(plane), rows_pad, k_pad, status, sms,
+                               stream);
+}
+
 cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const ConvertWork* work,
                                    int blocks, const ConvertTables& t, unsigned* status,
                                    cudaStream_t stream) {
@@ -291,6 +330,7 @@ cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const Conve
     case NN:                                                                                 \
         convert_grouped_kernel<NN><<<blocks, 256, 0, stream>>>(probs, work, t, status);      \
         break;
+        OZAKI2_CONVERT_GROUPED_CASE(1)  // the A-bar / B-bar planes of accurate mode
         OZAKI2_CONVERT_GROUPED_CASE(2) OZAKI2_CONVERT_GROUPED_CASE(3)
         OZAKI2_CONVERT_GROUPED_CASE(4) OZAKI2_CONVERT_GROUPED_CASE(5)
         OZAKI2_CONVERT_GROUPED_CASE(6) OZAKI2_CONVERT_GROUPED_CASE(7)

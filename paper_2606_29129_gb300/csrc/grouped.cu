@@ -54,6 +54,10 @@ struct Plan {
     std::vector<int> conv_n, conv_begin, conv_count;  // per distinct N: blocks in the table
     std::vector<int> crt_begin, crt_count;
     int total_tiles = 0;
+    // accurate mode: one auxiliary-product descriptor per problem (C-bar = A-bar B-bar)
+    bool accurate = false;
+    int64_t off_ga = 0;
+    int aux_tiles = 0;
 };
 
 int64_t problem_bytes(const ozaki2_problem& p) {
@@ -66,7 +70,9 @@ int64_t problem_bytes(const ozaki2_problem& p) {
            round_up64(N * m_pad * n_pad, 256);
 }
 
-void make_plan(int count, const ozaki2_problem* probs, Plan& P) {
+void make_plan(int count, const ozaki2_problem* probs, Plan& P,
+               int scaling = OZAKI2_SCALING_PROPOSED) {
+    P.accurate = scaling == OZAKI2_SCALING_ACCURATE;
     for (int i = 0; i < count; ++i)
         if (active(probs[i])) P.idx.push_back(i);
     // order by moduli count so that each conversion / CRT launch covers one contiguous range
@@ -105,6 +111,7 @@ void make_plan(int count, const ozaki2_problem* probs, Plan& P) {
         conv += cb;
         crt += rb;
         tiles += p.num_moduli * (int)(m_pad / 128) * (int)(n_pad / 256);
+        P.aux_tiles += (int)(m_pad / 128) * (int)(n_pad / 256);
     }
     P.n_scale = scale;
     P.n_conv = conv;
@@ -117,15 +124,20 @@ void make_plan(int count, const ozaki2_problem* probs, Plan& P) {
     P.off_sw = t;  t += round_up64((int64_t)scale * sizeof(ScaleWork), 256);
     P.off_cw = t;  t += round_up64((int64_t)conv * sizeof(ConvertWork), 256);
     P.off_rw = t;  t += round_up64((int64_t)crt * sizeof(CrtWork), 256);
+    if (P.accurate) {
+        P.off_ga = t;
+        t += round_up64(np * (int64_t)sizeof(GroupGemmProblem), 256);
+    }
     P.table_bytes = t;
 }
 
 }  // namespace
 
-// Bytes of workspace a grouped call needs (intermediates of every problem plus its tables).
+// Bytes of workspace a grouped call needs (intermediates of every problem plus its tables, sized
+// for the largest tables, those of accurate mode).
 size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs) {
     Plan P;
-    make_plan(count, probs, P);
+    make_plan(count, probs, P, OZAKI2_SCALING_ACCURATE);
     return (size_t)(P.ws_problems + P.table_bytes + 256);
 }
 
@@ -134,10 +146,12 @@ size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs) {
 int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char* host,
                          int chunk_k, int scaling) {
     Plan P;
-    make_plan(count, probs, P);
+    make_plan(count, probs, P, scaling);
     if (P.idx.empty()) return OZAKI2_SUCCESS;
     memset(host, 0, (size_t)P.table_bytes);
     auto* gg = reinterpret_cast<GroupGemmProblem*>(host + P.off_gg);
+    auto* ga = reinterpret_cast<GroupGemmProblem*>(host + P.off_ga);
+    int aux_begin = 0;
     auto* gp = reinterpret_cast<GroupProblem*>(host + P.off_gp);
     auto* sw = reinterpret_cast<ScaleWork*>(host + P.off_sw);
     auto* cw = reinterpret_cast<ConvertWork*>(host + P.off_cw);
@@ -183,6 +197,15 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
             return OZAKI2_ERROR_DRIVER;
         gg[a].tile_begin = tile_begin;
         tile_begin += p.num_moduli * gg[a].tiles_m * gg[a].tiles_n;
+        if (P.accurate) {
+            // A-bar / B-bar live in the first residue plane, the C-bar maxima in the product
+            // residues; both are overwritten later by the main stages
+            if (!make_group_aux_problem(&ga[a], (int)m_pad, (int)n_pad, (int)k_pad, g.pa, g.pb,
+                                        reinterpret_cast<uint32_t*>(g.res)))
+                return OZAKI2_ERROR_DRIVER;
+            ga[a].tile_begin = aux_begin;
+            aux_begin += ga[a].tiles_m * ga[a].tiles_n;
+        }
         for (int side = 0; side < 2; ++side) {
             const int lines = side ? p.n : p.m;
             for (int l0 = 0; l0 < lines; l0 += 128) sw[ns++] = ScaleWork{(int)a, side, l0};
@@ -198,9 +221,9 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
 
 // Launches every stage of a grouped call whose tables are already at `tables_dev`.
 int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_dev,
-                   unsigned* status, int num_sms, int chunk_k, cudaStream_t stream) {
+                   unsigned* status, int num_sms, int chunk_k, cudaStream_t stream, int scaling) {
     Plan P;
-    make_plan(count, probs, P);
+    make_plan(count, probs, P, scaling);
     // quick returns of inactive problems: C = beta C (m, n > 0)
     for (int i = 0; i < count; ++i) {
         const ozaki2_problem& p = probs[i];
@@ -216,6 +239,19 @@ int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_de
     const auto* drw = reinterpret_cast<const CrtWork*>(tables_dev + P.off_rw);
     if (launch_scale_grouped(dgp, dsw, P.n_scale, status, stream) != cudaSuccess)
         return OZAKI2_ERROR_CUDA;
+    if (P.accurate) {
+        // the first pass wrote the line exponents; A-bar and B-bar, the auxiliary product's
+        // maxima, then the shifts in place
+        if (launch_convert_grouped(1, dgp, dcw, P.n_conv, ConvertTables{}, status, stream) !=
+            cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+        const auto* dga = reinterpret_cast<const GroupGemmProblem*>(tables_dev + P.off_ga);
+        int rc = launch_aux_gemm_grouped(dga, (int)P.idx.size(), P.aux_tiles, status, num_sms,
+                                         stream);
+        if (rc) return rc;
+        if (launch_accu_shift_grouped(dgp, dsw, P.n_scale, stream) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+    }
     for (size_t g = 0; g < P.conv_n.size(); ++g)
         if (launch_convert_grouped(P.conv_n[g], dgp, dcw + P.conv_begin[g], P.conv_count[g],
                                    mod_tables(P.conv_n[g])->conv, status,
@@ -239,9 +275,9 @@ char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* 
     return ws + round_up64(P.ws_problems, 256);
 }
 
-int grouped_table_bytes(int count, const ozaki2_problem* probs) {
+int grouped_table_bytes(int count, const ozaki2_problem* probs, int scaling) {
     Plan P;
-    make_plan(count, probs, P);
+    make_plan(count, probs, P, scaling);
     return (int)P.table_bytes;
 }
 

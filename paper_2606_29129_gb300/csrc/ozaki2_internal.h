@@ -123,13 +123,35 @@ int convert_blocks(int lines, int64_t elem_stride, int rows_pad, int k_pad);
 
 // Grouped calls (grouped.cu).
 size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs);
-int grouped_table_bytes(int count, const ozaki2_problem* probs);
+int grouped_table_bytes(int count, const ozaki2_problem* probs,
+                        int scaling = OZAKI2_SCALING_PROPOSED);
 int grouped_check(int count, const ozaki2_problem* probs);
 int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char* host,
                          int chunk_k, int scaling = OZAKI2_SCALING_PROPOSED);
 int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_dev,
-                   unsigned* status, int num_sms, int chunk_k, cudaStream_t stream);
+                   unsigned* status, int num_sms, int chunk_k, cudaStream_t stream,
+                   int scaling = OZAKI2_SCALING_PROPOSED);
 char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* ws);
+
+// Accurate mode (scale.cu, convert.cu, residue_gemm.cu).
+// A-bar plane [rows_pad][k_pad] (bf16, K contiguous) from the exponent codes of the first pass.
+cudaError_t launch_convert_bar(const double* X, int64_t line_stride, int64_t elem_stride,
+                               int lines, int len, const int* codes, void* plane, int rows_pad,
+                               int k_pad, unsigned* status, cudaStream_t stream);
+// Row and column maxima of C-bar = A-bar B-bar into cmax[0, m_pad) and cmax[m_pad, m_pad+n_pad).
+int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const void* bar_a, const void* bar_b,
+                    uint32_t* cmax, unsigned* status, int num_sms, cudaStream_t stream);
+// Grouped form: one descriptor per problem (tensor maps over its A-bar / B-bar planes, the
+// maxima at `cmax`), and the persistent launch over all their tiles.
+bool make_group_aux_problem(GroupGemmProblem* g, int m_pad, int n_pad, int k_pad,
+                            const void* bar_a, const void* bar_b, uint32_t* cmax);
+int launch_aux_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
+                            unsigned* status, int num_sms, cudaStream_t stream);
+cudaError_t launch_accu_shift_grouped(const GroupProblem* probs, const ScaleWork* work,
+                                      int blocks, cudaStream_t stream);
+// Final shifts, in place over the exponent codes.
+cudaError_t launch_accu_shift(int* e, int m, int* f, int n, const uint32_t* cmax, int m_pad,
+                              float pprime, float delta, cudaStream_t stream);
 
 // Tables for 2 <= N <= 20 (cached, thread safe).  Returns nullptr for other N.
 const ModTables* mod_tables(int N);
@@ -138,6 +160,10 @@ const ModTables* mod_tables(int N);
 // Shifts for `lines` lines of length `len`.  Element h of line i is at
 //   X[i * line_stride + h * elem_stride]  with either line_stride == 1 (lines adjacent) or
 //   elem_stride == 1 (each line contiguous).
+// Accurate mode: the first scaling pass writes this code for a zero line (a real E is in
+// [-1074, 1023], OZAKI2_SHIFT_NONFINITE marks a non-finite line).
+constexpr int kAccuZeroLine = INT32_MAX;
+
 // scaling: OZAKI2_SCALING_PROPOSED (pprime = P'_prop) or OZAKI2_SCALING_FAST (pprime = P'_fast).
 cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                          int len, float pprime, int* shifts, unsigned* status,

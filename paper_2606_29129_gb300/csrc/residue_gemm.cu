@@ -317,13 +317,73 @@ struct GroupSource {
     }
 };
 
+// ---------------------------------------------------------------- accurate-mode epilogue
+// One chunk of the auxiliary product for the 32 rows of this warp (TMEM lane quarter q) and its
+// EPI_COLS columns from col0.  Intermediate chunks move x div 4096 into the carry columns;
+// the last one forms C-bar and merges the maxima.
+__device__ __forceinline__ void aux_epilogue(uint32_t taddr, const TileInfo& ti, int c, int q,
+                                             int lane, int col0) {
+    const uint32_t carry_addr = taddr + BN;
+    const bool last = c + 1 == ti.nchunks;
+    uint32_t row_max = 0;
+    uint32_t* mx = reinterpret_cast<uint32_t*>(ti.out);
+    const int64_t col_base = (int64_t)ti.nt * BN + col0;
+#pragma unroll 1
+    for (int col = 0; col < EPI_COLS; col += 32) {
+        uint32_t v[32], h[32];
+        tmem_ld32(taddr + col, v);
+        if (c > 0) {
+            tmem_ld32(carry_addr + col, h);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) h[j] = 0u;  // 0.0f
+        }
+        if (!last) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float x = __uint_as_float(v[j]);       // exact integer < 2^24
+                const float qq = truncf(x * (1.0f / 4096.0f));
+                v[j] = __float_as_uint(fmaf(-qq, 4096.0f, x));
+                h[j] = __float_as_uint(__uint_as_float(h[j]) + qq);
+            }
+            tmem_st32(taddr + col, v);
+            tmem_st32(carry_addr + col, h);
+        } else {
+            uint32_t mine = 0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t cbar = (uint32_t)__uint_as_float(h[j]) * 4096u +
+                                      (uint32_t)__uint_as_float(v[j]);
+                row_max = cbar > row_max ? cbar : row_max;
+                const uint32_t cm = __reduce_max_sync(0xffffffffu, cbar);
+                if (lane == j) mine = cm;
+            }
+            atomicMax(mx + ti.out_ld + col_base + col + lane, mine);
+        }
+    }
+    if (!last) {
+        tmem_wait_st();
+    } else {
+        const int64_t row = (int64_t)ti.mt * BM + q * 32 + lane;
+        atomicMax(mx + row, row_max);
+    }
+}
+
 // ---------------------------------------------------------------- the kernel body
 // Tiles t = blockIdx.x + i * gridDim.x of the source, taken two at a time: the two tiles of a
 // pair accumulate in the two TMEM buffers and their K chunks alternate (a tile with fewer chunks
 // simply drops out), so the reduction of one overlaps the MMAs of the other.
-template <class Src>
+//
+// AUX = true computes the auxiliary product C-bar = A-bar B-bar of accurate mode instead (one
+// plane of nonnegative integers <= 64, Section 2.3) and keeps only its row and column maxima:
+// tiles are taken one at a time, TMEM columns [BN, 2 BN) hold the carries of the exact sum
+// (after each chunk the accumulator x < 2^24 is split into x mod 4096, kept, and x div 4096,
+// added to the carry column), and the drain forms C-bar = 4096 carry + x as uint32 and merges
+// its row and column maxima into `out` (uint32 [rows_pad] then [cols_pad] from offset out_ld).
+template <class Src, bool AUX = false>
 __device__ __forceinline__ void residue_gemm_body(const Src& src, int total_tiles,
                                                   const GemmArgs& args) {
+    constexpr int PER = AUX ? 1 : 2;  // tiles in flight per CTA (TMEM accumulators in use)
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     uint8_t* smem = smem_raw + pad;
@@ -378,10 +438,11 @@ __device__ __forceinline__ void residue_gemm_body(const Src& src, int total_tile
         bool armed[STAGES];
         for (int s = 0; s < STAGES; ++s) armed[s] = false, armed_parity[s] = 0;
         bool ok = true;
-        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
-            const int npair = min(2, my_tiles - 2 * pr);
+        for (int pr = 0; ok && PER * pr < my_tiles; ++pr) {
+            const int npair = min(PER, my_tiles - PER * pr);
             TileInfo ti[2];
-            for (int s = 0; s < npair; ++s) ti[s] = src.get(blockIdx.x + (2 * pr + s) * gridDim.x);
+            for (int s = 0; s < npair; ++s)
+                ti[s] = src.get(blockIdx.x + (PER * pr + s) * gridDim.x);
             const int maxc = max(ti[0].nchunks, npair > 1 ? ti[1].nchunks : 0);
             for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
@@ -420,10 +481,11 @@ __device__ __forceinline__ void residue_gemm_body(const Src& src, int total_tile
         uint32_t phase = 0;
         uint32_t acc_cnt[2] = {0, 0};
         bool ok = true, issued = false;
-        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
-            const int npair = min(2, my_tiles - 2 * pr);
+        for (int pr = 0; ok && PER * pr < my_tiles; ++pr) {
+            const int npair = min(PER, my_tiles - PER * pr);
             TileInfo ti[2];
-            for (int s = 0; s < npair; ++s) ti[s] = src.get(blockIdx.x + (2 * pr + s) * gridDim.x);
+            for (int s = 0; s < npair; ++s)
+                ti[s] = src.get(blockIdx.x + (PER * pr + s) * gridDim.x);
             const int maxc = max(ti[0].nchunks, npair > 1 ? ti[1].nchunks : 0);
             for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
@@ -474,10 +536,11 @@ __device__ __forceinline__ void residue_gemm_body(const Src& src, int total_tile
         const uint32_t lane_base = ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
         uint32_t acc_cnt[2] = {0, 0};
         bool ok = true;
-        for (int pr = 0; ok && 2 * pr < my_tiles; ++pr) {
-            const int npair = min(2, my_tiles - 2 * pr);
+        for (int pr = 0; ok && PER * pr < my_tiles; ++pr) {
+            const int npair = min(PER, my_tiles - PER * pr);
             TileInfo ti[2];
-            for (int s = 0; s < npair; ++s) ti[s] = src.get(blockIdx.x + (2 * pr + s) * gridDim.x);
+            for (int s = 0; s < npair; ++s)
+                ti[s] = src.get(blockIdx.x + (PER * pr + s) * gridDim.x);
             const int maxc = max(ti[0].nchunks, npair > 1 ? ti[1].nchunks : 0);
             for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
@@ -495,7 +558,9 @@ __device__ __forceinline__ void residue_gemm_body(const Src& src, int total_tile
                     const uint32_t taddr = tmem_base + lane_base + (uint32_t)(s * BN);
                     const int l = ti[s].l;
                     const float p = args.ep.p[l], inv = args.ep.inv_p[l];
-                    if (c + 1 < ti[s].nchunks) {
+                    if (AUX) {
+                        aux_epilogue(taddr, ti[s], c, q, lane, col0);
+                    } else if (c + 1 < ti[s].nchunks) {
                         // in-place reduction modulo p: |r| <= ~0.52 p
 #pragma unroll 1
                         for (int col = 0; col < EPI_COLS; col += 32) {
@@ -569,6 +634,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                                 int total_tiles, const GemmArgs args) {
     const GroupSource src{probs, count};
     residue_gemm_body(src, total_tiles, args);
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    aux_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                    const __grid_constant__ CUtensorMap tmB, const GemmArgs args) {
+    const SingleSource src{&tmA, &tmB, &args};
+    residue_gemm_body<SingleSource, true>(src, args.total_tiles, args);
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    aux_gemm_grouped_kernel(const GroupGemmProblem* __restrict__ probs, int count,
+                            int total_tiles, const GemmArgs args) {
+    const GroupSource src{probs, count};
+    residue_gemm_body<GroupSource, true>(src, total_tiles, args);
 }
 
 // ---------------------------------------------------------------- the 2-SM kernel
@@ -902,6 +981,82 @@ int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int to
     const int grid = total_tiles < num_sms ? total_tiles : num_sms;
     residue_gemm_grouped_kernel<<<grid, NUM_THREADS, SMEM_BYTES, stream>>>(probs, count,
                                                                           total_tiles, a);
+    return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
+}
+
+// Products accumulated between carry passes of the auxiliary product: 63 x 64 x 64^2 plus a
+// kept remainder below 4096 stays under 2^24, where fp32 sums of integers are exact.
+constexpr int kAuxChunkBlocks = 63;
+
+int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const void* bar_a, const void* bar_b,
+                    uint32_t* cmax, unsigned* status, int num_sms, cudaStream_t stream) {
+    if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
+    if (cudaMemsetAsync(cmax, 0, sizeof(uint32_t) * ((size_t)m_pad + n_pad), stream) !=
+        cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    if (k_pad == 0) return OZAKI2_SUCCESS;
+    GemmArgs a = {};
+    a.k_blocks = k_pad / BK;
+    a.chunk_blocks = kAuxChunkBlocks;
+    a.nchunks = (a.k_blocks + kAuxChunkBlocks - 1) / kAuxChunkBlocks;
+    a.m_rows = m_pad;
+    a.out = reinterpret_cast<int8_t*>(cmax);
+    a.out_ld = m_pad;
+    a.out_plane = 0;
+    a.status = status;
+    CUtensorMap ta, tb;
+    if (!encode_planes(&ta, bar_a, 1, m_pad, k_pad, BM) ||
+        !encode_planes(&tb, bar_b, 1, n_pad, k_pad, BN))
+        return OZAKI2_ERROR_DRIVER;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(aux_gemm_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    a.tiles_m = m_pad / BM;
+    a.tiles_n = n_pad / BN;
+    a.total_tiles = a.tiles_m * a.tiles_n;
+    const int grid = a.total_tiles < num_sms ? a.total_tiles : num_sms;
+    aux_gemm_kernel<<<grid, NUM_THREADS, SMEM_BYTES, stream>>>(ta, tb, a);
+    return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
+}
+
+bool make_group_aux_problem(GroupGemmProblem* g, int m_pad, int n_pad, int k_pad,
+                            const void* bar_a, const void* bar_b, uint32_t* cmax) {
+    if (!encode_planes(&g->ta, bar_a, 1, m_pad, k_pad, BM) ||
+        !encode_planes(&g->tb, bar_b, 1, n_pad, k_pad, BN))
+        return false;
+    g->out = reinterpret_cast<int8_t*>(cmax);
+    g->out_ld = m_pad;  // the column maxima follow the m_pad row maxima
+    g->out_plane = 0;
+    g->tiles_m = m_pad / BM;
+    g->tiles_n = n_pad / BN;
+    g->k_blocks = k_pad / BK;
+    g->nchunks = (g->k_blocks + kAuxChunkBlocks - 1) / kAuxChunkBlocks;
+    g->tile_begin = 0;
+    return true;
+}
+
+int launch_aux_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
+                            unsigned* status, int num_sms, cudaStream_t stream) {
+    if (count <= 0 || total_tiles <= 0) return OZAKI2_SUCCESS;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(aux_gemm_grouped_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    GemmArgs a = {};
+    a.chunk_blocks = kAuxChunkBlocks;
+    a.status = status;
+    const int grid = total_tiles < num_sms ? total_tiles : num_sms;
+    aux_gemm_grouped_kernel<<<grid, NUM_THREADS, SMEM_BYTES, stream>>>(probs, count, total_tiles,
+                                                                      a);
     return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
 }
 

@@ -56,12 +56,44 @@ __device__ int alg1_shift(double a_norm, double a_max, float pprime_fast, float 
     return (int)floor(__dsub_rd((double)pprime_fast, mx)) - ilogb(a_max);
 }
 
-template <int SCALING>
-__device__ __forceinline__ int line_shift(double s, double mx, float pprime, float delta,
-                                          unsigned* status) {
-    if (SCALING == OZAKI2_SCALING_FAST) return alg1_shift(s, mx, pprime, delta, status);
-    return alg2_shift(s, pprime, status);
+// Accurate mode, first pass (Section 2.3): E = floor(log2 max_h |a_h|) of the line, from which
+// mu' = 2^(5 - E).  Returns E, kAccuZeroLine for a zero line, or OZAKI2_SHIFT_NONFINITE (and
+// raises the status flag) for a line with an Inf or NaN.  `mb` is the largest |a_h| as bits:
+// for nonnegative doubles the integer order is the value order, and NaN/Inf bits exceed every
+// finite value.
+__device__ __forceinline__ int accu_line_exponent(uint64_t mb, unsigned* status) {
+    if (mb >= 0x7FF0000000000000ull) {
+        atomicOr(status, OZAKI2_STATUS_NONFINITE);
+        return OZAKI2_SHIFT_NONFINITE;
+    }
+    if (mb == 0) return kAccuZeroLine;
+    return ilogb(__longlong_as_double((long long)mb));
 }
+
+// Running state of one line: the squared norm (proposed and fast modes), the maximum |a| as a
+// double (fast mode) or as bits (accurate mode).
+template <int SCALING>
+struct LineAcc {
+    double s = 0.0, mx = 0.0;
+    uint64_t mb = 0;
+    __device__ __forceinline__ void add(double v) {
+        if (SCALING == OZAKI2_SCALING_ACCURATE) {
+            const uint64_t b = (uint64_t)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+            mb = b > mb ? b : mb;
+        } else {
+            s = __fma_ru(v, v, s);
+            if (SCALING == OZAKI2_SCALING_FAST) mx = fmax(mx, fabs(v));
+        }
+    }
+    __device__ __forceinline__ int result(float pprime, float delta, unsigned* status) {
+        if (SCALING == OZAKI2_SCALING_ACCURATE) return accu_line_exponent(mb, status);
+        if (SCALING == OZAKI2_SCALING_FAST) {
+            if (isnan(s)) mx = s;  // fmax drops NaN; the norm keeps it
+            return alg1_shift(s, mx, pprime, delta, status);
+        }
+        return alg2_shift(s, pprime, status);
+    }
+};
 
 // Lines adjacent in memory (line_stride == 1): thread i walks line i in order; a warp reads 32
 // consecutive doubles per step, so every load is coalesced.  Loads run two batches of 16 ahead
@@ -73,7 +105,7 @@ __device__ __forceinline__ void scale_adjacent_line(const double* __restrict__ X
                                                     int i, int len, float pprime, float delta,
                                                     int* shifts, unsigned* status) {
     const double* p = X + i;
-    double s = 0.0, mx = 0.0;
+    LineAcc<SCALING> acc;
     const int full = len / kBatch * kBatch;
     double a[kBatch], b[kBatch];
     if (full > 0) {
@@ -87,10 +119,7 @@ __device__ __forceinline__ void scale_adjacent_line(const double* __restrict__ X
             for (int u = 0; u < kBatch; ++u) b[u] = __ldg(p + (int64_t)(h + kBatch + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            s = __fma_ru(a[u], a[u], s);
-            if (SCALING == OZAKI2_SCALING_FAST) mx = fmax(mx, fabs(a[u]));
-        }
+        for (int u = 0; u < kBatch; ++u) acc.add(a[u]);
         if (!has_b) break;
         if (h + 2 * kBatch < full) {
 #pragma unroll
@@ -98,18 +127,10 @@ __device__ __forceinline__ void scale_adjacent_line(const double* __restrict__ X
                 a[u] = __ldg(p + (int64_t)(h + 2 * kBatch + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            s = __fma_ru(b[u], b[u], s);
-            if (SCALING == OZAKI2_SCALING_FAST) mx = fmax(mx, fabs(b[u]));
-        }
+        for (int u = 0; u < kBatch; ++u) acc.add(b[u]);
     }
-    for (int h = full; h < len; ++h) {
-        const double v = __ldg(p + (int64_t)h * ld);
-        s = __fma_ru(v, v, s);
-        if (SCALING == OZAKI2_SCALING_FAST) mx = fmax(mx, fabs(v));
-    }
-    if (SCALING == OZAKI2_SCALING_FAST && isnan(s)) mx = s;
-    shifts[i] = line_shift<SCALING>(s, mx, pprime, delta, status);
+    for (int h = full; h < len; ++h) acc.add(__ldg(p + (int64_t)h * ld));
+    shifts[i] = acc.result(pprime, delta, status);
 }
 
 template <int SCALING>
@@ -144,7 +165,7 @@ __device__ __forceinline__ void scale_contiguous_warp(const double* __restrict__
             reg[r] = (r < nl && lane < cnt) ? __ldg(X + (int64_t)(line0 + r) * ld + h0 + lane)
                                             : 0.0;
     };
-    double s = 0.0, mx = 0.0;
+    LineAcc<SCALING> acc;
     if (len > 0) load(0);
     for (int h0 = 0; h0 < len; h0 += kTileLen) {
         const int cnt = min(kTileLen, len - h0);
@@ -153,16 +174,11 @@ __device__ __forceinline__ void scale_contiguous_warp(const double* __restrict__
         __syncwarp();
         if (h0 + kTileLen < len) load(h0 + kTileLen);
         if (lane < nl) {
-            for (int u = 0; u < cnt; ++u) {
-                const double v = t[lane][u];
-                s = __fma_ru(v, v, s);
-                if (SCALING == OZAKI2_SCALING_FAST) mx = fmax(mx, fabs(v));
-            }
+            for (int u = 0; u < cnt; ++u) acc.add(t[lane][u]);
         }
         __syncwarp();
     }
-    if (SCALING == OZAKI2_SCALING_FAST && isnan(s)) mx = s;
-    if (lane < nl) shifts[line0 + lane] = line_shift<SCALING>(s, mx, pprime, delta, status);
+    if (lane < nl) shifts[line0 + lane] = acc.result(pprime, delta, status);
 }
 
 template <int SCALING>
@@ -177,6 +193,24 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) scale_contiguous_kernel(
                                        tile[warp]);
 }
 
+template <int SCALING>
+__device__ __forceinline__ void scale_grouped_lines(const GroupProblem& P, const ScaleWork& w,
+                                                    const double* X, int64_t ls, int64_t es,
+                                                    int lines, int* shifts, unsigned* status,
+                                                    double (*tile)[32][kTileLen + 1]) {
+    if (es != 1 || ls == 1) {
+        const int i = w.line0 + (int)threadIdx.x;
+        if (i < lines)
+            scale_adjacent_line<SCALING>(X, es, i, P.k, P.pprime, P.delta, shifts, status);
+    } else {
+        const int warp = threadIdx.x >> 5;
+        const int line0 = w.line0 + 32 * warp;
+        if (line0 < lines)
+            scale_contiguous_warp<SCALING>(X, ls, lines, P.k, line0, P.pprime, P.delta, shifts,
+                                           status, tile[warp]);
+    }
+}
+
 // Grouped: each block takes 128 lines of one side of one problem (one thread per line for
 // adjacent lines, one warp per 32 lines for contiguous lines).
 __global__ void __launch_bounds__(128) scale_grouped_kernel(const GroupProblem* __restrict__ probs,
@@ -189,29 +223,23 @@ __global__ void __launch_bounds__(128) scale_grouped_kernel(const GroupProblem* 
     const int64_t ls = w.side ? P.b_ls : P.a_ls, es = w.side ? P.b_es : P.a_es;
     const int lines = w.side ? P.n : P.m;
     int* shifts = w.side ? P.f : P.e;
-    const bool fast = P.scaling == OZAKI2_SCALING_FAST;
-    if (es != 1 || ls == 1) {
+    if (P.scaling == OZAKI2_SCALING_ACCURATE) {
+        // clear this block's entries of the C-bar maxima (they live in the product residues)
+        uint32_t* cmax = reinterpret_cast<uint32_t*>(P.res);
         const int i = w.line0 + (int)threadIdx.x;
-        if (i < lines) {
-            if (fast)
-                scale_adjacent_line<OZAKI2_SCALING_FAST>(X, es, i, P.k, P.pprime, P.delta, shifts,
-                                                         status);
-            else
-                scale_adjacent_line<OZAKI2_SCALING_PROPOSED>(X, es, i, P.k, P.pprime, P.delta,
-                                                             shifts, status);
-        }
-    } else {
-        const int warp = threadIdx.x >> 5;
-        const int line0 = w.line0 + 32 * warp;
-        if (line0 < lines) {
-            if (fast)
-                scale_contiguous_warp<OZAKI2_SCALING_FAST>(X, ls, lines, P.k, line0, P.pprime,
-                                                           P.delta, shifts, status, tile[warp]);
-            else
-                scale_contiguous_warp<OZAKI2_SCALING_PROPOSED>(X, ls, lines, P.k, line0,
-                                                               P.pprime, P.delta, shifts, status,
-                                                               tile[warp]);
-        }
+        if (i < lines) cmax[(w.side ? P.m_pad : 0) + i] = 0u;
+    }
+    switch (P.scaling) {
+        case OZAKI2_SCALING_FAST:
+            scale_grouped_lines<OZAKI2_SCALING_FAST>(P, w, X, ls, es, lines, shifts, status, tile);
+            break;
+        case OZAKI2_SCALING_ACCURATE:
+            scale_grouped_lines<OZAKI2_SCALING_ACCURATE>(P, w, X, ls, es, lines, shifts, status,
+                                                         tile);
+            break;
+        default:
+            scale_grouped_lines<OZAKI2_SCALING_PROPOSED>(P, w, X, ls, es, lines, shifts, status,
+                                                         tile);
     }
 }
 
@@ -246,9 +274,69 @@ cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stri
     if (scaling == OZAKI2_SCALING_FAST)
         launch_scale_t<OZAKI2_SCALING_FAST>(X, line_stride, elem_stride, lines, len, pprime,
                                             delta, shifts, status, stream);
+    else if (scaling == OZAKI2_SCALING_ACCURATE)
+        launch_scale_t<OZAKI2_SCALING_ACCURATE>(X, line_stride, elem_stride, lines, len, pprime,
+                                                delta, shifts, status, stream);
     else
         launch_scale_t<OZAKI2_SCALING_PROPOSED>(X, line_stride, elem_stride, lines, len, pprime,
                                                 delta, shifts, status, stream);
+    return cudaGetLastError();
+}
+
+// ---- accurate mode, last pass: the shifts from E and the maxima of C-bar
+namespace {
+
+// log2 mu_i = 5 - E_i + floor(P'_accu - delta log2~(max_j c-bar_ij)) (eq. (mu_accu) with the
+// reading mu_i = mu'_i 2^floor(...)), log2~ of eq. (flog2) with the logarithm stand-in of
+// alg2_shift; the floor is of the exact value (delta * log2~ is exact in double, and so is the
+// difference).  A line whose c-bar maximum is 0 meets no nonzero product: OZAKI2_SHIFT_VANISH.
+__device__ __forceinline__ int accu_shift(int code, uint32_t cmax, float pprime, float delta) {
+    if (code == OZAKI2_SHIFT_NONFINITE) return code;
+    if (code == kAccuZeroLine) return 0;
+    if (cmax == 0) return OZAKI2_SHIFT_VANISH;
+    const int s = 31 - __clz(cmax);
+    const double xprime = scalbn((double)cmax, -s);           // [1, 2), exact
+    const float lg0 = __double2float_ru(log2((double)__double2float_ru(xprime)));
+    const float lg = __double2float_ru((double)lg0 + (double)s);
+    const double u = (double)delta * (double)lg;
+    return 5 - code + (int)floor(__dsub_rd((double)pprime, u));
+}
+
+__global__ void accu_shift_kernel(int* e, int m, int* f, int n, const uint32_t* __restrict__ cmax,
+                                  int m_pad, float pprime, float delta) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m) e[t] = accu_shift(e[t], cmax[t], pprime, delta);
+    else if (t < m + n) f[t - m] = accu_shift(f[t - m], cmax[m_pad + (t - m)], pprime, delta);
+}
+
+__global__ void accu_shift_grouped_kernel(const GroupProblem* __restrict__ probs,
+                                          const ScaleWork* __restrict__ work) {
+    const ScaleWork w = work[blockIdx.x];
+    const GroupProblem& P = probs[w.problem];
+    if (P.scaling != OZAKI2_SCALING_ACCURATE) return;
+    const int i = w.line0 + (int)threadIdx.x;
+    const uint32_t* cmax = reinterpret_cast<const uint32_t*>(P.res);
+    if (w.side == 0) {
+        if (i < P.m) P.e[i] = accu_shift(P.e[i], cmax[i], P.pprime, P.delta);
+    } else {
+        if (i < P.n) P.f[i] = accu_shift(P.f[i], cmax[P.m_pad + i], P.pprime, P.delta);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_accu_shift(int* e, int m, int* f, int n, const uint32_t* cmax, int m_pad,
+                              float pprime, float delta, cudaStream_t stream) {
+    if (m + n <= 0) return cudaSuccess;
+    accu_shift_kernel<<<(m + n + 255) / 256, 256, 0, stream>>>(e, m, f, n, cmax, m_pad, pprime,
+                                                              delta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accu_shift_grouped(const GroupProblem* probs, const ScaleWork* work,
+                                      int blocks, cudaStream_t stream) {
+    if (blocks <= 0) return cudaSuccess;
+    accu_shift_grouped_kernel<<<blocks, 128, 0, stream>>>(probs, work);
     return cudaGetLastError();
 }
 

@@ -23,12 +23,15 @@ ROWS_ALIGN_A = 128
 ROWS_ALIGN_B = 256
 K_ALIGN = 64
 SHIFT_NONFINITE = -(2**31)
+SHIFT_VANISH = -1100
+ACCURATE_MAX_K = 1048575
 ERROR_TOO_LARGE = 6
+ERROR_MODE = 7
 OPT_GEMM_VARIANT = 1
 OPT_CHUNK_K = 2
 OPT_GRAPH = 3
 OPT_SCALING = 4
-SCALING_PROPOSED, SCALING_FAST = 0, 1
+SCALING_PROPOSED, SCALING_FAST, SCALING_ACCURATE = 0, 1, 2
 GEMM_AUTO, GEMM_SINGLE, GEMM_PAIR = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -77,6 +80,8 @@ def lib() -> ctypes.CDLL:
                                i32],
             "ozaki2_scale_a": [vp, ch, i32, i32, vp, i32, i32, vp],
             "ozaki2_scale_b": [vp, ch, i32, i32, vp, i32, i32, vp],
+            "ozaki2_scale_accurate": [vp, ch, ch, i32, i32, i32, vp, i32, vp, i32, i32, vp, vp,
+                                      vp],
             "ozaki2_convert_a": [vp, ch, i32, i32, vp, i32, vp, i32, vp, i32, i32],
             "ozaki2_convert_b": [vp, ch, i32, i32, vp, i32, vp, i32, vp, i32, i32],
             "ozaki2_residue_gemm": [vp, i32, i32, i32, i32, vp, vp, vp],
@@ -237,6 +242,13 @@ def ozaki2_scale_a(transA, m, k, A, lda, num_moduli, shifts, handle=None) -> int
 def ozaki2_scale_b(transB, k, n, B, ldb, num_moduli, shifts, handle=None) -> int:
     return lib().ozaki2_scale_b(_h(handle), _ch(transB), k, n, _ptr(B), ldb, num_moduli,
                                 _ptr(shifts))
+
+
+def ozaki2_scale_accurate(transA, transB, m, n, k, A, lda, B, ldb, num_moduli, e, f, cmax=None,
+                          handle=None) -> int:
+    return lib().ozaki2_scale_accurate(_h(handle), _ch(transA), _ch(transB), m, n, k, _ptr(A),
+                                       lda, _ptr(B), ldb, num_moduli, _ptr(e), _ptr(f),
+                                       _ptr(cmax))
 
 
 def ozaki2_convert_a(transA, m, k, A, lda, shifts, num_moduli, planes, rows_pad, k_pad,

@@ -201,17 +201,29 @@ def test_torch_convenience(oz, orc):
     assert _gpu.same_bits(C.cpu().numpy().T, ref)
 
 
-@pytest.mark.parametrize("size", [8192, 16384])
-def test_full_size_sampled(oz, orc, size):
-    """The benchmark's problem (square, phi = 1, N = 14, one ozaki2_dgemm call): every row and
+FULL_CASES = [
+    # square (the benchmark's problem and the accuracy sweep's sizes, phi, scaled copies)
+    (8192, 8192, 8192, 14, 1.0, 1.0),
+    (16384, 16384, 16384, 16, 1.0, 1.0),
+    (16384, 16384, 16384, 16, 0.5, 2.0**40),
+    (8192, 8192, 8192, 20, 2.0, 3.7e-20),
+    # rectangular
+    (16384, 16384, 1024, 14, 1.0, 1.0),
+    (1024, 1024, 65536, 18, 1.0, 1.0),
+    (65536, 256, 4096, 14, 1.0, 1.0),
+    (65536, 256, 4096, 18, 1.0, 3.7e20),
+]
+
+
+@pytest.mark.parametrize("m,n,k,N,phi,alpha", FULL_CASES)
+def test_full_size_sampled(oz, orc, m, n, k, N, phi, alpha):
+    """Full sizes in the benchmark's launch configuration (one ozaki2_dgemm call): every row and
     column shift equals the oracle's, and a block of C with one row in every 128-row tile and
     one column in every 256-column tile is bit-identical to the oracle's."""
     import torch
 
-    m = n = k = size
-    N = 14
-    A = synthetic.paper_matrix_torch(m, k, 1.0, synthetic.seed_for(2, 1, 1))
-    B = synthetic.paper_matrix_torch(k, n, 1.0, synthetic.seed_for(2, 1, 2))
+    A = synthetic.paper_matrix_torch(m, k, phi, synthetic.seed_for(2, 1, 1)) * alpha
+    B = synthetic.paper_matrix_torch(k, n, phi, synthetic.seed_for(2, 1, 2)) * alpha
     C = torch.empty((n, m), dtype=torch.float64, device="cuda")
     _gpu.ok(oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N))
     e = torch.empty(m, dtype=torch.int32, device="cuda")
@@ -224,9 +236,13 @@ def test_full_size_sampled(oz, orc, size):
     f_ref, _ = orc.shifts_b(B_h, k, n, N)
     assert np.array_equal(e.cpu().numpy(), e_ref)
     assert np.array_equal(f.cpu().numpy(), f_ref)
-    rng = np.random.default_rng(size)
-    I = np.arange(0, m, 128) + rng.integers(0, 128, size=m // 128)
-    J = np.arange(0, n, 256) + rng.integers(0, 256, size=n // 256)
+    rng = np.random.default_rng(m + n + k)
+    I = np.minimum(np.arange(0, m, 128) + rng.integers(0, 128, size=(m + 127) // 128), m - 1)
+    J = np.minimum(np.arange(0, n, 256) + rng.integers(0, 256, size=(n + 255) // 256), n - 1)
+    if len(I) > 256:
+        I = np.sort(rng.choice(I, 256, replace=False))
     blk = orc.dgemm_block(A_h, B_h, m, n, k, N, I, J, e=e_ref, f=f_ref)
-    got = C.cpu().numpy()[np.ix_(J, I)]
+    Jd = torch.from_numpy(J.astype(np.int64)).cuda()
+    Id = torch.from_numpy(I.astype(np.int64)).cuda()
+    got = C[Jd][:, Id].cpu().numpy()
     assert _gpu.same_bits(got, blk)

@@ -31,7 +31,7 @@ def fast(oz):
 
 def test_scaling_option_values(oz):
     h = oz.Handle()
-    assert oz.lib().ozaki2_set_option(h.h, oz.OPT_SCALING, 2) == -3
+    assert oz.lib().ozaki2_set_option(h.h, oz.OPT_SCALING, 3) == -3
     assert oz.lib().ozaki2_set_option(h.h, oz.OPT_SCALING, -1) == -3
     assert oz.lib().ozaki2_set_option(h.h, oz.OPT_SCALING, oz.SCALING_FAST) == 0
     assert oz.lib().ozaki2_set_option(h.h, oz.OPT_SCALING, oz.SCALING_PROPOSED) == 0
