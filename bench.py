@@ -294,7 +294,7 @@ def run_gpu(args, world, rank, local):
         "stages_ms": stages,
         "roofline": roofline,
         "clocks": clk,
-        "gpu_launches": (10 if args.scaling == "accurate" else 6) * args.steps,
+        "gpu_launches": (9 if args.scaling == "accurate" else 5) * args.steps,
         "device_status": status,
         "e2e": e2e,
     }

@@ -168,10 +168,8 @@ int accurate_shifts(ozaki2_context* ctx, const double* A, int64_t als, int64_t a
     cudaStream_t st = ctx->stream;
     auto* cmax = static_cast<uint32_t*>(cmax_region);
     int rc;
-    if ((rc = cuda_rc(launch_scale(A, als, aes, m, k, T.pprime, e, ctx->d_status, st,
-                                   OZAKI2_SCALING_ACCURATE, T.delta))) ||
-        (rc = cuda_rc(launch_scale(B, bls, bes, n, k, T.pprime, f, ctx->d_status, st,
-                                   OZAKI2_SCALING_ACCURATE, T.delta))) ||
+    if ((rc = cuda_rc(launch_scale_pair(A, als, aes, m, B, bls, bes, n, k, T.pprime, T.delta, e,
+                                        f, ctx->d_status, st, OZAKI2_SCALING_ACCURATE))) ||
         (rc = cuda_rc(launch_convert_bar(A, als, aes, m, k, e, pa, (int)L.m_pad, (int)L.k_pad,
                                          ctx->d_status, st))) ||
         (rc = cuda_rc(launch_convert_bar(B, bls, bes, n, k, f, pb, (int)L.n_pad, (int)L.k_pad,
@@ -230,11 +228,8 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
             return rc;
     } else {
         const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
-        if ((rc = cuda_rc(launch_scale(A, als, aes, m, k, pp, e, ctx->d_status, st,
-                                       ctx->scaling, T->delta))))
-            return rc;
-        if ((rc = cuda_rc(launch_scale(B, bls, bes, n, k, pp, f, ctx->d_status, st,
-                                       ctx->scaling, T->delta))))
+        if ((rc = cuda_rc(launch_scale_pair(A, als, aes, m, B, bls, bes, n, k, pp, T->delta, e,
+                                            f, ctx->d_status, st, ctx->scaling))))
             return rc;
     }
     mark(1);

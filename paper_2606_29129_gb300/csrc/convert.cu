@@ -79,25 +79,38 @@ __device__ __forceinline__ uint32_t residue_bits(const Scaled& v, const ConvertT
         const uint32_t b = (v.neg ? 0u - v.low : v.low) & 0xFFu;
         return small_int_bits((int)(int8_t)(uint8_t)b);
     }
+    // Odd p, h = (p - 1)/2: t == |a'| (mod p), t < 2^31; x = t + h, or K p + h - t for a
+    // negative a' (K p >= 2^31 a multiple of p), so x == a' + h (mod p) with 0 <= x < 2^32.  One
+    // Barrett step leaves r in [0, 2p), one unsigned min brings it to [0, p), and r - h is the
+    // symmetric residue in [-h, h], written straight into the float bits.
     const uint32_t p = t.p[l];
-    uint32_t x = v.d[0];
+    uint32_t tt = v.d[0];
 #pragma unroll
-    for (int j = 1; j < L; ++j) x += v.d[j] * t.pow21[l][j];
+    for (int j = 1; j < L; ++j) tt += v.d[j] * t.pow21[l][j];
+    const uint32_t x = tt * (v.neg ? 0xFFFFFFFFu : 1u) + (v.neg ? t.off_neg[l] : t.off_pos[l]);
     uint32_t r = x - __umulhi(x, t.barrett[l]) * p;
-    if (r >= p) r -= p;
-    int s = (2 * r > p) ? (int)r - (int)p : (int)r;   // odd p: [-(p-1)/2, (p-1)/2]
-    s = v.neg ? -s : s;
-    return small_int_bits(s);
+    r = min(r, r - p);
+    return __float_as_uint(__uint_as_float(r + t.bias[l]) - 12582912.0f);
 }
 
 // Accurate mode (Section 2.3): a-bar = ceil(2^(5 - E) |a|) <= 64 with E = floor(log2 max |a|) of
-// the line.  The power-of-two product is exact unless it underflows, and then the exact value
-// lies in (0, 1), whose ceiling is 1.
+// the line, in integer arithmetic: |a| = M 2^(Ex - 1075) with the mantissa M (hidden bit
+// included for normal numbers), so 2^(5 - E) |a| = M 2^-rs with rs = 1070 + E - Ex, and the
+// ceiling is (M + 2^rs - 1) >> rs.  rs >= 47 for a normal a (a <= 2^(E+1)); a subnormal a in a
+// line of subnormals can give rs down to -5, a left shift of a small M.  For rs >= 64 the value
+// lies in (0, 1) and its ceiling is 1.
 __device__ __forceinline__ uint32_t bar_bits(double a, int E) {
-    const double x = fabs(a);
-    if (x == 0.0) return small_int_bits(0);
-    const double c = ceil(scalbn(x, 5 - E));
-    return small_int_bits(c < 1.0 ? 1 : (int)c);
+    const uint64_t bits = (uint64_t)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+    if (bits == 0) return small_int_bits(0);
+    int Ex = (int)(bits >> 52);
+    uint64_t M = bits & ((1ull << 52) - 1);
+    if (Ex) M |= 1ull << 52; else Ex = 1;
+    const int rs = 1070 + E - Ex;
+    uint32_t c;
+    if (rs >= 64) c = 1u;
+    else if (rs > 0) c = (uint32_t)((M + ((1ull << rs) - 1)) >> rs);
+    else c = (uint32_t)(M << -rs);
+    return small_int_bits((int)c);
 }
 
 // Writes the residues of 8 consecutive elements of one line into the N planes.  N = 1 is the

@@ -19,6 +19,9 @@ struct ConvertTables {
     uint32_t p[kMaxModuli];
     uint32_t barrett[kMaxModuli];   // floor(2^32 / p)
     uint32_t pow21[kMaxModuli][4];  // 2^(21 j) mod p
+    uint32_t off_pos[kMaxModuli];   // h = (p - 1) / 2
+    uint32_t off_neg[kMaxModuli];   // K p + h with K p the first multiple of p >= 2^31
+    uint32_t bias[kMaxModuli];      // float bits of 1.5 2^23, minus h
 };
 
 struct CrtTables {
@@ -160,6 +163,13 @@ const ModTables* mod_tables(int N);
 // Shifts for `lines` lines of length `len`.  Element h of line i is at
 //   X[i * line_stride + h * elem_stride]  with either line_stride == 1 (lines adjacent) or
 //   elem_stride == 1 (each line contiguous).
+// Shifts of the rows of op(A) (m lines) and the columns of op(B) (n lines), both of length len,
+// in one launch; strides as for launch_scale.
+cudaError_t launch_scale_pair(const double* A, int64_t a_ls, int64_t a_es, int m, const double* B,
+                              int64_t b_ls, int64_t b_es, int n, int len, float pprime,
+                              float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
+                              int scaling);
+
 // Accurate mode: the first scaling pass writes this code for a zero line (a real E is in
 // [-1074, 1023], OZAKI2_SHIFT_NONFINITE marks a non-finite line).
 constexpr int kAccuZeroLine = INT32_MAX;

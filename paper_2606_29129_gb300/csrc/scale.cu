@@ -211,6 +211,36 @@ __device__ __forceinline__ void scale_grouped_lines(const GroupProblem& P, const
     }
 }
 
+// Both operands of one product in one launch: blocks [0, blocks_a) take 128 rows of op(A) each,
+// the rest 128 columns of op(B), so the two matrices stream from HBM at the same time.
+struct ScaleSide {
+    const double* X;
+    int64_t ls, es;
+    int lines;
+    int* shifts;
+};
+
+template <int SCALING>
+__global__ void __launch_bounds__(128) scale_pair_kernel(ScaleSide a, ScaleSide b, int blocks_a,
+                                                         int len, float pprime, float delta,
+                                                         unsigned* status) {
+    __shared__ double tile[kWarpsPerBlock][32][kTileLen + 1];
+    const bool side_b = (int)blockIdx.x >= blocks_a;
+    const ScaleSide& S = side_b ? b : a;
+    const int line0 = ((int)blockIdx.x - (side_b ? blocks_a : 0)) * 128;
+    if (S.es != 1 || S.ls == 1) {
+        const int i = line0 + (int)threadIdx.x;
+        if (i < S.lines)
+            scale_adjacent_line<SCALING>(S.X, S.es, i, len, pprime, delta, S.shifts, status);
+    } else {
+        const int warp = threadIdx.x >> 5;
+        const int l0 = line0 + 32 * warp;
+        if (l0 < S.lines)
+            scale_contiguous_warp<SCALING>(S.X, S.ls, S.lines, len, l0, pprime, delta, S.shifts,
+                                           status, tile[warp]);
+    }
+}
+
 // Grouped: each block takes 128 lines of one side of one problem (one thread per line for
 // adjacent lines, one warp per 32 lines for contiguous lines).
 __global__ void __launch_bounds__(128) scale_grouped_kernel(const GroupProblem* __restrict__ probs,
@@ -280,6 +310,26 @@ cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stri
     else
         launch_scale_t<OZAKI2_SCALING_PROPOSED>(X, line_stride, elem_stride, lines, len, pprime,
                                                 delta, shifts, status, stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_pair(const double* A, int64_t a_ls, int64_t a_es, int m, const double* B,
+                              int64_t b_ls, int64_t b_es, int n, int len, float pprime,
+                              float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
+                              int scaling) {
+    const int blocks_a = (m + 127) / 128, blocks_b = (n + 127) / 128;
+    if (blocks_a + blocks_b == 0) return cudaSuccess;
+    const ScaleSide sa{A, a_ls, a_es, m, e}, sb{B, b_ls, b_es, n, f};
+    const int grid = blocks_a + blocks_b;
+    if (scaling == OZAKI2_SCALING_FAST)
+        scale_pair_kernel<OZAKI2_SCALING_FAST><<<grid, 128, 0, stream>>>(sa, sb, blocks_a, len,
+                                                                        pprime, delta, status);
+    else if (scaling == OZAKI2_SCALING_ACCURATE)
+        scale_pair_kernel<OZAKI2_SCALING_ACCURATE><<<grid, 128, 0, stream>>>(
+            sa, sb, blocks_a, len, pprime, delta, status);
+    else
+        scale_pair_kernel<OZAKI2_SCALING_PROPOSED><<<grid, 128, 0, stream>>>(
+            sa, sb, blocks_a, len, pprime, delta, status);
     return cudaGetLastError();
 }
 

@@ -101,6 +101,11 @@ void build(int N, ModTables& t) {
             for (int b = 0; b < 21 * j; ++b) v = (v * 2) % p;
             t.conv.pow21[l][j] = (uint32_t)v;
         }
+        const uint32_t h = (p - 1) / 2;
+        const uint64_t Kp = ((1ull << 31) + p - 1) / p * p;
+        t.conv.off_pos[l] = h;
+        t.conv.off_neg[l] = (uint32_t)(Kp + h);
+        t.conv.bias[l] = 0x4B400000u - h;
 
         t.crt.p[l] = p;
         t.crt.barrett[l] = (uint32_t)((1ull << 32) / p);
