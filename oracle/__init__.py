@@ -73,6 +73,7 @@ def lib():
         L.orc_accu_shift.restype = i32
         L.orc_accu_bar.argtypes = [i32, ch, i32, i32, P, i64, P, P, P]
         L.orc_accurate_shifts.argtypes = [ch, ch, i32, i32, i32, P, i64, P, i64, i32, P, P, P, P]
+        L.orc_sgemm.argtypes = [ch, ch, i32, i32, i32, f32, P, i64, P, i64, f32, P, i64, i32]
         _lib = L
     return _lib
 
@@ -344,3 +345,18 @@ def accurate_shifts(A, B, m, n, k, N, transA="N", transB="N", lda=None, ldb=None
     _ck(lib().orc_accurate_shifts(_b(transA), _b(transB), m, n, k, _p(A), lda, _p(B), ldb, N,
                                   _p(e), _p(f), _p(rm), _p(cm)))
     return e[:m], f[:n], rm[:m], cm[:n]
+
+
+# ---------------------------------------------------------------- SGEMM
+def sgemm(A, B, m, n, k, N, transA="N", transB="N", alpha=1.0, beta=0.0, Cin=None, lda=None,
+          ldb=None) -> np.ndarray:
+    """C = alpha op(A) op(B) + beta C in single precision through Ozaki scheme II; float32
+    column-major storage (n, m) returned."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    lda = lda if lda is not None else A.shape[-1]
+    ldb = ldb if ldb is not None else B.shape[-1]
+    C = np.zeros((n, m), np.float32) if Cin is None else np.array(Cin, dtype=np.float32, copy=True)
+    _ck(lib().orc_sgemm(_b(transA), _b(transB), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta,
+                        _p(C), max(m, 1), N))
+    return C

@@ -203,24 +203,26 @@ static i256 i256_rmod(i256 x, i256 P) {
 }
 
 /* Round a 256-bit integer to the nearest double, ties to even. */
-static double i256_to_double(i256 x) {
+/* x rounded to `bits` significant bits (ties to even), returned as a double (bits <= 53; the
+ * exponent is unbounded here, |x| < 2^255). */
+static double i256_round_bits(i256 x, int bits) {
     int neg = i256_is_neg(x);
     i256 a = i256_abs(x);
     int msb = u256_msb(a);
     double v;
     if (msb < 0) return 0.0;
-    if (msb <= 52) {
+    if (msb <= bits - 1) {
         v = (double)a.w[0];
     } else {
-        int shift = msb - 52;
+        int shift = msb - (bits - 1);
         i256 top = u256_shr(a, shift);
-        uint64_t mant = top.w[0]; /* 53 bits */
+        uint64_t mant = top.w[0]; /* `bits` bits */
         int half = u256_bit(a, shift - 1);
         int sticky = 0;
         for (int i = 0; i < shift - 1; ++i) sticky |= u256_bit(a, i);
         if (half && (sticky || (mant & 1u))) {
             mant += 1;
-            if (mant == (1ull << 53)) {
+            if (mant == (1ull << bits)) {
                 mant >>= 1;
                 shift += 1;
             }
@@ -229,6 +231,8 @@ static double i256_to_double(i256 x) {
     }
     return neg ? -v : v;
 }
+
+static double i256_to_double(i256 x) { return i256_round_bits(x, 53); }
 
 /* An integral double (|x| < 2^255) as a 256-bit integer. */
 static i256 i256_from_integral_double(double x) {
@@ -442,6 +446,22 @@ static double entry_output(i256 cpp, int e, int f, double alpha, double beta, do
     double y = ldexp(x, -(e + f));
     double out = alpha * y;
     if (beta != 0.0) out = out + beta * cin;
+    return out;
+}
+
+/* SGEMM output (reading of Step 4 for FP32, as R11 for FP64): x = C'' rounded to 24 bits,
+ * y = x 2^-(e+f) rounded once to single (the double carrier holds x and the product exactly,
+ * so the conversion to float is that one rounding, subnormal and overflow included), then
+ * alpha y (+ beta C) in single precision. */
+static float entry_output_float(i256 cpp, int e, int f, float alpha, float beta, float cin) {
+    if (e == ORC_SHIFT_NONFINITE || f == ORC_SHIFT_NONFINITE) return NAN;
+    double x = i256_round_bits(cpp, 24);
+    float y = (float)ldexp(x, -(e + f));
+    float out = alpha * y;
+    if (beta != 0.0f) {
+        float t = beta * cin;
+        out = out + t;
+    }
     return out;
 }
 
@@ -763,6 +783,68 @@ int orc_crt(int N, int m, int n, const int8_t* cres, const int* e, const int* f,
         }
     }
     return 0;
+}
+
+int orc_crt_float(int N, int m, int n, const int8_t* cres, const int* e, const int* f,
+                  float alpha, float beta, float* C, int64_t ldc) {
+    orc_consts c;
+    if (make_consts(N, &c)) return -1;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < n; ++j) {
+            int cl[ORC_MAX_MODULI];
+            for (int l = 0; l < N; ++l) cl[l] = cres[(int64_t)l * m * n + (int64_t)i * n + j];
+            i256 cpp = entry_crt(cl, &c);
+            float cin = beta != 0.0f ? C[i + (int64_t)j * ldc] : 0.0f;
+            C[i + (int64_t)j * ldc] = entry_output_float(cpp, e[i], f[j], alpha, beta, cin);
+        }
+    }
+    return 0;
+}
+
+/* SGEMM through Ozaki scheme II: every float is exactly a double, so Steps 1-3 and the
+ * scaling are those of the DGEMM on the widened inputs (the squared norms are the same upward
+ * rounded FP64 sums); only Step 4 rounds to single (entry_output_float). */
+int orc_sgemm(char transA, char transB, int m, int n, int k, float alpha, const float* A,
+              int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+              int N) {
+    if (N < 2 || N > ORC_MAX_MODULI || m < 0 || n < 0 || k < 0) return -1;
+    if (m == 0 || n == 0) return 0;
+    const int arows = (transA == 'N' || transA == 'n') ? m : k;
+    const int acols = (transA == 'N' || transA == 'n') ? k : m;
+    const int brows = (transB == 'N' || transB == 'n') ? k : n;
+    const int bcols = (transB == 'N' || transB == 'n') ? n : k;
+    double* Ad = (double*)malloc(sizeof(double) * (size_t)(lda * (acols ? acols : 1)));
+    double* Bd = (double*)malloc(sizeof(double) * (size_t)(ldb * (bcols ? bcols : 1)));
+    int* e = (int*)malloc(sizeof(int) * (size_t)m);
+    int* f = (int*)malloc(sizeof(int) * (size_t)n);
+    int8_t* RA = (int8_t*)malloc((size_t)N * m * (k ? k : 1));
+    int8_t* RB = (int8_t*)malloc((size_t)N * n * (k ? k : 1));
+    int8_t* cr = (int8_t*)malloc((size_t)N * m * n);
+    int rc = -2;
+    if (Ad && Bd && e && f && RA && RB && cr) {
+        for (int64_t c2 = 0; c2 < acols; ++c2)
+            for (int64_t r = 0; r < arows; ++r) Ad[r + c2 * lda] = (double)A[r + c2 * lda];
+        for (int64_t c2 = 0; c2 < bcols; ++c2)
+            for (int64_t r = 0; r < brows; ++r) Bd[r + c2 * ldb] = (double)B[r + c2 * ldb];
+        orc_shifts_mode(0, transA, m, k, Ad, lda, N, 0, e);
+        orc_shifts_mode(1, transB, n, k, Bd, ldb, N, 0, f);
+        orc_residues_a(transA, m, k, Ad, lda, e, N, RA);
+        orc_residues_b(transB, k, n, Bd, ldb, f, N, RB);
+        orc_residue_products(N, m, n, k, RA, RB, cr);
+        if (k == 0 || alpha == 0.0f) {
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < m; ++i) {
+                    float* p = &C[i + (int64_t)j * ldc];
+                    *p = beta == 0.0f ? 0.0f : beta * *p;
+                }
+            rc = 0;
+        } else {
+            rc = orc_crt_float(N, m, n, cr, e, f, alpha, beta, C, ldc);
+        }
+    }
+    free(Ad); free(Bd); free(e); free(f); free(RA); free(RB); free(cr);
+    return rc;
 }
 
 /* C'' = rmod(C', P) as 4 little-endian 64-bit words per entry, entry order i*n + j. */
