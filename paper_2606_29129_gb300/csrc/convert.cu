@@ -154,30 +154,59 @@ __device__ __forceinline__ void store_residues8(const double (&v)[8], int e, boo
 
 // Lines contiguous (elem_stride == 1): thread = (line, group of 8 elements); a warp covers 256
 // consecutive elements of one line, so loads and stores are both contiguous.
-template <int N>
+// Eight consecutive elements of one line as doubles (a float widens exactly); 16-byte vector
+// loads when the line start allows them.
+__device__ __forceinline__ void load8(const double* src, bool vec, double (&v)[8]) {
+    if (vec) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 d = __ldg(reinterpret_cast<const double2*>(src) + u);
+            v[2 * u] = d.x;
+            v[2 * u + 1] = d.y;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(src + u);
+    }
+}
+__device__ __forceinline__ void load8(const float* src, bool vec, double (&v)[8]) {
+    if (vec) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float4 d = __ldg(reinterpret_cast<const float4*>(src) + u);
+            v[4 * u] = d.x;
+            v[4 * u + 1] = d.y;
+            v[4 * u + 2] = d.z;
+            v[4 * u + 3] = d.w;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(src + u);
+    }
+}
+
+// T = double (DGEMM) or float (SGEMM).
+template <int N, typename T>
 __device__ __forceinline__ void convert_contiguous_item(
-    const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
+    const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
     int64_t g, unsigned* status) {
     const int groups = k_pad / 8;
     const int64_t plane_elems = (int64_t)rows_pad * k_pad;
-    const bool vec = ((ld & 1) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
+    constexpr int per16 = 16 / (int)sizeof(T);  // elements per 16 bytes
+    const bool vec = (ld % per16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
     {
         const int i = (int)(g / groups);
         const int h0 = (int)(g - (int64_t)i * groups) * 8;
         const bool row_live = i < lines;
         double v[8];
-        const double* src = X + (int64_t)i * ld + h0;
-        if (row_live && vec && h0 + 8 <= len) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double2 d = __ldg(reinterpret_cast<const double2*>(src) + u);
-                v[2 * u] = d.x;
-                v[2 * u + 1] = d.y;
-            }
+        const T* src = X + (int64_t)i * ld + h0;
+        if (row_live && h0 + 8 <= len) {
+            load8(src, vec, v);
         } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (row_live && h0 + u < len) ? __ldg(src + u) : 0.0;
+            for (int u = 0; u < 8; ++u)
+                v[u] = (row_live && h0 + u < len) ? (double)__ldg(src + u) : 0.0;
         }
         const int e = row_live ? shifts[i] : 0;
         store_residues8<N>(v, e, row_live, t, planes, plane_elems, (int64_t)i * k_pad + h0,
@@ -185,16 +214,16 @@ __device__ __forceinline__ void convert_contiguous_item(
     }
 }
 
-template <int N>
+template <int N, typename T>
 __global__ void __launch_bounds__(256) convert_contiguous_kernel(
-    const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
+    const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
     unsigned* status) {
     const int64_t total = (int64_t)rows_pad * (k_pad / 8);
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x)
-        convert_contiguous_item<N>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, g,
-                                   status);
+        convert_contiguous_item<N, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, g,
+                                      status);
 }
 
 // Lines adjacent (line_stride == 1): a block converts a tile of 64 lines x 64 elements.  The tile
@@ -205,9 +234,9 @@ constexpr int kTileLines = 64;
 constexpr int kTileK = 64;
 
 // Tile tt (64 lines x 64 elements) of an adjacent-line matrix; all 256 threads take part.
-template <int N>
+template <int N, typename T>
 __device__ __forceinline__ void convert_adjacent_tile(
-    const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
+    const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
     int64_t tt, double (*tile)[kTileLines + 1], unsigned* status) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -226,7 +255,7 @@ __device__ __forceinline__ void convert_adjacent_tile(
             for (int half = 0; half < 2; ++half) {
                 const int line = line0 + 32 * half + lane;
                 tile[hh][32 * half + lane] =
-                    (line < lines && h < len) ? __ldg(X + line + (int64_t)h * ld) : 0.0;
+                    (line < lines && h < len) ? (double)__ldg(X + line + (int64_t)h * ld) : 0.0;
             }
         }
         __syncthreads();
@@ -250,17 +279,17 @@ __device__ __forceinline__ void convert_adjacent_tile(
     }
 }
 
-template <int N>
+template <int N, typename T>
 __global__ void __launch_bounds__(256) convert_adjacent_kernel(
-    const double* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
+    const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
     unsigned* status) {
     __shared__ double tile[kTileK][kTileLines + 1];
     const int tiles_l = (rows_pad + kTileLines - 1) / kTileLines;
     const int64_t ntiles = (int64_t)tiles_l * (k_pad / kTileK);
     for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x)
-        convert_adjacent_tile<N>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, tt, tile,
-                                 status);
+        convert_adjacent_tile<N, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, tt,
+                                    tile, status);
 }
 
 // Grouped: each block converts one tile (adjacent lines) or 256 groups of 8 elements
@@ -279,18 +308,18 @@ __global__ void __launch_bounds__(256) convert_grouped_kernel(
     const int* shifts = w.side ? P.f : P.e;
     auto* planes = static_cast<__nv_bfloat16*>(w.side ? P.pb : P.pa);
     if (es != 1) {
-        convert_adjacent_tile<N>(X, es, lines, P.k, shifts, t, planes, rows_pad, P.k_pad, w.block,
-                                 tile, status);
+        convert_adjacent_tile<N, double>(X, es, lines, P.k, shifts, t, planes, rows_pad, P.k_pad,
+                                         w.block, tile, status);
     } else {
         const int64_t g = (int64_t)w.block * 256 + threadIdx.x;
         if (g < (int64_t)rows_pad * (P.k_pad / 8))
-            convert_contiguous_item<N>(X, ls, lines, P.k, shifts, t, planes, rows_pad, P.k_pad, g,
-                                       status);
+            convert_contiguous_item<N, double>(X, ls, lines, P.k, shifts, t, planes, rows_pad,
+                                               P.k_pad, g, status);
     }
 }
 
-template <int N>
-cudaError_t launch_convert_n(const double* X, int64_t line_stride, int64_t elem_stride,
+template <int N, typename T>
+cudaError_t launch_convert_n(const T* X, int64_t line_stride, int64_t elem_stride,
                              int lines, int len, const int* shifts, const ConvertTables& t,
                              __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
                              int sms, cudaStream_t stream) {
@@ -298,15 +327,16 @@ cudaError_t launch_convert_n(const double* X, int64_t line_stride, int64_t elem_
         const int64_t ntiles =
             (int64_t)((rows_pad + kTileLines - 1) / kTileLines) * (k_pad / kTileK);
         const int grid = (int)(ntiles < (int64_t)sms * 8 ? ntiles : (int64_t)sms * 8);
-        convert_adjacent_kernel<N><<<grid, 256, 0, stream>>>(X, elem_stride, lines, len, shifts,
-                                                             t, out, rows_pad, k_pad, status);
+        convert_adjacent_kernel<N, T><<<grid, 256, 0, stream>>>(X, elem_stride, lines, len,
+                                                                shifts, t, out, rows_pad, k_pad,
+                                                                status);
     } else {
         const int64_t total = (int64_t)rows_pad * (k_pad / 8);
         const int64_t blocks = (total + 255) / 256;
         const int grid = (int)(blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8);
-        convert_contiguous_kernel<N><<<grid, 256, 0, stream>>>(X, line_stride, lines, len,
-                                                               shifts, t, out, rows_pad, k_pad,
-                                                               status);
+        convert_contiguous_kernel<N, T><<<grid, 256, 0, stream>>>(X, line_stride, lines, len,
+                                                                  shifts, t, out, rows_pad,
+                                                                  k_pad, status);
     }
     return cudaGetLastError();
 }
@@ -320,18 +350,21 @@ int convert_blocks(int lines, int64_t elem_stride, int rows_pad, int k_pad) {
     return (int)(((int64_t)rows_pad * (k_pad / 8) + 255) / 256);
 }
 
-cudaError_t launch_convert_bar(const double* X, int64_t line_stride, int64_t elem_stride,
+cudaError_t launch_convert_bar(const void* X, int64_t line_stride, int64_t elem_stride,
                                int lines, int len, const int* codes, void* plane, int rows_pad,
-                               int k_pad, unsigned* status, cudaStream_t stream) {
+                               int k_pad, unsigned* status, cudaStream_t stream, bool f32) {
     if (rows_pad <= 0 || k_pad <= 0) return cudaSuccess;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     ConvertTables t = {};
     t.N = 1;
-    return launch_convert_n<1>(X, line_stride, elem_stride, lines, len, codes, t,
-                               static_cast<__nv_bfloat16*>(plane), rows_pad, k_pad, status, sms,
-                               stream);
+    auto* out = static_cast<__nv_bfloat16*>(plane);
+    if (f32)
+        return launch_convert_n<1>(static_cast<const float*>(X), line_stride, elem_stride, lines,
+                                   len, codes, t, out, rows_pad, k_pad, status, sms, stream);
+    return launch_convert_n<1>(static_cast<const double*>(X), line_stride, elem_stride, lines,
+                               len, codes, t, out, rows_pad, k_pad, status, sms, stream);
 }
 
 cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const ConvertWork* work,
@@ -360,14 +393,12 @@ cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const Conve
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
-                           int len, const int* shifts, const ConvertTables& t, void* planes,
-                           int rows_pad, int k_pad, unsigned* status, cudaStream_t stream) {
-    if (rows_pad <= 0 || k_pad <= 0) return cudaSuccess;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    auto* out = static_cast<__nv_bfloat16*>(planes);
+namespace {
+template <typename T>
+cudaError_t launch_convert_typed(const T* X, int64_t line_stride, int64_t elem_stride, int lines,
+                                 int len, const int* shifts, const ConvertTables& t,
+                                 __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
+                                 int sms, cudaStream_t stream) {
     switch (t.N) {
 #define OZAKI2_CONVERT_CASE(NN)                                                              \
     case NN:                                                                                 \
@@ -383,6 +414,23 @@ cudaError_t launch_convert(const double* X, int64_t line_stride, int64_t elem_st
 #undef OZAKI2_CONVERT_CASE
         default: return cudaErrorInvalidValue;
     }
+}
+}  // namespace
+
+cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stride, int lines,
+                           int len, const int* shifts, const ConvertTables& t, void* planes,
+                           int rows_pad, int k_pad, unsigned* status, cudaStream_t stream,
+                           bool f32) {
+    if (rows_pad <= 0 || k_pad <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto* out = static_cast<__nv_bfloat16*>(planes);
+    if (f32)
+        return launch_convert_typed(static_cast<const float*>(X), line_stride, elem_stride, lines,
+                                    len, shifts, t, out, rows_pad, k_pad, status, sms, stream);
+    return launch_convert_typed(static_cast<const double*>(X), line_stride, elem_stride, lines,
+                                len, shifts, t, out, rows_pad, k_pad, status, sms, stream);
 }
 
 }  // namespace ozaki2

@@ -138,9 +138,10 @@ char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* 
 
 // Accurate mode (scale.cu, convert.cu, residue_gemm.cu).
 // A-bar plane [rows_pad][k_pad] (bf16, K contiguous) from the exponent codes of the first pass.
-cudaError_t launch_convert_bar(const double* X, int64_t line_stride, int64_t elem_stride,
+cudaError_t launch_convert_bar(const void* X, int64_t line_stride, int64_t elem_stride,
                                int lines, int len, const int* codes, void* plane, int rows_pad,
-                               int k_pad, unsigned* status, cudaStream_t stream);
+                               int k_pad, unsigned* status, cudaStream_t stream,
+                               bool f32 = false);
 // Row and column maxima of C-bar = A-bar B-bar into cmax[0, m_pad) and cmax[m_pad, m_pad+n_pad).
 int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const void* bar_a, const void* bar_b,
                     uint32_t* cmax, unsigned* status, int num_sms, cudaStream_t stream);
@@ -165,10 +166,11 @@ const ModTables* mod_tables(int N);
 //   elem_stride == 1 (each line contiguous).
 // Shifts of the rows of op(A) (m lines) and the columns of op(B) (n lines), both of length len,
 // in one launch; strides as for launch_scale.
-cudaError_t launch_scale_pair(const double* A, int64_t a_ls, int64_t a_es, int m, const double* B,
+// f32: the matrices hold floats (SGEMM), else doubles.
+cudaError_t launch_scale_pair(const void* A, int64_t a_ls, int64_t a_es, int m, const void* B,
                               int64_t b_ls, int64_t b_es, int n, int len, float pprime,
                               float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
-                              int scaling);
+                              int scaling, bool f32 = false);
 
 // Accurate mode: the first scaling pass writes this code for a zero line (a real E is in
 // [-1074, 1023], OZAKI2_SHIFT_NONFINITE marks a non-finite line).
@@ -180,9 +182,11 @@ cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stri
                          cudaStream_t stream, int scaling = OZAKI2_SCALING_PROPOSED,
                          float delta = 0.0f);
 
-cudaError_t launch_convert(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
+// f32: X holds floats (SGEMM), else doubles.
+cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, const int* shifts, const ConvertTables& t, void* planes,
-                           int rows_pad, int k_pad, unsigned* status, cudaStream_t stream);
+                           int rows_pad, int k_pad, unsigned* status, cudaStream_t stream,
+                           bool f32 = false);
 
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
                         const void* planes_b, int8_t* out, const EpilogueTables& t,

@@ -100,14 +100,16 @@ struct LineAcc {
 // of the dependent FMA chain so that enough bytes are in flight with one thread per line.
 constexpr int kBatch = 16;
 
-template <int SCALING>
-__device__ __forceinline__ void scale_adjacent_line(const double* __restrict__ X, int64_t ld,
+// T = double (DGEMM) or float (SGEMM: every float is exactly a double, so the sums and the
+// shifts are those of the widened values).
+template <int SCALING, typename T = double>
+__device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int64_t ld,
                                                     int i, int len, float pprime, float delta,
                                                     int* shifts, unsigned* status) {
-    const double* p = X + i;
+    const T* p = X + i;
     LineAcc<SCALING> acc;
     const int full = len / kBatch * kBatch;
-    double a[kBatch], b[kBatch];
+    T a[kBatch], b[kBatch];
     if (full > 0) {
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) a[u] = __ldg(p + (int64_t)u * ld);
@@ -119,7 +121,7 @@ __device__ __forceinline__ void scale_adjacent_line(const double* __restrict__ X
             for (int u = 0; u < kBatch; ++u) b[u] = __ldg(p + (int64_t)(h + kBatch + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) acc.add(a[u]);
+        for (int u = 0; u < kBatch; ++u) acc.add((double)a[u]);
         if (!has_b) break;
         if (h + 2 * kBatch < full) {
 #pragma unroll
@@ -127,9 +129,9 @@ __device__ __forceinline__ void scale_adjacent_line(const double* __restrict__ X
                 a[u] = __ldg(p + (int64_t)(h + 2 * kBatch + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) acc.add(b[u]);
+        for (int u = 0; u < kBatch; ++u) acc.add((double)b[u]);
     }
-    for (int h = full; h < len; ++h) acc.add(__ldg(p + (int64_t)h * ld));
+    for (int h = full; h < len; ++h) acc.add((double)__ldg(p + (int64_t)h * ld));
     shifts[i] = acc.result(pprime, delta, status);
 }
 
@@ -149,28 +151,28 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kTileLen = 32;
 
 // Lines line0 .. line0 + 31 of a contiguous-line matrix, summed by one warp (t: its smem tile).
-template <int SCALING>
-__device__ __forceinline__ void scale_contiguous_warp(const double* __restrict__ X, int64_t ld,
+template <int SCALING, typename T = double>
+__device__ __forceinline__ void scale_contiguous_warp(const T* __restrict__ X, int64_t ld,
                                                       int lines, int len, int line0,
                                                       float pprime, float delta, int* shifts,
                                                       unsigned* status,
                                                       double (*t)[kTileLen + 1]) {
     const int lane = threadIdx.x & 31;
     const int nl = min(32, lines - line0);
-    double reg[32];
+    T reg[32];
     auto load = [&](int h0) {
         const int cnt = min(kTileLen, len - h0);
 #pragma unroll
         for (int r = 0; r < 32; ++r)
             reg[r] = (r < nl && lane < cnt) ? __ldg(X + (int64_t)(line0 + r) * ld + h0 + lane)
-                                            : 0.0;
+                                            : (T)0;
     };
     LineAcc<SCALING> acc;
     if (len > 0) load(0);
     for (int h0 = 0; h0 < len; h0 += kTileLen) {
         const int cnt = min(kTileLen, len - h0);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) t[r][lane] = reg[r];
+        for (int r = 0; r < 32; ++r) t[r][lane] = (double)reg[r];
         __syncwarp();
         if (h0 + kTileLen < len) load(h0 + kTileLen);
         if (lane < nl) {
@@ -214,30 +216,31 @@ __device__ __forceinline__ void scale_grouped_lines(const GroupProblem& P, const
 // Both operands of one product in one launch: blocks [0, blocks_a) take 128 rows of op(A) each,
 // the rest 128 columns of op(B), so the two matrices stream from HBM at the same time.
 struct ScaleSide {
-    const double* X;
+    const void* X;
     int64_t ls, es;
     int lines;
     int* shifts;
 };
 
-template <int SCALING>
+template <int SCALING, typename T>
 __global__ void __launch_bounds__(128) scale_pair_kernel(ScaleSide a, ScaleSide b, int blocks_a,
                                                          int len, float pprime, float delta,
                                                          unsigned* status) {
     __shared__ double tile[kWarpsPerBlock][32][kTileLen + 1];
     const bool side_b = (int)blockIdx.x >= blocks_a;
     const ScaleSide& S = side_b ? b : a;
+    const T* X = static_cast<const T*>(S.X);
     const int line0 = ((int)blockIdx.x - (side_b ? blocks_a : 0)) * 128;
     if (S.es != 1 || S.ls == 1) {
         const int i = line0 + (int)threadIdx.x;
         if (i < S.lines)
-            scale_adjacent_line<SCALING>(S.X, S.es, i, len, pprime, delta, S.shifts, status);
+            scale_adjacent_line<SCALING, T>(X, S.es, i, len, pprime, delta, S.shifts, status);
     } else {
         const int warp = threadIdx.x >> 5;
         const int l0 = line0 + 32 * warp;
         if (l0 < S.lines)
-            scale_contiguous_warp<SCALING>(S.X, S.ls, S.lines, len, l0, pprime, delta, S.shifts,
-                                           status, tile[warp]);
+            scale_contiguous_warp<SCALING, T>(X, S.ls, S.lines, len, l0, pprime, delta, S.shifts,
+                                              status, tile[warp]);
     }
 }
 
@@ -313,23 +316,35 @@ cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stri
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale_pair(const double* A, int64_t a_ls, int64_t a_es, int m, const double* B,
+template <typename T>
+static void launch_scale_pair_t(const ScaleSide& sa, const ScaleSide& sb, int blocks_a, int grid,
+                                int len, float pprime, float delta, unsigned* status,
+                                cudaStream_t stream, int scaling) {
+    if (scaling == OZAKI2_SCALING_FAST)
+        scale_pair_kernel<OZAKI2_SCALING_FAST, T><<<grid, 128, 0, stream>>>(
+            sa, sb, blocks_a, len, pprime, delta, status);
+    else if (scaling == OZAKI2_SCALING_ACCURATE)
+        scale_pair_kernel<OZAKI2_SCALING_ACCURATE, T><<<grid, 128, 0, stream>>>(
+            sa, sb, blocks_a, len, pprime, delta, status);
+    else
+        scale_pair_kernel<OZAKI2_SCALING_PROPOSED, T><<<grid, 128, 0, stream>>>(
+            sa, sb, blocks_a, len, pprime, delta, status);
+}
+
+cudaError_t launch_scale_pair(const void* A, int64_t a_ls, int64_t a_es, int m, const void* B,
                               int64_t b_ls, int64_t b_es, int n, int len, float pprime,
                               float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
-                              int scaling) {
+                              int scaling, bool f32) {
     const int blocks_a = (m + 127) / 128, blocks_b = (n + 127) / 128;
     if (blocks_a + blocks_b == 0) return cudaSuccess;
     const ScaleSide sa{A, a_ls, a_es, m, e}, sb{B, b_ls, b_es, n, f};
     const int grid = blocks_a + blocks_b;
-    if (scaling == OZAKI2_SCALING_FAST)
-        scale_pair_kernel<OZAKI2_SCALING_FAST><<<grid, 128, 0, stream>>>(sa, sb, blocks_a, len,
-                                                                        pprime, delta, status);
-    else if (scaling == OZAKI2_SCALING_ACCURATE)
-        scale_pair_kernel<OZAKI2_SCALING_ACCURATE><<<grid, 128, 0, stream>>>(
-            sa, sb, blocks_a, len, pprime, delta, status);
+    if (f32)
+        launch_scale_pair_t<float>(sa, sb, blocks_a, grid, len, pprime, delta, status, stream,
+                                   scaling);
     else
-        scale_pair_kernel<OZAKI2_SCALING_PROPOSED><<<grid, 128, 0, stream>>>(
-            sa, sb, blocks_a, len, pprime, delta, status);
+        launch_scale_pair_t<double>(sa, sb, blocks_a, grid, len, pprime, delta, status, stream,
+                                    scaling);
     return cudaGetLastError();
 }
 
