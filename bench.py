@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 SIZE = 16384
 PHI = 1.0
 NUM_MODULI = 16
+SGEMM_MODULI = 8
 METRIC = "Ozaki-II DGEMM effective TFLOPS at stated error vs cuBLAS DGEMM; p50/p99 lat"
 WORKLOAD = f"square FP64 GEMM m=n=k={SIZE}, phi={PHI}, N={NUM_MODULI} moduli"
 
@@ -147,7 +148,10 @@ def oracle_block_tflops(A_h, B_h, m, n, k, N, rows: int, cols: int):
     I = np.linspace(0, m - 1, rows).astype(np.int32)
     J = np.linspace(0, n - 1, cols).astype(np.int32)
     t0 = time.perf_counter()
-    oracle.dgemm_block(A_h, B_h, m, n, k, N, I, J)
+    if A_h.dtype == np.float32:
+        oracle.sgemm_block(A_h, B_h, k, N, I, J)
+    else:
+        oracle.dgemm_block(A_h, B_h, m, n, k, N, I, J)
     dt = time.perf_counter() - t0
     return 2.0 * rows * cols * k / dt / 1e12, dt
 
@@ -209,11 +213,15 @@ def run_gpu(args, world, rank, local):
     dev = torch.device("cuda", local)
     m = n = k = args.size
     N = args.moduli
+    f32 = args.dtype == "f32"
     seed_a = synthetic.seed_for(2, 1, 1) + 100 * rank
     seed_b = synthetic.seed_for(2, 1, 2) + 100 * rank
     A = synthetic.paper_matrix_torch(m, k, PHI, seed_a, device=dev)   # column-major m x k
     B = synthetic.paper_matrix_torch(k, n, PHI, seed_b, device=dev)   # column-major k x n
-    C = torch.empty((n, m), dtype=torch.float64, device=dev)
+    if f32:
+        A, B = A.float(), B.float()
+    C = torch.empty((n, m), dtype=A.dtype, device=dev)
+    gemm = oz.ozaki2_sgemm if f32 else oz.ozaki2_dgemm
     h = oz.Handle()
     h.set_timing(True)
     scaling = {"proposed": oz.SCALING_PROPOSED, "fast": oz.SCALING_FAST,
@@ -221,9 +229,9 @@ def run_gpu(args, world, rank, local):
     h.set_option(oz.OPT_SCALING, scaling)
 
     def step():
-        rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N, h)
+        rc = gemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N, h)
         if rc:
-            raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+            raise oz.Ozaki2Error(gemm.__name__, rc)
 
     for _ in range(args.warmup):
         step()
@@ -272,22 +280,25 @@ def run_gpu(args, world, rank, local):
     extra = {}
     if rank == 0:
         extra = accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np)
-    e2e = measure_e2e(args, oz, h, A, B, m, n, k, N, torch) if rank == 0 else None
+    e2e = measure_e2e(args, oz, h, A, B, m, n, k, N, torch, gemm) if rank == 0 else None
     if rank != 0:
         return
     clk = clocks.summary()
     line = {
-        "metric": METRIC, "value": value, "unit": "TFLOPS", "n_gpus": world,
+        "metric": METRIC if not f32 else METRIC.replace("DGEMM", "SGEMM"), "value": value,
+        "unit": "TFLOPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 emulated (bf16-held int8 residues on tcgen05, fp32 exact accumulate)",
+        "dtype": ("f32" if f32 else "f64") +
+                 " emulated (bf16-held int8 residues on tcgen05, fp32 exact accumulate)",
         "data": "synthetic",
-        "config": {"workload": f"square FP64 GEMM m=n=k={m}, phi={PHI}, N={N} moduli" +
+        "config": {"workload": f"square {'FP32' if f32 else 'FP64'} GEMM m=n=k={m}, phi={PHI}, "
+                               f"N={N} moduli" +
                    ("" if args.scaling == "proposed" else f", {args.scaling} scaling"),
                    "m": m, "n": n, "k": k, "phi": PHI,
                    "num_moduli": N, "scaling": args.scaling,
                    "parallelism": f"replicas x{world} (independent problems)",
-                   "l2": "inputs larger than L2 (A, B, C: 6 GiB)"},
+                   "l2": f"inputs larger than L2 (A, B, C: {3 * A.numel() * A.element_size() / 2**30:.0f} GiB)"},
         "latency_ms": {"p50": step_ms[len(step_ms) // 2],
                        "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
                        "min": step_ms[0], "max": step_ms[-1]},
@@ -309,13 +320,14 @@ def accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np):
 
     out = {}
     oracle.build()
+    f32 = A.dtype == torch.float32
     A_h = A.cpu().numpy()
     B_h = B.cpu().numpy()
     C_h = C.cpu().numpy()
     rng = np.random.default_rng(1)
     I = np.sort(rng.choice(m, size=args.err_block, replace=False)).astype(np.int32)
     J = np.sort(rng.choice(n, size=args.err_block, replace=False)).astype(np.int32)
-    hi, lo = oracle.dd_block(A_h, B_h, k, I, J)
+    hi, lo = oracle.dd_block(A_h.astype(np.float64), B_h.astype(np.float64), k, I, J)
     err, zeros = oracle.max_rel_error(C_h[np.ix_(J, I)], hi, lo)
     # cuBLAS DGEMM (native FP64) on the same inputs: C^T = B^T A^T in row-major terms
     At = A.view(k, m)    # row-major (k, m) = A^T
@@ -334,8 +346,8 @@ def accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np):
     cub_err, _ = oracle.max_rel_error(Cd.cpu().numpy()[np.ix_(J, I)], hi, lo)
     out["accuracy"] = {"max_rel_err": err, "zero_reference_entries": zeros,
                        "sample": f"{len(I)}x{len(J)} random block vs double-double"}
-    out["cublas_dgemm"] = {"tflops": 2.0 * m * n * k / (cub_ms * 1e-3) / 1e12, "ms": cub_ms,
-                           "max_rel_err": cub_err}
+    out["cublas_sgemm" if f32 else "cublas_dgemm"] = {
+        "tflops": 2.0 * m * n * k / (cub_ms * 1e-3) / 1e12, "ms": cub_ms, "max_rel_err": cub_err}
     if not args.no_cpu_baseline:
         tf, dt = oracle_block_tflops(A_h, B_h, m, n, k, N, args.cpu_block, args.cpu_block)
         out["cpu_baseline"] = {"value": tf, "unit": "TFLOPS", "cores": oracle.num_threads(),
@@ -345,21 +357,22 @@ def accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np):
     return out
 
 
-def measure_e2e(args, oz, h, A, B, m, n, k, N, torch):
+def measure_e2e(args, oz, h, A, B, m, n, k, N, torch, gemm=None):
     """The same metric through ozaki2_dgemm with host buffers: every step uploads its A and B
     from pinned host memory and downloads its C, all inside the timed region.  Steps are
     pipelined the way a caller would: two sets of device buffers, uploads on one stream,
     ozaki2_dgemm on the handle's stream, downloads on a third, ordered by events, so the copies
     of one step overlap the computation of its neighbours."""
-    A_h = torch.empty(A.shape, dtype=torch.float64, pin_memory=True)
-    B_h = torch.empty(B.shape, dtype=torch.float64, pin_memory=True)
-    C_h = [torch.empty((n, m), dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    gemm = gemm or oz.ozaki2_dgemm
+    A_h = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
+    B_h = torch.empty(B.shape, dtype=B.dtype, pin_memory=True)
+    C_h = [torch.empty((n, m), dtype=A.dtype, pin_memory=True) for _ in range(2)]
     A_h.copy_(A)
     B_h.copy_(B)
     dev = A.device
     dA = [torch.empty_like(A) for _ in range(2)]
     dB = [torch.empty_like(B) for _ in range(2)]
-    dC = [torch.empty((n, m), dtype=torch.float64, device=dev) for _ in range(2)]
+    dC = [torch.empty((n, m), dtype=A.dtype, device=dev) for _ in range(2)]
     s_up = torch.cuda.Stream(device=dev)
     s_comp = torch.cuda.Stream(device=dev)
     s_down = torch.cuda.Stream(device=dev)
@@ -383,10 +396,9 @@ def measure_e2e(args, oz, h, A, B, m, n, k, N, torch):
         with torch.cuda.stream(s_comp):
             s_comp.wait_event(uploaded[b])
             s_comp.wait_event(downloaded[b])
-            rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, dA[b], m, dB[b], k, 0.0, dC[b], m, N,
-                                 h)
+            rc = gemm("N", "N", m, n, k, 1.0, dA[b], m, dB[b], k, 0.0, dC[b], m, N, h)
             if rc:
-                raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+                raise oz.Ozaki2Error(gemm.__name__, rc)
             consumed[b].record(s_comp)
             computed[b].record(s_comp)
         with torch.cuda.stream(s_down):
@@ -405,8 +417,8 @@ def measure_e2e(args, oz, h, A, B, m, n, k, N, torch):
     ms = (time.perf_counter() - t0) * 1e3 / reps
     h.set_timing(True)
     return {"value": 2.0 * m * n * k / (ms * 1e-3) / 1e12, "unit": "TFLOPS",
-            "h2d_bytes_per_step": A.numel() * 8 + B.numel() * 8,
-            "d2h_bytes_per_step": m * n * 8, "ms_per_step": ms, "steps": reps,
+            "h2d_bytes_per_step": (A.numel() + B.numel()) * A.element_size(),
+            "d2h_bytes_per_step": m * n * A.element_size(), "ms_per_step": ms, "steps": reps,
             "pipelining": "double-buffered: uploads, compute and downloads on three streams",
             "clock": "host wall clock around the steps, synchronised on both sides"}
 
@@ -629,9 +641,10 @@ def run_serve(args):
 
 
 def run_sweep(args):
-    """Accuracy sweep: max relative error vs the double-double reference for N = 8..20, phi in
-    {0.5, 1, 2} and the copies scaled by 2^+-40 and 3.7e+-20, beside cuBLAS DGEMM on the same
-    inputs.  One JSON line per (size, phi, alpha)."""
+    """Accuracy sweep: max relative error vs the double-double reference for each N, phi and
+    scaled copy, beside cuBLAS on the same inputs.  f64: N = 8..20, phi in {0.5, 1, 2}, copies
+    scaled by 2^+-40 and 3.7e+-20.  f32 (SGEMM): N = 3..12, phi in {0, 0.5, 1, 1.5} (the paper's
+    SGEMM ranges), copies scaled by 2^+-20.  One JSON line per (size, phi, alpha)."""
     import numpy as np
     import torch
 
@@ -641,34 +654,44 @@ def run_sweep(args):
 
     oracle.build()
     torch.backends.cuda.matmul.allow_tf32 = False
+    f32 = args.dtype == "f32"
+    moduli = range(3, 13) if f32 else range(8, 21)
+    phis = (0.0, 0.5, 1.0, 1.5) if f32 else (0.5, 1.0, 2.0)
+    alphas = (1.0, 2.0**20, 2.0**-20) if f32 else (1.0, 2.0**40, 2.0**-40, 3.7e20, 3.7e-20)
+    gemm = oz.ozaki2_sgemm if f32 else oz.ozaki2_dgemm
     for size in args.sweep_sizes:
         m = n = k = size
-        for pi, phi in enumerate((0.5, 1.0, 2.0)):
+        for pi, phi in enumerate(phis):
             A0 = synthetic.paper_matrix_torch(m, k, phi, synthetic.seed_for(2, pi, 1))
             B0 = synthetic.paper_matrix_torch(k, n, phi, synthetic.seed_for(2, pi, 2))
+            if f32:
+                A0, B0 = A0.float(), B0.float()
             rng = np.random.default_rng(size + pi)
             I = np.sort(rng.choice(m, size=args.err_block, replace=False)).astype(np.int32)
             J = np.sort(rng.choice(n, size=args.err_block, replace=False)).astype(np.int32)
-            for alpha in (1.0, 2.0**40, 2.0**-40, 3.7e20, 3.7e-20):
+            for alpha in alphas:
                 A = A0 * alpha
                 B = B0 * alpha
-                A_h, B_h = A.cpu().numpy(), B.cpu().numpy()
+                A_h = A.cpu().numpy().astype(np.float64)
+                B_h = B.cpu().numpy().astype(np.float64)
                 hi, lo = oracle.dd_block(A_h, B_h, k, I, J)
-                C = torch.empty((n, m), dtype=torch.float64, device="cuda")
+                C = torch.empty((n, m), dtype=A.dtype, device="cuda")
                 errs = {}
-                for N in range(8, 21):
-                    rc = oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N)
+                for N in moduli:
+                    rc = gemm("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m, N)
                     if rc:
-                        raise oz.Ozaki2Error("ozaki2_dgemm", rc)
+                        raise oz.Ozaki2Error(gemm.__name__, rc)
                     torch.cuda.synchronize()
-                    errs[N] = oracle.max_rel_error(C.cpu().numpy()[np.ix_(J, I)], hi, lo)[0]
+                    errs[N] = oracle.max_rel_error(
+                        C.cpu().numpy()[np.ix_(J, I)].astype(np.float64), hi, lo)[0]
                 Cd = torch.matmul(B.view(n, k), A.view(k, m))
                 torch.cuda.synchronize()
-                cub = oracle.max_rel_error(Cd.cpu().numpy()[np.ix_(J, I)], hi, lo)[0]
-                default = next((N for N in range(8, 21) if errs[N] <= cub), None)
-                print(json.dumps({"size": size, "phi": phi, "alpha": alpha,
+                cub = oracle.max_rel_error(Cd.cpu().numpy()[np.ix_(J, I)].astype(np.float64),
+                                           hi, lo)[0]
+                default = next((N for N in moduli if errs[N] <= cub), None)
+                print(json.dumps({"dtype": args.dtype, "size": size, "phi": phi, "alpha": alpha,
                                   "sample": f"{len(I)}x{len(J)}", "max_rel_err": errs,
-                                  "cublas_dgemm": cub, "smallest_N_not_worse": default}),
+                                  "cublas": cub, "smallest_N_not_worse": default}),
                       flush=True)
                 del A, B, C, Cd
             del A0, B0
@@ -786,7 +809,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=SIZE)
-    ap.add_argument("--moduli", type=int, default=NUM_MODULI)
+    ap.add_argument("--moduli", type=int, default=None,
+                    help=f"moduli count (default {NUM_MODULI} for f64, {SGEMM_MODULI} for f32)")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"],
+                    help="f64: emulated DGEMM (the benchmark); f32: emulated SGEMM")
     ap.add_argument("--scaling", default="proposed", choices=["proposed", "fast", "accurate"],
                     help="scaling step: Algorithm 2 (default), Algorithm 1, or accurate mode")
     ap.add_argument("--err-block", type=int, default=96)
@@ -818,6 +844,8 @@ def main():
                     help="fast mode (Algorithm 1) against the proposed scaling over alpha = 2^s")
     ap.add_argument("--study-sizes", type=int, nargs="+", default=[1024, 16384])
     args = ap.parse_args()
+    if args.moduli is None:
+        args.moduli = SGEMM_MODULI if args.dtype == "f32" else NUM_MODULI
     if args.sweep:
         run_sweep(args)
         return

@@ -121,7 +121,7 @@ size_t ozaki2_workspace_size(int m, int n, int k, int num_moduli);
 int ozaki2_get_status(ozaki2_handle_t handle, unsigned* flags);
 
 /* Stage timing: with on = 1 the handle records CUDA events on its stream around the stages of
- * each later ozaki2_dgemm_h / ozaki2_dgemm call (scaling of A and B, conversion of A and B,
+ * each later ozaki2_dgemm_h / ozaki2_dgemm / ozaki2_sgemm_h call (scaling of A and B, conversion of A and B,
  * residue GEMMs, CRT); on = 0 stops.  Costs four event records per call. */
 int ozaki2_set_timing(ozaki2_handle_t handle, int on);
 
@@ -153,6 +153,22 @@ int ozaki2_dgemm(char transA, char transB, int m, int n, int k, double alpha, co
 int ozaki2_dgemm_h(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
                    double alpha, const double* A, int lda, const double* B, int ldb,
                    double beta, double* C, int ldc, int num_moduli);
+
+/* Emulated SGEMM (the single-precision case of Section 5): the same steps on FP32 operands and
+ * result.  Every float is exactly a double, so the scaling and the integer stages are those of
+ * ozaki2_dgemm on the widened inputs; Step 4 rounds C'' once to 24 bits, scales it by
+ * 2^-(e_i + f_j) with one rounding to single (subnormal results and overflow to infinity
+ * included), and applies alpha and beta in single precision.  Same conventions, quick returns,
+ * options (OZAKI2_OPT_SCALING included) and argument numbers as ozaki2_dgemm; the workspace is
+ * that of ozaki2_dgemm for the same sizes. */
+int ozaki2_sgemm(char transA, char transB, int m, int n, int k, float alpha, const float* A,
+                 int lda, const float* B, int ldb, float beta, float* C, int ldc,
+                 int num_moduli);
+
+/* Same as ozaki2_sgemm on an explicit handle (argument numbers shift by one). */
+int ozaki2_sgemm_h(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
+                   float alpha, const float* A, int lda, const float* B, int ldb, float beta,
+                   float* C, int ldc, int num_moduli);
 
 /* ---- many independent problems at once ---------------------------------------------------- */
 /* One problem of a grouped call: the arguments of ozaki2_dgemm. */

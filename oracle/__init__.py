@@ -74,6 +74,10 @@ def lib():
         L.orc_accu_bar.argtypes = [i32, ch, i32, i32, P, i64, P, P, P]
         L.orc_accurate_shifts.argtypes = [ch, ch, i32, i32, i32, P, i64, P, i64, i32, P, P, P, P]
         L.orc_sgemm.argtypes = [ch, ch, i32, i32, i32, f32, P, i64, P, i64, f32, P, i64, i32]
+        L.orc_sgemm_block.argtypes = [ch, ch, i32, f32, P, i64, P, i64, f32, P, i32, i32, P, i32,
+                                      P, P, P, P]
+        L.orc_sgemm_mode.argtypes = [ch, ch, i32, i32, i32, f32, P, i64, P, i64, f32, P, i64,
+                                     i32, i32]
         _lib = L
     return _lib
 
@@ -349,7 +353,7 @@ def accurate_shifts(A, B, m, n, k, N, transA="N", transB="N", lda=None, ldb=None
 
 # ---------------------------------------------------------------- SGEMM
 def sgemm(A, B, m, n, k, N, transA="N", transB="N", alpha=1.0, beta=0.0, Cin=None, lda=None,
-          ldb=None) -> np.ndarray:
+          ldb=None, mode=PROPOSED_MODE) -> np.ndarray:
     """C = alpha op(A) op(B) + beta C in single precision through Ozaki scheme II; float32
     column-major storage (n, m) returned."""
     A = np.ascontiguousarray(A, dtype=np.float32)
@@ -357,6 +361,25 @@ def sgemm(A, B, m, n, k, N, transA="N", transB="N", alpha=1.0, beta=0.0, Cin=Non
     lda = lda if lda is not None else A.shape[-1]
     ldb = ldb if ldb is not None else B.shape[-1]
     C = np.zeros((n, m), np.float32) if Cin is None else np.array(Cin, dtype=np.float32, copy=True)
-    _ck(lib().orc_sgemm(_b(transA), _b(transB), m, n, k, alpha, _p(A), lda, _p(B), ldb, beta,
-                        _p(C), max(m, 1), N))
+    _ck(lib().orc_sgemm_mode(_b(transA), _b(transB), m, n, k, alpha, _p(A), lda, _p(B), ldb,
+                             beta, _p(C), max(m, 1), N, mode))
     return C
+
+
+def sgemm_block(A, B, k, N, I, J, transA="N", transB="N", alpha=1.0, beta=0.0, Cin_block=None,
+                e=None, f=None, lda=None, ldb=None) -> np.ndarray:
+    """C(I, J) of the emulated SGEMM as float32 of shape (len(J), len(I)); shifts e/f (per row
+    of op(A) / column of op(B), full length) are used when given."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    lda = lda if lda is not None else A.shape[-1]
+    ldb = ldb if ldb is not None else B.shape[-1]
+    I = np.ascontiguousarray(I, np.int32)
+    J = np.ascontiguousarray(J, np.int32)
+    out = np.zeros((len(J), len(I)), np.float32)
+    cin = None if Cin_block is None else np.ascontiguousarray(Cin_block, np.float32)
+    e = None if e is None else np.ascontiguousarray(e, np.int32)
+    f = None if f is None else np.ascontiguousarray(f, np.int32)
+    _ck(lib().orc_sgemm_block(_b(transA), _b(transB), k, alpha, _p(A), lda, _p(B), ldb, beta,
+                              _p(cin), N, len(I), _p(I), len(J), _p(J), _p(e), _p(f), _p(out)))
+    return out

@@ -805,9 +805,9 @@ int orc_crt_float(int N, int m, int n, const int8_t* cres, const int* e, const i
 /* SGEMM through Ozaki scheme II: every float is exactly a double, so Steps 1-3 and the
  * scaling are those of the DGEMM on the widened inputs (the squared norms are the same upward
  * rounded FP64 sums); only Step 4 rounds to single (entry_output_float). */
-int orc_sgemm(char transA, char transB, int m, int n, int k, float alpha, const float* A,
-              int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
-              int N) {
+int orc_sgemm_mode(char transA, char transB, int m, int n, int k, float alpha, const float* A,
+                   int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                   int N, int mode) {
     if (N < 2 || N > ORC_MAX_MODULI || m < 0 || n < 0 || k < 0) return -1;
     if (m == 0 || n == 0) return 0;
     const int arows = (transA == 'N' || transA == 'n') ? m : k;
@@ -827,8 +827,16 @@ int orc_sgemm(char transA, char transB, int m, int n, int k, float alpha, const 
             for (int64_t r = 0; r < arows; ++r) Ad[r + c2 * lda] = (double)A[r + c2 * lda];
         for (int64_t c2 = 0; c2 < bcols; ++c2)
             for (int64_t r = 0; r < brows; ++r) Bd[r + c2 * ldb] = (double)B[r + c2 * ldb];
-        orc_shifts_mode(0, transA, m, k, Ad, lda, N, 0, e);
-        orc_shifts_mode(1, transB, n, k, Bd, ldb, N, 0, f);
+        if (mode == 2) {
+            int64_t* rmx = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+            int64_t* cmx = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+            if (rmx && cmx)
+                orc_accurate_shifts(transA, transB, m, n, k, Ad, lda, Bd, ldb, N, e, f, rmx, cmx);
+            free(rmx); free(cmx);
+        } else {
+            orc_shifts_mode(0, transA, m, k, Ad, lda, N, mode, e);
+            orc_shifts_mode(1, transB, n, k, Bd, ldb, N, mode, f);
+        }
         orc_residues_a(transA, m, k, Ad, lda, e, N, RA);
         orc_residues_b(transB, k, n, Bd, ldb, f, N, RB);
         orc_residue_products(N, m, n, k, RA, RB, cr);
@@ -845,6 +853,12 @@ int orc_sgemm(char transA, char transB, int m, int n, int k, float alpha, const 
     }
     free(Ad); free(Bd); free(e); free(f); free(RA); free(RB); free(cr);
     return rc;
+}
+
+int orc_sgemm(char transA, char transB, int m, int n, int k, float alpha, const float* A,
+              int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+              int N) {
+    return orc_sgemm_mode(transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, N, 0);
 }
 
 /* C'' = rmod(C', P) as 4 little-endian 64-bit words per entry, entry order i*n + j. */
@@ -954,6 +968,64 @@ int orc_dgemm_block(char transA, char transB, int m, int n, int k, double alpha,
         }
     }
     free(e); free(f); free(RA); free(RB);
+    return 0;
+}
+
+/* A block of the emulated SGEMM (proposed scaling): out[a + b*nI] = C(I[a], J[b]) in single
+ * precision.  The needed lines are widened to double (exactly); shifts come from e_in / f_in
+ * when given, else from the widened lines.  Cin (same layout as out) is read when beta != 0. */
+int orc_sgemm_block(char transA, char transB, int k, float alpha, const float* A, int64_t lda,
+                    const float* B, int64_t ldb, float beta, const float* Cin, int N, int nI,
+                    const int* I, int nJ, const int* J, const int* e_in, const int* f_in,
+                    float* out) {
+    orc_consts c;
+    if (make_consts(N, &c)) return -1;
+    int64_t kk = k ? k : 1;
+    int* e = (int*)malloc(sizeof(int) * (size_t)(nI ? nI : 1));
+    int* f = (int*)malloc(sizeof(int) * (size_t)(nJ ? nJ : 1));
+    double* la = (double*)malloc(sizeof(double) * (size_t)(nI ? nI : 1) * kk);
+    double* lb = (double*)malloc(sizeof(double) * (size_t)(nJ ? nJ : 1) * kk);
+    int8_t* RA = (int8_t*)malloc((size_t)N * (nI ? nI : 1) * kk);
+    int8_t* RB = (int8_t*)malloc((size_t)N * (nJ ? nJ : 1) * kk);
+    if (!e || !f || !la || !lb || !RA || !RB) {
+        free(e); free(f); free(la); free(lb); free(RA); free(RB);
+        return -2;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int a = 0; a < nI; ++a) {
+        const int notrans = transA == 'N' || transA == 'n';
+        double* x = la + (int64_t)a * kk;
+        for (int64_t h = 0; h < k; ++h)
+            x[h] = (double)(notrans ? A[I[a] + h * lda] : A[h + (int64_t)I[a] * lda]);
+        e[a] = e_in ? e_in[I[a]] : orc_alg2_shift(line_norm_ru(x, 1, k), c.pprime);
+        line_residues(x, 1, k, e[a], &c, RA + (int64_t)a * k, (int64_t)nI * k);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < nJ; ++b) {
+        const int notrans = transB == 'N' || transB == 'n';
+        double* x = lb + (int64_t)b * kk;
+        for (int64_t h = 0; h < k; ++h)
+            x[h] = (double)(notrans ? B[h + (int64_t)J[b] * ldb] : B[J[b] + h * ldb]);
+        f[b] = f_in ? f_in[J[b]] : orc_alg2_shift(line_norm_ru(x, 1, k), c.pprime);
+        line_residues(x, 1, k, f[b], &c, RB + (int64_t)b * k, (int64_t)nJ * k);
+    }
+#pragma omp parallel for collapse(2) schedule(dynamic, 8)
+    for (int b = 0; b < nJ; ++b) {
+        for (int a = 0; a < nI; ++a) {
+            int cl[ORC_MAX_MODULI];
+            for (int l = 0; l < N; ++l) {
+                const int8_t* ra = RA + (int64_t)l * nI * k + (int64_t)a * k;
+                const int8_t* rb = RB + (int64_t)l * nJ * k + (int64_t)b * k;
+                int64_t g = 0;
+                for (int h = 0; h < k; ++h) g += (int64_t)ra[h] * rb[h];
+                cl[l] = sym_from_mod(i64_mod(g, c.p[l]), c.p[l]);
+            }
+            i256 cpp = entry_crt(cl, &c);
+            float cin = beta != 0.0f ? Cin[a + (int64_t)b * nI] : 0.0f;
+            out[a + (int64_t)b * nI] = entry_output_float(cpp, e[a], f[b], alpha, beta, cin);
+        }
+    }
+    free(e); free(f); free(la); free(lb); free(RA); free(RB);
     return 0;
 }
 

@@ -161,19 +161,19 @@ void cols_of_op(char trans, int64_t ld, int64_t* line_stride, int64_t* elem_stri
 // Accurate mode (Section 2.3): line exponents, A-bar and B-bar in the first residue plane of
 // each operand's planes, the maxima of C-bar = A-bar B-bar in the product-residue region (at
 // least 4 (m_pad + n_pad) bytes), and the shifts written over the exponents.
-int accurate_shifts(ozaki2_context* ctx, const double* A, int64_t als, int64_t aes,
-                    const double* B, int64_t bls, int64_t bes, int m, int n, int k,
+int accurate_shifts(ozaki2_context* ctx, const void* A, int64_t als, int64_t aes,
+                    const void* B, int64_t bls, int64_t bes, int m, int n, int k,
                     const Layout& L, const ModTables& T, int* e, int* f, void* pa, void* pb,
-                    void* cmax_region) {
+                    void* cmax_region, bool f32 = false) {
     cudaStream_t st = ctx->stream;
     auto* cmax = static_cast<uint32_t*>(cmax_region);
     int rc;
     if ((rc = cuda_rc(launch_scale_pair(A, als, aes, m, B, bls, bes, n, k, T.pprime, T.delta, e,
-                                        f, ctx->d_status, st, OZAKI2_SCALING_ACCURATE))) ||
+                                        f, ctx->d_status, st, OZAKI2_SCALING_ACCURATE, f32))) ||
         (rc = cuda_rc(launch_convert_bar(A, als, aes, m, k, e, pa, (int)L.m_pad, (int)L.k_pad,
-                                         ctx->d_status, st))) ||
+                                         ctx->d_status, st, f32))) ||
         (rc = cuda_rc(launch_convert_bar(B, bls, bes, n, k, f, pb, (int)L.n_pad, (int)L.k_pad,
-                                         ctx->d_status, st))))
+                                         ctx->d_status, st, f32))))
         return rc;
     if ((rc = launch_aux_gemm((int)L.m_pad, (int)L.n_pad, (int)L.k_pad, pa, pb, cmax,
                               ctx->d_status, ctx->num_sms, st)))
@@ -181,9 +181,11 @@ int accurate_shifts(ozaki2_context* ctx, const double* A, int64_t als, int64_t a
     return cuda_rc(launch_accu_shift(e, m, f, n, cmax, (int)L.m_pad, T.pprime, T.delta, st));
 }
 
+// The emulated GEMM for FP64 (f32 = false) or FP32 (f32 = true) operands and result; alpha and
+// beta are passed as doubles (exact for single values).
 int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m, int n, int k,
-               double alpha, const double* A, int lda, const double* B, int ldb, double beta,
-               double* C, int ldc, int N) {
+               double alpha, const void* A, int lda, const void* B, int ldb, double beta,
+               void* C, int ldc, int N, bool f32 = false) {
     if (!is_trans_char(transA)) return -(argbase + 1);
     if (!is_trans_char(transB)) return -(argbase + 2);
     if (m < 0) return -(argbase + 3);
@@ -199,7 +201,8 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     if (k > 0 && n > 0 && !B) return -(argbase + 9);
     if (m > 0 && n > 0 && !C) return -(argbase + 12);
     if (m == 0 || n == 0) return OZAKI2_SUCCESS;
-    if (k == 0 || alpha == 0.0) return cuda_rc(launch_scale_c(m, n, beta, C, ldc, ctx->stream));
+    if (k == 0 || alpha == 0.0)
+        return cuda_rc(launch_scale_c(m, n, beta, C, ldc, ctx->stream, f32));
     if (ctx->scaling == OZAKI2_SCALING_ACCURATE && k > OZAKI2_ACCURATE_MAX_K)
         return OZAKI2_ERROR_TOO_LARGE;
 
@@ -224,20 +227,20 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     mark(0);
     if (ctx->scaling == OZAKI2_SCALING_ACCURATE) {
         if ((rc = accurate_shifts(ctx, A, als, aes, B, bls, bes, m, n, k, L, *T, e, f, pa, pb,
-                                  res)))
+                                  res, f32)))
             return rc;
     } else {
         const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
         if ((rc = cuda_rc(launch_scale_pair(A, als, aes, m, B, bls, bes, n, k, pp, T->delta, e,
-                                            f, ctx->d_status, st, ctx->scaling))))
+                                            f, ctx->d_status, st, ctx->scaling, f32))))
             return rc;
     }
     mark(1);
     if ((rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, (int)L.m_pad,
-                                     (int)L.k_pad, ctx->d_status, st))))
+                                     (int)L.k_pad, ctx->d_status, st, f32))))
         return rc;
     if ((rc = cuda_rc(launch_convert(B, bls, bes, n, k, f, T->conv, pb, (int)L.n_pad,
-                                     (int)L.k_pad, ctx->d_status, st))))
+                                     (int)L.k_pad, ctx->d_status, st, f32))))
         return rc;
     mark(2);
     if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, pa, pb, res,
@@ -246,7 +249,7 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
         return rc;
     mark(3);
     rc = cuda_rc(launch_crt(res, L.n_pad, L.m_pad * L.n_pad, m, n, e, f, alpha, beta, C, ldc, *T,
-                            ctx->d_status, st));
+                            ctx->d_status, st, f32));
     mark(4);
     if (ctx->timing) ctx->timed_call = true;
     return rc;
@@ -433,6 +436,26 @@ int ozaki2_dgemm_h(ozaki2_handle_t handle, char transA, char transB, int m, int 
     if (rc) return rc;
     return dgemm_impl(ctx, 1, transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
                       num_moduli);
+}
+
+int ozaki2_sgemm(char transA, char transB, int m, int n, int k, float alpha, const float* A,
+                 int lda, const float* B, int ldb, float beta, float* C, int ldc,
+                 int num_moduli) {
+    ozaki2_context* ctx;
+    int rc = resolve(nullptr, &ctx);
+    if (rc) return rc;
+    return dgemm_impl(ctx, 0, transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                      num_moduli, true);
+}
+
+int ozaki2_sgemm_h(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
+                   float alpha, const float* A, int lda, const float* B, int ldb, float beta,
+                   float* C, int ldc, int num_moduli) {
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    return dgemm_impl(ctx, 1, transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                      num_moduli, true);
 }
 
 size_t ozaki2_grouped_workspace_size(int count, const ozaki2_problem* problems) {

@@ -8,6 +8,7 @@
 //   Q    = round(sum_l w_l / p_l) = round(X / P) (48-bit fixed-point estimate)
 //   C''  = X - Q P                               (exact; corrected by +-P if the estimate sat
 //                                                 within 2^-10 of a half-integer)
+// X and Q P are formed modulo 2^(32 W) with W just large enough for Y (see crt_words).
 // The moduli are taken in groups of three (v_g = sum w_l coef_l < 3 prod_g < 2^26), so X needs
 // one 64-bit multiply-add per group and word instead of one per modulus and word; the kernel
 // is instantiated per N so every table entry is a compile-time constant-bank operand.
@@ -39,19 +40,26 @@ __device__ double scale_pow2_rn(double x, int s) {
     return __dmul_rn(m2, 0x1p-600);
 }
 
-// Words of X = sum_l P_l w_l < N P for N moduli (the same count the host tables use).
+// 32-bit words of the working integers.  X and Q P are only needed modulo 2^(32 W): the result
+// Y = X - Q P satisfies |Y| < P (Q is round(X/P) or one off near a tie), so W words holding
+// bits(P) + 2 bits carry Y exactly in two's complement.
 __host__ __device__ constexpr int crt_words(int N) {
     // bits(P) for N = 2..20: 16 24 32 40 48 56 64 72 80 88 95 103 111 118 126 133 141 148 156
-    return N <= 4 ? 2 : N <= 8 ? 3 : N <= 12 ? 4 : N <= 16 ? 5 : 6;
+    constexpr int b[21] = {0, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80,
+                           88, 95, 103, 111, 118, 126, 133, 141, 148, 156};
+    return (b[N] + 2 + 31) / 32;
 }
 
-template <int N>
-__device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int64_t plane, int ea,
-                                           int fb, const CrtTables& t) {
+// OutT = double (DGEMM) or float (SGEMM): C'' is rounded to 53 or 24 bits, then scaled.
+template <int N, typename OutT>
+__device__ __forceinline__ OutT crt_entry(const int8_t* __restrict__ res, int64_t plane, int ea,
+                                          int fb, const CrtTables& t) {
     constexpr int W = crt_words(N);
     constexpr int G = (N + 2) / 3;
-    if (ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE)
-        return __longlong_as_double(0x7FF8000000000000ll);
+    if (ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE) {
+        if constexpr (sizeof(OutT) == 4) return __uint_as_float(0x7FC00000u);
+        else return __longlong_as_double(0x7FF8000000000000ll);
+    }
     // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^48 X / P (fixed point)
     uint64_t acc[W];
 #pragma unroll
@@ -63,7 +71,7 @@ __device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int6
 #pragma unroll
         for (int l = 3 * g; l < 3 * g + 3 && l < N; ++l) {
             const int c = res[(int64_t)l * plane];
-            const uint32_t x = (uint32_t)(c + 128) * t.q[l] + t.off[l];   // = q_l c (mod p_l)
+            const uint32_t x = (uint32_t)c * t.q[l] + t.off128[l];  // = q_l c (mod p_l), >= 0
             uint32_t w = x - __umulhi(x, t.barrett[l]) * t.p[l];
             if (w >= t.p[l]) w -= t.p[l];
             v += w * t.coef[l];
@@ -146,7 +154,7 @@ __device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int6
 #pragma unroll
     for (int j = W - 1; j >= 0; --j)
         if (top < 0 && Y[j] != 0) top = j;
-    if (top < 0) return 0.0;
+    if (top < 0) return (OutT)0;
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         if (j == top) w0 = Y[j];
@@ -164,32 +172,60 @@ __device__ __forceinline__ double crt_entry(const int8_t* __restrict__ res, int6
     } else {
         sticky = sticky || (w2 != 0);
     }
-    uint64_t m53 = win >> 11;
-    const uint32_t rem = (uint32_t)(win & 0x7FF);
-    if (rem > 0x400 || (rem == 0x400 && (sticky || (m53 & 1)))) {
-        ++m53;
-        if (m53 >> 53) {
-            m53 >>= 1;
-            ++msb;
+    if constexpr (sizeof(OutT) == 4) {
+        // 24 bits, ties to even; then the exponent.  Outside the normal single range the value
+        // x 2^-(e+f) (24 bits, exponent within +-500 for single inputs) is exact in double and
+        // its conversion to float is the one rounding.
+        uint32_t m24 = (uint32_t)(win >> 40);
+        const uint64_t rem = win & ((1ull << 40) - 1);
+        if (rem > (1ull << 39) || (rem == (1ull << 39) && (sticky || (m24 & 1)))) {
+            ++m24;
+            if (m24 >> 24) {
+                m24 >>= 1;
+                ++msb;
+            }
         }
+        const uint32_t sign = neg ? 0x80000000u : 0u;
+        const int E = msb - (ea + fb);
+        if (E >= -126 && E <= 127)
+            return __uint_as_float(sign | ((uint32_t)(E + 127) << 23) | (m24 & 0x7FFFFFu));
+        const double d = __longlong_as_double((long long)(((uint64_t)sign << 32) |
+                                                          ((uint64_t)(E + 1023) << 52) |
+                                                          ((uint64_t)(m24 & 0x7FFFFFu) << 29)));
+        return __double2float_rn(d);
+    } else {
+        uint64_t m53 = win >> 11;
+        const uint32_t rem = (uint32_t)(win & 0x7FF);
+        if (rem > 0x400 || (rem == 0x400 && (sticky || (m53 & 1)))) {
+            ++m53;
+            if (m53 >> 53) {
+                m53 >>= 1;
+                ++msb;
+            }
+        }
+        const uint64_t sign = neg ? (1ull << 63) : 0ull;
+        const int E = msb - (ea + fb);  // unbiased exponent of C'' 2^-(e+f)
+        if (E >= -1022 && E <= 1023)
+            return __longlong_as_double((long long)(sign | ((uint64_t)(E + 1023) << 52) |
+                                                    (m53 & ((1ull << 52) - 1))));
+        const double x = __longlong_as_double(
+            (long long)(sign | ((uint64_t)(msb + 1023) << 52) | (m53 & ((1ull << 52) - 1))));
+        return scale_pow2_rn(x, -(ea + fb));
     }
-    const uint64_t sign = neg ? (1ull << 63) : 0ull;
-    const int E = msb - (ea + fb);  // unbiased exponent of C'' 2^-(e+f)
-    if (E >= -1022 && E <= 1023)
-        return __longlong_as_double((long long)(sign | ((uint64_t)(E + 1023) << 52) |
-                                                (m53 & ((1ull << 52) - 1))));
-    const double x = __longlong_as_double(
-        (long long)(sign | ((uint64_t)(msb + 1023) << 52) | (m53 & ((1ull << 52) - 1))));
-    return scale_pow2_rn(x, -(ea + fb));
 }
 
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
 // One 32 x 32 tile of C (rows i0.., columns j0..); all 256 threads take part.
-template <int N>
+template <int N, typename OutT>
 __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t ldr,
                                          int64_t plane, int m, int n, const int* __restrict__ sa,
-                                         const int* __restrict__ sb, double alpha, double beta,
-                                         double* __restrict__ C, int64_t ldc, const CrtTables& t,
-                                         int i0, int j0, double (*tile)[TI + 1]) {
+                                         const int* __restrict__ sb, OutT alpha, OutT beta,
+                                         OutT* __restrict__ C, int64_t ldc, const CrtTables& t,
+                                         int i0, int j0, OutT (*tile)[TI + 1]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = j0 + lane;
     const int fb = j < n ? sb[j] : 0;
@@ -197,36 +233,37 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
     for (int r = 0; r < TI / 8; ++r) {
         const int il = warp + 8 * r;
         const int i = i0 + il;
-        double y = 0.0;
-        if (i < m && j < n) y = crt_entry<N>(res + (int64_t)i * ldr + j, plane, sa[i], fb, t);
+        OutT y = 0;
+        if (i < m && j < n)
+            y = crt_entry<N, OutT>(res + (int64_t)i * ldr + j, plane, sa[i], fb, t);
         tile[lane][il] = y;
     }
     __syncthreads();
-    const bool plain = (alpha == 1.0 && beta == 0.0);
+    const bool plain = (alpha == (OutT)1 && beta == (OutT)0);
 #pragma unroll
     for (int r = 0; r < TJ / 8; ++r) {
         const int jl = warp + 8 * r;
         const int jj = j0 + jl, ii = i0 + lane;
         if (ii < m && jj < n) {
-            double* out = C + ii + (int64_t)jj * ldc;
-            const double y = tile[jl][lane];
-            double v = plain ? y : __dmul_rn(alpha, y);
-            if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, *out));
+            OutT* out = C + ii + (int64_t)jj * ldc;
+            const OutT y = tile[jl][lane];
+            OutT v = plain ? y : mul_rn(alpha, y);
+            if (beta != (OutT)0) v = add_rn(v, mul_rn(beta, *out));
             *out = v;
         }
     }
 }
 
-template <int N>
+template <int N, typename OutT>
 __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res, int64_t ldr,
                                                   int64_t plane, int m, int n,
                                                   const int* __restrict__ sa,
-                                                  const int* __restrict__ sb, double alpha,
-                                                  double beta, double* __restrict__ C,
+                                                  const int* __restrict__ sb, OutT alpha,
+                                                  OutT beta, OutT* __restrict__ C,
                                                   int64_t ldc, const CrtTables t) {
-    __shared__ double tile[TJ][TI + 1];
-    crt_tile<N>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t, blockIdx.y * TI,
-                blockIdx.x * TJ, tile);
+    __shared__ OutT tile[TJ][TI + 1];
+    crt_tile<N, OutT>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t, blockIdx.y * TI,
+                      blockIdx.x * TJ, tile);
 }
 
 // Grouped: each block reconstructs one 32 x 32 tile of one problem's C.
@@ -237,32 +274,34 @@ __global__ void __launch_bounds__(256) crt_grouped_kernel(const GroupProblem* __
     __shared__ double tile[TJ][TI + 1];
     const CrtWork w = work[blockIdx.x];
     const GroupProblem& P = probs[w.problem];
-    crt_tile<N>(P.res, P.n_pad, (int64_t)P.m_pad * P.n_pad, P.m, P.n, P.e, P.f, P.alpha, P.beta,
+    crt_tile<N, double>(P.res, P.n_pad, (int64_t)P.m_pad * P.n_pad, P.m, P.n, P.e, P.f, P.alpha,
+                        P.beta,
                 P.C, P.ldc, t, w.i0, w.j0, tile);
 }
 
-__global__ void scale_c_kernel(int m, int n, double beta, double* C, int64_t ldc) {
+template <typename T>
+__global__ void scale_c_kernel(int m, int n, T beta, T* C, int64_t ldc) {
     const int64_t total = (int64_t)m * n;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = g / m, i = g - j * m;
-        double* p = C + i + j * ldc;
-        *p = beta == 0.0 ? 0.0 : __dmul_rn(beta, *p);
+        T* p = C + i + j * ldc;
+        *p = beta == (T)0 ? (T)0 : mul_rn(beta, *p);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
-                       const int* sa, const int* sb, double alpha, double beta, double* C,
-                       int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream) {
-    (void)status;
-    if (m <= 0 || n <= 0) return cudaSuccess;
+namespace {
+template <typename OutT>
+cudaError_t launch_crt_typed(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
+                             const int* sa, const int* sb, OutT alpha, OutT beta, OutT* C,
+                             int64_t ldc, const ModTables& t, cudaStream_t stream) {
     dim3 grid((n + TJ - 1) / TJ, (m + TI - 1) / TI);
-#define OZAKI2_CRT_CASE(NN)                                                                      \
-    case NN:                                                                                     \
-        crt_kernel<NN><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, \
-                                                 ldc, t.crt);                                    \
+#define OZAKI2_CRT_CASE(NN)                                                                 \
+    case NN:                                                                                \
+        crt_kernel<NN, OutT><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, \
+                                                       beta, C, ldc, t.crt);                 \
         break;
     switch (t.N) {
         OZAKI2_CRT_CASE(2) OZAKI2_CRT_CASE(3) OZAKI2_CRT_CASE(4) OZAKI2_CRT_CASE(5)
@@ -274,6 +313,20 @@ cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int
     }
 #undef OZAKI2_CRT_CASE
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
+                       const int* sa, const int* sb, double alpha, double beta, void* C,
+                       int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream,
+                       bool f32) {
+    (void)status;
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (f32)
+        return launch_crt_typed<float>(res, ldr, plane, m, n, sa, sb, (float)alpha, (float)beta,
+                                       static_cast<float*>(C), ldc, t, stream);
+    return launch_crt_typed<double>(res, ldr, plane, m, n, sa, sb, alpha, beta,
+                                    static_cast<double*>(C), ldc, t, stream);
 }
 
 cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* work, int blocks,
@@ -297,12 +350,17 @@ cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale_c(int m, int n, double beta, double* C, int64_t ldc,
-                           cudaStream_t stream) {
+cudaError_t launch_scale_c(int m, int n, double beta, void* C, int64_t ldc,
+                           cudaStream_t stream, bool f32) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     const int64_t total = (int64_t)m * n;
     const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-    scale_c_kernel<<<grid, 256, 0, stream>>>(m, n, beta, C, ldc);
+    if (f32)
+        scale_c_kernel<float><<<grid, 256, 0, stream>>>(m, n, (float)beta, static_cast<float*>(C),
+                                                        ldc);
+    else
+        scale_c_kernel<double><<<grid, 256, 0, stream>>>(m, n, beta, static_cast<double*>(C),
+                                                         ldc);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct CrtTables {
     uint32_t barrett[kMaxModuli];   // floor(2^32 / p)
     uint32_t q[kMaxModuli];         // q_l = (P/p_l)^{-1} mod p_l
     uint32_t off[kMaxModuli];       // (-128 q_l) mod p_l, so (c + 128) q_l + off = q_l c (mod p_l)
+    uint32_t off128[kMaxModuli];    // 128 q_l + off: c q_l + off128 = (c + 128) q_l + off >= 0
     float inv_p[kMaxModuli];        // 1/p_l rounded to single
     uint32_t Pl[kMaxModuli][kMaxWords];  // P_l = P/p_l, little-endian 32-bit words
     uint32_t P[kMaxWords];
@@ -193,11 +194,14 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const v
                         unsigned* status, int num_sms, int chunk_k, int variant,
                         cudaStream_t stream);
 
+// f32: C holds floats (SGEMM: C'' rounded to 24 bits, alpha and beta applied in single
+// precision), else doubles.
 cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
-                       const int* sa, const int* sb, double alpha, double beta, double* C,
-                       int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream);
+                       const int* sa, const int* sb, double alpha, double beta, void* C,
+                       int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream,
+                       bool f32 = false);
 
-cudaError_t launch_scale_c(int m, int n, double beta, double* C, int64_t ldc,
-                           cudaStream_t stream);
+cudaError_t launch_scale_c(int m, int n, double beta, void* C, int64_t ldc,
+                           cudaStream_t stream, bool f32 = false);
 
 }  // namespace ozaki2

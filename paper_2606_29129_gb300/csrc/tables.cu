@@ -111,6 +111,7 @@ void build(int N, ModTables& t) {
         t.crt.barrett[l] = (uint32_t)((1ull << 32) / p);
         t.crt.q[l] = q;
         t.crt.off[l] = (uint32_t)((p - (128u * q) % p) % p);
+        t.crt.off128[l] = 128u * q + t.crt.off[l];
         t.crt.inv_p[l] = 1.0f / (float)p;
         for (int w = 0; w < kMaxWords; ++w) t.crt.Pl[l][w] = w < (int)Pl.size() ? Pl[w] : 0u;
 

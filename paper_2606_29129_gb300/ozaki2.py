@@ -66,8 +66,8 @@ def lib() -> ctypes.CDLL:
             raise ImportError(f"{LIB_PATH} is missing: build it with "
                               "`python -m paper_2606_29129_gb300.build` (needs nvcc)")
         L = ctypes.CDLL(LIB_PATH)
-        vp, i32, i64, f64, ch = (ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
-                                 ctypes.c_double, ctypes.c_char)
+        vp, i32, i64, f64, f32, ch = (ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+                                      ctypes.c_double, ctypes.c_float, ctypes.c_char)
         sig = {
             "ozaki2_create": [ctypes.POINTER(vp)],
             "ozaki2_destroy": [vp],
@@ -77,6 +77,9 @@ def lib() -> ctypes.CDLL:
             "ozaki2_constants": [i32, vp, vp, ctypes.POINTER(ctypes.c_float)],
             "ozaki2_dgemm": [ch, ch, i32, i32, i32, f64, vp, i32, vp, i32, f64, vp, i32, i32],
             "ozaki2_dgemm_h": [vp, ch, ch, i32, i32, i32, f64, vp, i32, vp, i32, f64, vp, i32,
+                               i32],
+            "ozaki2_sgemm": [ch, ch, i32, i32, i32, f32, vp, i32, vp, i32, f32, vp, i32, i32],
+            "ozaki2_sgemm_h": [vp, ch, ch, i32, i32, i32, f32, vp, i32, vp, i32, f32, vp, i32,
                                i32],
             "ozaki2_scale_a": [vp, ch, i32, i32, vp, i32, i32, vp],
             "ozaki2_scale_b": [vp, ch, i32, i32, vp, i32, i32, vp],
@@ -210,6 +213,12 @@ def ozaki2_workspace_size(m, n, k, num_moduli) -> int:
 def ozaki2_dgemm(transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli,
                  handle: Handle | None = None) -> int:
     return lib().ozaki2_dgemm_h(_h(handle), _ch(transA), _ch(transB), m, n, k, alpha, _ptr(A),
+                                lda, _ptr(B), ldb, beta, _ptr(C), ldc, num_moduli)
+
+
+def ozaki2_sgemm(transA, transB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, num_moduli,
+                 handle: Handle | None = None) -> int:
+    return lib().ozaki2_sgemm_h(_h(handle), _ch(transA), _ch(transB), m, n, k, alpha, _ptr(A),
                                 lda, _ptr(B), ldb, beta, _ptr(C), ldc, num_moduli)
 
 

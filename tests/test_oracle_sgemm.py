@@ -162,3 +162,31 @@ def test_cpp_rounded_once_to_24_bits(orc):
         assert got[0, 0] < np.float32(u) * np.float32(v)         # rounded down, not to the tie
         return
     pytest.fail("no constructed case found")
+
+
+def test_block_matches_whole_product(orc):
+    m, n, k, N = 37, 29, 150, 9
+    A = synthetic.paper_matrix(k, m, 2.0, 91).astype(np.float32)     # op(A) = A^T
+    B = synthetic.paper_matrix(n, k, 2.0, 92).astype(np.float32)     # op(B) = B^T
+    Cin = np.random.default_rng(3).standard_normal((n, m)).astype(np.float32)
+    full = orc.sgemm(A, B, m, n, k, N, "T", "T", 0.5, -2.0, Cin)
+    I = np.array([0, 5, 36], np.int32)
+    J = np.array([1, 28], np.int32)
+    blk = orc.sgemm_block(A, B, k, N, I, J, "T", "T", 0.5, -2.0, Cin[np.ix_(J, I)])
+    assert np.array_equal(blk.view(np.int32), full[np.ix_(J, I)].view(np.int32))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_agrees_with_the_dgemm_modes(orc, mode):
+    """SGEMM is the DGEMM pipeline on widened inputs up to the final rounding: every entry is
+    the single rounding of C'' while DGEMM rounds it to 53 bits, so the two agree to within one
+    unit in the last place of single (and exactly, apart from rare double-rounding cases)."""
+    m, n, k, N = 50, 40, 400, 10
+    A = synthetic.paper_matrix(m, k, 1.0, 71).astype(np.float32)
+    B = synthetic.paper_matrix(k, n, 1.0, 72).astype(np.float32)
+    S = orc.sgemm(A, B, m, n, k, N, mode=mode)
+    D = orc.dgemm_mode(A.astype(np.float64), B.astype(np.float64), m, n, k, N, mode)
+    Df = D.astype(np.float32)
+    ulp = np.spacing(np.abs(Df))
+    assert np.all(np.abs(S.astype(np.float64) - Df.astype(np.float64)) <= ulp)
+    assert np.mean(S == Df) > 0.999
