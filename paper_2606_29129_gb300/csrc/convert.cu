@@ -36,22 +36,19 @@ struct Scaled {
     bool neg;
 };
 
-// |trunc(a 2^e)| as 21-bit limbs.  Flags OZAKI2_STATUS_RANGE when the value needs more than
-// 21*L bits (only possible with shifts that break the bound of eq. (proposed-condition)).
+// |trunc(M 2^sh)| (M of mbits bits) as 21-bit limbs.  Flags OZAKI2_STATUS_RANGE when the value
+// needs more than 21*L bits (only possible with shifts that break the bound of
+// eq. (proposed-condition)).
 template <int L>
-__device__ __forceinline__ Scaled split_scaled(double a, int e, unsigned* status) {
+__device__ __forceinline__ Scaled split_mantissa(uint64_t M, int mbits, int sh, bool neg,
+                                                 unsigned* status) {
     Scaled r;
-    const uint64_t bits = (uint64_t)__double_as_longlong(a);
-    r.neg = (bits >> 63) != 0;
-    int E = (int)((bits >> 52) & 0x7FF);
-    uint64_t M = bits & ((1ull << 52) - 1);
-    if (E) M |= 1ull << 52; else E = 1;
-    int sh = E - 1075 + e;
+    r.neg = neg;
     uint64_t lo = 0, hi = 0;
-    if (M != 0 && sh > 21 * L - 53) {
+    if (M != 0 && sh > 21 * L - mbits) {
         // bits of |a'| = (64 - clz(M)) + sh must fit in 21 L
         if (sh > 21 * L - (64 - __clzll((long long)M))) atomicOr(status, OZAKI2_STATUS_RANGE);
-        sh = min(sh, 21 * L - 53 + 11);
+        sh = min(sh, min(21 * L - mbits + 11, 63));
     }
     if (sh >= 0) {
         lo = M << sh;
@@ -65,6 +62,24 @@ __device__ __forceinline__ Scaled split_scaled(double a, int e, unsigned* status
     r.d[2] = (uint32_t)(lo >> 42) & kMask21;
     r.d[3] = (uint32_t)((lo >> 63) | (hi << 1)) & kMask21;
     return r;
+}
+
+// |trunc(a 2^e)| of a double (53-bit mantissa) or a float (24-bit mantissa), from the bits.
+template <int L>
+__device__ __forceinline__ Scaled split_scaled(double a, int e, unsigned* status) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(a);
+    int E = (int)((bits >> 52) & 0x7FF);
+    uint64_t M = bits & ((1ull << 52) - 1);
+    if (E) M |= 1ull << 52; else E = 1;
+    return split_mantissa<L>(M, 53, E - 1075 + e, (bits >> 63) != 0, status);
+}
+template <int L>
+__device__ __forceinline__ Scaled split_scaled(float a, int e, unsigned* status) {
+    const uint32_t bits = __float_as_uint(a);
+    int E = (int)((bits >> 23) & 0xFF);
+    uint64_t M = bits & 0x7FFFFFu;
+    if (E) M |= 1ull << 23; else E = 1;
+    return split_mantissa<L>(M, 24, E - 150 + e, (bits >> 31) != 0, status);
 }
 
 // bf16 bits (in the upper half of a float) of the small integer s.
@@ -113,10 +128,25 @@ __device__ __forceinline__ uint32_t bar_bits(double a, int E) {
     return small_int_bits((int)c);
 }
 
+__device__ __forceinline__ uint32_t bar_bits(float a, int E) {
+    // as above with |a| = M 2^(Ex - 150): rs = 145 + E - Ex (>= 18 for a normal a)
+    const uint32_t bits = __float_as_uint(a) & 0x7FFFFFFFu;
+    if (bits == 0) return small_int_bits(0);
+    int Ex = (int)(bits >> 23);
+    uint64_t M = bits & 0x7FFFFFu;
+    if (Ex) M |= 1ull << 23; else Ex = 1;
+    const int rs = 145 + E - Ex;
+    uint32_t c;
+    if (rs >= 64) c = 1u;
+    else if (rs > 0) c = (uint32_t)((M + ((1ull << rs) - 1)) >> rs);
+    else c = (uint32_t)(M << -rs);
+    return small_int_bits((int)c);
+}
+
 // Writes the residues of 8 consecutive elements of one line into the N planes.  N = 1 is the
 // a-bar plane of accurate mode instead, with e the line's exponent code.
-template <int N>
-__device__ __forceinline__ void store_residues8(const double (&v)[8], int e, bool live,
+template <int N, typename V>
+__device__ __forceinline__ void store_residues8(const V (&v)[8], int e, bool live,
                                                 const ConvertTables& t, __nv_bfloat16* planes,
                                                 int64_t plane_elems, int64_t offset,
                                                 unsigned* status) {
@@ -169,7 +199,7 @@ __device__ __forceinline__ void load8(const double* src, bool vec, double (&v)[8
         for (int u = 0; u < 8; ++u) v[u] = __ldg(src + u);
     }
 }
-__device__ __forceinline__ void load8(const float* src, bool vec, double (&v)[8]) {
+__device__ __forceinline__ void load8(const float* src, bool vec, float (&v)[8]) {
     if (vec) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -199,14 +229,13 @@ __device__ __forceinline__ void convert_contiguous_item(
         const int i = (int)(g / groups);
         const int h0 = (int)(g - (int64_t)i * groups) * 8;
         const bool row_live = i < lines;
-        double v[8];
+        T v[8];
         const T* src = X + (int64_t)i * ld + h0;
         if (row_live && h0 + 8 <= len) {
             load8(src, vec, v);
         } else {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                v[u] = (row_live && h0 + u < len) ? (double)__ldg(src + u) : 0.0;
+            for (int u = 0; u < 8; ++u) v[u] = (row_live && h0 + u < len) ? __ldg(src + u) : (T)0;
         }
         const int e = row_live ? shifts[i] : 0;
         store_residues8<N>(v, e, row_live, t, planes, plane_elems, (int64_t)i * k_pad + h0,
@@ -238,7 +267,7 @@ template <int N, typename T>
 __device__ __forceinline__ void convert_adjacent_tile(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
-    int64_t tt, double (*tile)[kTileLines + 1], unsigned* status) {
+    int64_t tt, T (*tile)[kTileLines + 1], unsigned* status) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t plane_elems = (int64_t)rows_pad * k_pad;
     const int tiles_l = (rows_pad + kTileLines - 1) / kTileLines;
@@ -255,7 +284,7 @@ __device__ __forceinline__ void convert_adjacent_tile(
             for (int half = 0; half < 2; ++half) {
                 const int line = line0 + 32 * half + lane;
                 tile[hh][32 * half + lane] =
-                    (line < lines && h < len) ? (double)__ldg(X + line + (int64_t)h * ld) : 0.0;
+                    (line < lines && h < len) ? __ldg(X + line + (int64_t)h * ld) : (T)0;
             }
         }
         __syncthreads();
@@ -266,7 +295,7 @@ __device__ __forceinline__ void convert_adjacent_tile(
             const int ll = item >> 3, hg = item & 7;
             const int line = line0 + ll;
             if (line < rows_pad) {
-                double v[8];
+                T v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = tile[8 * hg + u][ll];
                 const bool live = line < lines;
@@ -284,7 +313,7 @@ __global__ void __launch_bounds__(256) convert_adjacent_kernel(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
     unsigned* status) {
-    __shared__ double tile[kTileK][kTileLines + 1];
+    __shared__ T tile[kTileK][kTileLines + 1];
     const int tiles_l = (rows_pad + kTileLines - 1) / kTileLines;
     const int64_t ntiles = (int64_t)tiles_l * (k_pad / kTileK);
     for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x)

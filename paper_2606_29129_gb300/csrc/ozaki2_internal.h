@@ -173,6 +173,30 @@ cudaError_t launch_scale_pair(const void* A, int64_t a_ls, int64_t a_es, int m, 
                               float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
                               int scaling, bool f32 = false);
 
+#ifdef __CUDACC__
+// The double of the same value as a float, built from the bits with integer operations (the
+// conversion instruction runs on the FP64 pipe, which GB300 keeps narrow).  Exact: normal floats
+// rebias the exponent; subnormals are normalised; Inf and NaN keep their class.
+__device__ __forceinline__ double widen_exact(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint64_t sign = (uint64_t)(b >> 31) << 63;
+    const uint32_t e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    uint64_t bits;
+    if (e == 0xFFu) {
+        bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);
+    } else if (e != 0u) {
+        bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+    } else if (m == 0u) {
+        bits = sign;
+    } else {
+        const int msb = 31 - __clz(m);  // value m 2^-149 = 2^(msb-149) (1.f)
+        bits = sign | ((uint64_t)(msb - 149 + 1023) << 52) |
+               (((uint64_t)m << (52 - msb)) & ((1ull << 52) - 1));
+    }
+    return __longlong_as_double((long long)bits);
+}
+#endif
+
 // Accurate mode: the first scaling pass writes this code for a zero line (a real E is in
 // [-1074, 1023], OZAKI2_SHIFT_NONFINITE marks a non-finite line).
 constexpr int kAccuZeroLine = INT32_MAX;

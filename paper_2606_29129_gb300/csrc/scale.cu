@@ -102,6 +102,8 @@ constexpr int kBatch = 16;
 
 // T = double (DGEMM) or float (SGEMM: every float is exactly a double, so the sums and the
 // shifts are those of the widened values).
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return widen_exact(x); }
 template <int SCALING, typename T = double>
 __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int64_t ld,
                                                     int i, int len, float pprime, float delta,
@@ -121,7 +123,7 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
             for (int u = 0; u < kBatch; ++u) b[u] = __ldg(p + (int64_t)(h + kBatch + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) acc.add((double)a[u]);
+        for (int u = 0; u < kBatch; ++u) acc.add(to_double(a[u]));
         if (!has_b) break;
         if (h + 2 * kBatch < full) {
 #pragma unroll
@@ -129,9 +131,9 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
                 a[u] = __ldg(p + (int64_t)(h + 2 * kBatch + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) acc.add((double)b[u]);
+        for (int u = 0; u < kBatch; ++u) acc.add(to_double(b[u]));
     }
-    for (int h = full; h < len; ++h) acc.add((double)__ldg(p + (int64_t)h * ld));
+    for (int h = full; h < len; ++h) acc.add(to_double(__ldg(p + (int64_t)h * ld)));
     shifts[i] = acc.result(pprime, delta, status);
 }
 
@@ -172,7 +174,7 @@ __device__ __forceinline__ void scale_contiguous_warp(const T* __restrict__ X, i
     for (int h0 = 0; h0 < len; h0 += kTileLen) {
         const int cnt = min(kTileLen, len - h0);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) t[r][lane] = (double)reg[r];
+        for (int r = 0; r < 32; ++r) t[r][lane] = to_double(reg[r]);
         __syncwarp();
         if (h0 + kTileLen < len) load(h0 + kTileLen);
         if (lane < nl) {
