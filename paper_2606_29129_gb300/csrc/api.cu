@@ -36,6 +36,7 @@ struct ozaki2_context {
     };
     std::vector<GraphEntry> graphs;
     cudaStream_t capture_stream = nullptr;
+    bool pageable_access = false;  // the device can address ordinary (pageable) host memory
 };
 
 namespace {
@@ -80,7 +81,24 @@ int init_context(ozaki2_context* ctx) {
     if (rc) return rc;
     if (cudaMalloc(&ctx->d_status, 256) != cudaSuccess) return OZAKI2_ERROR_CUDA;
     if (cudaMemset(ctx->d_status, 0, 256) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, ctx->device) !=
+        cudaSuccess)
+        pageable = 0;
+    ctx->pageable_access = pageable != 0;
     return OZAKI2_SUCCESS;
+}
+
+// True if the device can address p: device or managed memory, page-locked host memory (mapped
+// under unified addressing), or any host memory when the device has pageable-memory access
+// (a coherent CPU-GPU link).  Kernels never touch a pointer that fails this check.
+bool addressable(const ozaki2_context* ctx, const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx->pageable_access;
+    }
+    return a.type != cudaMemoryTypeUnregistered || ctx->pageable_access;
 }
 
 ozaki2_context* g_default = nullptr;
@@ -201,6 +219,9 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     if (k > 0 && n > 0 && !B) return -(argbase + 9);
     if (m > 0 && n > 0 && !C) return -(argbase + 12);
     if (m == 0 || n == 0) return OZAKI2_SUCCESS;
+    if (k > 0 && !addressable(ctx, A)) return -(argbase + 7);
+    if (k > 0 && !addressable(ctx, B)) return -(argbase + 9);
+    if (!addressable(ctx, C)) return -(argbase + 12);
     if (k == 0 || alpha == 0.0)
         return cuda_rc(launch_scale_c(m, n, beta, C, ldc, ctx->stream, f32));
     if (ctx->scaling == OZAKI2_SCALING_ACCURATE && k > OZAKI2_ACCURATE_MAX_K)

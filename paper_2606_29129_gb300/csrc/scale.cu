@@ -98,7 +98,7 @@ struct LineAcc {
 // Lines adjacent in memory (line_stride == 1): thread i walks line i in order; a warp reads 32
 // consecutive doubles per step, so every load is coalesced.  Loads run two batches of 16 ahead
 // of the dependent FMA chain so that enough bytes are in flight with one thread per line.
-constexpr int kBatch = 16;
+constexpr int kBatch = 16;  // loads per batch for doubles (twice as many for floats)
 
 // T = double (DGEMM) or float (SGEMM: every float is exactly a double, so the sums and the
 // shifts are those of the widened values).
@@ -108,30 +108,31 @@ template <int SCALING, typename T = double>
 __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int64_t ld,
                                                     int i, int len, float pprime, float delta,
                                                     int* shifts, unsigned* status) {
+    constexpr int kB = kBatch * 8 / (int)sizeof(T);  // 128 bytes per thread in flight
     const T* p = X + i;
     LineAcc<SCALING> acc;
-    const int full = len / kBatch * kBatch;
-    T a[kBatch], b[kBatch];
+    const int full = len / kB * kB;
+    T a[kB], b[kB];
     if (full > 0) {
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) a[u] = __ldg(p + (int64_t)u * ld);
+        for (int u = 0; u < kB; ++u) a[u] = __ldg(p + (int64_t)u * ld);
     }
-    for (int h = 0; h < full; h += 2 * kBatch) {
-        const bool has_b = h + kBatch < full;
+    for (int h = 0; h < full; h += 2 * kB) {
+        const bool has_b = h + kB < full;
         if (has_b) {
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) b[u] = __ldg(p + (int64_t)(h + kBatch + u) * ld);
+            for (int u = 0; u < kB; ++u) b[u] = __ldg(p + (int64_t)(h + kB + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) acc.add(to_double(a[u]));
+        for (int u = 0; u < kB; ++u) acc.add(to_double(a[u]));
         if (!has_b) break;
-        if (h + 2 * kBatch < full) {
+        if (h + 2 * kB < full) {
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-                a[u] = __ldg(p + (int64_t)(h + 2 * kBatch + u) * ld);
+            for (int u = 0; u < kB; ++u)
+                a[u] = __ldg(p + (int64_t)(h + 2 * kB + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) acc.add(to_double(b[u]));
+        for (int u = 0; u < kB; ++u) acc.add(to_double(b[u]));
     }
     for (int h = full; h < len; ++h) acc.add(to_double(__ldg(p + (int64_t)h * ld)));
     shifts[i] = acc.result(pprime, delta, status);

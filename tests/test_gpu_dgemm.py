@@ -246,3 +246,21 @@ def test_full_size_sampled(oz, orc, m, n, k, N, phi, alpha):
     Id = torch.from_numpy(I.astype(np.int64)).cuda()
     got = C[Jd][:, Id].cpu().numpy()
     assert _gpu.same_bits(got, blk)
+
+
+def test_host_resident_operands(oz, orc):
+    """A, B and C in page-locked host memory: the kernels read and write it over the CPU-GPU
+    link and the result is bit-identical to the device-memory call."""
+    import torch
+
+    m, n, k, N = 300, 200, 500, 14
+    A, B = make(m, n, k, 1.0, 77)
+    Cin = synthetic.paper_matrix(m, n, 1.0, 78)
+    ref = _gpu.dgemm(oz, A, B, m, n, k, N, alpha=0.5, beta=-1.0, Cin=Cin)
+    Ah = torch.from_numpy(np.ascontiguousarray(A)).pin_memory()
+    Bh = torch.from_numpy(np.ascontiguousarray(B)).pin_memory()
+    Ch = torch.from_numpy(np.ascontiguousarray(Cin)).pin_memory()
+    _gpu.ok(oz.ozaki2_dgemm("N", "N", m, n, k, 0.5, Ah, m, Bh, k, -1.0, Ch, m, N), "host dgemm")
+    torch.cuda.synchronize()
+    assert _gpu.same_bits(Ch.numpy(), ref)
+    assert _gpu.same_bits(ref, orc.dgemm(A, B, m, n, k, N, alpha=0.5, beta=-1.0, Cin=Cin))
