@@ -196,7 +196,8 @@ size_t ozaki2_grouped_workspace_size(int count, const ozaki2_problem* problems);
  * in a handful of launches: one grouped scaling launch, one grouped conversion launch per
  * distinct moduli count, ONE persistent residue-GEMM launch over the tiles of all problems, and
  * one grouped CRT launch per distinct moduli count.  Sizes, transposes, moduli counts and
- * alpha/beta may differ between problems; outputs must not overlap.  `problems` is a host array
+ * alpha/beta may differ between problems; outputs must not overlap.  A, B and C may be device
+ * or page-locked host memory, as for ozaki2_dgemm.  `problems` is a host array
  * that is read during the call only.  The per-problem tables are staged in pinned host memory
  * owned by the handle and copied with one cudaMemcpyAsync.  Errors: -2 count < 0, -3 problems
  * NULL; -(100 (i+1) + a) when argument a (numbered as for ozaki2_dgemm) of problem i is

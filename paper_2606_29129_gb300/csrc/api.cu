@@ -270,7 +270,7 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
         return rc;
     mark(3);
     rc = cuda_rc(launch_crt(res, L.n_pad, L.m_pad * L.n_pad, m, n, e, f, alpha, beta, C, ldc, *T,
-                            ctx->d_status, st, f32));
+                            ctx->d_status, st, f32, true));
     mark(4);
     if (ctx->timing) ctx->timed_call = true;
     return rc;
@@ -501,14 +501,25 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
         if (problems[i].k > OZAKI2_ACCURATE_MAX_K) return OZAKI2_ERROR_TOO_LARGE;
     const size_t tb = (size_t)grouped_table_bytes(count, problems, ctx->scaling);
     char* ws = static_cast<char*>(ctx->ws);
+    auto operands_ok = [&]() {
+        for (int i = 0; i < count; ++i) {
+            const ozaki2_problem& p = problems[i];
+            if (p.m <= 0 || p.n <= 0 || p.k <= 0 || p.alpha == 0.0) continue;
+            if (!addressable(ctx, p.A)) return -(100 * (i + 1) + 7);
+            if (!addressable(ctx, p.B)) return -(100 * (i + 1) + 9);
+            if (!addressable(ctx, p.C)) return -(100 * (i + 1) + 12);
+        }
+        return 0;
+    };
     if (ctx->use_graphs) {
         for (auto& g : ctx->graphs)
             if (g.chunk_k == ctx->chunk_k && g.scaling == ctx->scaling &&
                 same_problems(g.probs, count, problems))
                 return cudaGraphLaunch(g.exec, ctx->stream) == cudaSuccess ? OZAKI2_SUCCESS
                                                                             : OZAKI2_ERROR_CUDA;
-        // First call with these problems: upload the tables to a buffer of their own, capture
-        // the launches once, keep the instantiated graph.
+        // First call with these problems: check the operands, upload the tables to a buffer of
+        // their own, capture the launches once, keep the instantiated graph.
+        if ((rc = operands_ok())) return rc;
         ozaki2_context::GraphEntry g;
         g.probs.assign(problems, problems + count);
         g.chunk_k = ctx->chunk_k;
@@ -552,6 +563,7 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
                    ? OZAKI2_SUCCESS
                    : OZAKI2_ERROR_CUDA;
     }
+    if ((rc = operands_ok())) return rc;
     if (ctx->stage_bytes < tb) {
         if (cudaEventSynchronize(ctx->staged) != cudaSuccess) return OZAKI2_ERROR_CUDA;
         if (ctx->stage) cudaFreeHost(ctx->stage);

@@ -94,17 +94,17 @@ __device__ __forceinline__ uint32_t residue_bits(const Scaled& v, const ConvertT
         const uint32_t b = (v.neg ? 0u - v.low : v.low) & 0xFFu;
         return small_int_bits((int)(int8_t)(uint8_t)b);
     }
-    // Odd p, h = (p - 1)/2: t == |a'| (mod p), t < 2^31; x = t + h, or K p + h - t for a
-    // negative a' (K p >= 2^31 a multiple of p), so x == a' + h (mod p) with 0 <= x < 2^32.  One
-    // Barrett step leaves r in [0, 2p), one unsigned min brings it to [0, p), and r - h is the
-    // symmetric residue in [-h, h], written straight into the float bits.
+    // Odd p, h = (p - 1)/2: t == |a'| (mod p), t <= (2^21 - 1)(1 + 3(p - 1)) < 2^31; x = t + h,
+    // or K p + h - t for a negative a' (K p >= that bound, a multiple of p), so
+    // x == a' + h (mod p) with 0 <= x < 2^31.  The quotient by p is exact with the 2^39 magic
+    // (x (ceil(2^39/p) p - 2^39) < 2^39 for every such x and modulus), so r = x mod p directly,
+    // and r - h is the symmetric residue in [-h, h], written straight into the float bits.
     const uint32_t p = t.p[l];
     uint32_t tt = v.d[0];
 #pragma unroll
     for (int j = 1; j < L; ++j) tt += v.d[j] * t.pow21[l][j];
     const uint32_t x = tt * (v.neg ? 0xFFFFFFFFu : 1u) + (v.neg ? t.off_neg[l] : t.off_pos[l]);
-    uint32_t r = x - __umulhi(x, t.barrett[l]) * p;
-    r = min(r, r - p);
+    const uint32_t r = x - (__umulhi(x, t.magic39[l]) >> 7) * p;
     return __float_as_uint(__uint_as_float(r + t.bias[l]) - 12582912.0f);
 }
 

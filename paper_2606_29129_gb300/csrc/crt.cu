@@ -52,8 +52,8 @@ __host__ __device__ constexpr int crt_words(int N) {
 
 // OutT = double (DGEMM) or float (SGEMM): C'' is rounded to 53 or 24 bits, then scaled.
 template <int N, typename OutT>
-__device__ __forceinline__ OutT crt_entry(const int8_t* __restrict__ res, int64_t plane, int ea,
-                                          int fb, const CrtTables& t) {
+__device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
+                                          const CrtTables& t) {
     constexpr int W = crt_words(N);
     constexpr int G = (N + 2) / 3;
     if (ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE) {
@@ -70,7 +70,7 @@ __device__ __forceinline__ OutT crt_entry(const int8_t* __restrict__ res, int64_
         uint32_t v = 0;
 #pragma unroll
         for (int l = 3 * g; l < 3 * g + 3 && l < N; ++l) {
-            const int c = res[(int64_t)l * plane];
+            const int c = cres[l];
             const uint32_t x = (uint32_t)c * t.q[l] + t.off128[l];  // = q_l c (mod p_l), >= 0
             uint32_t w = x - __umulhi(x, t.barrett[l]) * t.p[l];
             if (w >= t.p[l]) w -= t.p[l];
@@ -219,24 +219,55 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
-// One 32 x 32 tile of C (rows i0.., columns j0..); all 256 threads take part.
-template <int N, typename OutT>
+// One 32 x 32 tile of C (rows i0.., columns j0..); all 256 threads take part.  VEC: the
+// residue planes are padded to whole 32 x 32 tiles and 4-byte aligned (the library's own
+// layout), so thread t reads four consecutive residues of row t/8 per plane with one 32-bit
+// load; otherwise each residue is read on its own.
+template <int N, typename OutT, bool VEC>
 __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t ldr,
                                          int64_t plane, int m, int n, const int* __restrict__ sa,
                                          const int* __restrict__ sb, OutT alpha, OutT beta,
                                          OutT* __restrict__ C, int64_t ldc, const CrtTables& t,
                                          int i0, int j0, OutT (*tile)[TI + 1]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = j0 + lane;
-    const int fb = j < n ? sb[j] : 0;
-#pragma unroll
-    for (int r = 0; r < TI / 8; ++r) {
-        const int il = warp + 8 * r;
+    if constexpr (VEC) {
+        const int il = threadIdx.x >> 3, jq = (threadIdx.x & 7) * 4;
         const int i = i0 + il;
-        OutT y = 0;
-        if (i < m && j < n)
-            y = crt_entry<N, OutT>(res + (int64_t)i * ldr + j, plane, sa[i], fb, t);
-        tile[lane][il] = y;
+        const int ea = i < m ? sa[i] : 0;
+        const int8_t* base = res + (int64_t)i * ldr + j0 + jq;
+        uint32_t wd[N];
+#pragma unroll
+        for (int l = 0; l < N; ++l)
+            wd[l] = __ldg(reinterpret_cast<const unsigned int*>(base + (int64_t)l * plane));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + jq + q;
+            OutT y = 0;
+            if (i < m && j < n) {
+                int c[N];
+#pragma unroll
+                for (int l = 0; l < N; ++l) c[l] = (int)(int8_t)(uint8_t)(wd[l] >> (8 * q));
+                y = crt_value<N, OutT>(c, ea, sb[j], t);
+            }
+            tile[jq + q][il] = y;
+        }
+    } else {
+        const int j = j0 + lane;
+        const int fb = j < n ? sb[j] : 0;
+#pragma unroll
+        for (int r = 0; r < TI / 8; ++r) {
+            const int il = warp + 8 * r;
+            const int i = i0 + il;
+            OutT y = 0;
+            if (i < m && j < n) {
+                const int8_t* p = res + (int64_t)i * ldr + j;
+                int c[N];
+#pragma unroll
+                for (int l = 0; l < N; ++l) c[l] = p[(int64_t)l * plane];
+                y = crt_value<N, OutT>(c, sa[i], fb, t);
+            }
+            tile[lane][il] = y;
+        }
     }
     __syncthreads();
     const bool plain = (alpha == (OutT)1 && beta == (OutT)0);
@@ -254,7 +285,7 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
     }
 }
 
-template <int N, typename OutT>
+template <int N, typename OutT, bool VEC>
 __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res, int64_t ldr,
                                                   int64_t plane, int m, int n,
                                                   const int* __restrict__ sa,
@@ -262,8 +293,8 @@ __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res
                                                   OutT beta, OutT* __restrict__ C,
                                                   int64_t ldc, const CrtTables t) {
     __shared__ OutT tile[TJ][TI + 1];
-    crt_tile<N, OutT>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t, blockIdx.y * TI,
-                      blockIdx.x * TJ, tile);
+    crt_tile<N, OutT, VEC>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t,
+                           blockIdx.y * TI, blockIdx.x * TJ, tile);
 }
 
 // Grouped: each block reconstructs one 32 x 32 tile of one problem's C.
@@ -274,8 +305,8 @@ __global__ void __launch_bounds__(256) crt_grouped_kernel(const GroupProblem* __
     __shared__ double tile[TJ][TI + 1];
     const CrtWork w = work[blockIdx.x];
     const GroupProblem& P = probs[w.problem];
-    crt_tile<N, double>(P.res, P.n_pad, (int64_t)P.m_pad * P.n_pad, P.m, P.n, P.e, P.f, P.alpha,
-                        P.beta,
+    crt_tile<N, double, true>(P.res, P.n_pad, (int64_t)P.m_pad * P.n_pad, P.m, P.n, P.e, P.f,
+                              P.alpha, P.beta,
                 P.C, P.ldc, t, w.i0, w.j0, tile);
 }
 
@@ -293,15 +324,15 @@ __global__ void scale_c_kernel(int m, int n, T beta, T* C, int64_t ldc) {
 }  // namespace
 
 namespace {
-template <typename OutT>
+template <typename OutT, bool VEC>
 cudaError_t launch_crt_typed(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
                              const int* sa, const int* sb, OutT alpha, OutT beta, OutT* C,
                              int64_t ldc, const ModTables& t, cudaStream_t stream) {
     dim3 grid((n + TJ - 1) / TJ, (m + TI - 1) / TI);
-#define OZAKI2_CRT_CASE(NN)                                                                 \
-    case NN:                                                                                \
-        crt_kernel<NN, OutT><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb, alpha, \
-                                                       beta, C, ldc, t.crt);                 \
+#define OZAKI2_CRT_CASE(NN)                                                                   \
+    case NN:                                                                                  \
+        crt_kernel<NN, OutT, VEC><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb,     \
+                                                            alpha, beta, C, ldc, t.crt);       \
         break;
     switch (t.N) {
         OZAKI2_CRT_CASE(2) OZAKI2_CRT_CASE(3) OZAKI2_CRT_CASE(4) OZAKI2_CRT_CASE(5)
@@ -319,14 +350,25 @@ cudaError_t launch_crt_typed(const int8_t* res, int64_t ldr, int64_t plane, int 
 cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
                        const int* sa, const int* sb, double alpha, double beta, void* C,
                        int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream,
-                       bool f32) {
+                       bool f32, bool padded) {
     (void)status;
     if (m <= 0 || n <= 0) return cudaSuccess;
-    if (f32)
-        return launch_crt_typed<float>(res, ldr, plane, m, n, sa, sb, (float)alpha, (float)beta,
-                                       static_cast<float*>(C), ldc, t, stream);
-    return launch_crt_typed<double>(res, ldr, plane, m, n, sa, sb, alpha, beta,
-                                    static_cast<double*>(C), ldc, t, stream);
+    // the 32-bit residue loads need 4-byte alignment and planes padded to whole 32 x 32 tiles
+    const bool vec = padded && (reinterpret_cast<uintptr_t>(res) & 3u) == 0 && ldr % 4 == 0 &&
+                     plane % 4 == 0 && ldr >= (int64_t)(n + TJ - 1) / TJ * TJ &&
+                     plane >= (int64_t)(m + TI - 1) / TI * TI * ldr;
+    if (f32) {
+        auto* c = static_cast<float*>(C);
+        return vec ? launch_crt_typed<float, true>(res, ldr, plane, m, n, sa, sb, (float)alpha,
+                                                   (float)beta, c, ldc, t, stream)
+                   : launch_crt_typed<float, false>(res, ldr, plane, m, n, sa, sb, (float)alpha,
+                                                    (float)beta, c, ldc, t, stream);
+    }
+    auto* c = static_cast<double*>(C);
+    return vec ? launch_crt_typed<double, true>(res, ldr, plane, m, n, sa, sb, alpha, beta, c, ldc,
+                                                t, stream)
+               : launch_crt_typed<double, false>(res, ldr, plane, m, n, sa, sb, alpha, beta, c,
+                                                 ldc, t, stream);
 }
 
 cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* work, int blocks,

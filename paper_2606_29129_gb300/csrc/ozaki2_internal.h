@@ -20,8 +20,11 @@ struct ConvertTables {
     uint32_t barrett[kMaxModuli];   // floor(2^32 / p)
     uint32_t pow21[kMaxModuli][4];  // 2^(21 j) mod p
     uint32_t off_pos[kMaxModuli];   // h = (p - 1) / 2
-    uint32_t off_neg[kMaxModuli];   // K p + h with K p the first multiple of p >= 2^31
+    uint32_t off_neg[kMaxModuli];   // K p + h with K p the first multiple of p >= the largest
+                                    // limb combination (2^21 - 1)(1 + 3 (p - 1))
     uint32_t bias[kMaxModuli];      // float bits of 1.5 2^23, minus h
+    uint32_t magic39[kMaxModuli];   // ceil(2^39 / p): floor(x / p) = umulhi(x, magic) >> 7 for
+                                    // every x below 2^39 / p, beyond any x formed here
 };
 
 struct CrtTables {
@@ -219,11 +222,12 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const v
                         cudaStream_t stream);
 
 // f32: C holds floats (SGEMM: C'' rounded to 24 bits, alpha and beta applied in single
-// precision), else doubles.
+// precision), else doubles.  padded: the residue buffer extends to whole 32 x 32 tiles in every
+// plane (true for the library's own layout), which allows 32-bit residue loads.
 cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
                        const int* sa, const int* sb, double alpha, double beta, void* C,
                        int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream,
-                       bool f32 = false);
+                       bool f32 = false, bool padded = false);
 
 cudaError_t launch_scale_c(int m, int n, double beta, void* C, int64_t ldc,
                            cudaStream_t stream, bool f32 = false);
