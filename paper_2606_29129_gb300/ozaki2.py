@@ -285,16 +285,11 @@ def ozaki2_crt(num_moduli, m, n, residues, ldr, plane_stride, shifts_a, shifts_b
 
 
 # ---------------------------------------------------------------- torch convenience
-def dgemm(A, B, num_moduli: int = 14, alpha: float = 1.0, beta: float = 0.0, C=None,
-          handle: Handle | None = None):
-    """C = alpha A @ B + beta C for row-major float64 CUDA tensors A (m, k), B (k, n).
-
-    Row-major storage of (m, k) is column-major storage of its transpose, so this calls
-    ozaki2_dgemm on C^T = B^T A^T.  Returns C (allocated when not given)."""
+def _rowmajor_gemm(name, entry, dtype, A, B, num_moduli, alpha, beta, C, handle):
     import torch
 
-    if A.dtype != torch.float64 or B.dtype != torch.float64 or not A.is_cuda or not B.is_cuda:
-        raise TypeError("dgemm expects float64 CUDA tensors")
+    if A.dtype != dtype or B.dtype != dtype or not A.is_cuda or not B.is_cuda:
+        raise TypeError(f"{name} expects {dtype} CUDA tensors")
     A = A.contiguous()
     B = B.contiguous()
     m, k = A.shape
@@ -302,10 +297,33 @@ def dgemm(A, B, num_moduli: int = 14, alpha: float = 1.0, beta: float = 0.0, C=N
     if k != k2:
         raise ValueError("inner dimensions differ")
     if C is None:
-        C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+        C = torch.empty((m, n), dtype=dtype, device=A.device)
         beta = 0.0
     elif not C.is_contiguous() or tuple(C.shape) != (m, n):
         raise ValueError("C must be a contiguous (m, n) tensor")
-    _check("ozaki2_dgemm", ozaki2_dgemm("N", "N", n, m, k, alpha, B, max(n, 1), A, max(k, 1),
-                                        beta, C, max(n, 1), num_moduli, handle))
+    _check(entry.__name__, entry("N", "N", n, m, k, alpha, B, max(n, 1), A, max(k, 1), beta, C,
+                                 max(n, 1), num_moduli, handle))
     return C
+
+
+def dgemm(A, B, num_moduli: int = 16, alpha: float = 1.0, beta: float = 0.0, C=None,
+          handle: Handle | None = None):
+    """C = alpha A @ B + beta C for row-major float64 CUDA tensors A (m, k), B (k, n).
+
+    Row-major storage of (m, k) is column-major storage of its transpose, so this calls
+    ozaki2_dgemm on C^T = B^T A^T.  Returns C (allocated when not given).  The default of 16
+    moduli is the smallest count not less accurate than cuBLAS DGEMM at m = n = k = 16384."""
+    import torch
+
+    return _rowmajor_gemm("dgemm", ozaki2_dgemm, torch.float64, A, B, num_moduli, alpha, beta, C,
+                          handle)
+
+
+def sgemm(A, B, num_moduli: int = 8, alpha: float = 1.0, beta: float = 0.0, C=None,
+          handle: Handle | None = None):
+    """The float32 counterpart of dgemm through ozaki2_sgemm (default 8 moduli, the smallest
+    count not less accurate than cuBLAS SGEMM at m = n = k = 16384)."""
+    import torch
+
+    return _rowmajor_gemm("sgemm", ozaki2_sgemm, torch.float32, A, B, num_moduli, alpha, beta, C,
+                          handle)

@@ -129,3 +129,16 @@ def test_full_size_sampled(oz, orc, size, N):
     blk = orc.sgemm_block(A.cpu().numpy(), B.cpu().numpy(), k, N, I, J)
     got = C[torch.from_numpy(J).cuda()][:, torch.from_numpy(I).cuda()].cpu().numpy()
     assert _gpu.same_bits(got, blk)
+
+
+def test_torch_convenience(oz, orc):
+    import torch
+
+    from paper_2606_29129_gb300 import sgemm
+
+    m, n, k = 33, 44, 55
+    A = torch.randn(m, k, dtype=torch.float32, device="cuda")
+    B = torch.randn(k, n, dtype=torch.float32, device="cuda")
+    C = sgemm(A, B)
+    ref = orc.sgemm(A.cpu().numpy(), B.cpu().numpy(), m, n, k, 8, "T", "T", lda=k, ldb=n)
+    assert _gpu.same_bits(C.cpu().numpy().T, ref)
