@@ -243,14 +243,16 @@ __device__ __forceinline__ void convert_contiguous_item(
     }
 }
 
+// One item per thread (a grid-stride loop here made the compiler keep two items' limbs live and
+// halved the occupancy).
 template <int N, typename T>
 __global__ void __launch_bounds__(256) convert_contiguous_kernel(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
     unsigned* status) {
     const int64_t total = (int64_t)rows_pad * (k_pad / 8);
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x)
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < total)
         convert_contiguous_item<N, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, g,
                                       status);
 }
@@ -314,11 +316,8 @@ __global__ void __launch_bounds__(256) convert_adjacent_kernel(
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
     unsigned* status) {
     __shared__ T tile[kTileK][kTileLines + 1];
-    const int tiles_l = (rows_pad + kTileLines - 1) / kTileLines;
-    const int64_t ntiles = (int64_t)tiles_l * (k_pad / kTileK);
-    for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x)
-        convert_adjacent_tile<N, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, tt,
-                                    tile, status);
+    convert_adjacent_tile<N, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad,
+                                blockIdx.x, tile, status);  // one tile per block
 }
 
 // Grouped: each block converts one tile (adjacent lines) or 256 groups of 8 elements
@@ -351,18 +350,16 @@ template <int N, typename T>
 cudaError_t launch_convert_n(const T* X, int64_t line_stride, int64_t elem_stride,
                              int lines, int len, const int* shifts, const ConvertTables& t,
                              __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
-                             int sms, cudaStream_t stream) {
+                             cudaStream_t stream) {
     if (elem_stride != 1) {  // then line_stride == 1: lines adjacent
-        const int64_t ntiles =
-            (int64_t)((rows_pad + kTileLines - 1) / kTileLines) * (k_pad / kTileK);
-        const int grid = (int)(ntiles < (int64_t)sms * 8 ? ntiles : (int64_t)sms * 8);
+        const int grid = (int)((int64_t)((rows_pad + kTileLines - 1) / kTileLines) *
+                               (k_pad / kTileK));
         convert_adjacent_kernel<N, T><<<grid, 256, 0, stream>>>(X, elem_stride, lines, len,
                                                                 shifts, t, out, rows_pad, k_pad,
                                                                 status);
     } else {
         const int64_t total = (int64_t)rows_pad * (k_pad / 8);
-        const int64_t blocks = (total + 255) / 256;
-        const int grid = (int)(blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8);
+        const int grid = (int)((total + 255) / 256);
         convert_contiguous_kernel<N, T><<<grid, 256, 0, stream>>>(X, line_stride, lines, len,
                                                                   shifts, t, out, rows_pad,
                                                                   k_pad, status);
@@ -383,17 +380,14 @@ cudaError_t launch_convert_bar(const void* X, int64_t line_stride, int64_t elem_
                                int lines, int len, const int* codes, void* plane, int rows_pad,
                                int k_pad, unsigned* status, cudaStream_t stream, bool f32) {
     if (rows_pad <= 0 || k_pad <= 0) return cudaSuccess;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     ConvertTables t = {};
     t.N = 1;
     auto* out = static_cast<__nv_bfloat16*>(plane);
     if (f32)
         return launch_convert_n<1>(static_cast<const float*>(X), line_stride, elem_stride, lines,
-                                   len, codes, t, out, rows_pad, k_pad, status, sms, stream);
+                                   len, codes, t, out, rows_pad, k_pad, status, stream);
     return launch_convert_n<1>(static_cast<const double*>(X), line_stride, elem_stride, lines,
-                               len, codes, t, out, rows_pad, k_pad, status, sms, stream);
+                               len, codes, t, out, rows_pad, k_pad, status, stream);
 }
 
 cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const ConvertWork* work,
@@ -427,12 +421,12 @@ template <typename T>
 cudaError_t launch_convert_typed(const T* X, int64_t line_stride, int64_t elem_stride, int lines,
                                  int len, const int* shifts, const ConvertTables& t,
                                  __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
-                                 int sms, cudaStream_t stream) {
+                                 cudaStream_t stream) {
     switch (t.N) {
 #define OZAKI2_CONVERT_CASE(NN)                                                              \
     case NN:                                                                                 \
         return launch_convert_n<NN>(X, line_stride, elem_stride, lines, len, shifts, t, out, \
-                                    rows_pad, k_pad, status, sms, stream);
+                                    rows_pad, k_pad, status, stream);
         OZAKI2_CONVERT_CASE(2) OZAKI2_CONVERT_CASE(3) OZAKI2_CONVERT_CASE(4)
         OZAKI2_CONVERT_CASE(5) OZAKI2_CONVERT_CASE(6) OZAKI2_CONVERT_CASE(7)
         OZAKI2_CONVERT_CASE(8) OZAKI2_CONVERT_CASE(9) OZAKI2_CONVERT_CASE(10)
@@ -451,15 +445,12 @@ cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stri
                            int rows_pad, int k_pad, unsigned* status, cudaStream_t stream,
                            bool f32) {
     if (rows_pad <= 0 || k_pad <= 0) return cudaSuccess;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     auto* out = static_cast<__nv_bfloat16*>(planes);
     if (f32)
         return launch_convert_typed(static_cast<const float*>(X), line_stride, elem_stride, lines,
-                                    len, shifts, t, out, rows_pad, k_pad, status, sms, stream);
+                                    len, shifts, t, out, rows_pad, k_pad, status, stream);
     return launch_convert_typed(static_cast<const double*>(X), line_stride, elem_stride, lines,
-                                len, shifts, t, out, rows_pad, k_pad, status, sms, stream);
+                                len, shifts, t, out, rows_pad, k_pad, status, stream);
 }
 
 }  // namespace ozaki2

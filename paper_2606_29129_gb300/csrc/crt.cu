@@ -72,8 +72,8 @@ __device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
         for (int l = 3 * g; l < 3 * g + 3 && l < N; ++l) {
             const int c = cres[l];
             const uint32_t x = (uint32_t)c * t.q[l] + t.off128[l];  // = q_l c (mod p_l), >= 0
-            uint32_t w = x - __umulhi(x, t.barrett[l]) * t.p[l];
-            if (w >= t.p[l]) w -= t.p[l];
+            // x < 2^16, so the rounded-up reciprocal gives the exact quotient
+            const uint32_t w = x - __umulhi(x, t.recip_up[l]) * t.p[l];
             v += w * t.coef[l];
         }
         S += (uint64_t)v * t.R48[g];

@@ -30,7 +30,7 @@ struct ConvertTables {
 struct CrtTables {
     int N;
     uint32_t p[kMaxModuli];
-    uint32_t barrett[kMaxModuli];   // floor(2^32 / p)
+    uint32_t recip_up[kMaxModuli];  // ceil(2^32 / p): umulhi(x, .) = floor(x / p) for x < 2^16
     uint32_t q[kMaxModuli];         // q_l = (P/p_l)^{-1} mod p_l
     uint32_t off[kMaxModuli];       // (-128 q_l) mod p_l, so (c + 128) q_l + off = q_l c (mod p_l)
     uint32_t off128[kMaxModuli];    // 128 q_l + off: c q_l + off128 = (c + 128) q_l + off >= 0

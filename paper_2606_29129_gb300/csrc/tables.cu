@@ -110,7 +110,7 @@ void build(int N, ModTables& t) {
         t.conv.magic39[l] = (uint32_t)(((1ull << 39) + p - 1) / p);
 
         t.crt.p[l] = p;
-        t.crt.barrett[l] = (uint32_t)((1ull << 32) / p);
+        t.crt.recip_up[l] = (uint32_t)(((1ull << 32) + p - 1) / p);
         t.crt.q[l] = q;
         t.crt.off[l] = (uint32_t)((p - (128u * q) % p) % p);
         t.crt.off128[l] = 128u * q + t.crt.off[l];
