@@ -223,12 +223,19 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 // residue planes are padded to whole 32 x 32 tiles and 4-byte aligned (the library's own
 // layout), so thread t reads four consecutive residues of row t/8 per plane with one 32-bit
 // load; otherwise each residue is read on its own.
+// ab: bit 0 set when alpha != 1 (multiply by alpha), bit 1 when beta != 0 (add beta C); the
+// host decides, so the kernel makes no floating-point comparisons.
+__host__ __device__ inline int ab_flags(double alpha, double beta) {
+    return (alpha != 1.0 ? 1 : 0) | (beta != 0.0 ? 2 : 0);
+}
+
 template <int N, typename OutT, bool VEC>
 __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t ldr,
                                          int64_t plane, int m, int n, const int* __restrict__ sa,
                                          const int* __restrict__ sb, OutT alpha, OutT beta,
-                                         OutT* __restrict__ C, int64_t ldc, const CrtTables& t,
-                                         int i0, int j0, OutT (*tile)[TI + 1]) {
+                                         int ab, OutT* __restrict__ C, int64_t ldc,
+                                         const CrtTables& t, int i0, int j0,
+                                         OutT (*tile)[TI + 1]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if constexpr (VEC) {
         const int il = threadIdx.x >> 3, jq = (threadIdx.x & 7) * 4;
@@ -270,7 +277,6 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
         }
     }
     __syncthreads();
-    const bool plain = (alpha == (OutT)1 && beta == (OutT)0);
 #pragma unroll
     for (int r = 0; r < TJ / 8; ++r) {
         const int jl = warp + 8 * r;
@@ -278,8 +284,8 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
         if (ii < m && jj < n) {
             OutT* out = C + ii + (int64_t)jj * ldc;
             const OutT y = tile[jl][lane];
-            OutT v = plain ? y : mul_rn(alpha, y);
-            if (beta != (OutT)0) v = add_rn(v, mul_rn(beta, *out));
+            OutT v = (ab & 1) ? mul_rn(alpha, y) : y;
+            if (ab & 2) v = add_rn(v, mul_rn(beta, *out));
             *out = v;
         }
     }
@@ -290,10 +296,10 @@ __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res
                                                   int64_t plane, int m, int n,
                                                   const int* __restrict__ sa,
                                                   const int* __restrict__ sb, OutT alpha,
-                                                  OutT beta, OutT* __restrict__ C,
+                                                  OutT beta, int ab, OutT* __restrict__ C,
                                                   int64_t ldc, const CrtTables t) {
     __shared__ OutT tile[TJ][TI + 1];
-    crt_tile<N, OutT, VEC>(res, ldr, plane, m, n, sa, sb, alpha, beta, C, ldc, t,
+    crt_tile<N, OutT, VEC>(res, ldr, plane, m, n, sa, sb, alpha, beta, ab, C, ldc, t,
                            blockIdx.y * TI, blockIdx.x * TJ, tile);
 }
 
@@ -306,7 +312,7 @@ __global__ void __launch_bounds__(256) crt_grouped_kernel(const GroupProblem* __
     const CrtWork w = work[blockIdx.x];
     const GroupProblem& P = probs[w.problem];
     crt_tile<N, double, true>(P.res, P.n_pad, (int64_t)P.m_pad * P.n_pad, P.m, P.n, P.e, P.f,
-                              P.alpha, P.beta,
+                              P.alpha, P.beta, P.ab,
                 P.C, P.ldc, t, w.i0, w.j0, tile);
 }
 
@@ -332,7 +338,9 @@ cudaError_t launch_crt_typed(const int8_t* res, int64_t ldr, int64_t plane, int 
 #define OZAKI2_CRT_CASE(NN)                                                                   \
     case NN:                                                                                  \
         crt_kernel<NN, OutT, VEC><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb,     \
-                                                            alpha, beta, C, ldc, t.crt);       \
+                                                            alpha, beta,                       \
+                                                            ab_flags(alpha, beta), C, ldc,     \
+                                                            t.crt);                            \
         break;
     switch (t.N) {
         OZAKI2_CRT_CASE(2) OZAKI2_CRT_CASE(3) OZAKI2_CRT_CASE(4) OZAKI2_CRT_CASE(5)

@@ -183,6 +183,7 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
         g.k_pad = (int)k_pad;
         g.alpha = p.alpha;
         g.beta = p.beta;
+        g.ab = (p.alpha != 1.0 ? 1 : 0) | (p.beta != 0.0 ? 2 : 0);
         g.scaling = scaling;
         g.pprime = scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
         g.delta = T->delta;

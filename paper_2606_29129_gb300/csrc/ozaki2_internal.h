@@ -79,6 +79,7 @@ struct GroupProblem {
     int m, n, k, N;
     int m_pad, n_pad, k_pad;
     double alpha, beta;
+    int ab;              // bit 0: alpha != 1, bit 1: beta != 0 (set on the host)
     float pprime;        // P'_prop, or P'_fast in the original fast mode
     float delta;
     int scaling;         // OZAKI2_SCALING_*

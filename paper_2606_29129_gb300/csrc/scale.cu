@@ -153,33 +153,43 @@ __global__ void __launch_bounds__(32) scale_adjacent_kernel(const double* __rest
 constexpr int kWarpsPerBlock = 4;
 constexpr int kTileLen = 32;
 
+// Elements per line and tile: 32 doubles or 64 floats (256 bytes), loaded as W = 8 / sizeof(T)
+// coalesced 128- or 256-byte rows per line.
+template <typename T>
+__host__ __device__ constexpr int tile_len() { return kTileLen * (8 / (int)sizeof(T)); }
+
 // Lines line0 .. line0 + 31 of a contiguous-line matrix, summed by one warp (t: its smem tile).
 template <int SCALING, typename T = double>
 __device__ __forceinline__ void scale_contiguous_warp(const T* __restrict__ X, int64_t ld,
                                                       int lines, int len, int line0,
                                                       float pprime, float delta, int* shifts,
                                                       unsigned* status,
-                                                      double (*t)[kTileLen + 1]) {
+                                                      T (*t)[tile_len<T>() + 1]) {
+    constexpr int W = 8 / (int)sizeof(T), TL = tile_len<T>();
     const int lane = threadIdx.x & 31;
     const int nl = min(32, lines - line0);
-    T reg[32];
+    T reg[32][W];
     auto load = [&](int h0) {
-        const int cnt = min(kTileLen, len - h0);
 #pragma unroll
         for (int r = 0; r < 32; ++r)
-            reg[r] = (r < nl && lane < cnt) ? __ldg(X + (int64_t)(line0 + r) * ld + h0 + lane)
-                                            : (T)0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const int h = h0 + 32 * w + lane;
+                reg[r][w] = (r < nl && h < len) ? __ldg(X + (int64_t)(line0 + r) * ld + h) : (T)0;
+            }
     };
     LineAcc<SCALING> acc;
     if (len > 0) load(0);
-    for (int h0 = 0; h0 < len; h0 += kTileLen) {
-        const int cnt = min(kTileLen, len - h0);
+    for (int h0 = 0; h0 < len; h0 += TL) {
+        const int cnt = min(TL, len - h0);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) t[r][lane] = to_double(reg[r]);
+        for (int r = 0; r < 32; ++r)
+#pragma unroll
+            for (int w = 0; w < W; ++w) t[r][32 * w + lane] = reg[r][w];
         __syncwarp();
-        if (h0 + kTileLen < len) load(h0 + kTileLen);
+        if (h0 + TL < len) load(h0 + TL);
         if (lane < nl) {
-            for (int u = 0; u < cnt; ++u) acc.add(t[lane][u]);
+            for (int u = 0; u < cnt; ++u) acc.add(to_double(t[lane][u]));
         }
         __syncwarp();
     }
@@ -229,7 +239,7 @@ template <int SCALING, typename T>
 __global__ void __launch_bounds__(128) scale_pair_kernel(ScaleSide a, ScaleSide b, int blocks_a,
                                                          int len, float pprime, float delta,
                                                          unsigned* status) {
-    __shared__ double tile[kWarpsPerBlock][32][kTileLen + 1];
+    __shared__ T tile[kWarpsPerBlock][32][tile_len<T>() + 1];
     const bool side_b = (int)blockIdx.x >= blocks_a;
     const ScaleSide& S = side_b ? b : a;
     const T* X = static_cast<const T*>(S.X);
