@@ -697,8 +697,8 @@ def run_sweep(args):
 
 
 def run_scaling_study(args):
-    """Figs. 1-3 on the GPU: the original fast mode (Algorithm 1) against the proposed scaling
-    (Algorithm 2), both at N = 20, for A = 2^s A^, B = 2^s B^, s = -10..10.
+    """Figs. 1-3 on the GPU: the original fast mode (Algorithm 1) and accurate mode against the
+    proposed scaling (Algorithm 2), all at N = 20, for A = 2^s A^, B = 2^s B^, s = -10..10.
 
     Random inputs (eq. random-matrix-generation, phi in {0.5, 1, 2}): per s, the max relative
     error of each mode against double-double on a sampled block (the block's reference is taken
@@ -722,6 +722,8 @@ def run_scaling_study(args):
     log2_half_P = sum(math.log2(p) for p in moduli) - 1.0
     hf = oz.Handle()
     hf.set_option(oz.OPT_SCALING, oz.SCALING_FAST)
+    ha = oz.Handle()
+    ha.set_option(oz.OPT_SCALING, oz.SCALING_ACCURATE)
     hp = oz.Handle()
 
     def emulate(A, B, C, m, n, k, h):
@@ -739,6 +741,7 @@ def run_scaling_study(args):
         m = n = k = size
         Cf = torch.empty((n, m), dtype=torch.float64, device="cuda")
         Cp = torch.empty_like(Cf)
+        Ca = torch.empty_like(Cf)
         for pi, phi in enumerate((0.5, 1.0, 2.0)):
             A0 = synthetic.paper_matrix_torch(m, k, phi, synthetic.seed_for(2, pi, 1))
             B0 = synthetic.paper_matrix_torch(k, n, phi, synthetic.seed_for(2, pi, 2))
@@ -756,12 +759,15 @@ def run_scaling_study(args):
                 hi, lo = hi0 * 4.0**s, lo0 * 4.0**s
                 emulate(A, B, Cf, m, n, k, hf)
                 emulate(A, B, Cp, m, n, k, hp)
+                emulate(A, B, Ca, m, n, k, ha)
                 torch.cuda.synchronize()
                 line = {"study": "fig2", "size": size, "phi": phi, "s": s, "N": N,
                         "sample": f"{len(I)}x{len(J)}",
                         "fast_vs_dd_block": oracle.max_rel_error(block(Cf), hi, lo)[0],
                         "proposed_vs_dd_block": oracle.max_rel_error(block(Cp), hi, lo)[0],
-                        "fast_full_vs_proposed": full_rel(Cf, Cp)}
+                        "accurate_vs_dd_block": oracle.max_rel_error(block(Ca), hi, lo)[0],
+                        "fast_full_vs_proposed": full_rel(Cf, Cp),
+                        "accurate_full_vs_proposed": full_rel(Ca, Cp)}
                 if s in (-10, 0, 10):
                     Cd = torch.matmul(B.view(n, k), A.view(k, m))
                     torch.cuda.synchronize()
@@ -779,6 +785,7 @@ def run_scaling_study(args):
             exact = torch.full_like(Cf, k * 4.0**s)
             emulate(A, B, Cf, m, n, k, hf)
             emulate(A, B, Cp, m, n, k, hp)
+            emulate(A, B, Ca, m, n, k, ha)
             rc = oz.ozaki2_scale_a("N", m, k, A, m, N, e, hf)
             if rc:
                 raise oz.Ozaki2Error("ozaki2_scale_a", rc)
@@ -794,9 +801,10 @@ def run_scaling_study(args):
                               "fast_log2_ApBp": math.log2(k) + 2 * (ef + s),
                               "proposed_log2_ApBp": math.log2(k) + 2 * (ep + s),
                               "fast_full_vs_exact": full_rel(Cf, exact),
-                              "proposed_full_vs_exact": full_rel(Cp, exact)}), flush=True)
+                              "proposed_full_vs_exact": full_rel(Cp, exact),
+                              "accurate_full_vs_exact": full_rel(Ca, exact)}), flush=True)
             del A, B, exact
-        del ones_A, ones_B, Cf, Cp
+        del ones_A, ones_B, Cf, Cp, Ca
         torch.cuda.empty_cache()
 
 

@@ -257,11 +257,12 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
             return rc;
     }
     mark(1);
+    const bool accurate = ctx->scaling == OZAKI2_SCALING_ACCURATE;
     if ((rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, (int)L.m_pad,
-                                     (int)L.k_pad, ctx->d_status, st, f32))))
+                                     (int)L.k_pad, ctx->d_status, st, f32, accurate))))
         return rc;
     if ((rc = cuda_rc(launch_convert(B, bls, bes, n, k, f, T->conv, pb, (int)L.n_pad,
-                                     (int)L.k_pad, ctx->d_status, st, f32))))
+                                     (int)L.k_pad, ctx->d_status, st, f32, accurate))))
         return rc;
     mark(2);
     if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, pa, pb, res,
@@ -706,8 +707,10 @@ static int convert_common(ozaki2_handle_t handle, bool is_a, char trans, int lin
     int64_t ls, es;
     if (is_a) rows_of_op(trans, ld, &ls, &es);
     else cols_of_op(trans, ld, &ls, &es);
+    // the shifts may come from any scaling mode: use the limb count that covers them all
     return cuda_rc(launch_convert(X, ls, es, lines, len, shifts, mod_tables(num_moduli)->conv,
-                                  planes, rows_pad, k_pad, ctx->d_status, ctx->stream));
+                                  planes, rows_pad, k_pad, ctx->d_status, ctx->stream, false,
+                                  true));
 }
 
 int ozaki2_convert_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,

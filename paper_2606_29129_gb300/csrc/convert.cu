@@ -29,6 +29,11 @@ __host__ __device__ constexpr int p_bits(int N) {
 // 2^(bits(P)/2); accurate mode allows up to 2^6 times more (|a| < 2^(E+1), mu' = 2^(5-E), and
 // the second factor is at most 2^P'), so floor(bits(P)/2) + 6 bits are provided.
 __host__ __device__ constexpr int limbs_for(int N) { return (p_bits(N) / 2 + 6 + 20) / 21; }
+// The proposed and fast scalings keep |a'| < 2^(log2(P-1)/2 - 0.5), i.e. at most
+// floor(bits(P)/2 - 0.5) + 1 bits: one limb fewer for N = 4, 5, 10, 15 and 16.
+__host__ __device__ constexpr int limbs_scaled(int N) {
+    return ((p_bits(N) * 2 - 1) / 4 + 1 + 20) / 21;
+}
 
 struct Scaled {
     uint32_t d[4];
@@ -145,7 +150,7 @@ __device__ __forceinline__ uint32_t bar_bits(float a, int E) {
 
 // Writes the residues of 8 consecutive elements of one line into the N planes.  N = 1 is the
 // a-bar plane of accurate mode instead, with e the line's exponent code.
-template <int N, typename V>
+template <int N, int L, typename V>
 __device__ __forceinline__ void store_residues8(const V (&v)[8], int e, bool live,
                                                 const ConvertTables& t, __nv_bfloat16* planes,
                                                 int64_t plane_elems, int64_t offset,
@@ -162,7 +167,6 @@ __device__ __forceinline__ void store_residues8(const V (&v)[8], int e, bool liv
         *reinterpret_cast<uint4*>(planes + offset) = make_uint4(w[0], w[1], w[2], w[3]);
         return;
     }
-    constexpr int L = limbs_for(N);
     Scaled sc[8];
     const bool zero = (e == OZAKI2_SHIFT_NONFINITE) || !live;
 #pragma unroll
@@ -216,7 +220,7 @@ __device__ __forceinline__ void load8(const float* src, bool vec, float (&v)[8])
 }
 
 // T = double (DGEMM) or float (SGEMM).
-template <int N, typename T>
+template <int N, int L, typename T>
 __device__ __forceinline__ void convert_contiguous_item(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
@@ -238,14 +242,14 @@ __device__ __forceinline__ void convert_contiguous_item(
             for (int u = 0; u < 8; ++u) v[u] = (row_live && h0 + u < len) ? __ldg(src + u) : (T)0;
         }
         const int e = row_live ? shifts[i] : 0;
-        store_residues8<N>(v, e, row_live, t, planes, plane_elems, (int64_t)i * k_pad + h0,
+        store_residues8<N, L>(v, e, row_live, t, planes, plane_elems, (int64_t)i * k_pad + h0,
                            status);
     }
 }
 
 // One item per thread (a grid-stride loop here made the compiler keep two items' limbs live and
 // halved the occupancy).
-template <int N, typename T>
+template <int N, int L, typename T>
 __global__ void __launch_bounds__(256) convert_contiguous_kernel(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(256) convert_contiguous_kernel(
     const int64_t total = (int64_t)rows_pad * (k_pad / 8);
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g < total)
-        convert_contiguous_item<N, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, g,
+        convert_contiguous_item<N, L, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, g,
                                       status);
 }
 
@@ -265,7 +269,7 @@ constexpr int kTileLines = 64;
 constexpr int kTileK = 64;
 
 // Tile tt (64 lines x 64 elements) of an adjacent-line matrix; all 256 threads take part.
-template <int N, typename T>
+template <int N, int L, typename T>
 __device__ __forceinline__ void convert_adjacent_tile(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
@@ -302,7 +306,7 @@ __device__ __forceinline__ void convert_adjacent_tile(
                 for (int u = 0; u < 8; ++u) v[u] = tile[8 * hg + u][ll];
                 const bool live = line < lines;
                 const int e = live ? shifts[line] : 0;
-                store_residues8<N>(v, e, live, t, planes, plane_elems,
+                store_residues8<N, L>(v, e, live, t, planes, plane_elems,
                                    (int64_t)line * k_pad + h0 + 8 * hg, status);
             }
         }
@@ -310,19 +314,19 @@ __device__ __forceinline__ void convert_adjacent_tile(
     }
 }
 
-template <int N, typename T>
+template <int N, int L, typename T>
 __global__ void __launch_bounds__(256) convert_adjacent_kernel(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
     unsigned* status) {
     __shared__ T tile[kTileK][kTileLines + 1];
-    convert_adjacent_tile<N, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad,
+    convert_adjacent_tile<N, L, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad,
                                 blockIdx.x, tile, status);  // one tile per block
 }
 
 // Grouped: each block converts one tile (adjacent lines) or 256 groups of 8 elements
 // (contiguous lines) of one side of one problem.
-template <int N>
+template <int N, int L>
 __global__ void __launch_bounds__(256) convert_grouped_kernel(
     const GroupProblem* __restrict__ probs, const ConvertWork* __restrict__ work,
     const ConvertTables t, unsigned* status) {
@@ -336,35 +340,51 @@ __global__ void __launch_bounds__(256) convert_grouped_kernel(
     const int* shifts = w.side ? P.f : P.e;
     auto* planes = static_cast<__nv_bfloat16*>(w.side ? P.pb : P.pa);
     if (es != 1) {
-        convert_adjacent_tile<N, double>(X, es, lines, P.k, shifts, t, planes, rows_pad, P.k_pad,
-                                         w.block, tile, status);
+        convert_adjacent_tile<N, L, double>(X, es, lines, P.k, shifts, t, planes, rows_pad,
+                                            P.k_pad, w.block, tile, status);
     } else {
         const int64_t g = (int64_t)w.block * 256 + threadIdx.x;
         if (g < (int64_t)rows_pad * (P.k_pad / 8))
-            convert_contiguous_item<N, double>(X, ls, lines, P.k, shifts, t, planes, rows_pad,
-                                               P.k_pad, g, status);
+            convert_contiguous_item<N, L, double>(X, ls, lines, P.k, shifts, t, planes, rows_pad,
+                                                  P.k_pad, g, status);
     }
 }
 
-template <int N, typename T>
-cudaError_t launch_convert_n(const T* X, int64_t line_stride, int64_t elem_stride,
-                             int lines, int len, const int* shifts, const ConvertTables& t,
-                             __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
-                             cudaStream_t stream) {
+template <int N, int L, typename T>
+cudaError_t launch_convert_nl(const T* X, int64_t line_stride, int64_t elem_stride,
+                              int lines, int len, const int* shifts, const ConvertTables& t,
+                              __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
+                              cudaStream_t stream) {
     if (elem_stride != 1) {  // then line_stride == 1: lines adjacent
         const int grid = (int)((int64_t)((rows_pad + kTileLines - 1) / kTileLines) *
                                (k_pad / kTileK));
-        convert_adjacent_kernel<N, T><<<grid, 256, 0, stream>>>(X, elem_stride, lines, len,
+        convert_adjacent_kernel<N, L, T><<<grid, 256, 0, stream>>>(X, elem_stride, lines, len,
                                                                 shifts, t, out, rows_pad, k_pad,
                                                                 status);
     } else {
         const int64_t total = (int64_t)rows_pad * (k_pad / 8);
         const int grid = (int)((total + 255) / 256);
-        convert_contiguous_kernel<N, T><<<grid, 256, 0, stream>>>(X, line_stride, lines, len,
+        convert_contiguous_kernel<N, L, T><<<grid, 256, 0, stream>>>(X, line_stride, lines, len,
                                                                   shifts, t, out, rows_pad,
                                                                   k_pad, status);
     }
     return cudaGetLastError();
+}
+
+// Accurate mode's a' can take six more bits than the proposed and fast scalings allow.
+template <int N, typename T>
+cudaError_t launch_convert_n(const T* X, int64_t line_stride, int64_t elem_stride,
+                             int lines, int len, const int* shifts, const ConvertTables& t,
+                             __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
+                             cudaStream_t stream, bool accurate = false) {
+    if constexpr (limbs_scaled(N) != limbs_for(N)) {
+        if (!accurate)
+            return launch_convert_nl<N, limbs_scaled(N), T>(X, line_stride, elem_stride, lines,
+                                                            len, shifts, t, out, rows_pad, k_pad,
+                                                            status, stream);
+    }
+    return launch_convert_nl<N, limbs_for(N), T>(X, line_stride, elem_stride, lines, len, shifts,
+                                                 t, out, rows_pad, k_pad, status, stream);
 }
 
 }  // namespace
@@ -390,14 +410,30 @@ cudaError_t launch_convert_bar(const void* X, int64_t line_stride, int64_t elem_
                                len, codes, t, out, rows_pad, k_pad, status, stream);
 }
 
+namespace {
+template <int N>
+void launch_convert_grouped_n(const GroupProblem* probs, const ConvertWork* work, int blocks,
+                              const ConvertTables& t, unsigned* status, cudaStream_t stream,
+                              bool accurate) {
+    if constexpr (limbs_scaled(N) != limbs_for(N)) {
+        if (!accurate) {
+            convert_grouped_kernel<N, limbs_scaled(N)><<<blocks, 256, 0, stream>>>(probs, work, t,
+                                                                                   status);
+            return;
+        }
+    }
+    convert_grouped_kernel<N, limbs_for(N)><<<blocks, 256, 0, stream>>>(probs, work, t, status);
+}
+}  // namespace
+
 cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const ConvertWork* work,
                                    int blocks, const ConvertTables& t, unsigned* status,
-                                   cudaStream_t stream) {
+                                   cudaStream_t stream, bool accurate) {
     if (blocks <= 0) return cudaSuccess;
     switch (N) {
 #define OZAKI2_CONVERT_GROUPED_CASE(NN)                                                      \
     case NN:                                                                                 \
-        convert_grouped_kernel<NN><<<blocks, 256, 0, stream>>>(probs, work, t, status);      \
+        launch_convert_grouped_n<NN>(probs, work, blocks, t, status, stream, accurate);      \
         break;
         OZAKI2_CONVERT_GROUPED_CASE(1)  // the A-bar / B-bar planes of accurate mode
         OZAKI2_CONVERT_GROUPED_CASE(2) OZAKI2_CONVERT_GROUPED_CASE(3)
@@ -421,12 +457,12 @@ template <typename T>
 cudaError_t launch_convert_typed(const T* X, int64_t line_stride, int64_t elem_stride, int lines,
                                  int len, const int* shifts, const ConvertTables& t,
                                  __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
-                                 cudaStream_t stream) {
+                                 cudaStream_t stream, bool accurate) {
     switch (t.N) {
 #define OZAKI2_CONVERT_CASE(NN)                                                              \
     case NN:                                                                                 \
         return launch_convert_n<NN>(X, line_stride, elem_stride, lines, len, shifts, t, out, \
-                                    rows_pad, k_pad, status, stream);
+                                    rows_pad, k_pad, status, stream, accurate);
         OZAKI2_CONVERT_CASE(2) OZAKI2_CONVERT_CASE(3) OZAKI2_CONVERT_CASE(4)
         OZAKI2_CONVERT_CASE(5) OZAKI2_CONVERT_CASE(6) OZAKI2_CONVERT_CASE(7)
         OZAKI2_CONVERT_CASE(8) OZAKI2_CONVERT_CASE(9) OZAKI2_CONVERT_CASE(10)
@@ -443,14 +479,15 @@ cudaError_t launch_convert_typed(const T* X, int64_t line_stride, int64_t elem_s
 cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, const int* shifts, const ConvertTables& t, void* planes,
                            int rows_pad, int k_pad, unsigned* status, cudaStream_t stream,
-                           bool f32) {
+                           bool f32, bool accurate) {
     if (rows_pad <= 0 || k_pad <= 0) return cudaSuccess;
     auto* out = static_cast<__nv_bfloat16*>(planes);
     if (f32)
         return launch_convert_typed(static_cast<const float*>(X), line_stride, elem_stride, lines,
-                                    len, shifts, t, out, rows_pad, k_pad, status, stream);
+                                    len, shifts, t, out, rows_pad, k_pad, status, stream,
+                                    accurate);
     return launch_convert_typed(static_cast<const double*>(X), line_stride, elem_stride, lines,
-                                len, shifts, t, out, rows_pad, k_pad, status, stream);
+                                len, shifts, t, out, rows_pad, k_pad, status, stream, accurate);
 }
 
 }  // namespace ozaki2

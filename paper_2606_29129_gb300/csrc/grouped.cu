@@ -255,8 +255,8 @@ int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_de
     }
     for (size_t g = 0; g < P.conv_n.size(); ++g)
         if (launch_convert_grouped(P.conv_n[g], dgp, dcw + P.conv_begin[g], P.conv_count[g],
-                                   mod_tables(P.conv_n[g])->conv, status,
-                                   stream) != cudaSuccess)
+                                   mod_tables(P.conv_n[g])->conv, status, stream,
+                                   P.accurate) != cudaSuccess)
             return OZAKI2_ERROR_CUDA;
     int rc = launch_residue_gemm_grouped(dgg, (int)P.idx.size(), P.total_tiles,
                                          mod_tables(OZAKI2_MAX_MODULI)->epi, status, num_sms,

@@ -123,7 +123,7 @@ cudaError_t launch_scale_grouped(const GroupProblem* probs, const ScaleWork* wor
                                  unsigned* status, cudaStream_t stream);
 cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const ConvertWork* work,
                                    int blocks, const ConvertTables& t, unsigned* status,
-                                   cudaStream_t stream);
+                                   cudaStream_t stream, bool accurate = false);
 cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* work, int blocks,
                                const CrtTables& t, cudaStream_t stream);
 // Blocks of the grouped convert for one side of one problem.
@@ -211,11 +211,12 @@ cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stri
                          cudaStream_t stream, int scaling = OZAKI2_SCALING_PROPOSED,
                          float delta = 0.0f);
 
-// f32: X holds floats (SGEMM), else doubles.
+// f32: X holds floats (SGEMM), else doubles.  accurate: the shifts come from accurate mode,
+// whose a' may need six more bits than the proposed and fast scalings allow.
 cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, const int* shifts, const ConvertTables& t, void* planes,
                            int rows_pad, int k_pad, unsigned* status, cudaStream_t stream,
-                           bool f32 = false);
+                           bool f32 = false, bool accurate = false);
 
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
                         const void* planes_b, int8_t* out, const EpilogueTables& t,
