@@ -406,7 +406,7 @@ def measure_e2e(args, oz, h, A, B, m, n, k, N, torch, gemm=None):
     step(0)
     step(1)
     torch.cuda.synchronize()
-    reps = max(2, min(args.steps, 6))
+    reps = max(4, min(args.steps, 10))
     t0 = time.perf_counter()
     for i in range(reps):
         step(i)
