@@ -4,10 +4,11 @@
 //
 // Integer-only arithmetic.  The double's 53-bit mantissa M and its exponent give
 // |a'| = floor(M 2^sh), held as L 21-bit limbs d_j (L = 1 for N <= 3, 2 up to N = 9, 3 up to
-// N = 14, 4 up to N = 20).  For an odd modulus, x = sum_j d_j (2^(21 j) mod p) < 2^31 and one
-// Barrett step gives |a'| mod p; the symmetric representative is negated for negative a'.  For p = 256 the residue
-// is the low byte of +-|a'| read as a signed byte ([-128, 127]).  Each small integer is exact in
-// bf16.  Kernels are instantiated per N so every per-modulus constant is an immediate operand.
+// N = 14, 4 up to N = 20).  For an odd modulus, t = sum_j d_j (2^(21 j) mod p) < 2^31 and one
+// exact quotient gives the symmetric residue of |a'|, negated for negative a'.  For p = 256 the
+// residue is the low byte of +-|a'| read as a signed byte ([-128, 127]).  Each small integer is
+// exact in bf16.  Kernels are instantiated per N so every per-modulus constant is an immediate
+// operand.
 //
 // Traffic per element: 8 bytes read, 2N bytes written.
 #include <cuda_bf16.h>
@@ -35,9 +36,15 @@ __host__ __device__ constexpr int limbs_scaled(int N) {
     return ((p_bits(N) * 2 - 1) / 4 + 1 + 20) / 21;
 }
 
+// The float 1.5 * 2^23 (bits 0x4B400000): for |s| < 2^22 the bits B + s are the float B + s.
+constexpr uint32_t kFloatB = 0x4B400000u;
+
+// |a'| as limbs.  d[0] carries kFloatB in its unused upper bits (d[0] = limb 0 | kFloatB, the
+// two never overlap), so a residue sum started from d[0] is offset by kFloatB at no cost.
 struct Scaled {
     uint32_t d[4];
     uint32_t low;  // low 32 bits of |a'|
+    float sgn;     // +1 or -1: the sign of a'
     bool neg;
 };
 
@@ -62,7 +69,8 @@ __device__ __forceinline__ Scaled split_mantissa(uint64_t M, int mbits, int sh, 
         lo = M >> (-sh);
     }
     r.low = (uint32_t)lo;
-    r.d[0] = (uint32_t)lo & kMask21;
+    r.sgn = neg ? -1.0f : 1.0f;
+    r.d[0] = ((uint32_t)lo & kMask21) | kFloatB;
     r.d[1] = (uint32_t)(lo >> 21) & kMask21;
     r.d[2] = (uint32_t)(lo >> 42) & kMask21;
     r.d[3] = (uint32_t)((lo >> 63) | (hi << 1)) & kMask21;
@@ -89,7 +97,7 @@ __device__ __forceinline__ Scaled split_scaled(float a, int e, unsigned* status)
 
 // bf16 bits (in the upper half of a float) of the small integer s.
 __device__ __forceinline__ uint32_t small_int_bits(int s) {
-    return __float_as_uint(__int_as_float(0x4B400000 + s) - 12582912.0f);
+    return __float_as_uint(__int_as_float((int)kFloatB + s) - 12582912.0f);
 }
 
 // Symmetric residue of +-|a'| modulo the l-th modulus, as bf16 bits.
@@ -99,18 +107,19 @@ __device__ __forceinline__ uint32_t residue_bits(const Scaled& v, const ConvertT
         const uint32_t b = (v.neg ? 0u - v.low : v.low) & 0xFFu;
         return small_int_bits((int)(int8_t)(uint8_t)b);
     }
-    // Odd p, h = (p - 1)/2: t == |a'| (mod p), t <= (2^21 - 1)(1 + 3(p - 1)) < 2^31; x = t + h,
-    // or K p + h - t for a negative a' (K p >= that bound, a multiple of p), so
-    // x == a' + h (mod p) with 0 <= x < 2^31.  The quotient by p is exact with the 2^39 magic
-    // (x (ceil(2^39/p) p - 2^39) < 2^39 for every such x and modulus), so r = x mod p directly,
-    // and r - h is the symmetric residue in [-h, h], written straight into the float bits.
+    // Odd p, h = (p - 1)/2: t == |a'| (mod p) with t <= (2^21 - 1)(1 + 3(p - 1)) < 2^31, summed
+    // from d[0] so y = kFloatB + t.  With q = floor((t + h)/p), s = t - q p lies in [-h, h] and is
+    // the symmetric residue of |a'|; y - q p = kFloatB + s is the float 1.5 2^23 + s, and one
+    // exact FMA gives sgn s.  x = t + h < 2^31 is y - (kFloatB - h) (table `bias`), and its
+    // quotient by p is exact with the 2^39 magic (x (ceil(2^39/p) p - 2^39) < 2^39 for every such
+    // x and modulus).
     const uint32_t p = t.p[l];
-    uint32_t tt = v.d[0];
+    uint32_t y = v.d[0];
 #pragma unroll
-    for (int j = 1; j < L; ++j) tt += v.d[j] * t.pow21[l][j];
-    const uint32_t x = tt * (v.neg ? 0xFFFFFFFFu : 1u) + (v.neg ? t.off_neg[l] : t.off_pos[l]);
-    const uint32_t r = x - (__umulhi(x, t.magic39[l]) >> 7) * p;
-    return __float_as_uint(__uint_as_float(r + t.bias[l]) - 12582912.0f);
+    for (int j = 1; j < L; ++j) y += v.d[j] * t.pow21[l][j];
+    const uint32_t x = y - t.bias[l];
+    const uint32_t fb = y - (__umulhi(x, t.magic39[l]) >> 7) * p;
+    return __float_as_uint(fmaf(v.sgn, __uint_as_float(fb), v.sgn * -12582912.0f));
 }
 
 // Accurate mode (Section 2.3): a-bar = ceil(2^(5 - E) |a|) <= 64 with E = floor(log2 max |a|) of
@@ -171,7 +180,8 @@ __device__ __forceinline__ void store_residues8(const V (&v)[8], int e, bool liv
     const bool zero = (e == OZAKI2_SHIFT_NONFINITE) || !live;
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-        sc[u] = zero ? Scaled{{0, 0, 0, 0}, 0, false} : split_scaled<L>(v[u], e, status);
+        sc[u] = zero ? Scaled{{kFloatB, 0, 0, 0}, 0, 1.0f, false}
+                     : split_scaled<L>(v[u], e, status);
 #pragma unroll
     for (int l = 0; l < N; ++l) {
         uint32_t w[4];

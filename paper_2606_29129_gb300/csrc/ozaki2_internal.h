@@ -17,12 +17,8 @@ constexpr int kMaxWords = 6;  // 32-bit words of sum_l P_l w_l < N P for N <= 20
 struct ConvertTables {
     int N;
     uint32_t p[kMaxModuli];
-    uint32_t barrett[kMaxModuli];   // floor(2^32 / p)
     uint32_t pow21[kMaxModuli][4];  // 2^(21 j) mod p
-    uint32_t off_pos[kMaxModuli];   // h = (p - 1) / 2
-    uint32_t off_neg[kMaxModuli];   // K p + h with K p the first multiple of p >= the largest
-                                    // limb combination (2^21 - 1)(1 + 3 (p - 1))
-    uint32_t bias[kMaxModuli];      // float bits of 1.5 2^23, minus h
+    uint32_t bias[kMaxModuli];      // float bits of 1.5 2^23, minus h = (p - 1) / 2
     uint32_t magic39[kMaxModuli];   // ceil(2^39 / p): floor(x / p) = umulhi(x, magic) >> 7 for
                                     // every x below 2^39 / p, beyond any x formed here
 };

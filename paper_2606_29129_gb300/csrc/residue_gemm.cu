@@ -13,7 +13,8 @@
 // Pipeline (one CTA per SM, persistent over (modulus, m-tile, n-tile) work):
 //   warp 0   TMA producer: 128x64 A and 256x64 B bf16 tiles, 128-byte swizzle, 4 stages.
 //   warp 1   TMEM allocator and MMA issuer (one thread): 4 x (M=128, N=256, K=16) per stage.
-//   warps 4-7 epilogue: TMEM lanes 32*(warp%4).. ; in-place reductions and the final drain.
+//   warps 4-11 epilogue: TMEM lanes 32*(warp%4).., one half of the columns each; in-place
+//            reductions and the final drain.
 // Two TMEM accumulators (2 x 256 columns) hold two tiles whose K chunks are interleaved, so the
 // in-place reduction of one tile overlaps the MMAs of the other.
 //
@@ -35,10 +36,10 @@ constexpr int A_BYTES = BM * BK * 2;           // 16 KiB
 constexpr int B_BYTES = BN * BK * 2;           // 32 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 2 * BN;              // two fp32 accumulators of 128 x 256
-constexpr int NUM_THREADS = 256;
-constexpr int EPI_WARP0 = 4;       // warps 4..7: one epilogue warp per TMEM lane quarter
-constexpr int EPI_WARPS = 4;
-constexpr int EPI_COLS = 256;      // accumulator columns drained by one epilogue warp
+constexpr int NUM_THREADS = 384;
+constexpr int EPI_WARP0 = 4;       // warps 4..11: two epilogue warps per TMEM lane quarter
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_COLS = 128;      // accumulator columns drained by one epilogue warp
 constexpr int NUM_BARRIERS = 2 * STAGES + 5;   // full, empty, acc_full[2], acc_empty[2], drain
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARRIERS * 8 + 16;
 constexpr int GROUP_M = 16;                    // m-tiles per group in the tile order (L2 reuse)
@@ -275,6 +276,7 @@ __device__ __forceinline__ void decode_local(int idx, int tiles_m, int tiles_n, 
 
 // One problem; tensor maps in kernel parameters.
 struct SingleSource {
+    static constexpr bool kPrefetchMaps = false;
     const CUtensorMap* ta;
     const CUtensorMap* tb;
     const GemmArgs* a;
@@ -292,18 +294,32 @@ struct SingleSource {
     }
 };
 
-// Many problems; each with its own tensor maps in device memory.
+// Many problems; each with its own tensor maps in device memory.  A CTA visits its tiles in
+// increasing order, so each role keeps the problem of its last tile and steps forward from it (a
+// step or two per tile), with a binary search over the rest when the jump is longer.
 struct GroupSource {
+    static constexpr bool kPrefetchMaps = true;
     const GroupGemmProblem* probs;
     int count;
-    __device__ __forceinline__ TileInfo get(int t) const {
-        int lo = 0, hi = count - 1;  // last problem whose first tile is <= t
+    int at = 0;  // problem of the last tile looked up
+    __device__ __forceinline__ int find(int t) {
+        int lo = at;
+#pragma unroll 1
+        for (int step = 0; step < 4; ++step) {
+            if (lo + 1 >= count || __ldg(&probs[lo + 1].tile_begin) > t) return at = lo;
+            ++lo;
+        }
+        int hi = count - 1;  // last problem whose first tile is <= t
+#pragma unroll 1
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (probs[mid].tile_begin <= t) lo = mid;
+            if (__ldg(&probs[mid].tile_begin) <= t) lo = mid;
             else hi = mid - 1;
         }
-        const GroupGemmProblem& P = probs[lo];
+        return at = lo;
+    }
+    __device__ __forceinline__ TileInfo get(int t) {
+        const GroupGemmProblem& P = probs[find(t)];
         TileInfo ti;
         decode_local(t - P.tile_begin, P.tiles_m, P.tiles_n, ti.l, ti.mt, ti.nt);
         ti.ta = &P.ta;
@@ -316,6 +332,10 @@ struct GroupSource {
         return ti;
     }
 };
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
 
 // ---------------------------------------------------------------- accurate-mode epilogue
 // One chunk of the auxiliary product for the 32 rows of this warp (TMEM lane quarter q) and its
@@ -381,7 +401,7 @@ __device__ __forceinline__ void aux_epilogue(uint32_t taddr, const TileInfo& ti,
 // added to the carry column), and the drain forms C-bar = 4096 carry + x as uint32 and merges
 // its row and column maxima into `out` (uint32 [rows_pad] then [cols_pad] from offset out_ld).
 template <class Src, bool AUX = false>
-__device__ __forceinline__ void residue_gemm_body(const Src& src, int total_tiles,
+__device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                                                   const GemmArgs& args) {
     constexpr int PER = AUX ? 1 : 2;  // tiles in flight per CTA (TMEM accumulators in use)
     extern __shared__ uint8_t smem_raw[];
@@ -441,8 +461,13 @@ __device__ __forceinline__ void residue_gemm_body(const Src& src, int total_tile
         for (int pr = 0; ok && PER * pr < my_tiles; ++pr) {
             const int npair = min(PER, my_tiles - PER * pr);
             TileInfo ti[2];
-            for (int s = 0; s < npair; ++s)
+            for (int s = 0; s < npair; ++s) {
                 ti[s] = src.get(blockIdx.x + (PER * pr + s) * gridDim.x);
+                if constexpr (Src::kPrefetchMaps) {
+                    prefetch_tensormap(ti[s].ta);
+                    prefetch_tensormap(ti[s].tb);
+                }
+            }
             const int maxc = max(ti[0].nchunks, npair > 1 ? ti[1].nchunks : 0);
             for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {

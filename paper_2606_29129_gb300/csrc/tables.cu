@@ -95,17 +95,12 @@ void build(int N, ModTables& t) {
         t.inverses[l] = (int)q;
 
         t.conv.p[l] = p;
-        t.conv.barrett[l] = (uint32_t)((1ull << 32) / p);
         for (int j = 0; j < 4; ++j) {
             uint64_t v = 1;
             for (int b = 0; b < 21 * j; ++b) v = (v * 2) % p;
             t.conv.pow21[l][j] = (uint32_t)v;
         }
         const uint32_t h = (p - 1) / 2;
-        const uint64_t tt_max = ((1ull << 21) - 1) * (1ull + 3ull * (p - 1));
-        const uint64_t Kp = (tt_max + p - 1) / p * p;
-        t.conv.off_pos[l] = h;
-        t.conv.off_neg[l] = (uint32_t)(Kp + h);
         t.conv.bias[l] = 0x4B400000u - h;
         t.conv.magic39[l] = (uint32_t)(((1ull << 39) + p - 1) / p);
 
