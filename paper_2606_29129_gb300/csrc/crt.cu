@@ -24,8 +24,10 @@ namespace {
 
 constexpr int TI = 32, TJ = 32;  // tile of the output: 32 rows x 32 columns, 256 threads
 
-// y * 2^s rounded to nearest once, for any s (x is a normal double).
-__device__ double scale_pow2_rn(double x, int s) {
+// y * 2^s rounded to nearest once, for any s (x is a normal double).  Only results outside the
+// normal range come here; kept out of line so that none of its FP64 multiplies is if-converted
+// into the common path.
+__device__ __noinline__ double scale_pow2_rn(double x, int s) {
     if (s > 0) {
         while (s > 1000) { x = __dmul_rn(x, 0x1p1000); s -= 1000; }
         return __dmul_rn(x, __longlong_as_double((long long)(s + 1023) << 52));
@@ -38,6 +40,11 @@ __device__ double scale_pow2_rn(double x, int s) {
     if (t < -1022 - 600) return __dmul_rn(m, 0.0);  // far below the smallest subnormal: +-0
     double m2 = __dmul_rn(m, __longlong_as_double((long long)(t + 600 + 1023) << 52));  // exact
     return __dmul_rn(m2, 0x1p-600);
+}
+
+// The double with these bits rounded to single (the out-of-range single results only).
+__device__ __noinline__ float double_bits_to_float(uint64_t bits) {
+    return __double2float_rn(__longlong_as_double((long long)bits));
 }
 
 // 32-bit words of the working integers.  X and Q P are only needed modulo 2^(32 W): the result
@@ -189,10 +196,8 @@ __device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
         const int E = msb - (ea + fb);
         if (E >= -126 && E <= 127)
             return __uint_as_float(sign | ((uint32_t)(E + 127) << 23) | (m24 & 0x7FFFFFu));
-        const double d = __longlong_as_double((long long)(((uint64_t)sign << 32) |
-                                                          ((uint64_t)(E + 1023) << 52) |
-                                                          ((uint64_t)(m24 & 0x7FFFFFu) << 29)));
-        return __double2float_rn(d);
+        return double_bits_to_float(((uint64_t)sign << 32) | ((uint64_t)(E + 1023) << 52) |
+                                    ((uint64_t)(m24 & 0x7FFFFFu) << 29));
     } else {
         uint64_t m53 = win >> 11;
         const uint32_t rem = (uint32_t)(win & 0x7FF);
@@ -277,16 +282,28 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
         }
     }
     __syncthreads();
+    // Two loops rather than one with selects: a select between the product and the plain value
+    // still issues the (predicated-off) floating-point multiply, which for doubles occupies the
+    // narrow FP64 pipe.
+    if (ab == 0) {
 #pragma unroll
-    for (int r = 0; r < TJ / 8; ++r) {
-        const int jl = warp + 8 * r;
-        const int jj = j0 + jl, ii = i0 + lane;
-        if (ii < m && jj < n) {
-            OutT* out = C + ii + (int64_t)jj * ldc;
-            const OutT y = tile[jl][lane];
-            OutT v = (ab & 1) ? mul_rn(alpha, y) : y;
-            if (ab & 2) v = add_rn(v, mul_rn(beta, *out));
-            *out = v;
+        for (int r = 0; r < TJ / 8; ++r) {
+            const int jl = warp + 8 * r;
+            const int jj = j0 + jl, ii = i0 + lane;
+            if (ii < m && jj < n) C[ii + (int64_t)jj * ldc] = tile[jl][lane];
+        }
+    } else {
+#pragma unroll 1
+        for (int r = 0; r < TJ / 8; ++r) {
+            const int jl = warp + 8 * r;
+            const int jj = j0 + jl, ii = i0 + lane;
+            if (ii < m && jj < n) {
+                OutT* out = C + ii + (int64_t)jj * ldc;
+                const OutT y = tile[jl][lane];
+                OutT v = (ab & 1) ? mul_rn(alpha, y) : y;
+                if (ab & 2) v = add_rn(v, mul_rn(beta, *out));
+                *out = v;
+            }
         }
     }
 }

@@ -123,8 +123,8 @@ extern "C" int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int 
     rc = launch_residue_gemm(num_moduli, (int)m_pad, (int)n_pad, (int)k_pad, pa, pb, res, T->epi,
                              status, sms, 960, OZAKI2_GEMM_AUTO, st);
     if (rc) return rc;
-    return launch_crt(res, n_pad, m_pad * n_pad, m, n, e, f, alpha, beta, C, ldc, *T, status, st) ==
-                   cudaSuccess
+    return launch_crt(res, n_pad, m_pad * n_pad, m, n, e, f, alpha, beta, C, ldc, *T, status, st,
+                      false, true) == cudaSuccess
                ? OZAKI2_SUCCESS
                : OZAKI2_ERROR_CUDA;
 }
