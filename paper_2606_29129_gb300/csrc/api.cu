@@ -141,6 +141,7 @@ int ensure_workspace(ozaki2_context* ctx, size_t bytes) {
 
 struct Layout {
     int64_t m_pad, n_pad, k_pad;
+    PlaneGeom geo;  // stored extent of the residue planes (no padding rows beyond one TMA box)
     size_t off_e, off_f, off_pa, off_pb, off_res, total;
 };
 
@@ -149,6 +150,7 @@ Layout make_layout(int m, int n, int k, int N) {
     L.m_pad = round_up(m > 0 ? m : 1, OZAKI2_ROWS_ALIGN_A);
     L.n_pad = round_up(n > 0 ? n : 1, OZAKI2_ROWS_ALIGN_B);
     L.k_pad = round_up(k > 0 ? k : 1, OZAKI2_K_ALIGN);
+    L.geo = compact_planes(m, n, k);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -157,8 +159,8 @@ Layout make_layout(int m, int n, int k, int N) {
     };
     L.off_e = take(sizeof(int) * (size_t)L.m_pad);
     L.off_f = take(sizeof(int) * (size_t)L.n_pad);
-    L.off_pa = take((size_t)2 * N * L.m_pad * L.k_pad);
-    L.off_pb = take((size_t)2 * N * L.n_pad * L.k_pad);
+    L.off_pa = take((size_t)2 * N * L.geo.rows_a * L.geo.ld);
+    L.off_pb = take((size_t)2 * N * L.geo.rows_b * L.geo.ld);
     L.off_res = take((size_t)N * L.m_pad * L.n_pad);
     L.total = off;
     return L;
@@ -188,12 +190,12 @@ int accurate_shifts(ozaki2_context* ctx, const void* A, int64_t als, int64_t aes
     int rc;
     if ((rc = cuda_rc(launch_scale_pair(A, als, aes, m, B, bls, bes, n, k, T.pprime, T.delta, e,
                                         f, ctx->d_status, st, OZAKI2_SCALING_ACCURATE, f32))) ||
-        (rc = cuda_rc(launch_convert_bar(A, als, aes, m, k, e, pa, (int)L.m_pad, (int)L.k_pad,
+        (rc = cuda_rc(launch_convert_bar(A, als, aes, m, k, e, pa, L.geo.rows_a, L.geo.ld,
                                          ctx->d_status, st, f32))) ||
-        (rc = cuda_rc(launch_convert_bar(B, bls, bes, n, k, f, pb, (int)L.n_pad, (int)L.k_pad,
+        (rc = cuda_rc(launch_convert_bar(B, bls, bes, n, k, f, pb, L.geo.rows_b, L.geo.ld,
                                          ctx->d_status, st, f32))))
         return rc;
-    if ((rc = launch_aux_gemm((int)L.m_pad, (int)L.n_pad, (int)L.k_pad, pa, pb, cmax,
+    if ((rc = launch_aux_gemm((int)L.m_pad, (int)L.n_pad, (int)L.k_pad, L.geo, pa, pb, cmax,
                               ctx->d_status, ctx->num_sms, st)))
         return rc;
     return cuda_rc(launch_accu_shift(e, m, f, n, cmax, (int)L.m_pad, T.pprime, T.delta, st));
@@ -258,14 +260,14 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     }
     mark(1);
     const bool accurate = ctx->scaling == OZAKI2_SCALING_ACCURATE;
-    if ((rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, (int)L.m_pad,
-                                     (int)L.k_pad, ctx->d_status, st, f32, accurate))))
+    if ((rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, L.geo.rows_a, L.geo.ld,
+                                     ctx->d_status, st, f32, accurate))))
         return rc;
-    if ((rc = cuda_rc(launch_convert(B, bls, bes, n, k, f, T->conv, pb, (int)L.n_pad,
-                                     (int)L.k_pad, ctx->d_status, st, f32, accurate))))
+    if ((rc = cuda_rc(launch_convert(B, bls, bes, n, k, f, T->conv, pb, L.geo.rows_b, L.geo.ld,
+                                     ctx->d_status, st, f32, accurate))))
         return rc;
     mark(2);
-    if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, pa, pb, res,
+    if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, L.geo, pa, pb, res,
                                   T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
                                   ctx->gemm_variant, st)))
         return rc;
@@ -745,7 +747,8 @@ int ozaki2_residue_gemm(ozaki2_handle_t handle, int num_moduli, int m_pad, int n
     ozaki2_context* ctx;
     int rc = resolve(handle, &ctx);
     if (rc) return rc;
-    return launch_residue_gemm(num_moduli, m_pad, n_pad, k_pad, planes_a, planes_b, residues,
+    return launch_residue_gemm(num_moduli, m_pad, n_pad, k_pad, PlaneGeom{m_pad, n_pad, k_pad},
+                               planes_a, planes_b, residues,
                                T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
                                ctx->gemm_variant, ctx->stream);
 }

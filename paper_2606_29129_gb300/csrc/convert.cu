@@ -310,7 +310,7 @@ __device__ __forceinline__ void convert_adjacent_tile(
             const int item = threadIdx.x + 256 * rep;
             const int ll = item >> 3, hg = item & 7;
             const int line = line0 + ll;
-            if (line < rows_pad) {
+            if (line < rows_pad && h0 + 8 * hg < k_pad) {
                 T v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = tile[8 * hg + u][ll];
@@ -346,17 +346,17 @@ __global__ void __launch_bounds__(256) convert_grouped_kernel(
     const double* X = w.side ? P.B : P.A;
     const int64_t ls = w.side ? P.b_ls : P.a_ls, es = w.side ? P.b_es : P.a_es;
     const int lines = w.side ? P.n : P.m;
-    const int rows_pad = w.side ? P.n_pad : P.m_pad;
+    const int rows = w.side ? P.geo.rows_b : P.geo.rows_a;
     const int* shifts = w.side ? P.f : P.e;
     auto* planes = static_cast<__nv_bfloat16*>(w.side ? P.pb : P.pa);
     if (es != 1) {
-        convert_adjacent_tile<N, L, double>(X, es, lines, P.k, shifts, t, planes, rows_pad,
-                                            P.k_pad, w.block, tile, status);
+        convert_adjacent_tile<N, L, double>(X, es, lines, P.k, shifts, t, planes, rows,
+                                            P.geo.ld, w.block, tile, status);
     } else {
         const int64_t g = (int64_t)w.block * 256 + threadIdx.x;
-        if (g < (int64_t)rows_pad * (P.k_pad / 8))
-            convert_contiguous_item<N, L, double>(X, ls, lines, P.k, shifts, t, planes, rows_pad,
-                                                  P.k_pad, g, status);
+        if (g < (int64_t)rows * (P.geo.ld / 8))
+            convert_contiguous_item<N, L, double>(X, ls, lines, P.k, shifts, t, planes, rows,
+                                                  P.geo.ld, g, status);
     }
 }
 
@@ -367,7 +367,7 @@ cudaError_t launch_convert_nl(const T* X, int64_t line_stride, int64_t elem_stri
                               cudaStream_t stream) {
     if (elem_stride != 1) {  // then line_stride == 1: lines adjacent
         const int grid = (int)((int64_t)((rows_pad + kTileLines - 1) / kTileLines) *
-                               (k_pad / kTileK));
+                               ((k_pad + kTileK - 1) / kTileK));
         convert_adjacent_kernel<N, L, T><<<grid, 256, 0, stream>>>(X, elem_stride, lines, len,
                                                                 shifts, t, out, rows_pad, k_pad,
                                                                 status);
@@ -399,11 +399,11 @@ cudaError_t launch_convert_n(const T* X, int64_t line_stride, int64_t elem_strid
 
 }  // namespace
 
-int convert_blocks(int lines, int64_t elem_stride, int rows_pad, int k_pad) {
+int convert_blocks(int lines, int64_t elem_stride, int rows, int ld) {
     (void)lines;
     if (elem_stride != 1)
-        return ((rows_pad + kTileLines - 1) / kTileLines) * (k_pad / kTileK);
-    return (int)(((int64_t)rows_pad * (k_pad / 8) + 255) / 256);
+        return ((rows + kTileLines - 1) / kTileLines) * ((ld + kTileK - 1) / kTileK);
+    return (int)(((int64_t)rows * (ld / 8) + 255) / 256);
 }
 
 cudaError_t launch_convert_bar(const void* X, int64_t line_stride, int64_t elem_stride,

@@ -63,11 +63,11 @@ struct Plan {
 int64_t problem_bytes(const ozaki2_problem& p) {
     const int64_t m_pad = round_up64(p.m, OZAKI2_ROWS_ALIGN_A);
     const int64_t n_pad = round_up64(p.n, OZAKI2_ROWS_ALIGN_B);
-    const int64_t k_pad = round_up64(p.k, OZAKI2_K_ALIGN);
+    const PlaneGeom geo = compact_planes(p.m, p.n, p.k);
     const int64_t N = p.num_moduli;
     return round_up64(4 * m_pad, 256) + round_up64(4 * n_pad, 256) +
-           round_up64(2 * N * m_pad * k_pad, 256) + round_up64(2 * N * n_pad * k_pad, 256) +
-           round_up64(N * m_pad * n_pad, 256);
+           round_up64(2 * N * geo.rows_a * geo.ld, 256) +
+           round_up64(2 * N * geo.rows_b * geo.ld, 256) + round_up64(N * m_pad * n_pad, 256);
 }
 
 void make_plan(int count, const ozaki2_problem* probs, Plan& P,
@@ -91,12 +91,12 @@ void make_plan(int count, const ozaki2_problem* probs, Plan& P,
         const ozaki2_problem& p = probs[i];
         const int64_t m_pad = round_up64(p.m, OZAKI2_ROWS_ALIGN_A);
         const int64_t n_pad = round_up64(p.n, OZAKI2_ROWS_ALIGN_B);
-        const int64_t k_pad = round_up64(p.k, OZAKI2_K_ALIGN);
+        const PlaneGeom geo = compact_planes(p.m, p.n, p.k);
         scale += (p.m + 127) / 128 + (p.n + 127) / 128;
         const int64_t aes = notrans(p.transA) ? p.lda : 1;
         const int64_t bes = notrans(p.transB) ? 1 : p.ldb;
-        const int cb = convert_blocks(p.m, aes, (int)m_pad, (int)k_pad) +
-                       convert_blocks(p.n, bes, (int)n_pad, (int)k_pad);
+        const int cb = convert_blocks(p.m, aes, geo.rows_a, geo.ld) +
+                       convert_blocks(p.n, bes, geo.rows_b, geo.ld);
         const int rb = ((p.m + 31) / 32) * ((p.n + 31) / 32);
         if (p.num_moduli != curN) {
             curN = p.num_moduli;
@@ -181,6 +181,7 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
         g.m_pad = (int)m_pad;
         g.n_pad = (int)n_pad;
         g.k_pad = (int)k_pad;
+        g.geo = compact_planes(p.m, p.n, p.k);
         g.alpha = p.alpha;
         g.beta = p.beta;
         g.ab = (p.alpha != 1.0 ? 1 : 0) | (p.beta != 0.0 ? 2 : 0);
@@ -190,19 +191,19 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
         int64_t o = 0;
         g.e = reinterpret_cast<int*>(base + o);  o += round_up64(4 * m_pad, 256);
         g.f = reinterpret_cast<int*>(base + o);  o += round_up64(4 * n_pad, 256);
-        g.pa = base + o;                         o += round_up64(2 * N * m_pad * k_pad, 256);
-        g.pb = base + o;                         o += round_up64(2 * N * n_pad * k_pad, 256);
+        g.pa = base + o;  o += round_up64(2 * N * g.geo.rows_a * g.geo.ld, 256);
+        g.pb = base + o;  o += round_up64(2 * N * g.geo.rows_b * g.geo.ld, 256);
         g.res = reinterpret_cast<int8_t*>(base + o);
         if (!make_group_gemm_problem(&gg[a], p.num_moduli, (int)m_pad, (int)n_pad, (int)k_pad,
-                                     g.pa, g.pb, g.res, chunk_k))
+                                     g.geo, g.pa, g.pb, g.res, chunk_k))
             return OZAKI2_ERROR_DRIVER;
         gg[a].tile_begin = tile_begin;
         tile_begin += p.num_moduli * gg[a].tiles_m * gg[a].tiles_n;
         if (P.accurate) {
             // A-bar / B-bar live in the first residue plane, the C-bar maxima in the product
             // residues; both are overwritten later by the main stages
-            if (!make_group_aux_problem(&ga[a], (int)m_pad, (int)n_pad, (int)k_pad, g.pa, g.pb,
-                                        reinterpret_cast<uint32_t*>(g.res)))
+            if (!make_group_aux_problem(&ga[a], (int)m_pad, (int)n_pad, (int)k_pad, g.geo, g.pa,
+                                        g.pb, reinterpret_cast<uint32_t*>(g.res)))
                 return OZAKI2_ERROR_DRIVER;
             ga[a].tile_begin = aux_begin;
             aux_begin += ga[a].tiles_m * ga[a].tiles_n;
@@ -211,7 +212,7 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
             const int lines = side ? p.n : p.m;
             for (int l0 = 0; l0 < lines; l0 += 128) sw[ns++] = ScaleWork{(int)a, side, l0};
             const int64_t es = side ? g.b_es : g.a_es;
-            const int cb = convert_blocks(lines, es, side ? g.n_pad : g.m_pad, g.k_pad);
+            const int cb = convert_blocks(lines, es, side ? g.geo.rows_b : g.geo.rows_a, g.geo.ld);
             for (int b = 0; b < cb; ++b) cw[nc++] = ConvertWork{(int)a, side, b};
         }
         for (int i0 = 0; i0 < p.m; i0 += 32)

@@ -86,11 +86,12 @@ extern "C" int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int 
     // Scratch layout: status word, shifts e and f, planes of A and B, product residues.
     const int64_t m_pad = up(m, OZAKI2_ROWS_ALIGN_A), n_pad = up(n, OZAKI2_ROWS_ALIGN_B);
     const int64_t k_pad = up(k > 0 ? k : 1, OZAKI2_K_ALIGN);
+    const PlaneGeom geo = compact_planes(m, n, k);  // as ozaki2_dgemm's workspace
     const int64_t off_e = 256;
     const int64_t off_f = off_e + up(4 * m_pad, 256);
     const int64_t off_pa = off_f + up(4 * n_pad, 256);
-    const int64_t off_pb = off_pa + up(2 * num_moduli * m_pad * k_pad, 256);
-    const int64_t off_res = off_pb + up(2 * num_moduli * n_pad * k_pad, 256);
+    const int64_t off_pb = off_pa + up(2 * num_moduli * (int64_t)geo.rows_a * geo.ld, 256);
+    const int64_t off_res = off_pb + up(2 * num_moduli * (int64_t)geo.rows_b * geo.ld, 256);
     const int64_t total = off_res + up(num_moduli * m_pad * n_pad, 256);
     if (total > (int64_t)OZAKI2_NOALLOC_SCRATCH_BYTES) return OZAKI2_ERROR_TOO_LARGE;
 
@@ -115,12 +116,13 @@ extern "C" int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int 
     const int64_t bls = notrans(transB) ? ldb : 1, bes = notrans(transB) ? 1 : ldb;
     if (launch_scale(A, als, aes, m, k, T->pprime, e, status, st) != cudaSuccess ||
         launch_scale(B, bls, bes, n, k, T->pprime, f, status, st) != cudaSuccess ||
-        launch_convert(A, als, aes, m, k, e, T->conv, pa, (int)m_pad, (int)k_pad, status, st) !=
+        launch_convert(A, als, aes, m, k, e, T->conv, pa, geo.rows_a, geo.ld, status, st) !=
             cudaSuccess ||
-        launch_convert(B, bls, bes, n, k, f, T->conv, pb, (int)n_pad, (int)k_pad, status, st) !=
+        launch_convert(B, bls, bes, n, k, f, T->conv, pb, geo.rows_b, geo.ld, status, st) !=
             cudaSuccess)
         return OZAKI2_ERROR_CUDA;
-    rc = launch_residue_gemm(num_moduli, (int)m_pad, (int)n_pad, (int)k_pad, pa, pb, res, T->epi,
+    rc = launch_residue_gemm(num_moduli, (int)m_pad, (int)n_pad, (int)k_pad, geo, pa, pb, res,
+                             T->epi,
                              status, sms, 960, OZAKI2_GEMM_AUTO, st);
     if (rc) return rc;
     return launch_crt(res, n_pad, m_pad * n_pad, m, n, e, f, alpha, beta, C, ldc, *T, status, st,

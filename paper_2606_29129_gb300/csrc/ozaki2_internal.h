@@ -64,6 +64,21 @@ struct ModTables {
     EpilogueTables epi;
 };
 
+// Stored extent of the bf16 residue planes [N][rows][ld] (K contiguous, row pitch ld elements, a
+// multiple of 8 so rows start on 16-byte boundaries).  The residue GEMM runs over m_pad x n_pad x
+// k_pad tiles; rows at or beyond `rows` and K at or beyond `ld` are not stored: the TMA reads them
+// as zeros.  The library's own layout stores the rows of op(A) and op(B) only (at least one TMA
+// box: 128 rows of A, 256 of B, so that no box is larger than the tensor) with ld = k_pad, which
+// keeps every row on a 128-byte boundary (a shorter pitch measured slower: rows straddling cache
+// lines); the stage entry points keep the padded extents.
+struct PlaneGeom {
+    int rows_a, rows_b, ld;
+};
+inline PlaneGeom compact_planes(int m, int n, int k) {
+    const int ld = (k + 63) / 64 * 64;
+    return PlaneGeom{m > 128 ? m : 128, n > 256 ? n : 256, ld > 64 ? ld : 64};
+}
+
 // One problem of a grouped call, as the grouped kernels see it (device memory).
 struct GroupProblem {
     const double* A;
@@ -74,6 +89,7 @@ struct GroupProblem {
     int64_t ldc;
     int m, n, k, N;
     int m_pad, n_pad, k_pad;
+    PlaneGeom geo;       // stored extent of pa / pb
     double alpha, beta;
     int ab;              // bit 0: alpha != 1, bit 1: beta != 0 (set on the host)
     float pprime;        // P'_prop, or P'_fast in the original fast mode
@@ -81,8 +97,8 @@ struct GroupProblem {
     int scaling;         // OZAKI2_SCALING_*
     int* e;              // shifts of the rows of op(A)   [m_pad]
     int* f;              // shifts of the columns of op(B) [n_pad]
-    void* pa;            // bf16 planes [N][m_pad][k_pad]
-    void* pb;            // bf16 planes [N][n_pad][k_pad]
+    void* pa;            // bf16 planes [N][geo.rows_a][geo.ld]
+    void* pb;            // bf16 planes [N][geo.rows_b][geo.ld]
     int8_t* res;         // product residues [N][m_pad][n_pad]
 };
 
@@ -99,8 +115,8 @@ struct CrtWork {         // one 32 x 32 tile of C
 
 // One problem of a grouped residue GEMM (device memory, 64-byte aligned for the tensor maps).
 struct alignas(64) GroupGemmProblem {
-    CUtensorMap ta;      // A planes [N][m_pad][k_pad], box 64 x 128
-    CUtensorMap tb;      // B planes [N][n_pad][k_pad], box 64 x 256
+    CUtensorMap ta;      // A planes [N][rows_a][ld], box 64 x 128
+    CUtensorMap tb;      // B planes [N][rows_b][ld], box 64 x 256
     int8_t* out;         // product residues [N][m_pad][n_pad]
     int64_t out_ld, out_plane;
     int tiles_m, tiles_n, k_blocks, nchunks;
@@ -109,8 +125,8 @@ struct alignas(64) GroupGemmProblem {
 
 // Fills the tensor maps and tile counts of one grouped-GEMM problem (host); false on failure.
 bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, int k_pad,
-                             const void* planes_a, const void* planes_b, int8_t* out,
-                             int chunk_k);
+                             const PlaneGeom& geo, const void* planes_a, const void* planes_b,
+                             int8_t* out, int chunk_k);
 int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
                                 const EpilogueTables& t, unsigned* status, int num_sms,
                                 int chunk_k, cudaStream_t stream);
@@ -122,8 +138,8 @@ cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const Conve
                                    cudaStream_t stream, bool accurate = false);
 cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* work, int blocks,
                                const CrtTables& t, cudaStream_t stream);
-// Blocks of the grouped convert for one side of one problem.
-int convert_blocks(int lines, int64_t elem_stride, int rows_pad, int k_pad);
+// Blocks of the grouped convert for one side of one problem (rows x ld stored).
+int convert_blocks(int lines, int64_t elem_stride, int rows, int ld);
 
 // Grouped calls (grouped.cu).
 size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs);
@@ -138,18 +154,20 @@ int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_de
 char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* ws);
 
 // Accurate mode (scale.cu, convert.cu, residue_gemm.cu).
-// A-bar plane [rows_pad][k_pad] (bf16, K contiguous) from the exponent codes of the first pass.
+// A-bar plane [rows][ld] (bf16, K contiguous) from the exponent codes of the first pass.
 cudaError_t launch_convert_bar(const void* X, int64_t line_stride, int64_t elem_stride,
-                               int lines, int len, const int* codes, void* plane, int rows_pad,
-                               int k_pad, unsigned* status, cudaStream_t stream,
+                               int lines, int len, const int* codes, void* plane, int rows,
+                               int ld, unsigned* status, cudaStream_t stream,
                                bool f32 = false);
 // Row and column maxima of C-bar = A-bar B-bar into cmax[0, m_pad) and cmax[m_pad, m_pad+n_pad).
-int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const void* bar_a, const void* bar_b,
-                    uint32_t* cmax, unsigned* status, int num_sms, cudaStream_t stream);
+int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const PlaneGeom& geo, const void* bar_a,
+                    const void* bar_b, uint32_t* cmax, unsigned* status, int num_sms,
+                    cudaStream_t stream);
 // Grouped form: one descriptor per problem (tensor maps over its A-bar / B-bar planes, the
 // maxima at `cmax`), and the persistent launch over all their tiles.
 bool make_group_aux_problem(GroupGemmProblem* g, int m_pad, int n_pad, int k_pad,
-                            const void* bar_a, const void* bar_b, uint32_t* cmax);
+                            const PlaneGeom& geo, const void* bar_a, const void* bar_b,
+                            uint32_t* cmax);
 int launch_aux_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
                             unsigned* status, int num_sms, cudaStream_t stream);
 cudaError_t launch_accu_shift_grouped(const GroupProblem* probs, const ScaleWork* work,
@@ -209,15 +227,16 @@ cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stri
 
 // f32: X holds floats (SGEMM), else doubles.  accurate: the shifts come from accurate mode,
 // whose a' may need six more bits than the proposed and fast scalings allow.
+// Writes planes [N][rows][ld]: rows at or beyond `lines` and K at or beyond `len` as zeros.
 cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, const int* shifts, const ConvertTables& t, void* planes,
-                           int rows_pad, int k_pad, unsigned* status, cudaStream_t stream,
+                           int rows, int ld, unsigned* status, cudaStream_t stream,
                            bool f32 = false, bool accurate = false);
 
-int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
-                        const void* planes_b, int8_t* out, const EpilogueTables& t,
-                        unsigned* status, int num_sms, int chunk_k, int variant,
-                        cudaStream_t stream);
+int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const PlaneGeom& geo,
+                        const void* planes_a, const void* planes_b, int8_t* out,
+                        const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
+                        int variant, cudaStream_t stream);
 
 // f32: C holds floats (SGEMM: C'' rounded to 24 bits, alpha and beta applied in single
 // precision), else doubles.  padded: the residue buffer extends to whole 32 x 32 tiles in every

@@ -847,13 +847,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// 3-D map over residue planes [N][rows_pad][k_pad] (bf16, K contiguous), box 64 x box_rows x 1.
-bool encode_planes(CUtensorMap* map, const void* base, int N, int rows_pad, int k_pad,
-                   int box_rows) {
+// 3-D map over residue planes [N][rows][ld] (bf16, K contiguous), box 64 x box_rows x 1; the
+// boxes of the tile grid that reach beyond rows or ld read zeros.
+bool encode_planes(CUtensorMap* map, const void* base, int N, int rows, int ld, int box_rows) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad, (cuuint64_t)N};
-    cuuint64_t strides[2] = {(cuuint64_t)k_pad * 2, (cuuint64_t)rows_pad * (cuuint64_t)k_pad * 2};
+    cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)rows, (cuuint64_t)N};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * (cuuint64_t)ld * 2};
     cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
@@ -873,10 +873,10 @@ static int chunk_blocks_of(int chunk_k) {
 }
 
 bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, int k_pad,
-                             const void* planes_a, const void* planes_b, int8_t* out,
-                             int chunk_k) {
-    if (!encode_planes(&g->ta, planes_a, N, m_pad, k_pad, BM) ||
-        !encode_planes(&g->tb, planes_b, N, n_pad, k_pad, BN))
+                             const PlaneGeom& geo, const void* planes_a, const void* planes_b,
+                             int8_t* out, int chunk_k) {
+    if (!encode_planes(&g->ta, planes_a, N, geo.rows_a, geo.ld, BM) ||
+        !encode_planes(&g->tb, planes_b, N, geo.rows_b, geo.ld, BN))
         return false;
     const int cb = chunk_blocks_of(chunk_k);
     g->out = out;
@@ -916,8 +916,9 @@ int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int to
 // kept remainder below 4096 stays under 2^24, where fp32 sums of integers are exact.
 constexpr int kAuxChunkBlocks = 63;
 
-int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const void* bar_a, const void* bar_b,
-                    uint32_t* cmax, unsigned* status, int num_sms, cudaStream_t stream) {
+int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const PlaneGeom& geo, const void* bar_a,
+                    const void* bar_b, uint32_t* cmax, unsigned* status, int num_sms,
+                    cudaStream_t stream) {
     if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
     if (cudaMemsetAsync(cmax, 0, sizeof(uint32_t) * ((size_t)m_pad + n_pad), stream) !=
         cudaSuccess)
@@ -933,8 +934,8 @@ int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const void* bar_a, const vo
     a.out_plane = 0;
     a.status = status;
     CUtensorMap ta, tb;
-    if (!encode_planes(&ta, bar_a, 1, m_pad, k_pad, BM) ||
-        !encode_planes(&tb, bar_b, 1, n_pad, k_pad, BN))
+    if (!encode_planes(&ta, bar_a, 1, geo.rows_a, geo.ld, BM) ||
+        !encode_planes(&tb, bar_b, 1, geo.rows_b, geo.ld, BN))
         return OZAKI2_ERROR_DRIVER;
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
@@ -953,9 +954,10 @@ int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const void* bar_a, const vo
 }
 
 bool make_group_aux_problem(GroupGemmProblem* g, int m_pad, int n_pad, int k_pad,
-                            const void* bar_a, const void* bar_b, uint32_t* cmax) {
-    if (!encode_planes(&g->ta, bar_a, 1, m_pad, k_pad, BM) ||
-        !encode_planes(&g->tb, bar_b, 1, n_pad, k_pad, BN))
+                            const PlaneGeom& geo, const void* bar_a, const void* bar_b,
+                            uint32_t* cmax) {
+    if (!encode_planes(&g->ta, bar_a, 1, geo.rows_a, geo.ld, BM) ||
+        !encode_planes(&g->tb, bar_b, 1, geo.rows_b, geo.ld, BN))
         return false;
     g->out = reinterpret_cast<int8_t*>(cmax);
     g->out_ld = m_pad;  // the column maxima follow the m_pad row maxima
@@ -988,10 +990,10 @@ int launch_aux_gemm_grouped(const GroupGemmProblem* probs, int count, int total_
     return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
 }
 
-int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const void* planes_a,
-                        const void* planes_b, int8_t* out, const EpilogueTables& t,
-                        unsigned* status, int num_sms, int chunk_k, int variant,
-                        cudaStream_t stream) {
+int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const PlaneGeom& geo,
+                        const void* planes_a, const void* planes_b, int8_t* out,
+                        const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
+                        int variant, cudaStream_t stream) {
     if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
     int cb = chunk_k / BK;
     if (cb < 1) cb = 1;
@@ -1015,8 +1017,8 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const v
     const bool use_pair = variant == OZAKI2_GEMM_PAIR;
     CUtensorMap ta, tb;
     if (use_pair) {
-        if (!encode_planes(&ta, planes_a, num_moduli, m_pad, k_pad, pair::HALF) ||
-            !encode_planes(&tb, planes_b, num_moduli, n_pad, k_pad, pair::HALF))
+        if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, pair::HALF) ||
+            !encode_planes(&tb, planes_b, num_moduli, geo.rows_b, geo.ld, pair::HALF))
             return OZAKI2_ERROR_DRIVER;
         static std::once_flag attr_once;
         static cudaError_t attr_err = cudaSuccess;
@@ -1053,8 +1055,8 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const v
             return OZAKI2_ERROR_CUDA;
         return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
     }
-    if (!encode_planes(&ta, planes_a, num_moduli, m_pad, k_pad, BM) ||
-        !encode_planes(&tb, planes_b, num_moduli, n_pad, k_pad, BN))
+    if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, BM) ||
+        !encode_planes(&tb, planes_b, num_moduli, geo.rows_b, geo.ld, BN))
         return OZAKI2_ERROR_DRIVER;
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
