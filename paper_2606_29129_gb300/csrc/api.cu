@@ -747,8 +747,9 @@ int ozaki2_residue_gemm(ozaki2_handle_t handle, int num_moduli, int m_pad, int n
     ozaki2_context* ctx;
     int rc = resolve(handle, &ctx);
     if (rc) return rc;
-    return launch_residue_gemm(num_moduli, m_pad, n_pad, k_pad, PlaneGeom{m_pad, n_pad, k_pad},
-                               planes_a, planes_b, residues,
+    // the caller's padded layout, every product residue stored
+    const PlaneGeom geo{m_pad, n_pad, k_pad, m_pad, n_pad};
+    return launch_residue_gemm(num_moduli, m_pad, n_pad, k_pad, geo, planes_a, planes_b, residues,
                                T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
                                ctx->gemm_variant, ctx->stream);
 }

@@ -71,12 +71,16 @@ struct ModTables {
 // box: 128 rows of A, 256 of B, so that no box is larger than the tensor) with ld = k_pad, which
 // keeps every row on a 128-byte boundary (a shorter pitch measured slower: rows straddling cache
 // lines); the stage entry points keep the padded extents.
+// out_rows x out_cols: the part of each m_pad x n_pad plane of product residues that the residue
+// GEMM stores (multiples of 32; the reconstruction reads 32 x 32 tiles over m x n only).
 struct PlaneGeom {
     int rows_a, rows_b, ld;
+    int out_rows, out_cols;
 };
 inline PlaneGeom compact_planes(int m, int n, int k) {
     const int ld = (k + 63) / 64 * 64;
-    return PlaneGeom{m > 128 ? m : 128, n > 256 ? n : 256, ld > 64 ? ld : 64};
+    return PlaneGeom{m > 128 ? m : 128, n > 256 ? n : 256, ld > 64 ? ld : 64, (m + 31) / 32 * 32,
+                     (n + 31) / 32 * 32};
 }
 
 // One problem of a grouped call, as the grouped kernels see it (device memory).
@@ -120,6 +124,7 @@ struct alignas(64) GroupGemmProblem {
     int8_t* out;         // product residues [N][m_pad][n_pad]
     int64_t out_ld, out_plane;
     int tiles_m, tiles_n, k_blocks, nchunks;
+    int m_live, n_live;  // stored part of each plane of `out` (PlaneGeom::out_rows, out_cols)
     int tile_begin;      // index of this problem's first tile in the grouped launch
 };
 

@@ -54,6 +54,7 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
 struct GemmArgs {
     int tiles_m, tiles_n, total_tiles, k_blocks, chunk_blocks, nchunks;
     int m_rows;  // rows of the A planes / product residues (m_pad)
+    int m_live, n_live;  // product residues stored: rows below m_live, columns below n_live
     int8_t* out;
     int64_t out_ld, out_plane;
     unsigned* status;
@@ -161,6 +162,7 @@ struct TileInfo {
     int l, mt, nt, k_blocks, nchunks;
     int8_t* out;
     int64_t out_ld, out_plane;
+    int m_live, n_live;  // rows and columns of the product residues that are stored
 };
 
 __device__ __forceinline__ void decode_local(int idx, int tiles_m, int tiles_n, int& l, int& mt,
@@ -193,6 +195,8 @@ struct SingleSource {
         ti.out = a->out;
         ti.out_ld = a->out_ld;
         ti.out_plane = a->out_plane;
+        ti.m_live = a->m_live;
+        ti.n_live = a->n_live;
         return ti;
     }
 };
@@ -232,6 +236,8 @@ struct GroupSource {
         ti.out = P.out;
         ti.out_ld = P.out_ld;
         ti.out_plane = P.out_plane;
+        ti.m_live = P.m_live;
+        ti.n_live = P.n_live;
         return ti;
     }
 };
@@ -505,11 +511,15 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                     } else {
                         // final drain: symmetric residue as int8
                         const float hi = args.ep.hi[l], lo = args.ep.lo[l];
+                        // (only rows below m_live and 32-column groups below n_live are stored:
+                        // the reconstruction reads no others)
                         const int64_t row = (int64_t)ti[s].mt * BM + q * 32 + lane;
+                        const bool row_live = row < ti[s].m_live;
+                        const int col_end = min(EPI_COLS, ti[s].n_live - ti[s].nt * BN - col0);
                         int8_t* dst = ti[s].out + (int64_t)l * ti[s].out_plane +
                                       row * ti[s].out_ld + (int64_t)ti[s].nt * BN + col0;
 #pragma unroll 1
-                        for (int col = 0; col < EPI_COLS; col += 32) {
+                        for (int col = 0; col < col_end; col += 32) {
                             uint32_t v[32];
                             tmem_ld32(taddr + col, v);
                             uint32_t packed[8];
@@ -526,9 +536,11 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                                 }
                                 packed[w] = word;
                             }
-                            uint4* o = reinterpret_cast<uint4*>(dst + col);
-                            o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                            o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                            if (row_live) {
+                                uint4* o = reinterpret_cast<uint4*>(dst + col);
+                                o[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                                o[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                            }
                         }
                     }
                     tc_fence_before();
@@ -886,6 +898,8 @@ bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, i
     g->tiles_n = n_pad / BN;
     g->k_blocks = k_pad / BK;
     g->nchunks = (g->k_blocks + cb - 1) / cb;
+    g->m_live = geo.out_rows;
+    g->n_live = geo.out_cols;
     g->tile_begin = 0;
     return true;
 }
@@ -1003,6 +1017,8 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
     a.chunk_blocks = cb;
     a.nchunks = a.k_blocks > 0 ? (a.k_blocks + cb - 1) / cb : 0;
     a.m_rows = m_pad;
+    a.m_live = geo.out_rows;
+    a.n_live = geo.out_cols;
     a.out = out;
     a.out_ld = n_pad;
     a.out_plane = (int64_t)m_pad * n_pad;
