@@ -57,6 +57,107 @@ __host__ __device__ constexpr int crt_words(int N) {
     return (b[N] + 2 + 31) / 32;
 }
 
+// ---- multi-word integer steps with the carry flag: each chain is one asm statement, so nothing
+// the compiler schedules can come between an instruction that sets the carry and the one that
+// reads it.  Words are little-endian; every result is modulo 2^(32 W), W = 1 .. 5.
+
+// X = sum_j acc[j] 2^(32 j): word j is lo(acc[j]) + hi(acc[j-1]) + carry.
+template <int W>
+__device__ __forceinline__ void fold_columns(const uint64_t (&acc)[W], uint32_t (&X)[W]) {
+    uint32_t lo[W], hi[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        lo[j] = (uint32_t)acc[j];
+        hi[j] = (uint32_t)(acc[j] >> 32);
+    }
+    X[0] = lo[0];
+    if constexpr (W == 2) {
+        X[1] = lo[1] + hi[0];
+    } else if constexpr (W == 3) {
+        asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, %5;"
+            : "=&r"(X[1]), "=&r"(X[2])
+            : "r"(lo[1]), "r"(hi[0]), "r"(lo[2]), "r"(hi[1]));
+    } else if constexpr (W == 4) {
+        asm("add.cc.u32 %0, %3, %4;\n\taddc.cc.u32 %1, %5, %6;\n\taddc.u32 %2, %7, %8;"
+            : "=&r"(X[1]), "=&r"(X[2]), "=&r"(X[3])
+            : "r"(lo[1]), "r"(hi[0]), "r"(lo[2]), "r"(hi[1]), "r"(lo[3]), "r"(hi[2]));
+    } else if constexpr (W == 5) {
+        asm("add.cc.u32 %0, %4, %5;\n\taddc.cc.u32 %1, %6, %7;\n\taddc.cc.u32 %2, %8, %9;\n\t"
+            "addc.u32 %3, %10, %11;"
+            : "=&r"(X[1]), "=&r"(X[2]), "=&r"(X[3]), "=&r"(X[4])
+            : "r"(lo[1]), "r"(hi[0]), "r"(lo[2]), "r"(hi[1]), "r"(lo[3]), "r"(hi[2]),
+              "r"(lo[4]), "r"(hi[3]));
+    }
+}
+
+// Y = X + Q M for a one-word Q: the low halves of the products in one carry chain, the high
+// halves (shifted one word up) in a second.
+template <int W>
+__device__ __forceinline__ void add_word_times(const uint32_t (&X)[W], uint32_t Q,
+                                               const uint32_t* M, uint32_t (&Y)[W]) {
+    if constexpr (W == 1) {
+        Y[0] = X[0] + Q * M[0];
+    } else if constexpr (W == 2) {
+        asm("mad.lo.cc.u32 %0, %2, %3, %5;\n\tmadc.lo.u32 %1, %2, %4, %6;\n\t"
+            "mad.hi.u32 %1, %2, %3, %1;"
+            : "=&r"(Y[0]), "=&r"(Y[1])
+            : "r"(Q), "r"(M[0]), "r"(M[1]), "r"(X[0]), "r"(X[1]));
+    } else if constexpr (W == 3) {
+        asm("mad.lo.cc.u32 %0, %3, %4, %7;\n\tmadc.lo.cc.u32 %1, %3, %5, %8;\n\t"
+            "madc.lo.u32 %2, %3, %6, %9;\n\t"
+            "mad.hi.cc.u32 %1, %3, %4, %1;\n\tmadc.hi.u32 %2, %3, %5, %2;"
+            : "=&r"(Y[0]), "=&r"(Y[1]), "=&r"(Y[2])
+            : "r"(Q), "r"(M[0]), "r"(M[1]), "r"(M[2]), "r"(X[0]), "r"(X[1]), "r"(X[2]));
+    } else if constexpr (W == 4) {
+        asm("mad.lo.cc.u32 %0, %4, %5, %9;\n\tmadc.lo.cc.u32 %1, %4, %6, %10;\n\t"
+            "madc.lo.cc.u32 %2, %4, %7, %11;\n\tmadc.lo.u32 %3, %4, %8, %12;\n\t"
+            "mad.hi.cc.u32 %1, %4, %5, %1;\n\tmadc.hi.cc.u32 %2, %4, %6, %2;\n\t"
+            "madc.hi.u32 %3, %4, %7, %3;"
+            : "=&r"(Y[0]), "=&r"(Y[1]), "=&r"(Y[2]), "=&r"(Y[3])
+            : "r"(Q), "r"(M[0]), "r"(M[1]), "r"(M[2]), "r"(M[3]), "r"(X[0]), "r"(X[1]),
+              "r"(X[2]), "r"(X[3]));
+    } else if constexpr (W == 5) {
+        asm("mad.lo.cc.u32 %0, %5, %6, %11;\n\tmadc.lo.cc.u32 %1, %5, %7, %12;\n\t"
+            "madc.lo.cc.u32 %2, %5, %8, %13;\n\tmadc.lo.cc.u32 %3, %5, %9, %14;\n\t"
+            "madc.lo.u32 %4, %5, %10, %15;\n\t"
+            "mad.hi.cc.u32 %1, %5, %6, %1;\n\tmadc.hi.cc.u32 %2, %5, %7, %2;\n\t"
+            "madc.hi.cc.u32 %3, %5, %8, %3;\n\tmadc.hi.u32 %4, %5, %9, %4;"
+            : "=&r"(Y[0]), "=&r"(Y[1]), "=&r"(Y[2]), "=&r"(Y[3]), "=&r"(Y[4])
+            : "r"(Q), "r"(M[0]), "r"(M[1]), "r"(M[2]), "r"(M[3]), "r"(M[4]), "r"(X[0]),
+              "r"(X[1]), "r"(X[2]), "r"(X[3]), "r"(X[4]));
+    }
+}
+
+// |Y| in place (two's complement): complement every word when negative, then add 1 through a
+// carry chain.  Returns the sign.
+template <int W>
+__device__ __forceinline__ bool abs_words(uint32_t (&Y)[W]) {
+    const uint32_t m = (uint32_t)((int32_t)Y[W - 1] >> 31);
+    const uint32_t one = m & 1u;
+#pragma unroll
+    for (int j = 0; j < W; ++j) Y[j] ^= m;
+    if constexpr (W == 1) {
+        Y[0] += one;
+    } else if constexpr (W == 2) {
+        asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(Y[0]), "+r"(Y[1]) : "r"(one));
+    } else if constexpr (W == 3) {
+        asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.u32 %2, %2, 0;"
+            : "+r"(Y[0]), "+r"(Y[1]), "+r"(Y[2])
+            : "r"(one));
+    } else if constexpr (W == 4) {
+        asm("add.cc.u32 %0, %0, %4;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.cc.u32 %2, %2, 0;\n\t"
+            "addc.u32 %3, %3, 0;"
+            : "+r"(Y[0]), "+r"(Y[1]), "+r"(Y[2]), "+r"(Y[3])
+            : "r"(one));
+    } else if constexpr (W == 5) {
+        asm("add.cc.u32 %0, %0, %5;\n\taddc.cc.u32 %1, %1, 0;\n\taddc.cc.u32 %2, %2, 0;\n\t"
+            "addc.cc.u32 %3, %3, 0;\n\taddc.u32 %4, %4, 0;"
+            : "+r"(Y[0]), "+r"(Y[1]), "+r"(Y[2]), "+r"(Y[3]), "+r"(Y[4])
+            : "r"(one));
+    }
+    return m != 0;
+}
+
 // OutT = double (DGEMM) or float (SGEMM): C'' is rounded to 53 or 24 bits, then scaled.
 template <int N, typename OutT>
 __device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
@@ -88,27 +189,12 @@ __device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
         for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.PG[g][j] * v;
     }
     uint32_t X[W];
-    uint64_t carry = 0;
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-        const uint64_t s = acc[j] + carry;
-        X[j] = (uint32_t)s;
-        carry = s >> 32;
-    }
+    fold_columns<W>(acc, X);
     // Q = round(X / P) from the fixed-point estimate; |S/2^48 - X/P| < 2^-20
     const uint64_t frac = S & ((1ull << 48) - 1);
     const uint32_t Q = (uint32_t)((S + (1ull << 47)) >> 48);
     uint32_t Y[W];
-    uint64_t qpc = 0;
-    int64_t borrow = 0;
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-        const uint64_t prod = (uint64_t)Q * t.P[j] + qpc;
-        qpc = prod >> 32;
-        const int64_t d = (int64_t)X[j] - (int64_t)(uint32_t)prod - borrow;
-        Y[j] = (uint32_t)d;
-        borrow = d < 0 ? 1 : 0;
-    }
+    add_word_times<W>(X, Q, t.negP, Y);  // Y = X - Q P (mod 2^(32 W))
     const uint64_t half = 1ull << 47;
     if ((frac > half ? frac - half : half - frac) < (1ull << 38)) {
         // The estimate sits within 2^-10 of a half-integer: make -P/2 <= Y < P/2 exactly.
@@ -146,15 +232,7 @@ __device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
         }
     }
     // |Y| and sign
-    const bool neg = (Y[W - 1] >> 31) != 0;
-    uint32_t cb = 1;
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-        const uint32_t v = neg ? ~Y[j] : Y[j];
-        const uint64_t s = (uint64_t)v + (neg ? cb : 0u);
-        Y[j] = (uint32_t)s;
-        cb = (uint32_t)(s >> 32);
-    }
+    const bool neg = abs_words<W>(Y);
     // leading word and the 96-bit window below the leading bit
     int top = -1;
     uint32_t w0 = 0, w1 = 0, w2 = 0, low_or = 0;

@@ -33,6 +33,7 @@ struct CrtTables {
     float inv_p[kMaxModuli];        // 1/p_l rounded to single
     uint32_t Pl[kMaxModuli][kMaxWords];  // P_l = P/p_l, little-endian 32-bit words
     uint32_t P[kMaxWords];
+    uint32_t negP[kMaxWords];       // 2^(32 kMaxWords) - P: -P modulo any 2^(32 W), W <= kMaxWords
     uint32_t halfP[kMaxWords];      // P/2 (P is even: 256 is always a modulus)
     // Moduli grouped in threes, g = 0.. : group g holds moduli 3g, 3g+1, 3g+2 (fewer at the end).
     // With w_l in [0, p_l), v_g = sum_{l in g} w_l coef_l where coef_l is the product of the

@@ -129,6 +129,15 @@ void build(int N, ModTables& t) {
         t.crt.R48[g] = (unsigned long long)(((unsigned __int128)1 << 48) / prod +
                                             ((((unsigned __int128)1 << 48) % prod) * 2 >= prod));
     }
+    {   // two's complement of P over kMaxWords words
+        uint64_t borrow = 0;
+        for (int w = 0; w < kMaxWords; ++w) {
+            const uint64_t pw = w < (int)P.size() ? P[w] : 0u;
+            const uint64_t d = (uint64_t)0 - pw - borrow;
+            t.crt.negP[w] = (uint32_t)d;
+            borrow = (pw + borrow) != 0 ? 1 : 0;
+        }
+    }
     for (int w = 0; w < kMaxWords; ++w) {
         t.crt.P[w] = w < (int)P.size() ? P[w] : 0u;
         uint32_t hi_bit = (w + 1 < (int)P.size()) ? (P[w + 1] & 1u) : 0u;
