@@ -169,8 +169,8 @@ def run_reference(args, world, rank):
     import synthetic
 
     oracle.build()
-    m = n = k = SIZE
-    rows = cols = args.ref_block
+    m = n = k = args.size
+    rows = cols = min(args.ref_block, args.size)
     # The oracle needs only the sampled rows of A and columns of B; the rest is never read, so
     # draw just those lines from the paper's generator (independent streams per line).
     I = np.linspace(0, m - 1, rows).astype(np.int32)
@@ -180,7 +180,7 @@ def run_reference(args, world, rank):
     times = []
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.dgemm_block(A_rows, B_cols, rows, cols, k, NUM_MODULI, np.arange(rows),
+        oracle.dgemm_block(A_rows, B_cols, rows, cols, k, args.moduli, np.arange(rows),
                            np.arange(cols))
         dt = time.perf_counter() - t0
         if it >= args.warmup:
@@ -193,15 +193,52 @@ def run_reference(args, world, rank):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 (int64 residue products, 256-bit CRT)",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{rows}x{cols} block"},
+        "data": "synthetic",
+        "config": {"workload": f"square FP64 GEMM m=n=k={m}, phi={PHI}, N={args.moduli} moduli",
+                   "sample": f"{rows}x{cols} block" if rows < m else "full"},
         "cpu_baseline": {"value": value, "unit": "TFLOPS", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": f"{rows}x{cols} block of C (full k={k}) per step"},
+                         "sample": (f"{rows}x{cols} block of C (full k={k}) per step" if rows < m
+                                    else "the full product per step")},
         "e2e": {"value": value, "unit": "TFLOPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     del I, J
     print(json.dumps(line), flush=True)
+
+
+def run_reference_batched(args):
+    """--impl reference --batched: the oracle over every problem of the batched workload, full,
+    on host cores (the same problems as the GPU run; N = 15, the moduli count the autotuner gives
+    most of them)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    items = batched_problems(args.batch, seed=4, device="cpu")
+    N = 15
+    flops = sum(2.0 * it["m"] * it["n"] * it["k"] for it in items)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for p in items:
+            oracle.dgemm(p["A"].numpy(), p["B"].numpy(), p["m"], p["n"], p["k"], N)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = flops * len(times) / total / 1e12
+    print(json.dumps({
+        "impl": "reference", "mode": "batched",
+        "metric": "batched Ozaki-II DGEMM effective TFLOPS (sum 2mnk / time)", "value": value,
+        "unit": "TFLOPS", "steps": args.steps, "warmup": args.warmup,
+        "ms_per_batch": 1e3 * total / len(times), "dtype": "f64 (int64 residue products, 256-bit CRT)",
+        "config": {"workload": f"{args.batch} problems, m, n, k log-uniform in [64, 2048], phi in "
+                               "{0.5, 1} alternating", "n_per_item": N},
+        "cpu_baseline": {"value": value, "unit": "TFLOPS", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": "every problem, full"},
+    }), flush=True)
 
 
 # ------------------------------------------------------------------------------- GPU arm
@@ -859,12 +896,16 @@ def main():
         run_scaling_study(args)
         return
     if args.batched:
-        run_batched(args)
+        if args.impl == "reference":
+            run_reference_batched(args)
+        else:
+            run_batched(args)
         return
     if args.serve:
         run_serve(args)
         return
-    if args.warmup < 3:
+    full_reference = args.impl == "reference" and args.ref_block >= args.size
+    if args.warmup < 3 and not full_reference:  # (a full oracle product needs no warm-up)
         log("warm-up raised to 3 steps")
         args.warmup = 3
     world, rank, local = dist_setup(args)
