@@ -37,6 +37,8 @@ struct ozaki2_context {
     std::vector<GraphEntry> graphs;
     cudaStream_t capture_stream = nullptr;
     bool pageable_access = false;  // the device can address ordinary (pageable) host memory
+    void* in_ws = nullptr;         // device copies of host-resident A and B (ozaki2_dgemm)
+    size_t in_ws_bytes = 0;
 };
 
 namespace {
@@ -99,6 +101,17 @@ bool addressable(const ozaki2_context* ctx, const void* p) {
         return ctx->pageable_access;
     }
     return a.type != cudaMemoryTypeUnregistered || ctx->pageable_access;
+}
+
+// True if p is host memory (page-locked, or pageable on a coherent link) rather than device or
+// managed memory.
+bool host_resident(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
 ozaki2_context* g_default = nullptr;
@@ -203,6 +216,23 @@ int accurate_shifts(ozaki2_context* ctx, const void* A, int64_t als, int64_t aes
 
 // The emulated GEMM for FP64 (f32 = false) or FP32 (f32 = true) operands and result; alpha and
 // beta are passed as doubles (exact for single values).
+// Device buffer for the copies of host-resident inputs (grown on demand, like the workspace).
+int ensure_input_stage(ozaki2_context* ctx, size_t bytes) {
+    if (ctx->in_ws_bytes >= bytes) return OZAKI2_SUCCESS;
+    if (ctx->in_ws) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        cudaFree(ctx->in_ws);
+        ctx->in_ws = nullptr;
+        ctx->in_ws_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->in_ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return OZAKI2_ERROR_ALLOC;
+    }
+    ctx->in_ws_bytes = bytes;
+    return OZAKI2_SUCCESS;
+}
+
 int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m, int n, int k,
                double alpha, const void* A, int lda, const void* B, int ldb, double beta,
                void* C, int ldc, int N, bool f32 = false) {
@@ -240,6 +270,32 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     void* pb = ws + L.off_pb;
     int8_t* res = reinterpret_cast<int8_t*>(ws + L.off_res);
     cudaStream_t st = ctx->stream;
+
+    // Host-resident A or B (page-locked, or pageable on a coherent link) are first copied into
+    // device memory by a kernel, so the scaling and the conversion, which each read the inputs,
+    // read them from HBM.  A handle with a caller-provided workspace allocates nothing and reads
+    // them in place.
+    if (!ctx->user_ws) {
+        const size_t esz = f32 ? 4 : 8;
+        const int acols = is_notrans(transA) ? k : m, bcols = is_notrans(transB) ? n : k;
+        const size_t a_span = ((size_t)lda * (size_t)(acols - 1) + (size_t)arows) * esz;
+        const size_t b_span = ((size_t)ldb * (size_t)(bcols - 1) + (size_t)brows) * esz;
+        const bool stage_a = host_resident(A), stage_b = host_resident(B);
+        if (stage_a || stage_b) {
+            const size_t a_room = stage_a ? (size_t)round_up((int64_t)a_span, 256) : 0;
+            if ((rc = ensure_input_stage(ctx, a_room + (stage_b ? b_span : 0)))) return rc;
+            char* p = static_cast<char*>(ctx->in_ws);
+            if (stage_a) {
+                if ((rc = cuda_rc(launch_stage_in(p, A, a_span, ctx->num_sms, st)))) return rc;
+                A = p;
+            }
+            if (stage_b) {
+                if ((rc = cuda_rc(launch_stage_in(p + a_room, B, b_span, ctx->num_sms, st))))
+                    return rc;
+                B = p + a_room;
+            }
+        }
+    }
 
     auto mark = [&](int i) {
         if (ctx->timing) cudaEventRecord(ctx->ev[i], st);
@@ -301,6 +357,7 @@ int ozaki2_destroy(ozaki2_handle_t handle) {
     if (!handle) return -1;
     cudaStreamSynchronize(handle->stream);
     if (handle->ws && !handle->user_ws) cudaFree(handle->ws);
+    if (handle->in_ws) cudaFree(handle->in_ws);
     if (handle->d_status) cudaFree(handle->d_status);
     for (auto& e : handle->ev)
         if (e) cudaEventDestroy(e);

@@ -252,6 +252,12 @@ cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int
                        int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream,
                        bool f32 = false, bool padded = false);
 
+// Device copy of `bytes` from host memory the device can address (page-locked, or any host
+// memory on a coherent link): a kernel reads the host memory at the link's rate, where a copy-
+// engine upload measured erratic on GB300 after kernels had touched host memory.
+cudaError_t launch_stage_in(void* dst, const void* src, size_t bytes, int num_sms,
+                            cudaStream_t stream);
+
 cudaError_t launch_scale_c(int m, int n, double beta, void* C, int64_t ldc,
                            cudaStream_t stream, bool f32 = false);
 

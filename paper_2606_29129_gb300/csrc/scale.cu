@@ -401,7 +401,50 @@ __global__ void accu_shift_grouped_kernel(const GroupProblem* __restrict__ probs
     }
 }
 
+// Copy of `count` words of W bytes from host memory the device can address into device memory.
+// Each thread keeps four loads in flight: the link to host memory has a long latency.
+template <typename Word>
+__global__ void __launch_bounds__(256) stage_in_kernel(Word* __restrict__ dst,
+                                                       const Word* __restrict__ src,
+                                                       int64_t count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < count; i += 4 * stride) {
+        Word w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = src[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dst[i + u * stride] = w[u];
+    }
+    for (; i < count; i += stride) dst[i] = src[i];
+}
+
 }  // namespace
+
+cudaError_t launch_stage_in(void* dst, const void* src, size_t bytes, int num_sms,
+                            cudaStream_t stream) {
+    if (bytes == 0) return cudaSuccess;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) |
+                        (uintptr_t)bytes;
+    const int grid = 8 * (num_sms > 0 ? num_sms : 1);
+    if ((a & 15) == 0)
+        stage_in_kernel<<<grid, 256, 0, stream>>>(static_cast<uint4*>(dst),
+                                                  static_cast<const uint4*>(src),
+                                                  (int64_t)(bytes / 16));
+    else if ((a & 7) == 0)
+        stage_in_kernel<<<grid, 256, 0, stream>>>(static_cast<uint2*>(dst),
+                                                  static_cast<const uint2*>(src),
+                                                  (int64_t)(bytes / 8));
+    else if ((a & 3) == 0)
+        stage_in_kernel<<<grid, 256, 0, stream>>>(static_cast<unsigned*>(dst),
+                                                  static_cast<const unsigned*>(src),
+                                                  (int64_t)(bytes / 4));
+    else
+        stage_in_kernel<<<grid, 256, 0, stream>>>(static_cast<unsigned char*>(dst),
+                                                  static_cast<const unsigned char*>(src),
+                                                  (int64_t)bytes);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_accu_shift(int* e, int m, int* f, int n, const uint32_t* cmax, int m_pad,
                               float pprime, float delta, cudaStream_t stream) {
