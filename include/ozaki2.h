@@ -142,9 +142,12 @@ int ozaki2_constants(int num_moduli, int* moduli, int* inverses, float* pprime);
 /* ---- the whole path ----------------------------------------------------------------------- */
 /* Emulated DGEMM: C = alpha op(A) op(B) + beta C through Steps 1-4 with N = num_moduli moduli
  * (2..20).  op(A) is m x k, op(B) k x n, C is m x n with ldc >= max(1, m).  A, B and C may be
- * device memory or page-locked host memory (the kernels read and write it over the CPU-GPU link;
- * on a device with pageable-memory access any host memory); a pointer the device cannot address
- * is an argument error.  Quick returns:
+ * device memory or page-locked host memory (on a device with pageable-memory access any host
+ * memory); a pointer the device cannot address is an argument error.  Host-resident A and B are
+ * first copied into a device buffer that the handle allocates and keeps (a kernel reads them over
+ * the CPU-GPU link); with a workspace set by ozaki2_set_workspace nothing is allocated and they
+ * are read in place.  A host-resident C is written (and, for beta != 0, read) in place by the
+ * reconstruction kernel.  Quick returns:
  * m = 0 or n = 0 does nothing; k = 0 or alpha = 0 computes C = beta C (C = 0 when beta = 0).
  * Uses the default handle.  Argument numbers for errors: transA 1, transB 2, m 3, n 4, k 5,
  * alpha 6, A 7, lda 8, B 9, ldb 10, beta 11, C 12, ldc 13, num_moduli 14. */
