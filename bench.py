@@ -32,7 +32,7 @@ NUM_MODULI = 16
 SGEMM_MODULI = 8
 # DRAM bytes (read + write) of one residue-GEMM launch measured with ncu for (dtype, size, N);
 # the roofline line reports it for the matching configuration only.
-MEASURED_GEMM_TRAFFIC = {("f64", 16384, 16): 105.84e9 + 4.30e9}
+MEASURED_GEMM_TRAFFIC = {("f64", 16384, 16): 105.85e9 + 4.30e9, ("f32", 16384, 8): 52.89e9 + 2.14e9}
 METRIC = "Ozaki-II DGEMM effective TFLOPS at stated error vs cuBLAS DGEMM; p50/p99 lat"
 WORKLOAD = f"square FP64 GEMM m=n=k={SIZE}, phi={PHI}, N={NUM_MODULI} moduli"
 

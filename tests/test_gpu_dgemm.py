@@ -264,3 +264,43 @@ def test_host_resident_operands(oz, orc):
     torch.cuda.synchronize()
     assert _gpu.same_bits(Ch.numpy(), ref)
     assert _gpu.same_bits(ref, orc.dgemm(A, B, m, n, k, N, alpha=0.5, beta=-1.0, Cin=Cin))
+
+
+def _pinned_view(a, offset_elems):
+    """Page-locked host copy of `a` (flattened) starting `offset_elems` elements into its buffer,
+    so that the view is not 16-byte aligned when the offset is odd."""
+    import torch
+
+    flat = np.ascontiguousarray(a).reshape(-1)
+    buf = torch.empty(flat.size + offset_elems, dtype=torch.from_numpy(flat[:1]).dtype).pin_memory()
+    view = buf[offset_elems:]
+    view.copy_(torch.from_numpy(flat))
+    return buf, view
+
+
+@pytest.mark.parametrize("trans", [("N", "N"), ("T", "N"), ("N", "T")])
+@pytest.mark.parametrize("own_workspace", [False, True])
+def test_host_operands_unaligned_transposed(oz, orc, trans, own_workspace):
+    """Host-resident A and B one element past a 16-byte boundary, any transpose: the handle stages
+    them into device memory (8-byte copies), or with a caller-provided workspace reads them in
+    place; either way C is bit-identical to the device-memory call and to the oracle."""
+    import torch
+
+    tA, tB = trans
+    m, n, k, N = 130, 257, 333, 15
+    A, B = make(m, n, k, 1.0, 91, tA, tB)
+    lda, ldb = A.shape[-1], B.shape[-1]
+    ref = _gpu.dgemm(oz, A, B, m, n, k, N, tA, tB, lda=lda, ldb=ldb)
+    keep_a, Ah = _pinned_view(A, 1)
+    keep_b, Bh = _pinned_view(B, 1)
+    h = oz.Handle()
+    if own_workspace:
+        ws = torch.empty(oz.ozaki2_workspace_size(m, n, k, N), dtype=torch.uint8, device="cuda")
+        h.set_workspace(ws, ws.numel())
+    C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    _gpu.ok(oz.ozaki2_dgemm(tA, tB, m, n, k, 1.0, Ah, lda, Bh, ldb, 0.0, C, m, N, h),
+            "host dgemm")
+    torch.cuda.synchronize()
+    assert _gpu.same_bits(C.cpu().numpy(), ref)
+    assert _gpu.same_bits(ref, orc.dgemm(A, B, m, n, k, N, tA, tB))
+    del keep_a, keep_b

@@ -142,3 +142,28 @@ def test_torch_convenience(oz, orc):
     C = sgemm(A, B)
     ref = orc.sgemm(A.cpu().numpy(), B.cpu().numpy(), m, n, k, 8, "T", "T", lda=k, ldb=n)
     assert _gpu.same_bits(C.cpu().numpy().T, ref)
+
+
+@pytest.mark.parametrize("offset", [1, 2, 4])
+def test_host_operands_unaligned(oz, orc, offset):
+    """Host-resident float A, B and C (A and B `offset` floats past a 16-byte boundary: 4- and
+    8-byte staging copies): bit-identical to the device-memory call and to the oracle."""
+    import torch
+
+    m, n, k, N = 200, 130, 517, 8
+    A, B = make(m, n, k, 1.0, 93)
+    ref = gpu_sgemm(oz, A, B, m, n, k, N)
+    bufs = []
+    views = []
+    for X in (A, B):
+        flat = X.reshape(-1)
+        buf = torch.empty(flat.size + offset, dtype=torch.float32).pin_memory()
+        buf[offset:].copy_(torch.from_numpy(flat))
+        bufs.append(buf)
+        views.append(buf[offset:])
+    Ch = torch.zeros((n, m), dtype=torch.float32).pin_memory()
+    _gpu.ok(oz.ozaki2_sgemm("N", "N", m, n, k, 1.0, views[0], m, views[1], k, 0.0, Ch, m, N),
+            "host sgemm")
+    torch.cuda.synchronize()
+    assert _gpu.same_bits(Ch.numpy(), ref)
+    assert _gpu.same_bits(ref, orc.sgemm(A, B, m, n, k, N))
