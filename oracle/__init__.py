@@ -1,7 +1,7 @@
 """CPU oracle for Ozaki scheme II (fast mode, Algorithm 2 scaling) -- test infrastructure.
 
-Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may use
-this package.  It wraps ``ozaki2_oracle.c`` (plain C + OpenMP) through ctypes and shares no
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline and
+reference (``--impl reference``) legs may use this package.  It wraps ``ozaki2_oracle.c`` (plain C + OpenMP) through ctypes and shares no
 code with the CUDA library.  Matrices are column-major: a rows x cols matrix is a
 C-contiguous numpy array of storage shape (cols, rows) with leading dimension rows.
 """

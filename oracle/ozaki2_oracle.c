@@ -5,7 +5,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the CUDA path is
  * checked against.  Only the test suite, the smoke check and the benchmark's CPU-baseline
- * leg may load it.  It shares no code, header, table or constant generator with the CUDA
+ * and reference legs may load it.  It shares no code, header, table or constant generator with the CUDA
  * library; it takes matrices as arguments and never calls the GPU.
  *
  * Every step follows the paper's definitions in the paper's order:
