@@ -233,19 +233,27 @@ __device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
     }
     // |Y| and sign
     const bool neg = abs_words<W>(Y);
-    // leading word and the 96-bit window below the leading bit
-    int top = -1;
-    uint32_t w0 = 0, w1 = 0, w2 = 0, low_or = 0;
+    // leading word and the 96-bit window below the leading bit.  The top word is almost always
+    // the leading one (the shifts make |C''| large against P), so that case is straight-line
+    // code and the search for a lower leading word is a branch.
+    int top = W - 1;
+    uint32_t w0 = Y[W - 1], w1 = W > 1 ? Y[W - 2] : 0u, w2 = W > 2 ? Y[W - 3] : 0u, low_or = 0;
 #pragma unroll
-    for (int j = W - 1; j >= 0; --j)
-        if (top < 0 && Y[j] != 0) top = j;
-    if (top < 0) return (OutT)0;
+    for (int j = 0; j < W - 3; ++j) low_or |= Y[j];
+    if (w0 == 0) {
+        top = -1;
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-        if (j == top) w0 = Y[j];
-        if (j == top - 1) w1 = Y[j];
-        if (j == top - 2) w2 = Y[j];
-        if (j < top - 2) low_or |= Y[j];
+        for (int j = W - 1; j >= 0; --j)
+            if (top < 0 && Y[j] != 0) top = j;
+        if (top < 0) return (OutT)0;
+        w0 = w1 = w2 = low_or = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            if (j == top) w0 = Y[j];
+            if (j == top - 1) w1 = Y[j];
+            if (j == top - 2) w2 = Y[j];
+            if (j < top - 2) low_or |= Y[j];
+        }
     }
     const int lz = __clz(w0);
     int msb = 32 * top + 31 - lz;
