@@ -3,16 +3,17 @@
 //
 // GB300 design: FP64 throughput is a small fraction of the integer rate on this part, so the
 // reconstruction is exact multi-word integer arithmetic instead of split FP64 constants:
-//   w_l  = q_l c_l mod p_l                       (in [0, p_l))
-//   X    = sum_l P_l w_l                         (P_l = P/p_l, W 32-bit words, 64-bit column sums)
-//   Q    = round(sum_l w_l / p_l) = round(X / P) (48-bit fixed-point estimate)
+//   X    = sum_l P_l q_l c_l modulo P, as sum_g PG_g v_g over pairs of moduli (below)
+//          (W 32-bit words, 64-bit column sums)
+//   Q    = round(X / P)                          (48-bit fixed-point estimate of sum_g v_g/prod_g)
 //   C''  = X - Q P                               (exact; corrected by +-P if the estimate sat
 //                                                 within 2^-10 of a half-integer)
 // X and Q P are formed modulo 2^(32 W) with W just large enough for Y (see crt_words).
-// The moduli are taken in groups of three (v_g = sum w_l coef_l < 3 prod_g < 2^26), so X needs
-// one 64-bit multiply-add per group and word instead of one per modulus and word; the kernel
-// is instantiated per N so every table entry is a compile-time constant-bank operand.
-// Since P_l q_l w_l == P_l q_l c_l (mod P), C'' = rmod(sum_l P_l q_l c_l, P) of eq. (os2-C'').
+// The moduli are taken in pairs: with prod_g the pair's product and K_l = (prod_g / p_l) q_l mod
+// prod_g, v_g = bias_g + sum_{l in g} c_l K_l is congruent modulo prod_g to the pair's share of
+// X / PG_g, so each residue costs one multiply-add and X one 64-bit multiply-add per pair and
+// word; the kernel is instantiated per N so every table entry is a constant-bank operand.
+// Since X == sum_l P_l q_l c_l (mod P), C'' = rmod(sum_l P_l q_l c_l, P) of eq. (os2-C'').
 // C'' is rounded to the nearest double (ties to even) with the unscaling 2^-(e_i + f_j) folded
 // into the exponent; results outside the normal range take a two-multiply path that rounds once.
 //
@@ -163,27 +164,23 @@ template <int N, typename OutT>
 __device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
                                           const CrtTables& t) {
     constexpr int W = crt_words(N);
-    constexpr int G = (N + 2) / 3;
+    constexpr int G = (N + 1) / 2;
     if (ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE) {
         if constexpr (sizeof(OutT) == 4) return __uint_as_float(0x7FC00000u);
         else return __longlong_as_double(0x7FF8000000000000ll);
     }
-    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^48 X / P (fixed point)
+    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^48 X / P (fixed point).  Per pair of
+    // moduli, v_g = bias_g + sum c_l K_l: one multiply-add per residue (the signed product wraps
+    // modulo 2^32 to the exact value, which lies in [0, 2^25)).
     uint64_t acc[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) acc[j] = 0;
     uint64_t S = 0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        uint32_t v = 0;
+        uint32_t v = t.grp_bias[g];
 #pragma unroll
-        for (int l = 3 * g; l < 3 * g + 3 && l < N; ++l) {
-            const int c = cres[l];
-            const uint32_t x = (uint32_t)c * t.q[l] + t.off128[l];  // = q_l c (mod p_l), >= 0
-            // x < 2^16, so the rounded-up reciprocal gives the exact quotient
-            const uint32_t w = x - __umulhi(x, t.recip_up[l]) * t.p[l];
-            v += w * t.coef[l];
-        }
+        for (int l = 2 * g; l < 2 * g + 2 && l < N; ++l) v += (uint32_t)cres[l] * t.K[l];
         S += (uint64_t)v * t.R48[g];
 #pragma unroll
         for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.PG[g][j] * v;

@@ -25,23 +25,19 @@ struct ConvertTables {
 
 struct CrtTables {
     int N;
-    uint32_t p[kMaxModuli];
-    uint32_t recip_up[kMaxModuli];  // ceil(2^32 / p): umulhi(x, .) = floor(x / p) for x < 2^16
-    uint32_t q[kMaxModuli];         // q_l = (P/p_l)^{-1} mod p_l
-    uint32_t off[kMaxModuli];       // (-128 q_l) mod p_l, so (c + 128) q_l + off = q_l c (mod p_l)
-    uint32_t off128[kMaxModuli];    // 128 q_l + off: c q_l + off128 = (c + 128) q_l + off >= 0
-    float inv_p[kMaxModuli];        // 1/p_l rounded to single
-    uint32_t Pl[kMaxModuli][kMaxWords];  // P_l = P/p_l, little-endian 32-bit words
     uint32_t P[kMaxWords];
     uint32_t negP[kMaxWords];       // 2^(32 kMaxWords) - P: -P modulo any 2^(32 W), W <= kMaxWords
     uint32_t halfP[kMaxWords];      // P/2 (P is even: 256 is always a modulus)
-    // Moduli grouped in threes, g = 0.. : group g holds moduli 3g, 3g+1, 3g+2 (fewer at the end).
-    // With w_l in [0, p_l), v_g = sum_{l in g} w_l coef_l where coef_l is the product of the
-    // other moduli of the group, so v_g / prod_g = sum_{l in g} w_l / p_l and
-    // X = sum_l P_l w_l = sum_g PG_g v_g with PG_g = P / prod_g.
-    uint32_t coef[kMaxModuli];
-    uint32_t PG[(kMaxModuli + 2) / 3][kMaxWords];
-    unsigned long long R48[(kMaxModuli + 2) / 3];  // round(2^48 / prod_g)
+    // Moduli grouped in pairs, g = 0.. : group g holds moduli 2g and 2g+1 (one at the end for
+    // odd N), prod_g their product and PG_g = P / prod_g.  P_l = PG_g cf_l with cf_l = prod_g /
+    // p_l, and cf_l w_l == cf_l q_l c_l (mod prod_g) for any w_l == q_l c_l (mod p_l), so with
+    // K_l = cf_l q_l mod prod_g the group sum v_g = bias_g + sum_{l in g} c_l K_l (bias_g =
+    // 256 prod_g keeps it in [0, 2^25)) gives X = sum_g PG_g v_g == sum_l P_l q_l c_l (mod P),
+    // and X / P = sum_g v_g / prod_g.
+    uint32_t K[kMaxModuli];
+    uint32_t grp_bias[(kMaxModuli + 1) / 2];
+    uint32_t PG[(kMaxModuli + 1) / 2][kMaxWords];
+    unsigned long long R48[(kMaxModuli + 1) / 2];  // round(2^48 / prod_g)
 };
 
 struct EpilogueTables {

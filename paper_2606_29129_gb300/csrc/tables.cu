@@ -104,24 +104,20 @@ void build(int N, ModTables& t) {
         t.conv.bias[l] = 0x4B400000u - h;
         t.conv.magic39[l] = (uint32_t)(((1ull << 39) + p - 1) / p);
 
-        t.crt.p[l] = p;
-        t.crt.recip_up[l] = (uint32_t)(((1ull << 32) + p - 1) / p);
-        t.crt.q[l] = q;
-        t.crt.off[l] = (uint32_t)((p - (128u * q) % p) % p);
-        t.crt.off128[l] = 128u * q + t.crt.off[l];
-        t.crt.inv_p[l] = 1.0f / (float)p;
-        for (int w = 0; w < kMaxWords; ++w) t.crt.Pl[l][w] = w < (int)Pl.size() ? Pl[w] : 0u;
-
         t.epi.p[l] = (float)p;
         t.epi.inv_p[l] = 1.0f / (float)p;
         t.epi.hi[l] = (p % 2) ? (float)((p - 1) / 2) : (float)(p / 2 - 1);
         t.epi.lo[l] = (p % 2) ? -(float)((p - 1) / 2) : -(float)(p / 2);
     }
-    for (int g = 0; 3 * g < N; ++g) {
-        const int l0 = 3 * g, l1 = (3 * g + 3 < N) ? 3 * g + 3 : N;
+    for (int g = 0; 2 * g < N; ++g) {
+        const int l0 = 2 * g, l1 = (2 * g + 2 < N) ? 2 * g + 2 : N;
         uint64_t prod = 1;
         for (int l = l0; l < l1; ++l) prod *= (uint64_t)kModuli[l];
-        for (int l = l0; l < l1; ++l) t.crt.coef[l] = (uint32_t)(prod / (uint64_t)kModuli[l]);
+        for (int l = l0; l < l1; ++l) {
+            const uint64_t cf = prod / (uint64_t)kModuli[l];
+            t.crt.K[l] = (uint32_t)(cf * (uint64_t)t.inverses[l] % prod);
+        }
+        t.crt.grp_bias[g] = (uint32_t)(256 * prod);  // >= 128 sum K_l: the group sum stays >= 0
         Words PG{1};
         for (int j = 0; j < N; ++j)
             if (j < l0 || j >= l1) mul_small(PG, (uint32_t)kModuli[j]);
