@@ -111,14 +111,15 @@ __device__ __forceinline__ uint32_t residue_bits(const Scaled& v, const ConvertT
     // from d[0] so y = kFloatB + t.  With q = floor((t + h)/p), s = t - q p lies in [-h, h] and is
     // the symmetric residue of |a'|; y - q p = kFloatB + s is the float 1.5 2^23 + s, and one
     // exact FMA gives sgn s.  x = t + h < 2^31 is y - (kFloatB - h) (table `bias`), and its
-    // quotient by p is exact with the 2^39 magic (x (ceil(2^39/p) p - 2^39) < 2^39 for every such
-    // x and modulus).
+    // quotient by p is exact with the 2^39 magic m (x (ceil(2^39/p) p - 2^39) < 2^39 for every
+    // such x and modulus); x m comes from y m plus the table's -(bias m) modulo 2^64.
     const uint32_t p = t.p[l];
     uint32_t y = v.d[0];
 #pragma unroll
     for (int j = 1; j < L; ++j) y += v.d[j] * t.pow21[l][j];
-    const uint32_t x = y - t.bias[l];
-    const uint32_t fb = y - (__umulhi(x, t.magic39[l]) >> 7) * p;
+    // x m = y m - bias m exactly (x < 2^31, so x m < 2^63): one 64-bit multiply-add
+    const uint64_t xm = (uint64_t)y * t.magic39[l] + t.neg_bias_magic[l];
+    const uint32_t fb = y - (uint32_t)(xm >> 39) * p;
     return __float_as_uint(fmaf(v.sgn, __uint_as_float(fb), v.sgn * -12582912.0f));
 }
 

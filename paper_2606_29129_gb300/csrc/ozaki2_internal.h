@@ -19,8 +19,9 @@ struct ConvertTables {
     uint32_t p[kMaxModuli];
     uint32_t pow21[kMaxModuli][4];  // 2^(21 j) mod p
     uint32_t bias[kMaxModuli];      // float bits of 1.5 2^23, minus h = (p - 1) / 2
-    uint32_t magic39[kMaxModuli];   // ceil(2^39 / p): floor(x / p) = umulhi(x, magic) >> 7 for
-                                    // every x below 2^39 / p, beyond any x formed here
+    uint32_t magic39[kMaxModuli];   // ceil(2^39 / p): floor(x / p) = (x magic) >> 39 for every
+                                    // x below 2^39 / p, beyond any x formed here
+    unsigned long long neg_bias_magic[kMaxModuli];  // -(bias magic39) modulo 2^64
 };
 
 struct CrtTables {

@@ -103,6 +103,8 @@ void build(int N, ModTables& t) {
         const uint32_t h = (p - 1) / 2;
         t.conv.bias[l] = 0x4B400000u - h;
         t.conv.magic39[l] = (uint32_t)(((1ull << 39) + p - 1) / p);
+        t.conv.neg_bias_magic[l] =
+            (unsigned long long)(0ull - (uint64_t)t.conv.bias[l] * t.conv.magic39[l]);
 
         t.epi.p[l] = (float)p;
         t.epi.inv_p[l] = 1.0f / (float)p;
