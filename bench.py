@@ -207,6 +207,18 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_tune_tiles(args):
+    """Residue-GEMM configuration per size class by timing: kernel variant (128 x 256 tiles on
+    one SM, or 256 x 256 on an SM pair) and K chunk, for square DGEMMs of each size."""
+    from paper_2606_29129_gb300 import autotune
+
+    table = autotune.tune_tiles(sizes=tuple(args.tune_sizes), N=args.moduli)
+    print(json.dumps({"mode": "tile_tuning", "N": args.moduli,
+                      "table": autotune.tiles_to_json(table),
+                      "variants": {"1": "128 x 256 tiles, one CTA per SM",
+                                   "2": "256 x 256 tiles on SM pairs"}}), flush=True)
+
+
 def run_reference_batched(args):
     """--impl reference --batched: the oracle over every problem of the batched workload, full,
     on host cores (the same problems as the GPU run; N = 15, the moduli count the autotuner gives
@@ -499,6 +511,8 @@ def run_batched(args):
         torch.cuda.synchronize()
         return s.elapsed_time(e) / reps
 
+    # the K chunk of the grouped residue GEMM, by timing (results identical for every chunk)
+    chunk_ms, chunk_best = autotune.tune_grouped_chunk(grouped, h)
     t_grouped = ev_loop(grouped, args.steps)
     status = h.status()
     # per-request loops on the same inputs
@@ -555,6 +569,9 @@ def run_batched(args):
                      "items_worse_than_cublas": int(worse_than_cublas),
                      "sample": "32x32 random block per item vs double-double"},
         "calibration": {"seconds": calib_s, "table": autotune.table_to_json(table)},
+        "tile_tuning": {"chunk_k_ms": {str(c): t for c, t in chunk_ms.items()},
+                        "chunk_k": chunk_best,
+                        "tile": "128 x 256 (the grouped kernel's one tile shape)"},
         "device_status": status,
     }
     print(json.dumps(line), flush=True)
@@ -862,6 +879,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="accuracy sweep over N, phi and alpha instead of the benchmark")
     ap.add_argument("--sweep-sizes", type=int, nargs="+", default=[8192, 16384])
+    ap.add_argument("--tune-tiles", action="store_true",
+                    help="time the residue-GEMM kernel variants and K chunks per size class")
+    ap.add_argument("--tune-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
     ap.add_argument("--scaling-study", action="store_true",
                     help="fast mode (Algorithm 1) against the proposed scaling over alpha = 2^s")
     ap.add_argument("--study-sizes", type=int, nargs="+", default=[1024, 16384])
@@ -873,6 +893,9 @@ def main():
         return
     if args.scaling_study:
         run_scaling_study(args)
+        return
+    if args.tune_tiles:
+        run_tune_tiles(args)
         return
     if args.batched:
         if args.impl == "reference":

@@ -82,7 +82,8 @@ extern "C" {
 #define OZAKI2_SCALING_ACCURATE 2 /* accurate mode (Section 2.3, eq. (mu_accu)/(nu_accu)): shifts
                                      from the row/column maxima of an auxiliary product
                                      C-bar = A-bar B-bar of integers <= 64; k <= 2^20 - 1 */
-#define OZAKI2_GEMM_AUTO 0        /* the kernel measured fastest on GB300 (currently SINGLE) */
+#define OZAKI2_GEMM_AUTO 0        /* by size, as measured fastest on GB300: PAIR when the padded m
+                                   * and n both lie in [2048, 8192], SINGLE otherwise */
 #define OZAKI2_GEMM_SINGLE 1      /* 128 x 256 tiles, one CTA per SM (tcgen05 cta_group::1) */
 #define OZAKI2_GEMM_PAIR 2        /* 256 x 256 tiles on SM pairs (tcgen05 cta_group::2) */
 

@@ -1,4 +1,5 @@
-"""Choice of the number of moduli N per size class (accuracy autotuning).
+"""Autotuning per size class: the number of moduli N (by accuracy) and the residue-GEMM
+configuration, kernel variant (tile shape) and K chunk (by time).
 
 More moduli make P larger, so the scaled integers keep more bits and the emulated product is
 more accurate (Section 2.2; the error falls roughly 16-20x per modulus).  The cost grows
@@ -7,7 +8,8 @@ paper's (eq. random-matrix-generation), the maximum relative error of the emulat
 candidate N, and that of cuBLAS DGEMM on the same inputs.  The reference is the emulation with
 N = 20, whose error is at the level of one rounding of the result (~1e-16), far below the
 errors being compared.  `choose_n` then picks the smallest N that is not worse than cuBLAS
-(equal accuracy) or that meets a stated relative-error target.
+(equal accuracy) or that meets a stated relative-error target.  `tune_tiles` and
+`tune_grouped_chunk` time the residue-GEMM configurations (see below).
 """
 from __future__ import annotations
 
@@ -95,3 +97,95 @@ def table_from_json(d):
 
 def log2_gap(a: float, b: float) -> float:
     return math.log2(max(a, 1e-300) / max(b, 1e-300))
+
+
+# ---- residue-GEMM configuration (timing autotuning) ------------------------------------------
+# The residue GEMM has two kernels, 128 x 256 tiles with one CTA per SM (OZAKI2_GEMM_SINGLE) and
+# 256 x 256 tiles on SM pairs (OZAKI2_GEMM_PAIR), and a K chunk between the in-place modular
+# reductions (OZAKI2_OPT_CHUNK_K, at most 960 products to keep the FP32 accumulator exact).  The
+# product residues, and so the results, are bit-identical for every configuration; only the time
+# differs, so the choice is made by timing.
+TILE_VARIANTS = (oz.GEMM_SINGLE, oz.GEMM_PAIR)
+CHUNKS = (960, 640, 448, 320)
+
+
+def best_config(timings):
+    """The fastest configuration of a {config: ms} mapping (the first listed on a tie)."""
+    order = list(timings)
+    return min(order, key=lambda c: (timings[c], order.index(c)))
+
+
+def _time_ms(fn, reps):
+    import torch
+
+    fn()  # warm-up (and, for grouped calls, the graph capture)
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def tune_tiles(sizes=(1024, 2048, 4096, 8192, 16384), N=16, variants=TILE_VARIANTS,
+               chunks=CHUNKS, reps=3, seed=0, device="cuda"):
+    """Times ozaki2_dgemm on m = n = k = size for every (kernel variant, K chunk) and returns
+    {size_class(size): {"size": size, "ms": {(variant, chunk): ms}, "best": (variant, chunk)}}."""
+    import torch
+
+    import synthetic
+
+    out = {}
+    for size in sizes:
+        m = n = k = size
+        A = synthetic.paper_matrix_torch(m, k, 1.0, seed + 3 * size + 1, device=device)
+        B = synthetic.paper_matrix_torch(k, n, 1.0, seed + 3 * size + 2, device=device)
+        C = torch.empty((n, m), dtype=torch.float64, device=device)
+        h = oz.Handle()
+        ms = {}
+        for variant in variants:
+            for chunk in chunks:
+                h.set_option(oz.OPT_GEMM_VARIANT, variant)
+                h.set_option(oz.OPT_CHUNK_K, chunk)
+
+                def call():
+                    oz._check("ozaki2_dgemm", oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k,
+                                                              0.0, C, m, N, h))
+
+                ms[(variant, chunk)] = _time_ms(call, reps)
+        out[size_class(k)] = {"size": size, "ms": ms, "best": best_config(ms)}
+    return out
+
+
+def apply_tiles(handle, table, k: int) -> bool:
+    """Sets the handle's kernel variant and K chunk to the tuned ones of k's size class; False
+    (handle unchanged) when the class was not tuned."""
+    entry = table.get(size_class(k))
+    if entry is None:
+        return False
+    variant, chunk = entry["best"]
+    handle.set_option(oz.OPT_GEMM_VARIANT, variant)
+    handle.set_option(oz.OPT_CHUNK_K, chunk)
+    return True
+
+
+def tune_grouped_chunk(call, handle, chunks=CHUNKS, reps=3):
+    """K chunk for a grouped call (one kernel, one tile shape for every problem): times `call()`,
+    which issues the grouped call on `handle`, for each chunk; leaves the fastest set on the
+    handle and returns ({chunk: ms}, best chunk)."""
+    ms = {}
+    for chunk in chunks:
+        handle.set_option(oz.OPT_CHUNK_K, chunk)
+        ms[chunk] = _time_ms(call, reps)
+    best = best_config(ms)
+    handle.set_option(oz.OPT_CHUNK_K, best)
+    return ms, best
+
+
+def tiles_to_json(table):
+    return {str(c): {"size": v["size"], "best": {"variant": v["best"][0], "chunk_k": v["best"][1]},
+                     "ms": {f"{var}/{ch}": t for (var, ch), t in v["ms"].items()}}
+            for c, v in table.items()}

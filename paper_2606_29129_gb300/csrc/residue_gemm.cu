@@ -1028,9 +1028,12 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
         cudaError_t e = cudaMemsetAsync(out, 0, (size_t)num_moduli * m_pad * n_pad, stream);
         return e == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
     }
-    // Measured at 16384^3 on GB300 the one-SM kernel is the faster of the two, so it is the
-    // automatic choice; the pair kernel stays available through OZAKI2_OPT_GEMM_VARIANT.
-    const bool use_pair = variant == OZAKI2_GEMM_PAIR;
+    // Automatic choice, from timings on GB300 (square DGEMMs, N = 16): the SM-pair kernel is
+    // 2-3% faster when both padded dimensions lie in [2048, 8192]; the one-SM kernel is faster
+    // below (equal at 1024) and 11% faster at 16384, where 304 tiles in flight fill the machine.
+    const bool auto_pair = m_pad >= 2048 && n_pad >= 2048 && m_pad <= 8192 && n_pad <= 8192;
+    const bool use_pair =
+        variant == OZAKI2_GEMM_PAIR || (variant == OZAKI2_GEMM_AUTO && auto_pair);
     CUtensorMap ta, tb;
     if (use_pair) {
         if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, pair::HALF) ||

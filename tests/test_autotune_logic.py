@@ -1,0 +1,41 @@
+"""Host logic of the autotuner: size classes, the moduli choice from a calibration table, and
+the residue-GEMM configuration choice from timings (no GPU)."""
+from paper_2606_29129_gb300 import autotune
+from paper_2606_29129_gb300 import ozaki2 as oz
+
+
+class FakeHandle:
+    def __init__(self):
+        self.options = {}
+
+    def set_option(self, option, value):
+        self.options[option] = value
+
+
+def test_size_classes():
+    assert autotune.size_class(1) == 0
+    assert autotune.size_class(64) == 0
+    assert autotune.size_class(65) == 1
+    assert autotune.size_class(16384) == len(autotune.CLASS_EDGES) - 1
+    assert autotune.size_class(10 ** 6) == len(autotune.CLASS_EDGES) - 1
+
+
+def test_choose_n_equal_accuracy_and_target():
+    table = {3: {"k": 512, "cublas": 1e-11, "N": {13: 5e-10, 14: 2e-11, 15: 9e-12, 16: 1e-14}}}
+    assert autotune.choose_n(table, 500) == 15            # smallest N not worse than cuBLAS
+    assert autotune.choose_n(table, 500, target=1e-13) == 16
+    assert autotune.choose_n(table, 500, target=1e-20) == 16   # none meets it: the largest
+    assert autotune.choose_n(table, 5000) == 16           # class not calibrated: the default
+
+
+def test_best_config_and_apply():
+    ms = {(oz.GEMM_SINGLE, 960): 3.0, (oz.GEMM_PAIR, 960): 2.5, (oz.GEMM_SINGLE, 640): 2.5}
+    assert autotune.best_config(ms) == (oz.GEMM_PAIR, 960)   # fastest, first listed on a tie
+    table = {autotune.size_class(4096): {"size": 4096, "ms": ms, "best": (oz.GEMM_PAIR, 960)}}
+    h = FakeHandle()
+    assert autotune.apply_tiles(h, table, 4096)
+    assert h.options == {oz.OPT_GEMM_VARIANT: oz.GEMM_PAIR, oz.OPT_CHUNK_K: 960}
+    h2 = FakeHandle()
+    assert not autotune.apply_tiles(h2, table, 64) and h2.options == {}
+    js = autotune.tiles_to_json(table)
+    assert js[str(autotune.size_class(4096))]["best"] == {"variant": oz.GEMM_PAIR, "chunk_k": 960}
