@@ -221,8 +221,8 @@ def run_tune_tiles(args):
 
 def run_reference_batched(args):
     """--impl reference --batched: the oracle over every problem of the batched workload, full,
-    on host cores (the same problems as the GPU run; N = 15, the moduli count the autotuner gives
-    most of them)."""
+    on host cores (the GPU run's problem sizes, entries drawn on the host; N = 15, the moduli
+    count the autotuner gives most of them)."""
     import numpy as np
 
     import oracle
