@@ -56,7 +56,6 @@ struct ModTables {
     float pprime;           // P'_prop
     float pprime_fast;      // P'_fast (original fast mode)
     float delta;            // single-up(0.5 / (1 - 4u_32)), eq. (delta)
-    int words;              // 32-bit words used by the CRT accumulator
     ConvertTables conv;
     CrtTables crt;
     EpilogueTables epi;

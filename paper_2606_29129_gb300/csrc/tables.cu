@@ -81,9 +81,6 @@ void build(int N, ModTables& t) {
         t.delta = d;
     }
 
-    const int pbits = bit_length(P);
-    t.words = (pbits + 5 + 31) / 32;  // sum_l P_l w_l < N P < 2^(pbits + 5)
-
     t.conv.N = t.crt.N = t.epi.N = N;
     for (int l = 0; l < N; ++l) {
         const uint32_t p = (uint32_t)kModuli[l];
