@@ -41,6 +41,38 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def hbm_peak():
+    """Measured HBM copy bandwidth in GB/s (the fallback figure when no measurement exists)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def stage_rooflines(m, n, k, N, esz, stages_ms, hbm_gbs, scaling="proposed", beta_reads=False):
+    """Achieved GB/s of the HBM-side stages from their algorithmic bytes and the library's stage
+    times: scale reads each input element once (esz bytes); convert reads it again and writes N
+    bf16 residues (2N bytes); the reconstruction reads N residue bytes per entry and writes the
+    entry (esz bytes, plus esz more read when beta != 0).  Accurate mode's scale stage also
+    builds and multiplies A-bar and B-bar, so its bytes are not those of a stream and it is
+    left out.  frac is against the measured HBM copy bandwidth."""
+    elems = m * k + k * n
+    out = {}
+    work = {"convert": elems * (esz + 2 * N),
+            "crt": m * n * (N + esz + (esz if beta_reads else 0))}
+    if scaling != "accurate":
+        work["scale"] = elems * esz
+    for name, nbytes in work.items():
+        ms = stages_ms.get(name)
+        if not ms:
+            continue
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"algorithmic_bytes": nbytes, "ms": ms, "achieved_gbs": gbs,
+                     "frac_of_hbm": gbs / hbm_gbs}
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -331,6 +363,10 @@ def run_gpu(args, world, rank, local):
                 "kernel": "residue_gemm_kernel (tcgen05 kind::f16, bf16 residues)"}
     stages = {name: statistics.mean(s[i] for s in stage_ms)
               for i, name in enumerate(["scale", "convert", "residue_gemm", "crt"])}
+    hbm, hbm_src = hbm_peak()
+    stage_bw = stage_rooflines(m, n, k, N, A.element_size(), stages, hbm, args.scaling)
+    stage_bw["peak_gbs"] = hbm
+    stage_bw["peak_source"] = f"hbm_gbs ({hbm_src})"
 
     extra = {}
     if rank == 0:
@@ -358,6 +394,7 @@ def run_gpu(args, world, rank, local):
                        "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
                        "min": step_ms[0], "max": step_ms[-1]},
         "stages_ms": stages,
+        "stage_bandwidth": stage_bw,
         "roofline": roofline,
         "clocks": clk,
         "gpu_launches": (9 if args.scaling == "accurate" else 5) * args.steps,

@@ -39,3 +39,20 @@ def test_reference_batched():
     assert rec["mode"] == "batched" and rec["value"] > 0
     assert rec["config"]["n_per_item"] == 15
     assert rec["cpu_baseline"]["sample"] == "every problem, full"
+
+
+def test_stage_rooflines():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    m = n = k = 1024
+    N = 16
+    st = {"scale": 1.0, "convert": 2.0, "residue_gemm": 10.0, "crt": 1.0}
+    r = bench.stage_rooflines(m, n, k, N, 8, st, 1000.0)
+    elems = 2 * m * k
+    assert r["scale"]["algorithmic_bytes"] == elems * 8
+    assert r["convert"]["algorithmic_bytes"] == elems * (8 + 2 * N)
+    assert r["crt"]["algorithmic_bytes"] == m * n * (N + 8)
+    assert abs(r["scale"]["achieved_gbs"] - elems * 8 / 1e-3 / 1e9) < 1e-6
+    assert abs(r["crt"]["frac_of_hbm"] - m * n * (N + 8) / 1e-3 / 1e9 / 1000.0) < 1e-9
+    assert "scale" not in bench.stage_rooflines(m, n, k, N, 8, st, 1000.0, "accurate")
