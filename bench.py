@@ -30,9 +30,6 @@ SIZE = 16384
 PHI = 1.0
 NUM_MODULI = 16
 SGEMM_MODULI = 8
-# DRAM bytes (read + write) of one residue-GEMM launch measured with ncu for (dtype, size, N);
-# the roofline line reports it for the matching configuration only.
-MEASURED_GEMM_TRAFFIC = {("f64", 16384, 16): 105.85e9 + 4.30e9, ("f32", 16384, 8): 52.89e9 + 2.14e9}
 METRIC = "Ozaki-II DGEMM effective TFLOPS at stated error vs cuBLAS DGEMM; p50/p99 lat"
 WORKLOAD = f"square FP64 GEMM m=n=k={SIZE}, phi={PHI}, N={NUM_MODULI} moduli"
 
@@ -295,7 +292,7 @@ def run_gpu(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    m = n = k = args.size
+    m, n, k = args.shape if args.shape else (args.size,) * 3
     N = args.moduli
     f32 = args.dtype == "f32"
     seed_a = synthetic.seed_for(2, 1, 1) + 100 * rank
@@ -355,9 +352,8 @@ def run_gpu(args, world, rank, local):
     achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                 "frac": achieved / sustained if sustained else None,
-                "traffic": args.gemm_traffic if args.gemm_traffic is not None else
-                MEASURED_GEMM_TRAFFIC.get((args.dtype, m, N)) if args.scaling == "proposed"
-                else None,
+                # DRAM bytes per launch from an ncu capture of the current kernel, when given
+                "traffic": args.gemm_traffic,
                 "algorithmic_bytes": 2.0 * N * (m * k + k * n) + N * m * n,
                 "peak_source": f"bf16_tflops_sustained ({src}); kernel timed inside the step",
                 "kernel": "residue_gemm_kernel (tcgen05 kind::f16, bf16 residues)"}
@@ -368,13 +364,18 @@ def run_gpu(args, world, rank, local):
     stage_bw["peak_gbs"] = hbm
     stage_bw["peak_source"] = f"hbm_gbs ({hbm_src})"
 
+    clk = clocks.summary()
+    if clk.get("sm_mhz"):
+        # flops per second per SM clock: compares runs taken at different power-capped clocks
+        roofline["tflops_per_ghz"] = achieved / (clk["sm_mhz"] / 1e3)
     extra = {}
     if rank == 0:
         extra = accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np)
     e2e = measure_e2e(args, oz, h, A, B, m, n, k, N, torch, gemm) if rank == 0 else None
     if rank != 0:
         return
-    clk = clocks.summary()
+    square = m == n == k
+    shape = f"m=n=k={m}" if square else f"m={m}, n={n}, k={k}"
     line = {
         "metric": METRIC if not f32 else METRIC.replace("DGEMM", "SGEMM"), "value": value,
         "unit": "TFLOPS", "n_gpus": world,
@@ -383,13 +384,16 @@ def run_gpu(args, world, rank, local):
         "dtype": ("f32" if f32 else "f64") +
                  " emulated (bf16-held int8 residues on tcgen05, fp32 exact accumulate)",
         "data": "synthetic",
-        "config": {"workload": f"square {'FP32' if f32 else 'FP64'} GEMM m=n=k={m}, phi={PHI}, "
-                               f"N={N} moduli" +
+        "config": {"workload": f"{'square ' if square else ''}{'FP32' if f32 else 'FP64'} GEMM "
+                               f"{shape}, phi={PHI}, N={N} moduli" +
                    ("" if args.scaling == "proposed" else f", {args.scaling} scaling"),
                    "m": m, "n": n, "k": k, "phi": PHI,
                    "num_moduli": N, "scaling": args.scaling,
                    "parallelism": f"replicas x{world} (independent problems)",
-                   "l2": f"inputs larger than L2 (A, B, C: {3 * A.numel() * A.element_size() / 2**30:.0f} GiB)"},
+                   "l2": "A, B, C: {:.2f} GiB ({})".format(
+                       (A.numel() + B.numel() + C.numel()) * A.element_size() / 2**30,
+                       "larger than L2" if (A.numel() + B.numel() + C.numel()) *
+                       A.element_size() > 129e6 else "not larger than L2")},
         "latency_ms": {"p50": step_ms[len(step_ms) // 2],
                        "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
                        "min": step_ms[0], "max": step_ms[-1]},
@@ -417,8 +421,8 @@ def accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np):
     B_h = B.cpu().numpy()
     C_h = C.cpu().numpy()
     rng = np.random.default_rng(1)
-    I = np.sort(rng.choice(m, size=args.err_block, replace=False)).astype(np.int32)
-    J = np.sort(rng.choice(n, size=args.err_block, replace=False)).astype(np.int32)
+    I = np.sort(rng.choice(m, size=min(args.err_block, m), replace=False)).astype(np.int32)
+    J = np.sort(rng.choice(n, size=min(args.err_block, n), replace=False)).astype(np.int32)
     hi, lo = oracle.dd_block(A_h.astype(np.float64), B_h.astype(np.float64), k, I, J)
     err, zeros = oracle.max_rel_error(C_h[np.ix_(J, I)], hi, lo)
     # cuBLAS DGEMM (native FP64) on the same inputs: C^T = B^T A^T in row-major terms
@@ -441,11 +445,13 @@ def accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np):
     out["cublas_sgemm" if f32 else "cublas_dgemm"] = {
         "tflops": 2.0 * m * n * k / (cub_ms * 1e-3) / 1e12, "ms": cub_ms, "max_rel_err": cub_err}
     if not args.no_cpu_baseline:
-        tf, dt = oracle_block_tflops(A_h, B_h, m, n, k, N, args.cpu_block, args.cpu_block)
+        # a block of about the same work as cpu_block^2 x 16384 (10-30 s of CPU time)
+        side = max(32, int(args.cpu_block * math.sqrt(16384.0 / max(k, 1))))
+        rows, cols = min(side, m), min(side, n)
+        tf, dt = oracle_block_tflops(A_h, B_h, m, n, k, N, rows, cols)
         out["cpu_baseline"] = {"value": tf, "unit": "TFLOPS", "cores": oracle.num_threads(),
                                "kind": "oracle",
-                               "sample": f"{args.cpu_block}x{args.cpu_block} block of C "
-                                         f"(full k={k}), {dt:.1f} s"}
+                               "sample": f"{rows}x{cols} block of C (full k={k}), {dt:.1f} s"}
     return out
 
 
@@ -548,8 +554,10 @@ def run_batched(args):
         torch.cuda.synchronize()
         return s.elapsed_time(e) / reps
 
-    # the K chunk of the grouped residue GEMM, by timing (results identical for every chunk)
+    # the K chunk of the grouped residue GEMM, then the tile width and chunk per size class, by
+    # timing (results identical for every configuration)
     chunk_ms, chunk_best = autotune.tune_grouped_chunk(grouped, h)
+    tiles = autotune.tune_grouped_tiles(grouped, h)
     t_grouped = ev_loop(grouped, args.steps)
     status = h.status()
     # per-request loops on the same inputs
@@ -579,15 +587,26 @@ def run_batched(args):
     torch.cuda.synchronize()
     rng = np.random.default_rng(7)
     worst, worst_cub, worse_than_cublas = 0.0, 0.0, 0
-    for it in items[: args.err_items]:
+    per_item = []
+    side = args.err_side
+    for idx, it in enumerate(items[: args.err_items]):
         A_h, B_h = it["A"].cpu().numpy(), it["B"].cpu().numpy()
-        I = np.sort(rng.choice(it["m"], size=min(32, it["m"]), replace=False)).astype(np.int32)
-        J = np.sort(rng.choice(it["n"], size=min(32, it["n"]), replace=False)).astype(np.int32)
+        I = np.sort(rng.choice(it["m"], size=min(side, it["m"]), replace=False)).astype(np.int32)
+        J = np.sort(rng.choice(it["n"], size=min(side, it["n"]), replace=False)).astype(np.int32)
         hi, lo = oracle.dd_block(A_h, B_h, it["k"], I, J)
         e1 = oracle.max_rel_error(it["C"].cpu().numpy()[np.ix_(J, I)], hi, lo)[0]
         e2 = oracle.max_rel_error(it["Cd"].cpu().numpy()[np.ix_(J, I)], hi, lo)[0]
         worst, worst_cub = max(worst, e1), max(worst_cub, e2)
         worse_than_cublas += e1 > e2
+        per_item.append({"item": idx, "m": it["m"], "n": it["n"], "k": it["k"],
+                         "phi": it["phi"], "N": it["N"], "max_rel_err": e1,
+                         "cublas_max_rel_err": e2})
+    if args.items_out:
+        with open(args.items_out, "w") as fh:
+            json.dump({"sample": f"{side}x{side} random block per item (all rows/columns when "
+                                 "smaller) vs the double-double reference of the oracle",
+                       "items": per_item}, fh, indent=0)
+    errs = np.array([r["max_rel_err"] for r in per_item]) if per_item else np.zeros(1)
     line = {
         "mode": "batched", "metric": "batched Ozaki-II DGEMM effective TFLOPS (sum 2mnk / time)",
         "value": flops / (t_grouped * 1e-3) / 1e12, "unit": "TFLOPS", "n_gpus": 1,
@@ -603,22 +622,39 @@ def run_batched(args):
         "speedup_vs_per_request_ozaki2": t_loop / t_grouped,
         "accuracy": {"items_checked": min(args.err_items, len(items)),
                      "max_rel_err": worst, "cublas_max_rel_err": worst_cub,
+                     "median_item_max_rel_err": float(np.median(errs)),
                      "items_worse_than_cublas": int(worse_than_cublas),
-                     "sample": "32x32 random block per item vs double-double"},
+                     "sample": f"{side}x{side} random block per item vs double-double",
+                     "per_item_file": args.items_out},
         "calibration": {"seconds": calib_s, "table": autotune.table_to_json(table)},
         "tile_tuning": {"chunk_k_ms": {str(c): t for c, t in chunk_ms.items()},
                         "chunk_k": chunk_best,
-                        "tile": "128 x 256 (the grouped kernel's one tile shape)"},
+                        "rules_n_max_k_max_tile_n_chunk_k": tiles["rules"],
+                        "auto_ms": tiles["auto_ms"], "tuned_ms": tiles["best_ms"],
+                        "tile_histogram": tile_histogram(items, tiles["rules"]),
+                        "tiles": "128 rows x 256, 128 or 64 columns, per problem"},
         "device_status": status,
     }
     print(json.dumps(line), flush=True)
 
 
+def tile_histogram(items, rules):
+    """Problems per tile width under the given rules (the library's automatic width for n
+    otherwise: 64 for n <= 64, 128 for n <= 128, else 256)."""
+    hist = {}
+    for it in items:
+        tn = next((r[2] for r in rules if it["n"] <= r[0] and it["k"] <= r[1]),
+                  64 if it["n"] <= 64 else 128 if it["n"] <= 128 else 256)
+        hist[str(tn)] = hist.get(str(tn), 0) + 1
+    return hist
+
+
 def run_serve(args):
-    """Serving: a Poisson stream of requests (sizes log-uniform in [64, serve_max], relative-error
+    """Serving: Poisson streams of requests (sizes log-uniform in [64, serve_max], relative-error
     targets 1e-10 / 1e-13 / 1e-15 in turn, N from the calibration table) through the
-    continuous-batching server; p50/p99 latency and throughput, beside a per-request cuBLAS
-    DGEMM loop over the same stream."""
+    continuous-batching server with its residue cache, at each offered rate (0 = every request
+    at once: the server's capacity); p50/p99 latency, throughput and a makespan breakdown per
+    rate, and a per-request cuBLAS DGEMM loop over the same stream at saturation."""
     import numpy as np
     import torch
 
@@ -641,71 +677,96 @@ def run_serve(args):
     calib_s = time.perf_counter() - t0
     slot_ws = args.serve_slot_ws_gb << 30
     budget = args.serve_budget_gb << 30
-    ex = GpuExecutor(slots=args.serve_slots, slot_workspace_bytes=slot_ws)
-    srv = Server(ex, io_budget_bytes=budget - args.serve_slots * slot_ws, max_batch=64,
-                 calibration=table)
-    # arrival times of a Poisson process of rate lam over the stream
-    lam = args.serve_rate
+    cache_bytes = args.serve_cache_gb << 30
     count = args.serve_requests
-    # rate 0: every request arrives at once (the server's capacity, not the arrival rate, sets
-    # the makespan)
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=count)) if lam > 0 else np.zeros(count)
-    picks = rng.integers(0, len(pool), size=count)
-    reqs = []
-    start = time.perf_counter()
-    i = 0
-    while i < count or not srv.idle():
-        now = time.perf_counter() - start
-        while i < count and arrivals[i] <= now:
-            m, n, k, A, B = pool[picks[i]]
-            r = Request(rid=i, m=m, n=n, k=k, target=targets[i % 3], A=A, B=B,
-                        arrival=start + arrivals[i])
-            srv.submit(r)
-            reqs.append(r)
-            i += 1
-        srv.step()
-    makespan = time.perf_counter() - start
-    lat = sorted(r.latency for r in reqs if r.error is None)
-    ok = [r for r in reqs if r.error is None]
-    flops = sum(2.0 * r.m * r.n * r.k for r in ok)
-    # per-request cuBLAS DGEMM loop over the same stream (device-resident inputs, as the
-    # cuBLAS baseline is given every advantage)
-    torch.backends.cuda.matmul.allow_tf32 = False
-    dev_pool = [(A.cuda(), B.cuda()) for (_, _, _, A, B) in pool]
-    cub_ms = []
-    for (m, n, k, _, _), (dA, dB) in zip(pool, dev_pool):
-        out = torch.empty((n, m), dtype=torch.float64, device="cuda")
-        torch.matmul(dB.view(n, k), dA.view(k, m), out=out)
-        torch.cuda.synchronize()
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        s.record()
-        torch.matmul(dB.view(n, k), dA.view(k, m), out=out)
-        e.record()
-        torch.cuda.synchronize()
-        cub_ms.append(s.elapsed_time(e))
-    cub_total = sum(cub_ms[picks[r.rid]] for r in ok) / 1e3
-    line = {
-        "mode": "serving", "metric": "served emulated DGEMM p50/p99 latency and throughput",
-        "requests": len(reqs), "completed": len(ok), "rate_per_s": lam,
-        "makespan_s": makespan, "throughput_req_per_s": len(ok) / makespan,
-        "effective_tflops": flops / makespan / 1e12,
-        "latency_ms": {"p50": 1e3 * lat[len(lat) // 2],
-                       "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                       "max": 1e3 * lat[-1]},
-        "moduli_histogram": {str(N): sum(1 for r in ok if r.num_moduli == N)
-                             for N in sorted({r.num_moduli for r in ok})},
-        "peak_io_gb": srv.peak_io / 2**30, "budget_gb": args.serve_budget_gb,
-        "cublas_dgemm_loop_s": cub_total,
-        "cublas_loop_tflops": flops / cub_total / 1e12,
-        "speedup_vs_cublas_loop": cub_total / makespan,
-        "config": {"sizes": f"m, n, k log-uniform in [64, {args.serve_max}]",
-                   "targets": list(targets), "slots": args.serve_slots,
-                   "slot_workspace_gb": args.serve_slot_ws_gb, "pool": len(pool),
-                   "arrivals": "Poisson" if lam > 0 else "all at t = 0"},
-        "calibration_s": calib_s,
-    }
-    print(json.dumps(line), flush=True)
+    cub_ms = None
+    for lam in args.serve_rates:
+        rng_s = np.random.default_rng(args.serve_seed + 1)
+        arrivals = (np.cumsum(rng_s.exponential(1.0 / lam, size=count)) if lam > 0
+                    else np.zeros(count))
+        picks = rng_s.integers(0, len(pool), size=count)
+        ex = GpuExecutor(slots=args.serve_slots, slot_workspace_bytes=slot_ws,
+                         cache_bytes=cache_bytes)
+        io_budget = budget - args.serve_slots * slot_ws - cache_bytes
+        srv = Server(ex, io_budget_bytes=io_budget, max_batch=64, calibration=table,
+                     max_batch_flops=args.serve_batch_tflop * 1e12)
+        reqs = []
+        start = time.perf_counter()
+        i = 0
+        while i < count or not srv.idle():
+            now = time.perf_counter() - start
+            while i < count and arrivals[i] <= now:
+                p = int(picks[i])
+                m, n, k, A, B = pool[p]
+                r = Request(rid=i, m=m, n=n, k=k, target=targets[i % 3], A=A, B=B,
+                            a_key=("A", p), b_key=("B", p), arrival=start + arrivals[i])
+                srv.submit(r)
+                reqs.append(r)
+                i += 1
+            srv.step()
+        makespan = time.perf_counter() - start
+        bd = ex.breakdown()
+        lat = sorted(r.latency for r in reqs if r.error is None)
+        ok = [r for r in reqs if r.error is None]
+        flops = sum(2.0 * r.m * r.n * r.k for r in ok)
+        line = {
+            "mode": "serving", "metric": "served emulated DGEMM p50/p99 latency and throughput",
+            "requests": len(reqs), "completed": len(ok), "rate_per_s": lam,
+            "makespan_s": makespan, "throughput_req_per_s": len(ok) / makespan,
+            "effective_tflops": flops / makespan / 1e12,
+            "latency_ms": {"p50": 1e3 * lat[len(lat) // 2],
+                           "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": 1e3 * lat[-1]},
+            "moduli_histogram": {str(N): sum(1 for r in ok if r.num_moduli == N)
+                                 for N in sorted({r.num_moduli for r in ok})},
+            "peak_upload_gb": srv.peak_io / 2**30, "budget_gb": args.serve_budget_gb,
+            "breakdown": {
+                "host_scheduling_s": srv.step_seconds,
+                "link_upload_gb": bd["upload_bytes"] / 1e9,
+                "link_result_gb": bd["result_bytes"] / 1e9,
+                "encode_device_s": bd["encode_ms"] / 1e3,
+                "batch_device_s": bd["batch_ms"] / 1e3,
+                "batches": bd["batches"],
+                "encoded_operands": bd["encoded_operands"],
+                "cache_hits": bd.get("cache_hits"), "cache_misses": bd.get("cache_misses"),
+                "cache_evictions": bd.get("cache_evictions"),
+                "cache_peak_gb": bd.get("cache_peak_gb"),
+                "note": "batch_device_s sums the slots' grouped calls (GEMM + CRT writing C to "
+                        "host memory), which overlap on the device; host_scheduling_s is the "
+                        "time spent inside Server.step"},
+            "config": {"sizes": f"m, n, k log-uniform in [64, {args.serve_max}]",
+                       "targets": list(targets), "slots": args.serve_slots,
+                       "slot_workspace_gb": args.serve_slot_ws_gb,
+                       "residue_cache_gb": args.serve_cache_gb, "pool": len(pool),
+                       "batch_work_cap_tflop": args.serve_batch_tflop,
+                       "arrivals": "Poisson" if lam > 0 else "all at t = 0"},
+            "calibration_s": calib_s,
+        }
+        if lam == 0:
+            # a per-request cuBLAS DGEMM loop over the same stream (device-resident inputs)
+            if cub_ms is None:
+                torch.backends.cuda.matmul.allow_tf32 = False
+                cub_ms = []
+                for (m, n, k, A, B) in pool:
+                    dA, dB = A.cuda(), B.cuda()
+                    out = torch.empty((n, m), dtype=torch.float64, device="cuda")
+                    torch.matmul(dB.view(n, k), dA.view(k, m), out=out)
+                    torch.cuda.synchronize()
+                    s_ev = torch.cuda.Event(enable_timing=True)
+                    e_ev = torch.cuda.Event(enable_timing=True)
+                    s_ev.record()
+                    torch.matmul(dB.view(n, k), dA.view(k, m), out=out)
+                    e_ev.record()
+                    torch.cuda.synchronize()
+                    cub_ms.append(s_ev.elapsed_time(e_ev))
+                    del dA, dB, out
+            cub_total = sum(cub_ms[int(picks[r.rid])] for r in ok) / 1e3
+            line["cublas_dgemm_loop_s"] = cub_total
+            line["cublas_loop_tflops"] = flops / cub_total / 1e12
+            line["speedup_vs_cublas_loop"] = cub_total / makespan
+        print(json.dumps(line), flush=True)
+        del ex, srv
+        torch.cuda.empty_cache()
 
 
 def run_sweep(args):
@@ -885,6 +946,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=SIZE)
+    ap.add_argument("--shape", type=int, nargs=3, default=None, metavar=("M", "N", "K"),
+                    help="a rectangular problem (the configurations m=n=16384, k=1024; "
+                         "m=n=1024, k=65536; m=65536, n=256, k=4096) instead of --size")
     ap.add_argument("--moduli", type=int, default=None,
                     help=f"moduli count (default {NUM_MODULI} for f64, {SGEMM_MODULI} for f32)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"],
@@ -901,11 +965,18 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="the batched workload (grouped call) instead of the benchmark")
     ap.add_argument("--batch", type=int, default=512)
-    ap.add_argument("--err-items", type=int, default=64)
+    ap.add_argument("--err-items", type=int, default=512)
+    ap.add_argument("--err-side", type=int, default=48,
+                    help="batched mode: rows and columns of each item's error block")
+    ap.add_argument("--items-out", default=None,
+                    help="batched mode: write every item's size, N and errors to this JSON file")
     ap.add_argument("--serve", action="store_true",
                     help="the serving workload (Poisson stream) instead of the benchmark")
-    ap.add_argument("--serve-rate", type=float, default=200.0,
-                    help="Poisson arrival rate per second; 0 = all requests at once")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.0, 100.0, 400.0],
+                    help="offered loads in requests per second (0: every request at once)")
+    ap.add_argument("--serve-cache-gb", type=int, default=60)
+    ap.add_argument("--serve-batch-tflop", type=float, default=2.0,
+                    help="work cap of one serving batch, in units of 10^12 flops (sum 2mnk)")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-max", type=int, default=8192)
     ap.add_argument("--serve-pool", type=int, default=64)

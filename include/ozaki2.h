@@ -74,6 +74,14 @@ extern "C" {
                                      the option is turned off, or the workspace is reallocated. */
 #define OZAKI2_OPT_SCALING 4      /* scaling step: OZAKI2_SCALING_PROPOSED (default) or
                                      OZAKI2_SCALING_FAST */
+#define OZAKI2_OPT_WAIT_LIMIT_NS 5 /* bound, in nanoseconds, of every wait inside the residue-GEMM
+                                     kernels (default 2000000000 = 2 s; any value >= 0).  A wait
+                                     that runs out raises OZAKI2_STATUS_TIMEOUT: the kernel stops,
+                                     lets its copies and tensor-core work finish, frees its
+                                     tensor memory and returns, and the call's outputs are
+                                     undefined.  A bound shorter than the kernel needs makes every
+                                     call time out; tests use it to exercise that path.  Graphs
+                                     of grouped calls are keyed on it. */
 #define OZAKI2_SCALING_PROPOSED 0 /* Algorithm 2 (Section 4): scale-invariant, CRT bound by
                                      construction */
 #define OZAKI2_SCALING_FAST 1     /* Algorithm 1 (Section 2.3): the original fast mode, kept for
@@ -193,6 +201,20 @@ typedef struct ozaki2_problem {
     int num_moduli;
 } ozaki2_problem;
 
+/* Residue-GEMM tile configuration of grouped calls, by size class.  Rule i (i < count) matches
+ * a problem with n <= n_max[i] and k <= k_max[i]; the first matching rule gives that problem's
+ * tile width tile_n[i] (256, 128 or 64 columns of C per tile; the tiles are 128 rows high) and
+ * K chunk chunk_k[i] (products accumulated between modular reductions: a multiple of 64 in
+ * [64, 960], or 0 for the handle's OZAKI2_OPT_CHUNK_K).  A problem that no rule matches gets an
+ * automatic width (64 for n <= 64, 128 for n <= 128, else 256) and the handle's chunk.  count = 0
+ * clears the rules.  Results never depend on the configuration, only the time does.  Setting
+ * rules drops the handle's captured graphs of grouped calls.  Arrays are host memory of count
+ * ints, read during the call.  Errors: -2 count < 0 or > OZAKI2_MAX_TILE_RULES, -3/-4/-5/-6 an
+ * array is NULL (count > 0), -5 a tile width not in {64, 128, 256}, -6 an invalid chunk. */
+#define OZAKI2_MAX_TILE_RULES 16
+int ozaki2_set_grouped_tiles(ozaki2_handle_t handle, int count, const int* n_max,
+                             const int* k_max, const int* tile_n, const int* chunk_k);
+
 /* Workspace bytes ozaki2_dgemm_grouped needs for these problems (0 if one is invalid). */
 size_t ozaki2_grouped_workspace_size(int count, const ozaki2_problem* problems);
 
@@ -207,6 +229,61 @@ size_t ozaki2_grouped_workspace_size(int count, const ozaki2_problem* problems);
  * NULL; -(100 (i+1) + a) when argument a (numbered as for ozaki2_dgemm) of problem i is
  * invalid. */
 int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem* problems);
+
+/* ---- device-resident encoded operands ------------------------------------------------------ */
+/* An operand of the emulated product kept in device memory after Step 2: the shifts of its
+ * lines and its bf16 residue planes.  Under the proposed scaling (Section 4, eq. (proposed-mu),
+ * (proposed-nu)) and the original fast mode, the shift of a row of op(A) depends on that row
+ * only, and the shift of a column of op(B) on that column only, so the encoding of an operand
+ * is a function of the operand and N alone and can be reused by every product it takes part in
+ * (a server's residue cache).  Accurate mode's shifts depend on both operands: it has no
+ * encoded operands (OZAKI2_ERROR_MODE).
+ *
+ * side 'A' encodes the rows of op(A) (lines = m), side 'B' the columns of op(B) (lines = n),
+ * each of length k; trans, X and ld are as transA, A, lda (or transB, B, ldb) of ozaki2_dgemm
+ * (device memory, or host memory the device can address, read in place).  `data` is a
+ * caller-owned device buffer of ozaki2_operand_bytes(side, lines, k, num_moduli) bytes, 256-byte
+ * aligned; ozaki2_encode_operands writes it and sets `scaling` to the handle's scaling mode. */
+typedef struct ozaki2_operand {
+    char side, trans;
+    int lines, k;
+    const double* X;
+    int ld;
+    int num_moduli;
+    void* data;
+    int scaling;
+} ozaki2_operand;
+
+/* Bytes of the encoding of one operand (0 for invalid arguments). */
+size_t ozaki2_operand_bytes(char side, int lines, int k, int num_moduli);
+
+/* Encodes `count` operands (Step 2: Algorithm 2 shifts, or Algorithm 1 in the original fast
+ * mode, and the residue planes) in one grouped scaling launch and one grouped conversion launch
+ * per distinct moduli count, asynchronously on the handle's stream.  `ops` is a host array; its
+ * `scaling` fields are written during the call.  Errors: -2 count < 0, -3 ops NULL;
+ * -(100 (i+1) + a) for operand i with a = 1 side, 2 trans, 3 lines, 4 k, 5 X, 6 ld,
+ * 7 num_moduli, 8 data (NULL or not 256-byte aligned, or not device memory);
+ * OZAKI2_ERROR_MODE in accurate mode. */
+int ozaki2_encode_operands(ozaki2_handle_t handle, int count, ozaki2_operand* ops);
+
+/* ozaki2_dgemm_grouped with encoded operands: for problem i, enc_a[i] (when enc_a and enc_a[i]
+ * are not NULL) replaces transA, A and lda, and enc_b[i] replaces transB, B and ldb; those sides
+ * skip the scaling and the conversion, and the problem runs the residue GEMMs and the
+ * reconstruction on the encoded planes.  The result is bit-identical to ozaki2_dgemm on the
+ * operands that were encoded.  An encoded operand must match its problem (side 'A' with
+ * lines = m, side 'B' with lines = n, the same k and num_moduli) and the handle's scaling mode,
+ * else -(100 (i+1) + 7) (A) or -(100 (i+1) + 9) (B).  Its data must stay alive and unchanged
+ * until the call's work has run.  OZAKI2_ERROR_MODE in accurate mode. */
+int ozaki2_dgemm_grouped_encoded(ozaki2_handle_t handle, int count,
+                                 const ozaki2_problem* problems,
+                                 const ozaki2_operand* const* enc_a,
+                                 const ozaki2_operand* const* enc_b);
+
+/* Workspace bytes ozaki2_dgemm_grouped_encoded needs (the planes of encoded sides are not part
+ * of it); 0 if a problem is invalid. */
+size_t ozaki2_grouped_encoded_workspace_size(int count, const ozaki2_problem* problems,
+                                             const ozaki2_operand* const* enc_a,
+                                             const ozaki2_operand* const* enc_b);
 
 /* ---- the stages, one entry point each ------------------------------------------------------ */
 /* Step 2 scaling (Algorithm 2, eq. (proposed-mu)): shifts[i] = log2(mu_i) for the m rows of
@@ -294,7 +371,10 @@ int ozaki2_crt(ozaki2_handle_t handle, int num_moduli, int m, int n, const int8_
  * Its intermediates (shifts, residue planes, product residues, a status word) live in one
  * file-scope device array of OZAKI2_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the
  * library holds until the process exits.  The caller passes the inputs and the output as for
- * ozaki2_dgemm, plus the cudaStream_t (as void*) to queue on.
+ * ozaki2_dgemm, plus the cudaStream_t (as void*) to queue on.  A, B and C must be memory the
+ * device can address (device memory, page-locked host memory, or any host memory on a device
+ * with pageable-memory access; otherwise -7, -9 or -12).  Host-resident operands are read, and
+ * a host-resident C written, in place over the CPU-GPU link: nothing is staged.
  *
  * Limit: the problem must fit the array, i.e. the workspace of ozaki2_dgemm plus 256 bytes
  * (ozaki2_workspace_size(m, n, k, N) + 256) must not exceed OZAKI2_NOALLOC_SCRATCH_BYTES;
@@ -306,7 +386,10 @@ int ozaki2_crt(ozaki2_handle_t handle, int num_moduli, int m, int n, const int8_
  * Sharing: every call uses the same array and it keeps the last call's contents, so calls that
  * overlap on the GPU (other streams, other threads) race and must be serialised by the caller.
  * The status word is cleared at the start of each call; device-side status flags are not
- * reported by this entry point (non-finite lines still produce NaN outputs).
+ * reported by this entry point.  Failures show in C instead: non-finite lines produce NaN
+ * outputs, and if a bounded wait inside the residue GEMM expires (OZAKI2_STATUS_TIMEOUT) every
+ * entry of C is set to NaN.  k = 0 or alpha = 0 computes C = beta C for any size (no scratch is
+ * used).
  * Argument numbers for errors: as ozaki2_dgemm, stream 15. */
 int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int k, double alpha,
                          const double* A, int lda, const double* B, int ldb, double beta,

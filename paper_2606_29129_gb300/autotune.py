@@ -9,7 +9,7 @@ candidate N, and that of cuBLAS DGEMM on the same inputs.  The reference is the 
 N = 20, whose error is at the level of one rounding of the result (~1e-16), far below the
 errors being compared.  `choose_n` then picks the smallest N that is not worse than cuBLAS
 (equal accuracy) or that meets a stated relative-error target.  `tune_tiles` and
-`tune_grouped_chunk` time the residue-GEMM configurations (see below).
+`tune_grouped_chunk` / `tune_grouped_tiles` time the residue-GEMM configurations (see below).
 """
 from __future__ import annotations
 
@@ -170,6 +170,68 @@ def apply_tiles(handle, table, k: int) -> bool:
     handle.set_option(oz.OPT_GEMM_VARIANT, variant)
     handle.set_option(oz.OPT_CHUNK_K, chunk)
     return True
+
+
+# Size classes of grouped calls for the residue-GEMM tile configuration, by the number of columns
+# n of op(B) (the tile width is the number of columns of C one tile covers: 256, 128 or 64).
+GROUPED_N_EDGES = (64, 128, 256, 512, 1 << 30)
+TILE_WIDTHS = oz.TILE_WIDTHS
+_ANY_K = 1 << 30
+
+
+def grouped_rules(config):
+    """ozaki2_set_grouped_tiles rules from {n_edge: (tile_n, chunk_k)} (classes by n)."""
+    return [(edge, _ANY_K, tn, ck) for edge, (tn, ck) in sorted(config.items())]
+
+
+def tune_grouped_tiles(call, handle, n_edges=GROUPED_N_EDGES, widths=TILE_WIDTHS,
+                       chunks=CHUNKS, reps=3, rounds=1):
+    """Tile width and K chunk per size class (classes by n, the edges `n_edges`) for a grouped
+    call: `call()` issues the grouped call on `handle`.  Coordinate descent from the automatic
+    configuration: for each class in turn, each tile width, then each chunk, is timed with the
+    other classes at their current best; a change is kept only when it is faster.  Leaves the
+    best rules set on the handle and returns a dict with the rules, the start and best times
+    and every timing.  Results are bit-identical for every configuration."""
+    handle.set_grouped_tiles([])
+    base = _time_ms(call, reps)
+    # start: every class at its automatic width (as the library picks it) and the handle's chunk
+    config = {e: (_auto_width(e), 0) for e in n_edges}
+    handle.set_grouped_tiles(grouped_rules(config))
+    best = _time_ms(call, reps)
+    trials = {"auto": base, "start": best}
+    for _ in range(rounds):
+        for e in n_edges:
+            for tn in widths:
+                if tn == config[e][0]:
+                    continue
+                trial = dict(config)
+                trial[e] = (tn, config[e][1])
+                handle.set_grouped_tiles(grouped_rules(trial))
+                t = _time_ms(call, reps)
+                trials[f"n<={e}:tile={tn},chunk={config[e][1]}"] = t
+                if t < best:
+                    best, config = t, trial
+            for ck in chunks:
+                if ck == config[e][1]:
+                    continue
+                trial = dict(config)
+                trial[e] = (config[e][0], ck)
+                handle.set_grouped_tiles(grouped_rules(trial))
+                t = _time_ms(call, reps)
+                trials[f"n<={e}:tile={config[e][0]},chunk={ck}"] = t
+                if t < best:
+                    best, config = t, trial
+    if base <= best:  # the automatic choice was not beaten
+        handle.set_grouped_tiles([])
+        return {"rules": [], "auto_ms": base, "best_ms": base, "trials": trials}
+    handle.set_grouped_tiles(grouped_rules(config))
+    return {"rules": grouped_rules(config), "auto_ms": base, "best_ms": best, "trials": trials}
+
+
+def _auto_width(n_edge: int) -> int:
+    """The library's automatic width for the widest problem of a class (64 for n <= 64, 128 for
+    n <= 128, else 256)."""
+    return 64 if n_edge <= 64 else 128 if n_edge <= 128 else 256
 
 
 def tune_grouped_chunk(call, handle, chunks=CHUNKS, reps=3):

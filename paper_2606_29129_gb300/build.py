@@ -41,7 +41,8 @@ def _flags(verbose: bool):
 
 def _inputs_mtime() -> float:
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "ozaki2_internal.h"), os.path.join(INCLUDE, "ozaki2.h"),
+    files += [os.path.join(CSRC, "ozaki2_internal.h"), os.path.join(CSRC, "sm103_ptx.cuh"),
+              os.path.join(INCLUDE, "ozaki2.h"),
               os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files)
 

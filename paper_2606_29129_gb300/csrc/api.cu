@@ -20,6 +20,8 @@ struct ozaki2_context {
     int chunk_k = 960;             // products accumulated between modular reductions
     int gemm_variant = OZAKI2_GEMM_AUTO;
     int scaling = OZAKI2_SCALING_PROPOSED;  // Algorithm 2, or Algorithm 1 (original fast mode)
+    unsigned long long wait_limit_ns = ozaki2::kDefaultWaitLimitNs;  // residue-GEMM wait bound
+    ozaki2::TileRules tiles;       // grouped calls: tile width and K chunk by size class
     bool timing = false;           // record stage events in ozaki2_dgemm
     bool timed_call = false;       // a timed call has been queued
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -31,6 +33,7 @@ struct ozaki2_context {
         std::vector<ozaki2_problem> probs;
         int chunk_k;
         int scaling;
+        unsigned long long wait_limit_ns;
         void* tables = nullptr;    // device copy of the call's tables
         cudaGraphExec_t exec = nullptr;
     };
@@ -209,7 +212,7 @@ int accurate_shifts(ozaki2_context* ctx, const void* A, int64_t als, int64_t aes
                                          ctx->d_status, st, f32))))
         return rc;
     if ((rc = launch_aux_gemm((int)L.m_pad, (int)L.n_pad, (int)L.k_pad, L.geo, pa, pb, cmax,
-                              ctx->d_status, ctx->num_sms, st)))
+                              ctx->d_status, ctx->num_sms, st, ctx->wait_limit_ns)))
         return rc;
     return cuda_rc(launch_accu_shift(e, m, f, n, cmax, (int)L.m_pad, T.pprime, T.delta, st));
 }
@@ -325,7 +328,7 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     mark(2);
     if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, L.geo, pa, pb, res,
                                   T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
-                                  ctx->gemm_variant, st)))
+                                  ctx->gemm_variant, st, ctx->wait_limit_ns)))
         return rc;
     mark(3);
     rc = cuda_rc(launch_crt(res, L.n_pad, L.m_pad * L.n_pad, m, n, e, f, alpha, beta, C, ldc, *T,
@@ -401,6 +404,10 @@ int ozaki2_set_option(ozaki2_handle_t handle, int option, int value) {
                 value != OZAKI2_SCALING_ACCURATE)
                 return -3;
             ctx->scaling = value;
+            return OZAKI2_SUCCESS;
+        case OZAKI2_OPT_WAIT_LIMIT_NS:
+            if (value < 0) return -3;
+            ctx->wait_limit_ns = (unsigned long long)value;
             return OZAKI2_SUCCESS;
         default:
             return -2;
@@ -545,36 +552,41 @@ size_t ozaki2_grouped_workspace_size(int count, const ozaki2_problem* problems) 
     return grouped_workspace_bytes(count, problems);
 }
 
-int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem* problems) {
+static int grouped_impl(ozaki2_handle_t handle, int count, const ozaki2_problem* problems,
+                        const Encoded& enc) {
     if (count < 0) return -2;
     if (count > 0 && !problems) return -3;
     int rc = grouped_check(count, problems);
     if (rc) return rc;
     if (count == 0) return OZAKI2_SUCCESS;
+    const bool encoded = enc.a || enc.b;
     ozaki2_context* ctx;
     if ((rc = resolve(handle, &ctx))) return rc;
-    if ((rc = ensure_workspace(ctx, grouped_workspace_bytes(count, problems)))) return rc;
+    if (encoded && ctx->scaling == OZAKI2_SCALING_ACCURATE) return OZAKI2_ERROR_MODE;
+    if ((rc = ensure_workspace(ctx, grouped_workspace_bytes(count, problems, enc)))) return rc;
     if (!ctx->staged &&
         cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess)
         return OZAKI2_ERROR_CUDA;
     for (int i = 0; ctx->scaling == OZAKI2_SCALING_ACCURATE && i < count; ++i)
         if (problems[i].k > OZAKI2_ACCURATE_MAX_K) return OZAKI2_ERROR_TOO_LARGE;
-    const size_t tb = (size_t)grouped_table_bytes(count, problems, ctx->scaling);
+    const size_t tb =
+        (size_t)grouped_table_bytes(count, problems, ctx->tiles, ctx->chunk_k, ctx->scaling, enc);
     char* ws = static_cast<char*>(ctx->ws);
     auto operands_ok = [&]() {
         for (int i = 0; i < count; ++i) {
             const ozaki2_problem& p = problems[i];
             if (p.m <= 0 || p.n <= 0 || p.k <= 0 || p.alpha == 0.0) continue;
-            if (!addressable(ctx, p.A)) return -(100 * (i + 1) + 7);
-            if (!addressable(ctx, p.B)) return -(100 * (i + 1) + 9);
+            const bool has_a = enc.a && enc.a[i], has_b = enc.b && enc.b[i];
+            if (!has_a && !addressable(ctx, p.A)) return -(100 * (i + 1) + 7);
+            if (!has_b && !addressable(ctx, p.B)) return -(100 * (i + 1) + 9);
             if (!addressable(ctx, p.C)) return -(100 * (i + 1) + 12);
         }
         return 0;
     };
-    if (ctx->use_graphs) {
+    if (ctx->use_graphs && !encoded) {
         for (auto& g : ctx->graphs)
             if (g.chunk_k == ctx->chunk_k && g.scaling == ctx->scaling &&
-                same_problems(g.probs, count, problems))
+                g.wait_limit_ns == ctx->wait_limit_ns && same_problems(g.probs, count, problems))
                 return cudaGraphLaunch(g.exec, ctx->stream) == cudaSuccess ? OZAKI2_SUCCESS
                                                                             : OZAKI2_ERROR_CUDA;
         // First call with these problems: check the operands, upload the tables to a buffer of
@@ -584,9 +596,10 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
         g.probs.assign(problems, problems + count);
         g.chunk_k = ctx->chunk_k;
         g.scaling = ctx->scaling;
+        g.wait_limit_ns = ctx->wait_limit_ns;
         std::vector<char> host(tb ? tb : 1);
-        if ((rc = build_grouped_tables(count, problems, ws, host.data(), ctx->chunk_k,
-                                       ctx->scaling)))
+        if ((rc = build_grouped_tables(count, problems, ws, host.data(), ctx->tiles,
+                                       ctx->chunk_k, ctx->scaling)))
             return rc;
         if (cudaMalloc(&g.tables, tb ? tb : 1) != cudaSuccess) {
             cudaGetLastError();
@@ -608,7 +621,8 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
             return OZAKI2_ERROR_CUDA;
         }
         rc = launch_grouped(count, problems, static_cast<const char*>(g.tables), ctx->d_status,
-                            ctx->num_sms, ctx->chunk_k, ctx->capture_stream, ctx->scaling);
+                            ctx->num_sms, ctx->tiles, ctx->chunk_k, ctx->capture_stream,
+                            ctx->scaling, ctx->wait_limit_ns);
         const cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (rc || ce != cudaSuccess ||
             cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
@@ -637,15 +651,160 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
     }
     // the staging buffer may still be read by the previous call's copy
     if (cudaEventSynchronize(ctx->staged) != cudaSuccess) return OZAKI2_ERROR_CUDA;
-    if ((rc = build_grouped_tables(count, problems, ws, ctx->stage, ctx->chunk_k, ctx->scaling)))
+    if ((rc = build_grouped_tables(count, problems, ws, ctx->stage, ctx->tiles, ctx->chunk_k,
+                                   ctx->scaling, enc)))
         return rc;
-    char* tables_dev = grouped_tables_in_workspace(count, problems, ws);
+    char* tables_dev = grouped_tables_in_workspace(count, problems, ws, enc);
     if (tb && (cudaMemcpyAsync(tables_dev, ctx->stage, tb, cudaMemcpyHostToDevice,
                                ctx->stream) != cudaSuccess ||
                cudaEventRecord(ctx->staged, ctx->stream) != cudaSuccess))
         return OZAKI2_ERROR_CUDA;
-    return launch_grouped(count, problems, tables_dev, ctx->d_status, ctx->num_sms,
-                          ctx->chunk_k, ctx->stream, ctx->scaling);
+    return launch_grouped(count, problems, tables_dev, ctx->d_status, ctx->num_sms, ctx->tiles,
+                          ctx->chunk_k, ctx->stream, ctx->scaling, ctx->wait_limit_ns, enc);
+}
+
+int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem* problems) {
+    return grouped_impl(handle, count, problems, Encoded());
+}
+
+// 0 if every encoded operand matches its problem, else the negative error of the first that
+// does not (argument 7 for op(A), 9 for op(B) of problem i).
+static int check_encoded(int count, const ozaki2_problem* problems,
+                         const ozaki2_operand* const* enc_a, const ozaki2_operand* const* enc_b,
+                         int scaling) {
+    auto bad = [&](const ozaki2_operand* o, bool side_b, const ozaki2_problem& p) {
+        const bool sb = o->side == 'B' || o->side == 'b';
+        const bool sa = o->side == 'A' || o->side == 'a';
+        return (side_b ? !sb : !sa) || o->lines != (side_b ? p.n : p.m) || o->k != p.k ||
+               o->num_moduli != p.num_moduli || o->scaling != scaling || !o->data ||
+               (reinterpret_cast<uintptr_t>(o->data) & 255u);
+    };
+    for (int i = 0; i < count; ++i) {
+        if (enc_a && enc_a[i] && bad(enc_a[i], false, problems[i])) return -(100 * (i + 1) + 7);
+        if (enc_b && enc_b[i] && bad(enc_b[i], true, problems[i])) return -(100 * (i + 1) + 9);
+    }
+    return OZAKI2_SUCCESS;
+}
+
+int ozaki2_dgemm_grouped_encoded(ozaki2_handle_t handle, int count,
+                                 const ozaki2_problem* problems,
+                                 const ozaki2_operand* const* enc_a,
+                                 const ozaki2_operand* const* enc_b) {
+    if (count < 0) return -2;
+    if (count > 0 && !problems) return -3;
+    int rc = grouped_check(count, problems);
+    if (rc) return rc;
+    ozaki2_context* ctx;
+    if ((rc = resolve(handle, &ctx))) return rc;
+    if (ctx->scaling == OZAKI2_SCALING_ACCURATE && (enc_a || enc_b)) return OZAKI2_ERROR_MODE;
+    if ((rc = check_encoded(count, problems, enc_a, enc_b, ctx->scaling))) return rc;
+    Encoded enc;
+    enc.a = enc_a;
+    enc.b = enc_b;
+    return grouped_impl(handle, count, problems, enc);
+}
+
+size_t ozaki2_grouped_encoded_workspace_size(int count, const ozaki2_problem* problems,
+                                             const ozaki2_operand* const* enc_a,
+                                             const ozaki2_operand* const* enc_b) {
+    if (count < 0 || (count > 0 && !problems)) return 0;
+    if (grouped_check(count, problems)) return 0;
+    Encoded enc;
+    enc.a = enc_a;
+    enc.b = enc_b;
+    return grouped_workspace_bytes(count, problems, enc);
+}
+
+size_t ozaki2_operand_bytes(char side, int lines, int k, int num_moduli) {
+    const bool a = side == 'A' || side == 'a', b = side == 'B' || side == 'b';
+    if ((!a && !b) || lines < 0 || k < 0 || !mod_tables(num_moduli)) return 0;
+    return (size_t)operand_layout(b, lines, k, num_moduli).bytes;
+}
+
+int ozaki2_encode_operands(ozaki2_handle_t handle, int count, ozaki2_operand* ops) {
+    if (count < 0) return -2;
+    if (count > 0 && !ops) return -3;
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    if (ctx->scaling == OZAKI2_SCALING_ACCURATE) return OZAKI2_ERROR_MODE;
+    for (int i = 0; i < count; ++i) {
+        ozaki2_operand& o = ops[i];
+        const int e = -(100 * (i + 1));
+        const bool sa = o.side == 'A' || o.side == 'a', sb = o.side == 'B' || o.side == 'b';
+        if (!sa && !sb) return e - 1;
+        if (!is_trans_char(o.trans)) return e - 2;
+        if (o.lines < 0) return e - 3;
+        if (o.k < 0) return e - 4;
+        // rows of the stored matrix: op(A) m x k is A (m x k) or A^T; op(B) k x n likewise
+        const bool nt = is_notrans(o.trans);
+        const int stored_rows = sa ? (nt ? o.lines : o.k) : (nt ? o.k : o.lines);
+        if (o.lines > 0 && o.k > 0 && !o.X) return e - 5;
+        if (o.ld < (stored_rows > 1 ? stored_rows : 1)) return e - 6;
+        if (!mod_tables(o.num_moduli)) return e - 7;
+        if (!o.data || (reinterpret_cast<uintptr_t>(o.data) & 255u)) return e - 8;
+        if (o.lines > 0 && o.k > 0 && !addressable(ctx, o.X)) return e - 5;
+        if (host_resident(o.data)) return e - 8;
+        o.scaling = ctx->scaling;
+    }
+    if (count == 0) return OZAKI2_SUCCESS;
+    // lines of length 0: zero shifts, zero planes (no kernel touches them otherwise)
+    for (int i = 0; i < count; ++i) {
+        const ozaki2_operand& o = ops[i];
+        if (o.lines > 0 && o.k == 0) {
+            const OperandLayout L = operand_layout(o.side == 'B' || o.side == 'b', o.lines, 0,
+                                                   o.num_moduli);
+            if (cudaMemsetAsync(o.data, 0, (size_t)L.bytes, ctx->stream) != cudaSuccess)
+                return OZAKI2_ERROR_CUDA;
+        }
+    }
+    const size_t tb = (size_t)encode_table_bytes(count, ops);
+    if ((rc = ensure_workspace(ctx, tb))) return rc;
+    if (!ctx->staged &&
+        cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    if (cudaEventSynchronize(ctx->staged) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if (ctx->stage_bytes < tb) {
+        if (ctx->stage) cudaFreeHost(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        if (cudaMallocHost(&ctx->stage, tb) != cudaSuccess) {
+            cudaGetLastError();
+            return OZAKI2_ERROR_ALLOC;
+        }
+        ctx->stage_bytes = tb;
+    }
+    build_encode_tables(count, ops, ctx->scaling, ctx->stage);
+    char* tables_dev = static_cast<char*>(ctx->ws);
+    if (cudaMemcpyAsync(tables_dev, ctx->stage, tb, cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess ||
+        cudaEventRecord(ctx->staged, ctx->stream) != cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    return launch_encode(count, ops, tables_dev, ctx->d_status, ctx->stream);
+}
+
+
+int ozaki2_set_grouped_tiles(ozaki2_handle_t handle, int count, const int* n_max,
+                             const int* k_max, const int* tile_n, const int* chunk_k) {
+    if (count < 0 || count > OZAKI2_MAX_TILE_RULES) return -2;
+    if (count > 0 && !n_max) return -3;
+    if (count > 0 && !k_max) return -4;
+    if (count > 0 && !tile_n) return -5;
+    if (count > 0 && !chunk_k) return -6;
+    TileRules r;
+    r.count = count;
+    for (int i = 0; i < count; ++i) {
+        const int tn = tile_n[i], ck = chunk_k[i];
+        if (tn != 64 && tn != 128 && tn != 256) return -5;
+        if (ck != 0 && (ck < 64 || ck > 960 || ck % 64)) return -6;
+        r.r[i] = TileRule{n_max[i], k_max[i], tn, ck};
+    }
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    clear_graphs(ctx);
+    ctx->tiles = r;
+    return OZAKI2_SUCCESS;
 }
 
 int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
@@ -808,7 +967,7 @@ int ozaki2_residue_gemm(ozaki2_handle_t handle, int num_moduli, int m_pad, int n
     const PlaneGeom geo{m_pad, n_pad, k_pad, m_pad, n_pad};
     return launch_residue_gemm(num_moduli, m_pad, n_pad, k_pad, geo, planes_a, planes_b, residues,
                                T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
-                               ctx->gemm_variant, ctx->stream);
+                               ctx->gemm_variant, ctx->stream, ctx->wait_limit_ns);
 }
 
 int ozaki2_crt(ozaki2_handle_t handle, int num_moduli, int m, int n, const int8_t* residues,

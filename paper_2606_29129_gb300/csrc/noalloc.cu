@@ -23,10 +23,11 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[OZAKI2_NOALLOC_
 constexpr int kMaxDevices = 64;
 void* g_scratch_dev[kMaxDevices];   // device address of g_noalloc_scratch, per device
 int g_scratch_sms[kMaxDevices];
+bool g_pageable[kMaxDevices];       // the device can address ordinary (pageable) host memory
 std::mutex g_scratch_mu;
 
 // Device address of the scratch array for the current device; sets it up on first use.
-int scratch_for_current_device(unsigned char** ptr, int* num_sms) {
+int scratch_for_current_device(unsigned char** ptr, int* num_sms, bool* pageable) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return OZAKI2_ERROR_NO_DEVICE;
@@ -45,12 +46,45 @@ int scratch_for_current_device(unsigned char** ptr, int* num_sms) {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return OZAKI2_ERROR_CUDA;
+        int pg = 0;
+        if (cudaDeviceGetAttribute(&pg, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+            cudaGetLastError();
+            pg = 0;
+        }
+        g_pageable[dev] = pg != 0;
         g_scratch_sms[dev] = sms;
         g_scratch_dev[dev] = p;
     }
     *ptr = static_cast<unsigned char*>(g_scratch_dev[dev]);
     *num_sms = g_scratch_sms[dev];
+    *pageable = g_pageable[dev];
     return OZAKI2_SUCCESS;
+}
+
+// True if the device can address p: device or managed memory, page-locked host memory, or any
+// host memory on a device with pageable-memory access.  Looks only at the pointer's attributes
+// (no allocation).
+bool addressable(const void* p, bool pageable) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return pageable;
+    }
+    return a.type != cudaMemoryTypeUnregistered || pageable;
+}
+
+// After the reconstruction: if a bounded wait in the residue GEMM expired during this call (the
+// status word is cleared at the start of each call), C holds no valid result, and every entry
+// is set to NaN so that the caller, who gets no status from this entry point, can see it.
+__global__ void nan_on_timeout_kernel(const unsigned* __restrict__ status, double* C, int m,
+                                      int n, int64_t ldc) {
+    if (!(__ldg(status) & OZAKI2_STATUS_TIMEOUT)) return;
+    const int64_t total = (int64_t)m * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / m, i = t - j * m;
+        C[i + j * ldc] = __longlong_as_double(0x7FF8000000000000ll);
+    }
 }
 
 int64_t up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -83,6 +117,19 @@ extern "C" int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int 
     if (m == 0 || n == 0) return OZAKI2_SUCCESS;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
+    unsigned char* s = nullptr;
+    int sms = 0;
+    bool pageable = false;
+    int rc = scratch_for_current_device(&s, &sms, &pageable);
+    if (rc) return rc;
+    // operands are read (and C written) in place, wherever they live
+    if (k > 0 && !addressable(A, pageable)) return -7;
+    if (k > 0 && !addressable(B, pageable)) return -9;
+    if (!addressable(C, pageable)) return -12;
+    if (k == 0 || alpha == 0.0)  // C = beta C: no scratch needed
+        return launch_scale_c(m, n, beta, C, ldc, st) == cudaSuccess ? OZAKI2_SUCCESS
+                                                                     : OZAKI2_ERROR_CUDA;
+
     // Scratch layout: status word, shifts e and f, planes of A and B, product residues.
     const int64_t m_pad = up(m, OZAKI2_ROWS_ALIGN_A), n_pad = up(n, OZAKI2_ROWS_ALIGN_B);
     const int64_t k_pad = up(k > 0 ? k : 1, OZAKI2_K_ALIGN);
@@ -94,14 +141,6 @@ extern "C" int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int 
     const int64_t off_res = off_pb + up(2 * num_moduli * (int64_t)geo.rows_b * geo.ld, 256);
     const int64_t total = off_res + up(num_moduli * m_pad * n_pad, 256);
     if (total > (int64_t)OZAKI2_NOALLOC_SCRATCH_BYTES) return OZAKI2_ERROR_TOO_LARGE;
-
-    unsigned char* s = nullptr;
-    int sms = 0;
-    int rc = scratch_for_current_device(&s, &sms);
-    if (rc) return rc;
-    if (k == 0 || alpha == 0.0)
-        return launch_scale_c(m, n, beta, C, ldc, st) == cudaSuccess ? OZAKI2_SUCCESS
-                                                                     : OZAKI2_ERROR_CUDA;
 
     unsigned* status = reinterpret_cast<unsigned*>(s);
     int* e = reinterpret_cast<int*>(s + off_e);
@@ -125,8 +164,11 @@ extern "C" int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int 
                              T->epi,
                              status, sms, 960, OZAKI2_GEMM_AUTO, st);
     if (rc) return rc;
-    return launch_crt(res, n_pad, m_pad * n_pad, m, n, e, f, alpha, beta, C, ldc, *T, status, st,
-                      false, true) == cudaSuccess
-               ? OZAKI2_SUCCESS
-               : OZAKI2_ERROR_CUDA;
+    if (launch_crt(res, n_pad, m_pad * n_pad, m, n, e, f, alpha, beta, C, ldc, *T, status, st,
+                   false, true) != cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    const int64_t entries = (int64_t)m * n;
+    const int blocks = (int)((entries + 255) / 256 < sms ? (entries + 255) / 256 : sms);
+    nan_on_timeout_kernel<<<blocks, 256, 0, st>>>(status, C, m, n, ldc);
+    return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
 }

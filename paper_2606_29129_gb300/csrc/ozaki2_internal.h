@@ -12,6 +12,8 @@ namespace ozaki2 {
 
 constexpr int kMaxModuli = OZAKI2_MAX_MODULI;
 constexpr int kMaxWords = 6;  // 32-bit words of sum_l P_l w_l < N P for N <= 20 (161 bits)
+// Default bound of every wait inside the residue-GEMM kernels (OZAKI2_OPT_WAIT_LIMIT_NS).
+constexpr unsigned long long kDefaultWaitLimitNs = 2000000000ull;
 
 // Per-N tables derived from Step 1 (Section 2.2) on the host, passed to kernels by value.
 struct ConvertTables {
@@ -36,6 +38,7 @@ struct CrtTables {
     // 256 prod_g keeps it in [0, 2^25)) gives X = sum_g PG_g v_g == sum_l P_l q_l c_l (mod P),
     // and X / P = sum_g v_g / prod_g.
     uint32_t K[kMaxModuli];
+    uint32_t Kpair[(kMaxModuli + 1) / 2];  // K_2g | K_2g+1 << 16 (every K_l < prod_g < 2^16)
     uint32_t grp_bias[(kMaxModuli + 1) / 2];
     uint32_t PG[(kMaxModuli + 1) / 2][kMaxWords];
     unsigned long long R48[(kMaxModuli + 1) / 2];  // round(2^48 / prod_g)
@@ -74,10 +77,31 @@ struct PlaneGeom {
     int rows_a, rows_b, ld;
     int out_rows, out_cols;
 };
-inline PlaneGeom compact_planes(int m, int n, int k) {
+// bn: width of the residue-GEMM tiles (rows of op(B) in one TMA box: 256, or 128 or 64 for the
+// narrower tiles of grouped calls).
+inline PlaneGeom compact_planes(int m, int n, int k, int bn = 256) {
     const int ld = (k + 63) / 64 * 64;
-    return PlaneGeom{m > 128 ? m : 128, n > 256 ? n : 256, ld > 64 ? ld : 64, (m + 31) / 32 * 32,
+    return PlaneGeom{m > 128 ? m : 128, n > bn ? n : bn, ld > 64 ? ld : 64, (m + 31) / 32 * 32,
                      (n + 31) / 32 * 32};
+}
+
+// Layout of an encoded operand (ozaki2_encode_operands): int32 shifts of lines_pad lines, then
+// bf16 residue planes [N][rows][ld] from off_planes (rows of op(A) or columns of op(B), K
+// contiguous).  Side A pads to 128 lines, side B to 256 (one TMA box of the widest tile).
+struct OperandLayout {
+    int lines_pad, rows, ld;
+    int64_t off_planes, bytes;
+};
+inline OperandLayout operand_layout(bool side_b, int lines, int k, int N) {
+    const int align = side_b ? 256 : 128;
+    OperandLayout L;
+    L.lines_pad = ((lines > 0 ? lines : 1) + align - 1) / align * align;
+    L.rows = lines > align ? lines : align;
+    const int ld = (k + 63) / 64 * 64;
+    L.ld = ld > 64 ? ld : 64;
+    L.off_planes = ((int64_t)4 * L.lines_pad + 255) / 256 * 256;
+    L.bytes = L.off_planes + ((int64_t)2 * N * L.rows * L.ld + 255) / 256 * 256;
+    return L;
 }
 
 // One problem of a grouped call, as the grouped kernels see it (device memory).
@@ -117,21 +141,25 @@ struct CrtWork {         // one 32 x 32 tile of C
 // One problem of a grouped residue GEMM (device memory, 64-byte aligned for the tensor maps).
 struct alignas(64) GroupGemmProblem {
     CUtensorMap ta;      // A planes [N][rows_a][ld], box 64 x 128
-    CUtensorMap tb;      // B planes [N][rows_b][ld], box 64 x 256
+    CUtensorMap tb;      // B planes [N][rows_b][ld], box 64 x bn
     int8_t* out;         // product residues [N][m_pad][n_pad]
     int64_t out_ld, out_plane;
     int tiles_m, tiles_n, k_blocks, nchunks;
     int m_live, n_live;  // stored part of each plane of `out` (PlaneGeom::out_rows, out_cols)
     int tile_begin;      // index of this problem's first tile in the grouped launch
+    int bn;              // tile width (256, 128 or 64 columns); the B box has bn rows
+    int chunk_blocks;    // K blocks of 64 between modular reductions
 };
 
 // Fills the tensor maps and tile counts of one grouped-GEMM problem (host); false on failure.
+// bn: tile width, 256, 128 or 64 (n_pad a multiple of bn, geo.rows_b >= bn).
 bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, int k_pad,
                              const PlaneGeom& geo, const void* planes_a, const void* planes_b,
-                             int8_t* out, int chunk_k);
+                             int8_t* out, int chunk_k, int bn = 256);
 int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
                                 const EpilogueTables& t, unsigned* status, int num_sms,
-                                int chunk_k, cudaStream_t stream);
+                                int chunk_k, cudaStream_t stream,
+                                unsigned long long limit_ns = kDefaultWaitLimitNs);
 
 cudaError_t launch_scale_grouped(const GroupProblem* probs, const ScaleWork* work, int blocks,
                                  unsigned* status, cudaStream_t stream);
@@ -143,17 +171,52 @@ cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* 
 // Blocks of the grouped convert for one side of one problem (rows x ld stored).
 int convert_blocks(int lines, int64_t elem_stride, int rows, int ld);
 
-// Grouped calls (grouped.cu).
-size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs);
-int grouped_table_bytes(int count, const ozaki2_problem* probs,
-                        int scaling = OZAKI2_SCALING_PROPOSED);
+// Residue-GEMM configuration of the problems of a grouped call: the first rule whose bounds
+// hold (n <= n_max and k <= k_max) gives the problem's tile width (256, 128 or 64 columns) and K
+// chunk (0: the handle's OZAKI2_OPT_CHUNK_K); a problem that no rule matches gets the automatic
+// width (auto_tile_n) and the handle's chunk.
+struct TileRule {
+    int n_max, k_max, tile_n, chunk_k;
+};
+struct TileRules {
+    int count = 0;
+    TileRule r[OZAKI2_MAX_TILE_RULES];
+};
+// Automatic tile width for a problem with n columns of op(B): the fewest estimated cycles per
+// 128-row m-tile and K block of 64, a tile taking max(2 bn, (16 KiB + 128 bn) / 96) cycles (its
+// MMAs, or loading its A and B blocks at ~96 bytes per cycle and SM); ties go to the wider tile.
+int auto_tile_n(int n);
+// Tile width and K chunk of a problem under `rules` (chunk_k: the handle's default chunk).
+void grouped_tile(const TileRules& rules, int n, int k, int chunk_k, int* bn, int* chunk);
+
+// Grouped calls (grouped.cu).  `rules` and `chunk_k` select each problem's tile width and K chunk.
+// enc_a / enc_b: NULL, or per problem NULL or an encoded operand replacing op(A) / op(B) (already
+// checked against the problem).
+struct Encoded {
+    const ozaki2_operand* const* a = nullptr;
+    const ozaki2_operand* const* b = nullptr;
+};
+size_t grouped_workspace_bytes(int count, const ozaki2_problem* probs,
+                               const Encoded& enc = Encoded());
+int grouped_table_bytes(int count, const ozaki2_problem* probs, const TileRules& rules,
+                        int chunk_k, int scaling = OZAKI2_SCALING_PROPOSED,
+                        const Encoded& enc = Encoded());
 int grouped_check(int count, const ozaki2_problem* probs);
 int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char* host,
-                         int chunk_k, int scaling = OZAKI2_SCALING_PROPOSED);
+                         const TileRules& rules, int chunk_k,
+                         int scaling = OZAKI2_SCALING_PROPOSED, const Encoded& enc = Encoded());
 int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_dev,
-                   unsigned* status, int num_sms, int chunk_k, cudaStream_t stream,
-                   int scaling = OZAKI2_SCALING_PROPOSED);
-char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* ws);
+                   unsigned* status, int num_sms, const TileRules& rules, int chunk_k,
+                   cudaStream_t stream, int scaling = OZAKI2_SCALING_PROPOSED,
+                   unsigned long long limit_ns = kDefaultWaitLimitNs,
+                   const Encoded& enc = Encoded());
+char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* ws,
+                                  const Encoded& enc = Encoded());
+// Encoding of operands (ozaki2_encode_operands): table bytes, the tables (host), the launches.
+int encode_table_bytes(int count, const ozaki2_operand* ops);
+void build_encode_tables(int count, const ozaki2_operand* ops, int scaling, char* host);
+int launch_encode(int count, const ozaki2_operand* ops, const char* tables_dev, unsigned* status,
+                  cudaStream_t stream);
 
 // Accurate mode (scale.cu, convert.cu, residue_gemm.cu).
 // A-bar plane [rows][ld] (bf16, K contiguous) from the exponent codes of the first pass.
@@ -164,14 +227,15 @@ cudaError_t launch_convert_bar(const void* X, int64_t line_stride, int64_t elem_
 // Row and column maxima of C-bar = A-bar B-bar into cmax[0, m_pad) and cmax[m_pad, m_pad+n_pad).
 int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const PlaneGeom& geo, const void* bar_a,
                     const void* bar_b, uint32_t* cmax, unsigned* status, int num_sms,
-                    cudaStream_t stream);
+                    cudaStream_t stream, unsigned long long limit_ns = kDefaultWaitLimitNs);
 // Grouped form: one descriptor per problem (tensor maps over its A-bar / B-bar planes, the
 // maxima at `cmax`), and the persistent launch over all their tiles.
 bool make_group_aux_problem(GroupGemmProblem* g, int m_pad, int n_pad, int k_pad,
                             const PlaneGeom& geo, const void* bar_a, const void* bar_b,
                             uint32_t* cmax);
 int launch_aux_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
-                            unsigned* status, int num_sms, cudaStream_t stream);
+                            unsigned* status, int num_sms, cudaStream_t stream,
+                            unsigned long long limit_ns = kDefaultWaitLimitNs);
 cudaError_t launch_accu_shift_grouped(const GroupProblem* probs, const ScaleWork* work,
                                       int blocks, cudaStream_t stream);
 // Final shifts, in place over the exponent codes.
@@ -238,7 +302,8 @@ cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stri
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const PlaneGeom& geo,
                         const void* planes_a, const void* planes_b, int8_t* out,
                         const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
-                        int variant, cudaStream_t stream);
+                        int variant, cudaStream_t stream,
+                        unsigned long long limit_ns = kDefaultWaitLimitNs);
 
 // f32: C holds floats (SGEMM: C'' rounded to 24 bits, alpha and beta applied in single
 // precision), else doubles.  padded: the residue buffer extends to whole 32 x 32 tiles in every

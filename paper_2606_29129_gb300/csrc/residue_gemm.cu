@@ -50,6 +50,12 @@ constexpr int GROUP_M = 16;                    // m-tiles per group in the tile 
 // M >> 4 at bits 24-28.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
+// The same for a tile of bn columns (bn = 64, 128 or 256: N >> 3 at bits 17-22).
+__host__ __device__ constexpr uint32_t idesc_for(int bn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+static_assert(idesc_for(BN) == IDESC, "instruction descriptor");
 
 struct GemmArgs {
     int tiles_m, tiles_n, total_tiles, k_blocks, chunk_blocks, nchunks;
@@ -58,6 +64,7 @@ struct GemmArgs {
     int8_t* out;
     int64_t out_ld, out_plane;
     unsigned* status;
+    unsigned long long limit_ns;  // bound of every mbarrier wait of the main loops
     EpilogueTables ep;
 };
 
@@ -71,11 +78,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t accumulate) {
+                                          uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 // Nearest integer, ties to even.  (On this power-capped part the single rounding instruction
@@ -160,6 +167,8 @@ struct TileInfo {
     const CUtensorMap* ta;
     const CUtensorMap* tb;
     int l, mt, nt, k_blocks, nchunks;
+    int bn;            // tile width: 256, 128 or 64 columns (rows of the B box)
+    int chunk_blocks;  // K blocks of 64 between modular reductions
     int8_t* out;
     int64_t out_ld, out_plane;
     int m_live, n_live;  // rows and columns of the product residues that are stored
@@ -192,6 +201,8 @@ struct SingleSource {
         ti.tb = tb;
         ti.k_blocks = a->k_blocks;
         ti.nchunks = a->nchunks;
+        ti.bn = BN;
+        ti.chunk_blocks = a->chunk_blocks;
         ti.out = a->out;
         ti.out_ld = a->out_ld;
         ti.out_plane = a->out_plane;
@@ -233,6 +244,8 @@ struct GroupSource {
         ti.tb = &P.tb;
         ti.k_blocks = P.k_blocks;
         ti.nchunks = P.nchunks;
+        ti.bn = P.bn;
+        ti.chunk_blocks = P.chunk_blocks;
         ti.out = P.out;
         ti.out_ld = P.out_ld;
         ti.out_plane = P.out_plane;
@@ -328,6 +341,7 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long lim = args.limit_ns;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -381,18 +395,18 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
             for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
                     if (c >= ti[s].nchunks) continue;
-                    const int kb0 = c * args.chunk_blocks;
-                    const int kb1 = min(kb0 + args.chunk_blocks, ti[s].k_blocks);
+                    const int kb0 = c * ti[s].chunk_blocks;
+                    const int kb1 = min(kb0 + ti[s].chunk_blocks, ti[s].k_blocks);
                     for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, args.status)) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, args.status, lim)) {
                             ok = false;
                             break;
                         }
-                        mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
+                        mbar_arrive_expect_tx(&full[stage], A_BYTES + ti[s].bn * (BK * 2));
                         tma_load_3d(sA + stage * A_BYTES, ti[s].ta, &full[stage], kb * BK,
                                     ti[s].mt * BM, ti[s].l);
                         tma_load_3d(sB + stage * B_BYTES, ti[s].tb, &full[stage], kb * BK,
-                                    ti[s].nt * BN, ti[s].l);
+                                    ti[s].nt * ti[s].bn, ti[s].l);
                         armed[stage] = true;
                         armed_parity[stage] = phase;
                         if (++stage == STAGES) {
@@ -424,17 +438,19 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
             for (int c = 0; ok && c < maxc; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
                     if (c >= ti[s].nchunks) continue;
-                    if (!mbar_wait(&acc_empty[s], (acc_cnt[s] & 1) ^ 1, abort_flag, args.status)) {
+                    if (!mbar_wait(&acc_empty[s], (acc_cnt[s] & 1) ^ 1, abort_flag, args.status,
+                                   lim)) {
                         ok = false;
                         break;
                     }
                     ++acc_cnt[s];
                     tc_fence_after();
                     const uint32_t d_tmem = tmem_base + (uint32_t)(s * BN);
-                    const int kb0 = c * args.chunk_blocks;
-                    const int kb1 = min(kb0 + args.chunk_blocks, ti[s].k_blocks);
+                    const uint32_t idesc = idesc_for(ti[s].bn);
+                    const int kb0 = c * ti[s].chunk_blocks;
+                    const int kb1 = min(kb0 + ti[s].chunk_blocks, ti[s].k_blocks);
                     for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag, args.status)) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, args.status, lim)) {
                             ok = false;
                             break;
                         }
@@ -445,7 +461,7 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                         for (int kk = 0; kk < BK / UMMA_K; ++kk) {
                             const uint32_t acc = (c > 0 || kb > kb0 || kk > 0) ? 1u : 0u;
                             umma_bf16(d_tmem, sw128_desc(a0 + kk * UMMA_K * 2),
-                                      sw128_desc(b0 + kk * UMMA_K * 2), acc);
+                                      sw128_desc(b0 + kk * UMMA_K * 2), idesc, acc);
                         }
                         issued = true;
                         umma_commit(&empty[stage]);
@@ -466,8 +482,8 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
     } else if (warp >= EPI_WARP0) {
         // ------------------------------------------------------------ epilogue
         const int q = warp & 3;
-        const int col0 = ((warp - EPI_WARP0) >> 2) * EPI_COLS;  // this warp's share of columns
-        const uint32_t lane_base = ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
+        const int half = (warp - EPI_WARP0) >> 2;  // this warp's half of the tile's columns
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t acc_cnt[2] = {0, 0};
         bool ok = true;
         for (int pr = 0; ok && PER * pr < my_tiles; ++pr) {
@@ -481,7 +497,8 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                     if (c >= ti[s].nchunks) continue;
                     bool got = true;
                     if (lane == 0)
-                        got = mbar_wait(&acc_full[s], acc_cnt[s] & 1, abort_flag, args.status);
+                        got = mbar_wait(&acc_full[s], acc_cnt[s] & 1, abort_flag, args.status,
+                                        lim);
                     got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
                     if (!got) {
                         ok = false;
@@ -489,7 +506,10 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                     }
                     ++acc_cnt[s];
                     tc_fence_after();
-                    const uint32_t taddr = tmem_base + lane_base + (uint32_t)(s * BN);
+                    const int ncols = ti[s].bn >> 1;  // columns per warp: 128, 64 or 32
+                    const int col0 = half * ncols;
+                    const uint32_t taddr =
+                        tmem_base + lane_base + (uint32_t)(s * BN) + (uint32_t)col0;
                     const int l = ti[s].l;
                     const float p = args.ep.p[l], inv = args.ep.inv_p[l];
                     if (AUX) {
@@ -497,7 +517,7 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                     } else if (c + 1 < ti[s].nchunks) {
                         // in-place reduction modulo p: |r| <= ~0.52 p
 #pragma unroll 1
-                        for (int col = 0; col < EPI_COLS; col += 32) {
+                        for (int col = 0; col < ncols; col += 32) {
                             uint32_t v[32];
                             tmem_ld32(taddr + col, v);
 #pragma unroll
@@ -515,9 +535,10 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                         // the reconstruction reads no others)
                         const int64_t row = (int64_t)ti[s].mt * BM + q * 32 + lane;
                         const bool row_live = row < ti[s].m_live;
-                        const int col_end = min(EPI_COLS, ti[s].n_live - ti[s].nt * BN - col0);
+                        const int col_end =
+                            min(ncols, ti[s].n_live - ti[s].nt * ti[s].bn - col0);
                         int8_t* dst = ti[s].out + (int64_t)l * ti[s].out_plane +
-                                      row * ti[s].out_ld + (int64_t)ti[s].nt * BN + col0;
+                                      row * ti[s].out_ld + (int64_t)ti[s].nt * ti[s].bn + col0;
 #pragma unroll 1
                         for (int col = 0; col < col_end; col += 32) {
                             uint32_t v[32];
@@ -629,6 +650,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long lim = args.limit_ns;
     const uint32_t rank = cluster_rank();
     const bool leader = rank == 0;
     const int cluster = (int)(blockIdx.x >> 1), nclusters = (int)(gridDim.x >> 1);
@@ -679,7 +701,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const int kb0 = c * args.chunk_blocks;
                     const int kb1 = min(kb0 + args.chunk_blocks, args.k_blocks);
                     for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, args.status)) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, args.status, lim)) {
                             ok = false;
                             break;
                         }
@@ -709,7 +731,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const int npair = min(2, my_tiles - 2 * pr);
             for (int c = 0; ok && c < args.nchunks; ++c) {
                 for (int s = 0; ok && s < npair; ++s) {
-                    if (!mbar_wait(&acc_empty[s], (acc_cnt[s] & 1) ^ 1, abort_flag, args.status)) {
+                    if (!mbar_wait(&acc_empty[s], (acc_cnt[s] & 1) ^ 1, abort_flag, args.status,
+                                   lim)) {
                         ok = false;
                         break;
                     }
@@ -719,7 +742,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const int kb0 = c * args.chunk_blocks;
                     const int kb1 = min(kb0 + args.chunk_blocks, args.k_blocks);
                     for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!mbar_wait(&full[stage], phase, abort_flag, args.status)) {
+                        if (!mbar_wait(&full[stage], phase, abort_flag, args.status, lim)) {
                             ok = false;
                             break;
                         }
@@ -766,7 +789,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     decode_tile(tile, args, l, mt, nt);
                     bool got = true;
                     if (lane == 0)
-                        got = mbar_wait(&acc_full[s], acc_cnt[s] & 1, abort_flag, args.status);
+                        got = mbar_wait(&acc_full[s], acc_cnt[s] & 1, abort_flag, args.status,
+                                        lim);
                     got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
                     if (!got) {
                         ok = false;
@@ -875,6 +899,23 @@ bool encode_planes(CUtensorMap* map, const void* base, int N, int rows, int ld, 
     return r == CUDA_SUCCESS;
 }
 
+// The dynamic shared-memory limit is a per-device attribute of a kernel: set it once for each
+// device a launch is made on (bit d of `done` marks device d).
+std::mutex g_attr_mu;
+cudaError_t ensure_smem_attr(const void* kernel, int bytes, uint64_t& done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+    const uint64_t bit = dev < 64 ? 1ull << dev : 0;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (bit && (done & bit)) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done |= bit;
+    return e;
+}
+uint64_t g_attr_grouped = 0, g_attr_aux = 0, g_attr_aux_grouped = 0, g_attr_pair = 0,
+         g_attr_single = 0;
+
 }  // namespace
 
 static int chunk_blocks_of(int chunk_k) {
@@ -886,16 +927,20 @@ static int chunk_blocks_of(int chunk_k) {
 
 bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, int k_pad,
                              const PlaneGeom& geo, const void* planes_a, const void* planes_b,
-                             int8_t* out, int chunk_k) {
+                             int8_t* out, int chunk_k, int bn) {
+    if (bn != 64 && bn != 128 && bn != BN) return false;
+    if (n_pad % bn || geo.rows_b < bn) return false;
     if (!encode_planes(&g->ta, planes_a, N, geo.rows_a, geo.ld, BM) ||
-        !encode_planes(&g->tb, planes_b, N, geo.rows_b, geo.ld, BN))
+        !encode_planes(&g->tb, planes_b, N, geo.rows_b, geo.ld, bn))
         return false;
     const int cb = chunk_blocks_of(chunk_k);
     g->out = out;
     g->out_ld = n_pad;
     g->out_plane = (int64_t)m_pad * n_pad;
+    g->bn = bn;
+    g->chunk_blocks = cb;
     g->tiles_m = m_pad / BM;
-    g->tiles_n = n_pad / BN;
+    g->tiles_n = n_pad / bn;
     g->k_blocks = k_pad / BK;
     g->nchunks = (g->k_blocks + cb - 1) / cb;
     g->m_live = geo.out_rows;
@@ -906,19 +951,15 @@ bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, i
 
 int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
                                 const EpilogueTables& t, unsigned* status, int num_sms,
-                                int chunk_k, cudaStream_t stream) {
+                                int chunk_k, cudaStream_t stream, unsigned long long limit_ns) {
     if (count <= 0 || total_tiles <= 0) return OZAKI2_SUCCESS;
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(residue_gemm_grouped_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)SMEM_BYTES);
-    });
-    if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if (ensure_smem_attr((const void*)residue_gemm_grouped_kernel, (int)SMEM_BYTES,
+                         g_attr_grouped) != cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
     GemmArgs a = {};
     a.chunk_blocks = chunk_blocks_of(chunk_k);
     a.status = status;
+    a.limit_ns = limit_ns;
     a.ep = t;
     const int grid = total_tiles < num_sms ? total_tiles : num_sms;
     residue_gemm_grouped_kernel<<<grid, NUM_THREADS, SMEM_BYTES, stream>>>(probs, count,
@@ -932,7 +973,7 @@ constexpr int kAuxChunkBlocks = 63;
 
 int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const PlaneGeom& geo, const void* bar_a,
                     const void* bar_b, uint32_t* cmax, unsigned* status, int num_sms,
-                    cudaStream_t stream) {
+                    cudaStream_t stream, unsigned long long limit_ns) {
     if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
     if (cudaMemsetAsync(cmax, 0, sizeof(uint32_t) * ((size_t)m_pad + n_pad), stream) !=
         cudaSuccess)
@@ -947,18 +988,14 @@ int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const PlaneGeom& geo, const
     a.out_ld = m_pad;
     a.out_plane = 0;
     a.status = status;
+    a.limit_ns = limit_ns;
     CUtensorMap ta, tb;
     if (!encode_planes(&ta, bar_a, 1, geo.rows_a, geo.ld, BM) ||
         !encode_planes(&tb, bar_b, 1, geo.rows_b, geo.ld, BN))
         return OZAKI2_ERROR_DRIVER;
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(aux_gemm_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)SMEM_BYTES);
-    });
-    if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if (ensure_smem_attr((const void*)aux_gemm_kernel, (int)SMEM_BYTES, g_attr_aux) !=
+        cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
     a.tiles_m = m_pad / BM;
     a.tiles_n = n_pad / BN;
     a.total_tiles = a.tiles_m * a.tiles_n;
@@ -976,6 +1013,8 @@ bool make_group_aux_problem(GroupGemmProblem* g, int m_pad, int n_pad, int k_pad
     g->out = reinterpret_cast<int8_t*>(cmax);
     g->out_ld = m_pad;  // the column maxima follow the m_pad row maxima
     g->out_plane = 0;
+    g->bn = BN;
+    g->chunk_blocks = kAuxChunkBlocks;
     g->tiles_m = m_pad / BM;
     g->tiles_n = n_pad / BN;
     g->k_blocks = k_pad / BK;
@@ -985,19 +1024,16 @@ bool make_group_aux_problem(GroupGemmProblem* g, int m_pad, int n_pad, int k_pad
 }
 
 int launch_aux_gemm_grouped(const GroupGemmProblem* probs, int count, int total_tiles,
-                            unsigned* status, int num_sms, cudaStream_t stream) {
+                            unsigned* status, int num_sms, cudaStream_t stream,
+                            unsigned long long limit_ns) {
     if (count <= 0 || total_tiles <= 0) return OZAKI2_SUCCESS;
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(aux_gemm_grouped_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)SMEM_BYTES);
-    });
-    if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if (ensure_smem_attr((const void*)aux_gemm_grouped_kernel, (int)SMEM_BYTES,
+                         g_attr_aux_grouped) != cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
     GemmArgs a = {};
     a.chunk_blocks = kAuxChunkBlocks;
     a.status = status;
+    a.limit_ns = limit_ns;
     const int grid = total_tiles < num_sms ? total_tiles : num_sms;
     aux_gemm_grouped_kernel<<<grid, NUM_THREADS, SMEM_BYTES, stream>>>(probs, count, total_tiles,
                                                                       a);
@@ -1007,7 +1043,7 @@ int launch_aux_gemm_grouped(const GroupGemmProblem* probs, int count, int total_
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const PlaneGeom& geo,
                         const void* planes_a, const void* planes_b, int8_t* out,
                         const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
-                        int variant, cudaStream_t stream) {
+                        int variant, cudaStream_t stream, unsigned long long limit_ns) {
     if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
     int cb = chunk_k / BK;
     if (cb < 1) cb = 1;
@@ -1023,6 +1059,7 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
     a.out_ld = n_pad;
     a.out_plane = (int64_t)m_pad * n_pad;
     a.status = status;
+    a.limit_ns = limit_ns;
     a.ep = t;
     if (a.k_blocks == 0) {  // empty inner dimension: every product residue is zero
         cudaError_t e = cudaMemsetAsync(out, 0, (size_t)num_moduli * m_pad * n_pad, stream);
@@ -1039,14 +1076,9 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
         if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, pair::HALF) ||
             !encode_planes(&tb, planes_b, num_moduli, geo.rows_b, geo.ld, pair::HALF))
             return OZAKI2_ERROR_DRIVER;
-        static std::once_flag attr_once;
-        static cudaError_t attr_err = cudaSuccess;
-        std::call_once(attr_once, [] {
-            attr_err = cudaFuncSetAttribute(residue_gemm_pair_kernel,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)pair::SMEM_BYTES);
-        });
-        if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        if (ensure_smem_attr((const void*)residue_gemm_pair_kernel, (int)pair::SMEM_BYTES,
+                             g_attr_pair) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
         a.tiles_m = (m_pad + pair::BM - 1) / pair::BM;
         a.tiles_n = n_pad / pair::BN;
         a.total_tiles = a.tiles_m * a.tiles_n * num_moduli;
@@ -1077,14 +1109,9 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
     if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, BM) ||
         !encode_planes(&tb, planes_b, num_moduli, geo.rows_b, geo.ld, BN))
         return OZAKI2_ERROR_DRIVER;
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(residue_gemm_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)SMEM_BYTES);
-    });
-    if (attr_err != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if (ensure_smem_attr((const void*)residue_gemm_kernel, (int)SMEM_BYTES, g_attr_single) !=
+        cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
     a.tiles_m = m_pad / BM;
     a.tiles_n = n_pad / BN;
     a.total_tiles = a.tiles_m * a.tiles_n * num_moduli;

@@ -26,36 +26,39 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// try_wait whose suspension lasts at most about `hint_ns` nanoseconds (the thread still wakes as
+// soon as the phase completes), so that the caller gets to check its bound regularly.
+__device__ __forceinline__ bool mbar_try_wait_for(uint64_t* bar, uint32_t parity,
+                                                  uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
 // Wait for the phase of `bar` with the given parity.  Returns false (and stops the CTA) when
-// the CTA was told to abort or the wait exceeded kTimeoutNs.
+// the CTA was told to abort or the wait exceeded limit_ns.  Every try suspends for at most ~1 us
+// (the system's own suspend limit is unspecified and may exceed a short bound), and every try
+// that fails is followed by a look at the abort flag and the clock.
 __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                           unsigned* status, unsigned long long limit_ns = kTimeoutNs) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_for(bar, parity, 1000u)) return true;
     const uint64_t t0 = global_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63) == 0) {
-            if (*abort_flag) return false;
-            if (global_ns() - t0 > limit_ns) {
-                atomicOr(status, OZAKI2_STATUS_TIMEOUT);
-                *abort_flag = 1;
-                return false;
-            }
+    for (;;) {
+        if (mbar_try_wait_for(bar, parity, 1000u)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(status, OZAKI2_STATUS_TIMEOUT);
+            *abort_flag = 1;
+            return false;
         }
     }
 }

@@ -31,9 +31,12 @@ OPT_GEMM_VARIANT = 1
 OPT_CHUNK_K = 2
 OPT_GRAPH = 3
 OPT_SCALING = 4
+OPT_WAIT_LIMIT_NS = 5
 SCALING_PROPOSED, SCALING_FAST, SCALING_ACCURATE = 0, 1, 2
 GEMM_AUTO, GEMM_SINGLE, GEMM_PAIR = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 8 << 20
+MAX_TILE_RULES = 16
+TILE_WIDTHS = (256, 128, 64)
 
 _lib = None
 _lock = threading.Lock()
@@ -46,6 +49,15 @@ class Problem(ctypes.Structure):
                 ("A", ctypes.c_void_p), ("lda", ctypes.c_int), ("B", ctypes.c_void_p),
                 ("ldb", ctypes.c_int), ("beta", ctypes.c_double), ("C", ctypes.c_void_p),
                 ("ldc", ctypes.c_int), ("num_moduli", ctypes.c_int)]
+
+
+class Operand(ctypes.Structure):
+    """ozaki2_operand: one operand to encode (side 'A': rows of op(A); 'B': columns of op(B))
+    and, after ozaki2_encode_operands, the description of its encoding in `data`."""
+    _fields_ = [("side", ctypes.c_char), ("trans", ctypes.c_char), ("lines", ctypes.c_int),
+                ("k", ctypes.c_int), ("X", ctypes.c_void_p), ("ld", ctypes.c_int),
+                ("num_moduli", ctypes.c_int), ("data", ctypes.c_void_p),
+                ("scaling", ctypes.c_int)]
 
 
 class Ozaki2Error(RuntimeError):
@@ -94,6 +106,9 @@ def lib() -> ctypes.CDLL:
             "ozaki2_dgemm_grouped": [vp, i32, vp],
             "ozaki2_set_timing": [vp, i32],
             "ozaki2_set_option": [vp, i32, i32],
+            "ozaki2_set_grouped_tiles": [vp, i32, vp, vp, vp, vp],
+            "ozaki2_encode_operands": [vp, i32, vp],
+            "ozaki2_dgemm_grouped_encoded": [vp, i32, vp, vp, vp],
             "ozaki2_get_timing": [vp, ctypes.POINTER(ctypes.c_float)],
         }
         for name, args in sig.items():
@@ -102,6 +117,10 @@ def lib() -> ctypes.CDLL:
             fn.restype = i32
         L.ozaki2_grouped_workspace_size.argtypes = [i32, vp]
         L.ozaki2_grouped_workspace_size.restype = ctypes.c_size_t
+        L.ozaki2_grouped_encoded_workspace_size.argtypes = [i32, vp, vp, vp]
+        L.ozaki2_grouped_encoded_workspace_size.restype = ctypes.c_size_t
+        L.ozaki2_operand_bytes.argtypes = [ch, i32, i32, i32]
+        L.ozaki2_operand_bytes.restype = ctypes.c_size_t
         L.ozaki2_workspace_size.argtypes = [i32, i32, i32, i32]
         L.ozaki2_workspace_size.restype = ctypes.c_size_t
         L.ozaki2_error_string.argtypes = [i32]
@@ -166,6 +185,17 @@ class Handle:
 
     def set_option(self, option: int, value: int):
         _check("ozaki2_set_option", lib().ozaki2_set_option(self.h, option, value))
+
+    def set_grouped_tiles(self, rules):
+        """Tile configuration of grouped calls by size class: rules is a sequence of
+        (n_max, k_max, tile_n, chunk_k); the first rule with n <= n_max and k <= k_max applies
+        (chunk_k 0: the handle's OPT_CHUNK_K).  An empty sequence restores the automatic
+        choice."""
+        rules = list(rules)
+        cols = [(ctypes.c_int * max(1, len(rules)))(*(int(r[c]) for r in rules))
+                for c in range(4)]
+        _check("ozaki2_set_grouped_tiles",
+               lib().ozaki2_set_grouped_tiles(self.h, len(rules), *cols))
 
     def set_timing(self, on: bool = True):
         _check("ozaki2_set_timing", lib().ozaki2_set_timing(self.h, 1 if on else 0))
@@ -241,6 +271,52 @@ def ozaki2_dgemm_grouped(count, problems, handle=None) -> int:
 
 def ozaki2_grouped_workspace_size(count, problems) -> int:
     return lib().ozaki2_grouped_workspace_size(count, ctypes.cast(problems, ctypes.c_void_p))
+
+
+def ozaki2_operand_bytes(side, lines, k, num_moduli) -> int:
+    return lib().ozaki2_operand_bytes(_ch(side), lines, k, num_moduli)
+
+
+def operands_array(operands):
+    """A ctypes array of Operand from dicts with the field names (matrices and data buffers as
+    tensors or addresses)."""
+    arr = (Operand * len(operands))()
+    for i, o in enumerate(operands):
+        arr[i] = Operand(_ch(o["side"]), _ch(o.get("trans", "N")), o["lines"], o["k"],
+                         _ptr(o["X"]), o["ld"], o["num_moduli"], _ptr(o["data"]), 0)
+    return arr
+
+
+def ozaki2_encode_operands(count, operands, handle=None) -> int:
+    """operands: a ctypes array of Operand (see operands_array); its scaling fields are set."""
+    return lib().ozaki2_encode_operands(_h(handle), count, ctypes.cast(operands, ctypes.c_void_p))
+
+
+def encoded_refs(operands, picks):
+    """A ctypes array of pointers into `operands` (an Operand array): entry i points at
+    operands[picks[i]], or is NULL when picks[i] is None."""
+    arr = (ctypes.POINTER(Operand) * len(picks))()
+    base = ctypes.addressof(operands)
+    size = ctypes.sizeof(Operand)
+    for i, j in enumerate(picks):
+        if j is not None:
+            arr[i] = ctypes.cast(base + j * size, ctypes.POINTER(Operand))
+    return arr
+
+
+def ozaki2_dgemm_grouped_encoded(count, problems, enc_a=None, enc_b=None, handle=None) -> int:
+    """problems: a Problem array; enc_a / enc_b: None or pointer arrays (see encoded_refs)."""
+    cast = (lambda a: None if a is None else ctypes.cast(a, ctypes.c_void_p))
+    return lib().ozaki2_dgemm_grouped_encoded(_h(handle), count,
+                                              ctypes.cast(problems, ctypes.c_void_p),
+                                              cast(enc_a), cast(enc_b))
+
+
+def ozaki2_grouped_encoded_workspace_size(count, problems, enc_a=None, enc_b=None) -> int:
+    cast = (lambda a: None if a is None else ctypes.cast(a, ctypes.c_void_p))
+    return lib().ozaki2_grouped_encoded_workspace_size(count,
+                                                       ctypes.cast(problems, ctypes.c_void_p),
+                                                       cast(enc_a), cast(enc_b))
 
 
 def ozaki2_scale_a(transA, m, k, A, lda, num_moduli, shifts, handle=None) -> int:

@@ -5,13 +5,24 @@ keeps a FIFO of waiting requests and a set of execution slots (CUDA streams, eac
 and a fixed device workspace).  Each scheduling step
 
   1. retires finished batches: their results are on the host, their device memory is released;
-  2. admits waiting requests, in order, while their device inputs and outputs fit the HBM
-     budget (the residue planes live in the slot workspaces, which are part of the budget);
-     admission uploads the inputs;
-  3. starts a batch on every idle slot: the admitted requests that fit the slot's workspace go
-     out as one grouped call (ozaki2_dgemm_grouped), whose residue matrices stay in device memory
-     for the life of the batch; the CRT writes each result straight into a page-locked host
-     buffer (the device writes host memory faster than a device-to-host copy runs).
+  2. admits waiting requests, in order, while their device inputs fit the HBM budget (the
+     residue planes live in the slot workspaces and the residue cache, which have their own
+     shares of the budget); admission uploads the inputs, or finds them already encoded;
+  3. starts a batch on every idle slot: the admitted requests that fit the slot's workspace (and
+     the batch's work cap) go out as one grouped call, whose residue matrices stay in device
+     memory for the life of the batch; the CRT writes each result straight into a page-locked
+     host buffer (the device writes host memory faster than a device-to-host copy runs).
+
+Residue cache.  Under the proposed scaling (Section 4, eq. (proposed-mu)/(proposed-nu)) the
+shift of a row of op(A) depends on that row alone and the shift of a column of op(B) on that
+column alone, so the shifts and bf16 residue planes of an operand (Step 2) are a function of the
+operand and N.  With a cache, every operand is encoded once on the device
+(ozaki2_encode_operands) into a buffer of the cache, keyed by the request's operand identity
+(`a_key`, `b_key`) and N; later requests with the same operand skip its upload, scaling and
+conversion, and every batch runs only the residue GEMMs and the reconstruction
+(ozaki2_dgemm_grouped_encoded).  Entries are evicted least recently used when room is needed,
+never while a queued or running batch uses them.  Operands without a key are encoded into
+private entries that are dropped after their request.
 
 Requests that arrive while others run are admitted as memory frees up and start on the next
 idle slot, so their work overlaps the batches already on the device.  Each request's N comes
@@ -19,8 +30,8 @@ from its accuracy target through the calibration table of `autotune`.  Every res
 same bits the request would get alone (the grouped call computes each problem exactly as
 ozaki2_dgemm does).
 
-The executor is separate from the scheduling logic, so the admission and batching rules can be
-exercised without a GPU.
+The executor is separate from the scheduling logic, so the admission, batching and cache rules
+can be exercised without a GPU.
 """
 from __future__ import annotations
 
@@ -40,6 +51,8 @@ class Request:
     target: float | None          # max relative error wanted; None = as accurate as cuBLAS
     A: object = None              # host column-major storage (k, m) float64
     B: object = None              # host column-major storage (n, k) float64
+    a_key: object = None          # identity of A for the residue cache (None: not reused)
+    b_key: object = None          # identity of B
     arrival: float = 0.0
     num_moduli: int = 0
     admitted: float | None = None
@@ -51,7 +64,13 @@ class Request:
 
     @property
     def io_bytes(self) -> int:
-        return 8 * (self.m * self.k + self.k * self.n + self.m * self.n)
+        """Device bytes of the request's FP64 inputs while they are uploaded (the result is
+        written to host memory)."""
+        return 8 * (self.m * self.k + self.k * self.n)
+
+    @property
+    def flops(self) -> float:
+        return 2.0 * self.m * self.n * self.k
 
     @property
     def latency(self):
@@ -62,11 +81,16 @@ class Server:
     """Scheduling logic: admission by memory budget, batching onto idle slots, retirement."""
 
     def __init__(self, executor, io_budget_bytes: int, max_batch: int = 64,
-                 calibration=None, default_n: int = 16, clock=time.perf_counter):
+                 calibration=None, default_n: int = 16, clock=time.perf_counter,
+                 max_batch_flops: float | None = None):
         self.ex = executor
         self.io_budget = io_budget_bytes
         self.io_used = 0
         self.max_batch = max_batch
+        # work cap of one batch (sum of 2mnk): a batch takes requests while it stays under the
+        # cap (always at least one), so small requests are not held behind a long batch
+        self.max_batch_flops = max_batch_flops
+        self.step_seconds = 0.0        # host time spent in step() (scheduling and launches)
         self.calibration = calibration or {}
         self.default_n = default_n
         self.clock = clock
@@ -82,7 +106,9 @@ class Server:
             req.arrival = self.clock()
         req.num_moduli = autotune.choose_n(self.calibration, req.k, req.target, self.default_n)
         need = self.ex.workspace_bytes([req])
-        if req.io_bytes > self.io_budget or need > self.ex.slot_workspace:
+        too_large = getattr(self.ex, "too_large", None)
+        if req.io_bytes > self.io_budget or need > self.ex.slot_workspace or \
+                (too_large is not None and too_large(req)):
             req.error = "request larger than the server's memory budget"
             req.done = self.clock()
             self.finished.append(req)
@@ -95,6 +121,13 @@ class Server:
     # ---------------------------------------------------------------- one step
     def step(self) -> int:
         """Retire, admit, launch.  Returns the number of requests started."""
+        t0 = time.perf_counter()
+        try:
+            return self._step()
+        finally:
+            self.step_seconds += time.perf_counter() - t0
+
+    def _step(self) -> int:
         for slot in list(self.running):
             token, reqs = self.running[slot]
             if self.ex.poll(token):
@@ -107,10 +140,12 @@ class Server:
                     self.finished.append(r)
                 del self.running[slot]
         while self.waiting and self.io_used + self.waiting[0].io_bytes <= self.io_budget:
-            r = self.waiting.popleft()
+            r = self.waiting[0]
+            if self.ex.admit(r) is False:   # no room in the executor yet (its cache is full)
+                break
+            self.waiting.popleft()
             self.io_used += r.io_bytes
             self.peak_io = max(self.peak_io, self.io_used)
-            self.ex.admit(r)
             r.admitted = self.clock()
             self.admitted.append(r)
         started = 0
@@ -118,8 +153,13 @@ class Server:
             if slot in self.running or not self.admitted:
                 continue
             batch = []
+            work = 0.0
             while self.admitted and len(batch) < self.max_batch and \
                     self.ex.workspace_bytes(batch + [self.admitted[0]]) <= self.ex.slot_workspace:
+                nxt = self.admitted[0]
+                if batch and self.max_batch_flops and work + nxt.flops > self.max_batch_flops:
+                    break
+                work += nxt.flops
                 batch.append(self.admitted.popleft())
             if not batch:
                 continue
@@ -136,10 +176,87 @@ class Server:
                 time.sleep(poll_sleep)
 
 
-class GpuExecutor:
-    """Execution slots on one GPU: a stream, an ozaki2 handle and a fixed workspace per slot."""
+class CacheEntry:
+    __slots__ = ("key", "nbytes", "refs", "private", "buf", "op", "ready")
 
-    def __init__(self, slots: int = 2, slot_workspace_bytes: int = 8 << 30, device: int = 0):
+    def __init__(self, key, nbytes, private):
+        self.key, self.nbytes, self.refs, self.private = key, nbytes, 1, private
+        self.buf = self.op = self.ready = None
+
+
+class ResidueCache:
+    """Encoded operands kept in device memory, least recently used first out, within a byte
+    capacity.  Host logic only: the executor attaches the device buffer to each entry.  An entry
+    is referenced while a request that uses it waits or runs; referenced entries are never
+    evicted.  Private entries (operands without a key) are dropped when their last reference
+    goes."""
+
+    def __init__(self, capacity_bytes: int):
+        self.capacity = capacity_bytes
+        self.used = 0
+        self.peak = 0
+        self.entries = collections.OrderedDict()    # key -> entry, least recently used first
+        self.hits = self.misses = self.evictions = 0
+
+    def get(self, key):
+        """The entry of `key` with one more reference, or None (a miss)."""
+        e = self.entries.get(key)
+        if e is None:
+            self.misses += 1
+            return None
+        self.hits += 1
+        e.refs += 1
+        self.entries.move_to_end(key)
+        return e
+
+    def fits(self, nbytes: int) -> bool:
+        """Whether nbytes could be made room for by evicting unreferenced entries."""
+        free = self.capacity - self.used
+        free += sum(e.nbytes for e in self.entries.values() if e.refs == 0)
+        return nbytes <= free
+
+    def put(self, key, nbytes: int, private: bool = False):
+        """A new entry with one reference, after evicting unreferenced entries (least recently
+        used first) until it fits; None when it cannot fit now."""
+        if not self.fits(nbytes):
+            return None
+        for k in [k for k, e in self.entries.items() if e.refs == 0]:
+            if self.used + nbytes <= self.capacity:
+                break
+            self._drop(k)
+            self.evictions += 1
+        e = CacheEntry(key, nbytes, private)
+        self.entries[key] = e
+        self.used += nbytes
+        self.peak = max(self.peak, self.used)
+        return e
+
+    def release(self, e: CacheEntry):
+        e.refs -= 1
+        if e.refs == 0 and e.private and e.key in self.entries:
+            self._drop(e.key)
+
+    def discard(self, e: CacheEntry):
+        """Remove an entry that was never filled (its admission was undone)."""
+        if self.entries.get(e.key) is e:
+            self._drop(e.key)
+
+    def _drop(self, key):
+        e = self.entries.pop(key)
+        self.used -= e.nbytes
+        e.buf = e.op = e.ready = None
+
+
+class GpuExecutor:
+    """Execution slots on one GPU: a stream, an ozaki2 handle and a fixed workspace per slot.
+
+    cache_bytes > 0 turns on the residue cache: operands are encoded once (on the upload stream)
+    into entries of at most cache_bytes in total, and batches run ozaki2_dgemm_grouped_encoded.
+    With cache_bytes = 0 the inputs are uploaded per request and batches run
+    ozaki2_dgemm_grouped."""
+
+    def __init__(self, slots: int = 2, slot_workspace_bytes: int = 8 << 30, device: int = 0,
+                 cache_bytes: int = 0):
         import torch
 
         from . import ozaki2 as oz
@@ -156,9 +273,25 @@ class GpuExecutor:
             h.set_workspace(ws, slot_workspace_bytes)
             self._slots.append({"stream": stream, "handle": h, "ws": ws})
         self.upload = torch.cuda.Stream(device=self.device)
+        self.cache = ResidueCache(cache_bytes) if cache_bytes > 0 else None
+        self.encoder = oz.Handle() if self.cache else None
+        # makespan breakdown: bytes over the link, device time of the encodings and of the
+        # batches (CUDA events, read when each batch retires)
+        self.stats = {"upload_bytes": 0, "result_bytes": 0, "encoded_operands": 0,
+                      "encode_ms": 0.0, "batch_ms": 0.0, "batches": 0}
+        self._encode_events = []
 
     def slots(self):
         return range(len(self._slots))
+
+    def _operand_bytes(self, side, r):
+        lines = r.m if side == "A" else r.n
+        return self.oz.ozaki2_operand_bytes(side, lines, r.k, r.num_moduli)
+
+    def too_large(self, r: Request) -> bool:
+        if not self.cache:
+            return False
+        return self._operand_bytes("A", r) + self._operand_bytes("B", r) > self.cache.capacity
 
     def workspace_bytes(self, reqs) -> int:
         if not reqs:
@@ -166,49 +299,165 @@ class GpuExecutor:
         probs = self.oz.problems_array([dict(m=r.m, n=r.n, k=r.k, A=1, lda=max(1, r.m), B=1,
                                              ldb=max(1, r.k), C=1, ldc=max(1, r.m),
                                              num_moduli=r.num_moduli) for r in reqs])
-        return self.oz.ozaki2_grouped_workspace_size(len(reqs), probs)
+        if not self.cache:
+            return self.oz.ozaki2_grouped_workspace_size(len(reqs), probs)
+        # every side encoded: the workspace holds the product residues and the tables
+        ops = (self.oz.Operand * (2 * len(reqs)))()
+        for i, r in enumerate(reqs):
+            ops[2 * i] = self.oz.Operand(b"A", b"N", r.m, r.k, 1, max(1, r.m), r.num_moduli,
+                                         256, 0)
+            ops[2 * i + 1] = self.oz.Operand(b"B", b"N", r.n, r.k, 1, max(1, r.k),
+                                             r.num_moduli, 256, 0)
+        ra = self.oz.encoded_refs(ops, [2 * i for i in range(len(reqs))])
+        rb = self.oz.encoded_refs(ops, [2 * i + 1 for i in range(len(reqs))])
+        return self.oz.ozaki2_grouped_encoded_workspace_size(len(reqs), probs, ra, rb)
+
+    @staticmethod
+    def _pinned(torch, x):
+        t = x if isinstance(x, torch.Tensor) else torch.from_numpy(x)
+        return t if t.is_pinned() else t.pin_memory()
 
     def admit(self, r: Request):
-        """Device buffers for the request and the upload of its inputs."""
+        """Device buffers for the request: its encoded operands (cache hits, or new entries
+        encoded from an upload), or the uploaded inputs without a cache.  Returns False, with
+        nothing held, when the cache cannot make room now."""
         torch = self.torch
-
-        def host(x):
-            t = x if isinstance(x, torch.Tensor) else torch.from_numpy(x)
-            return t if t.is_pinned() else t.pin_memory()
-
+        if self.cache:
+            return self._admit_cached(r)
         with torch.cuda.stream(self.upload):
-            r.dev["A"] = host(r.A).to(self.device, non_blocking=True)
-            r.dev["B"] = host(r.B).to(self.device, non_blocking=True)
+            r.dev["A"] = self._pinned(torch, r.A).to(self.device, non_blocking=True)
+            r.dev["B"] = self._pinned(torch, r.B).to(self.device, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(self.upload)
             r.dev["uploaded"] = ev
+        self.stats["upload_bytes"] += 8 * (r.m * r.k + r.k * r.n)
         # the result is written by the CRT kernel straight into page-locked host memory
         r.dev["host_C"] = torch.empty((r.n, r.m), dtype=torch.float64, pin_memory=True)
+        return True
+
+    def _admit_cached(self, r: Request):
+        torch, oz, cache = self.torch, self.oz, self.cache
+        entries, fresh = {}, []
+        for side, key, X in (("A", r.a_key, r.A), ("B", r.b_key, r.B)):
+            lines = r.m if side == "A" else r.n
+            ckey = None if key is None else (side, key, lines, r.k, r.num_moduli)
+            e = cache.get(ckey) if ckey is not None else None
+            if e is None:
+                private = ckey is None
+                e = cache.put(("private", r.rid, side) if private else ckey,
+                              self._operand_bytes(side, r), private)
+                if e is None:  # undo: hits lose their reference, new entries go
+                    new = {id(f[1]) for f in fresh}
+                    for held in entries.values():
+                        if id(held) in new:
+                            cache.discard(held)
+                        else:
+                            cache.release(held)
+                    return False
+                fresh.append((side, e, X, lines))
+            entries[side] = e
+        if fresh:
+            # upload the missing operands and encode them, all on the upload stream
+            with torch.cuda.stream(self.upload):
+                ops = []
+                keep = []
+                for side, e, X, lines in fresh:
+                    e.buf = torch.empty(e.nbytes, dtype=torch.uint8, device=self.device)
+                    dX = self._pinned(torch, X).to(self.device, non_blocking=True)
+                    keep.append(dX)
+                    self.stats["upload_bytes"] += 8 * lines * r.k
+                    # A as stored: column-major m x k (ld m); B: k x n (ld k)
+                    ld = max(1, r.m if side == "A" else r.k)
+                    ops.append(dict(side=side, trans="N", lines=lines, k=r.k, X=dX, ld=ld,
+                                    num_moduli=r.num_moduli, data=e.buf))
+                arr = oz.operands_array(ops)
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record(self.upload)
+                rc = oz.ozaki2_encode_operands(len(ops), arr, self.encoder)
+                if rc:
+                    raise oz.Ozaki2Error("ozaki2_encode_operands", rc)
+                t1.record(self.upload)
+                for i, (_, e, _, _) in enumerate(fresh):
+                    e.op = oz.Operand.from_buffer_copy(arr[i])
+                    e.ready = t1
+                self._encode_events.append((t0, t1))
+                self.stats["encoded_operands"] += len(fresh)
+                del keep   # the allocator reuses these bytes only after the upload stream's work
+        r.dev["enc"] = entries
+        r.dev["host_C"] = torch.empty((r.n, r.m), dtype=torch.float64, pin_memory=True)
+        return True
 
     def launch(self, slot: int, reqs):
         torch, oz = self.torch, self.oz
         s = self._slots[slot]
         with torch.cuda.stream(s["stream"]):
-            for r in reqs:
-                s["stream"].wait_event(r.dev["uploaded"])
-            probs = oz.problems_array([dict(m=r.m, n=r.n, k=r.k, A=r.dev["A"], lda=max(1, r.m),
-                                            B=r.dev["B"], ldb=max(1, r.k), C=r.dev["host_C"],
-                                            ldc=max(1, r.m), num_moduli=r.num_moduli)
-                                       for r in reqs])
-            rc = oz.ozaki2_dgemm_grouped(len(reqs), probs, s["handle"])
-            if rc:
-                raise oz.Ozaki2Error("ozaki2_dgemm_grouped", rc)
-            ev = torch.cuda.Event()
-            ev.record(s["stream"])
-        return ev
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            if not self.cache:
+                for r in reqs:
+                    s["stream"].wait_event(r.dev["uploaded"])
+                probs = oz.problems_array([dict(m=r.m, n=r.n, k=r.k, A=r.dev["A"],
+                                                lda=max(1, r.m), B=r.dev["B"], ldb=max(1, r.k),
+                                                C=r.dev["host_C"], ldc=max(1, r.m),
+                                                num_moduli=r.num_moduli) for r in reqs])
+                start.record(s["stream"])
+                rc = oz.ozaki2_dgemm_grouped(len(reqs), probs, s["handle"])
+                if rc:
+                    raise oz.Ozaki2Error("ozaki2_dgemm_grouped", rc)
+            else:
+                waited = set()
+                for r in reqs:
+                    for e in r.dev["enc"].values():
+                        if e.ready is not None and id(e.ready) not in waited:
+                            s["stream"].wait_event(e.ready)
+                            waited.add(id(e.ready))
+                ops = (oz.Operand * (2 * len(reqs)))()
+                for i, r in enumerate(reqs):
+                    ops[2 * i] = r.dev["enc"]["A"].op
+                    ops[2 * i + 1] = r.dev["enc"]["B"].op
+                # A and B are not read for encoded sides; the encodings' buffers stand in
+                probs = oz.problems_array([dict(m=r.m, n=r.n, k=r.k, A=r.dev["enc"]["A"].buf,
+                                                lda=max(1, r.m), B=r.dev["enc"]["B"].buf,
+                                                ldb=max(1, r.k), C=r.dev["host_C"],
+                                                ldc=max(1, r.m), num_moduli=r.num_moduli)
+                                           for r in reqs])
+                ra = oz.encoded_refs(ops, [2 * i for i in range(len(reqs))])
+                rb = oz.encoded_refs(ops, [2 * i + 1 for i in range(len(reqs))])
+                start.record(s["stream"])
+                rc = oz.ozaki2_dgemm_grouped_encoded(len(reqs), probs, ra, rb, s["handle"])
+                if rc:
+                    raise oz.Ozaki2Error("ozaki2_dgemm_grouped_encoded", rc)
+            end.record(s["stream"])
+        return (start, end)
 
     def poll(self, token) -> bool:
-        return token.query()
+        return token[1].query()
 
     def finish(self, token, reqs):
-        token.synchronize()
+        start, end = token
+        end.synchronize()
+        self.stats["batch_ms"] += start.elapsed_time(end)
+        self.stats["batches"] += 1
         for r in reqs:
             r.C = r.dev["host_C"].numpy()
+            self.stats["result_bytes"] += 8 * r.m * r.n
 
     def release(self, r: Request):
+        if self.cache and "enc" in r.dev:
+            for e in r.dev["enc"].values():
+                self.cache.release(e)
         r.dev.clear()
+
+    def breakdown(self) -> dict:
+        """Link bytes, device milliseconds of the encodings and batches, cache counters."""
+        self.torch.cuda.synchronize()
+        enc = sum(a.elapsed_time(b) for a, b in self._encode_events)
+        self._encode_events.clear()
+        self.stats["encode_ms"] += enc
+        out = dict(self.stats)
+        if self.cache:
+            out.update(cache_hits=self.cache.hits, cache_misses=self.cache.misses,
+                       cache_evictions=self.cache.evictions,
+                       cache_peak_gb=self.cache.peak / 2**30)
+        return out

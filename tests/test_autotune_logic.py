@@ -39,3 +39,41 @@ def test_best_config_and_apply():
     assert not autotune.apply_tiles(h2, table, 64) and h2.options == {}
     js = autotune.tiles_to_json(table)
     assert js[str(autotune.size_class(4096))]["best"] == {"variant": oz.GEMM_PAIR, "chunk_k": 960}
+
+
+class FakeGroupedHandle:
+    def __init__(self):
+        self.rules = []
+
+    def set_grouped_tiles(self, rules):
+        self.rules = list(rules)
+
+
+def test_tune_grouped_tiles_coordinate_descent(monkeypatch):
+    """The per-class tuner keeps, class by class, the tile width and chunk that time fastest;
+    with a cost that is a sum of independent per-class costs it reaches the optimum."""
+    best_width = {64: 64, 128: 64, 256: 128, 512: 256, 1 << 30: 256}
+    best_chunk = {64: 0, 128: 0, 256: 640, 512: 448, 1 << 30: 960}
+    h = FakeGroupedHandle()
+
+    def cost(rules):
+        if not rules:                     # the automatic configuration
+            return 100.0
+        t = 0.0
+        for n_max, _, tn, ck in rules:
+            t += 1.0 + (tn != best_width[n_max]) * 2.0 + (ck != best_chunk[n_max]) * 0.5
+        return t
+
+    monkeypatch.setattr(autotune, "_time_ms", lambda call, reps: cost(h.rules))
+    res = autotune.tune_grouped_tiles(lambda: None, h)
+    got = {r[0]: (r[2], r[3]) for r in res["rules"]}
+    assert got == {e: (best_width[e], best_chunk[e] if best_chunk[e] else 0)
+                   for e in autotune.GROUPED_N_EDGES}
+    assert h.rules == res["rules"] and res["best_ms"] == 5.0 and res["auto_ms"] == 100.0
+
+
+def test_tune_grouped_tiles_keeps_automatic_when_not_beaten(monkeypatch):
+    h = FakeGroupedHandle()
+    monkeypatch.setattr(autotune, "_time_ms", lambda call, reps: 1.0 if not h.rules else 2.0)
+    res = autotune.tune_grouped_tiles(lambda: None, h)
+    assert res["rules"] == [] and h.rules == [] and res["best_ms"] == 1.0

@@ -146,3 +146,36 @@ def test_grouped_cuda_graph_replay(oz):
         torch.cuda.synchronize()
         for i, it in enumerate(items):
             assert _gpu.same_bits(it["C"].cpu().numpy(), run_separately(oz, it)), (rep, i)
+
+
+@pytest.mark.parametrize("rules", [
+    [(1 << 30, 1 << 30, 64, 64)],                       # every problem on 64-wide tiles
+    [(1 << 30, 1 << 30, 128, 320)],                     # 128-wide tiles, K chunk 320
+    [(1 << 30, 1 << 30, 256, 960)],                     # 256-wide tiles
+    [(64, 1 << 30, 64, 128), (128, 200, 128, 0), (1 << 30, 1 << 30, 256, 192)],  # by class
+    [],                                                 # automatic width per problem
+])
+def test_grouped_tile_widths_match_oracle(oz, orc, rules):
+    """Each tile width of the grouped residue GEMM (256, 128 and 64 columns) and several K chunks,
+    chosen per size class: every problem bit-identical to the oracle."""
+    rng = np.random.default_rng(77)
+    items = make_batch(rng, 14, 1, 420, [8, 14, 20])
+    h = oz.Handle()
+    h.set_grouped_tiles(rules)
+    got = run_grouped(oz, items, h)
+    for i, it in enumerate(items):
+        ref = orc.dgemm(it["A_np"], it["B_np"], it["m"], it["n"], it["k"], it["num_moduli"],
+                        it["transA"], it["transB"], it["alpha"], it["beta"], it["Cin"],
+                        lda=it["lda"], ldb=it["ldb"])
+        assert _gpu.same_bits(got[i], ref), (rules, i, it["m"], it["n"], it["k"])
+
+
+def test_grouped_tile_rules_errors(oz):
+    h = oz.Handle()
+    with pytest.raises(oz.Ozaki2Error):
+        h.set_grouped_tiles([(64, 64, 96, 0)])          # not a supported width
+    with pytest.raises(oz.Ozaki2Error):
+        h.set_grouped_tiles([(64, 64, 64, 1000)])       # chunk above 960
+    with pytest.raises(oz.Ozaki2Error):
+        h.set_grouped_tiles([(1, 1, 64, 0)] * (oz.MAX_TILE_RULES + 1))
+    h.set_grouped_tiles([])

@@ -107,3 +107,111 @@ def test_late_arrivals_start_while_a_batch_runs():
     assert ex.batches[0]["left"] > 0         # the first batch has not finished yet
     srv.run_until_idle()
     assert len(srv.finished) == 2
+
+
+# ---------------------------------------------------------------- residue cache (host logic)
+from paper_2606_29129_gb300.serve import ResidueCache  # noqa: E402
+
+
+def test_cache_hits_and_lru_eviction_under_capacity():
+    c = ResidueCache(100)
+    a = c.put("a", 40)
+    b = c.put("b", 40)
+    assert c.used == 80 and a.refs == b.refs == 1
+    assert c.put("c", 40) is None              # a and b are referenced: no room
+    c.release(a)
+    c.release(b)
+    assert c.get("a") is a and a.refs == 1     # a is now the most recently used
+    c.release(a)
+    d = c.put("d", 40)                         # evicts b, the least recently used
+    assert d is not None and "b" not in c.entries and "a" in c.entries
+    assert c.used == 80 and c.evictions == 1 and c.peak <= c.capacity
+    assert c.get("b") is None and c.misses == 1 and c.hits == 1
+
+
+def test_cache_never_evicts_referenced_and_drops_private():
+    c = ResidueCache(100)
+    p = c.put(("private", 1, "A"), 60, private=True)
+    assert not c.fits(50)
+    c.release(p)                               # private entries go with their last reference
+    assert c.used == 0 and not c.entries
+    x = c.put("x", 100)
+    assert c.put("y", 1) is None
+    c.discard(x)
+    assert c.used == 0
+
+
+class CachingFakeExecutor(FakeExecutor):
+    """A fake executor whose admissions take cache entries for A and B, like the GPU one."""
+
+    def __init__(self, capacity, **kw):
+        super().__init__(**kw)
+        self.cache = ResidueCache(capacity)
+        self.encoded = 0
+
+    def too_large(self, r):
+        return 2 * r.m * r.k > self.cache.capacity
+
+    def admit(self, r):
+        got = []
+        for side, key in (("A", r.a_key), ("B", r.b_key)):
+            ck = None if key is None else (side, key, r.num_moduli)
+            e = self.cache.get(ck) if ck is not None else None
+            if e is None:
+                e = self.cache.put(ck or ("private", r.rid, side), r.m * r.k, ck is None)
+                if e is None:
+                    for g in got:
+                        self.cache.release(g)
+                    return False
+                self.encoded += 1
+            got.append(e)
+        r.dev["enc"] = got
+        self.live.add(r.rid)
+        return True
+
+    def release(self, r):
+        for e in r.dev.pop("enc", []):
+            self.cache.release(e)
+        self.live.discard(r.rid)
+
+
+def test_server_with_cache_reuses_operands_and_respects_capacity():
+    ex = CachingFakeExecutor(capacity=1000, slots=2, latency=2)
+    srv = Server(ex, io_budget_bytes=10**9, calibration=CAL, clock=lambda: 0.0)
+    # 40 requests over 4 operand pairs (10 x 10 x 10: 100 bytes per operand in this fake)
+    for i in range(40):
+        r = make(i)
+        r.a_key, r.b_key = ("A", i % 4), ("B", i % 4)
+        srv.submit(r)
+    steps = 0
+    while not srv.idle():
+        srv.step()
+        steps += 1
+        assert ex.cache.used <= ex.cache.capacity
+        assert steps < 1000
+    assert len(srv.finished) == 40 and all(r.error is None for r in srv.finished)
+    assert ex.encoded == 8                      # every operand encoded once
+    assert ex.cache.hits == 72 and not ex.live
+
+
+def test_server_admission_waits_for_cache_room():
+    """Operands without keys take private entries; when the cache is full of entries in use the
+    next request waits and is admitted after a batch retires."""
+    ex = CachingFakeExecutor(capacity=400, slots=1, latency=2)
+    srv = Server(ex, io_budget_bytes=10**9, max_batch=1, calibration=CAL, clock=lambda: 0.0)
+    for i in range(6):
+        srv.submit(make(i))
+    srv.step()
+    assert len(srv.waiting) == 4                # two requests hold the 400 bytes
+    srv.run_until_idle()
+    assert len(srv.finished) == 6 and ex.cache.used == 0
+
+
+def test_batch_work_cap():
+    ex = FakeExecutor(slots=1, latency=1)
+    srv = Server(ex, io_budget_bytes=10**9, calibration=CAL, clock=lambda: 0.0,
+                 max_batch_flops=2.0 * 10 * 10 * 10 * 3)
+    for i in range(7):
+        srv.submit(make(i))
+    srv.run_until_idle()
+    assert [len(b["reqs"]) for b in ex.batches] == [3, 3, 1]
