@@ -327,18 +327,28 @@ static int make_consts(int N, orc_consts* c) {
 /* Step 2 scaling: row/column squared norms and Algorithm 2                              */
 /* ------------------------------------------------------------------------------------ */
 
-/* a_norm := sum_h a_h^2 "computed with rounding-up" (Algorithm 2, input).  Reading: one fused
- * multiply-add per term, rounded upward, accumulated in the natural order h = 1..k. */
+/* a_norm := sum_h a_h^2 "computed with rounding-up" (Section 4, the input of Algorithm 2).  The
+ * paper fixes the rounding direction but no order of the terms.  Reading: the terms in blocks of
+ * ORC_NORM_BLOCK consecutive h; within a block one fused multiply-add per term, rounded upward,
+ * from 0 in the order h; then the block sums added in block order, each addition rounded
+ * upward.  Every operation rounds up and every term is nonnegative, so the result bounds the
+ * exact sum from above; a line of at most ORC_NORM_BLOCK terms is the plain sequential sum. */
+#define ORC_NORM_BLOCK 256
 static double line_norm_ru(const double* x, int64_t stride, int64_t len) {
     int old = fegetround();
     fesetround(FE_UPWARD);
-    double s = 0.0;
-    for (int64_t h = 0; h < len; ++h) {
-        double a = x[h * stride];
-        s = fma(a, a, s);
+    double total = 0.0;
+    for (int64_t b0 = 0; b0 < len; b0 += ORC_NORM_BLOCK) {
+        const int64_t b1 = b0 + ORC_NORM_BLOCK < len ? b0 + ORC_NORM_BLOCK : len;
+        double s = 0.0;
+        for (int64_t h = b0; h < b1; ++h) {
+            double a = x[h * stride];
+            s = fma(a, a, s);
+        }
+        total = total + s;
     }
     fesetround(old);
-    return s;
+    return total;
 }
 
 /* Stand-in for __log2f on x in [1, 2] (eqs. flog2 and logf-bound).  Reading: libm's double

@@ -183,3 +183,50 @@ def test_log2_margin_of_proposed_mu(orc, N):
             assert e >= limit - 1
             hit += math.floor(Decimal(c["pprime"]) - Decimal("0.5") * lg) != limit
     assert hit > 0      # the scan reached points where only the margin moves the floor
+
+
+def _ru(x: Fraction) -> float:
+    """The smallest double >= x (rounding upward), from exact rational arithmetic."""
+    d = float(x)
+    return d if Fraction(d) >= x else math.nextafter(d, math.inf)
+
+
+def blocked_norm_ru(line, block=256):
+    """Upward-rounded squared norm in the blocked order, every operation rounded upward from its
+    exact rational value: fma per term within each block of `block` terms, then the block sums
+    added in order."""
+    total = 0.0
+    for b0 in range(0, len(line), block):
+        s = 0.0
+        for a in line[b0:b0 + block]:
+            s = _ru(Fraction(float(a)) ** 2 + Fraction(s))
+        total = _ru(Fraction(total) + Fraction(s))
+    return total
+
+
+@pytest.mark.parametrize("k", [255, 256, 257, 700, 2048])
+def test_blocked_norm_order_and_bound(orc, k):
+    """The squared norm of Section 4 rounds every operation up; with no order given by the paper,
+    the reading sums blocks of 256 terms in order, then the block sums in order.  The oracle
+    matches that sequence of upward roundings bit for bit (against exact rationals), bounds the
+    exact sum from above and stays within (k + blocks + 2) 2^-52 of it."""
+    m = 6
+    A = synthetic.paper_matrix(m, k, 2.0, 40 + k)
+    _, nr = orc.shifts_a(A, m, k, 14)
+    M = synthetic.colmajor_view(A)
+    blocks = -(-k // 256)
+    for i, S in enumerate(exact_sq_norms_rows(A)):
+        assert float(nr[i]) == blocked_norm_ru(M[i]), i
+        assert Fraction(float(nr[i])) >= S
+        assert Fraction(float(nr[i])) <= S * (1 + Fraction(k + blocks + 2, 2**52))
+
+
+def test_blocked_norm_differs_from_sequential_where_it_should():
+    """The blocked and the sequential upward sums are different readings of the same definition:
+    on a line whose first block ends on a large partial sum they differ in the last bit, which the
+    order pin above can tell apart."""
+    line = [1.0] * 256 + [2.0**-30] * 300
+    seq = 0.0
+    for a in line:
+        seq = _ru(Fraction(a) ** 2 + Fraction(seq))
+    assert blocked_norm_ru(line) != seq
