@@ -236,6 +236,43 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_calibrate(args):
+    """The accuracy table of the autotuner, measured against the double-double reference of the
+    oracle (on a random 64 x 64 block of C per problem) instead of the emulation with N = 20:
+    for each size class (square problems of the class edge, m = n capped at 4096) and each
+    phi, the maximum relative error of the emulation for N = 8..20 and of cuBLAS DGEMM.  Writes
+    the table to --calibration-out (the package's calibration file is this output)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2606_29129_gb300 import autotune
+
+    oracle.build()
+    rng = np.random.default_rng(17)
+    torch.backends.cuda.matmul.allow_tf32 = False
+
+    def dd_reference(A, B, m, n, k):
+        I = np.sort(rng.choice(m, size=min(64, m), replace=False)).astype(np.int32)
+        J = np.sort(rng.choice(n, size=min(64, n), replace=False)).astype(np.int32)
+        hi, _ = oracle.dd_block(A.cpu().numpy(), B.cpu().numpy(), k, I, J)
+        dev = A.device
+        return (torch.from_numpy(I.astype(np.int64)).to(dev),
+                torch.from_numpy(J.astype(np.int64)).to(dev), torch.from_numpy(hi).to(dev))
+
+    t0 = time.perf_counter()
+    table = autotune.calibrate(reference=dd_reference)
+    out = {"table": autotune.table_to_json(table),
+           "how": "bench.py --calibrate: square problems m = n = min(k, 4096) at each class edge "
+                  "k, phi in {0.5, 1, 2}, maximum relative error on a random 64 x 64 block of C "
+                  "against the double-double reference (TwoProd/TwoSum accumulation)",
+           "seconds": time.perf_counter() - t0}
+    if args.calibration_out:
+        with open(args.calibration_out, "w") as fh:
+            json.dump(out, fh, indent=1)
+    print(json.dumps({"mode": "calibration", **out}), flush=True)
+
+
 def run_tune_tiles(args):
     """Residue-GEMM configuration per size class by timing: kernel variant (128 x 256 tiles on
     one SM, or 256 x 256 on an SM pair) and K chunk, for square DGEMMs of each size."""
@@ -524,10 +561,14 @@ def run_batched(args):
     oracle.build()
     items = batched_problems(args.batch, seed=4)
     t0 = time.perf_counter()
-    table = autotune.calibrate(ks=(64, 128, 256, 512, 1024, 2048))
+    table = autotune.load_calibration()
+    calib_src = "committed table (double-double reference)"
+    if table is None:
+        table = autotune.calibrate(ks=(64, 128, 256, 512, 1024, 2048))
+        calib_src = "measured now (reference: the emulation with N = 20)"
     calib_s = time.perf_counter() - t0
     for it in items:
-        it["N"] = autotune.choose_n(table, it["k"])
+        it["N"] = autotune.choose_n(table, it["k"], margin=args.n_margin)
         it["C"] = torch.empty((it["n"], it["m"]), dtype=torch.float64, device="cuda")
     flops = sum(2.0 * it["m"] * it["n"] * it["k"] for it in items)
     probs = oz.problems_array([dict(m=it["m"], n=it["n"], k=it["k"], A=it["A"], lda=it["m"],
@@ -626,7 +667,8 @@ def run_batched(args):
                      "items_worse_than_cublas": int(worse_than_cublas),
                      "sample": f"{side}x{side} random block per item vs double-double",
                      "per_item_file": args.items_out},
-        "calibration": {"seconds": calib_s, "table": autotune.table_to_json(table)},
+        "calibration": {"seconds": calib_s, "source": calib_src, "margin": args.n_margin,
+                        "table": autotune.table_to_json(table)},
         "tile_tuning": {"chunk_k_ms": {str(c): t for c, t in chunk_ms.items()},
                         "chunk_k": chunk_best,
                         "rules_n_max_k_max_tile_n_chunk_k": tiles["rules"],
@@ -660,7 +702,7 @@ def run_serve(args):
 
     import synthetic
     from paper_2606_29129_gb300 import autotune
-    from paper_2606_29129_gb300.serve import GpuExecutor, Request, Server
+    from paper_2606_29129_gb300.serve import GpuExecutor, Request, ResultPool, Server
 
     rng = np.random.default_rng(args.serve_seed)
     pool = []
@@ -673,26 +715,41 @@ def run_serve(args):
         pool.append((m, n, k, A, B))
     targets = (1e-10, 1e-13, 1e-15)
     t0 = time.perf_counter()
-    table = autotune.calibrate(ks=tuple(e for e in autotune.CLASS_EDGES if e <= args.serve_max))
+    table = autotune.load_calibration()
+    if table is None:
+        table = autotune.calibrate(ks=tuple(e for e in autotune.CLASS_EDGES
+                                            if e <= args.serve_max))
     calib_s = time.perf_counter() - t0
     slot_ws = args.serve_slot_ws_gb << 30
     budget = args.serve_budget_gb << 30
     cache_bytes = args.serve_cache_gb << 30
     count = args.serve_requests
     cub_ms = None
+    # page-locked result buffers, reused: the client consumes each result when it completes and
+    # hands the buffer back; allocated before the timed streams (up to 64 per size bucket)
+    results = ResultPool(lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True))
+    picks0 = np.random.default_rng(args.serve_seed + 1).integers(0, len(pool), size=count)
+    per_bucket = {}
+    for p in picks0:
+        b = ResultPool.bucket(pool[int(p)][0] * pool[int(p)][1])
+        per_bucket[b] = per_bucket.get(b, 0) + 1
+    for b, c in per_bucket.items():
+        results.prewarm(b, min(c, 64))
+    prewarmed = results.allocated
     for lam in args.serve_rates:
         rng_s = np.random.default_rng(args.serve_seed + 1)
         arrivals = (np.cumsum(rng_s.exponential(1.0 / lam, size=count)) if lam > 0
                     else np.zeros(count))
         picks = rng_s.integers(0, len(pool), size=count)
         ex = GpuExecutor(slots=args.serve_slots, slot_workspace_bytes=slot_ws,
-                         cache_bytes=cache_bytes)
+                         cache_bytes=cache_bytes, result_pool=results)
         io_budget = budget - args.serve_slots * slot_ws - cache_bytes
         srv = Server(ex, io_budget_bytes=io_budget, max_batch=64, calibration=table,
                      max_batch_flops=args.serve_batch_tflop * 1e12)
         reqs = []
         start = time.perf_counter()
         i = 0
+        consumed = 0
         while i < count or not srv.idle():
             now = time.perf_counter() - start
             while i < count and arrivals[i] <= now:
@@ -704,6 +761,9 @@ def run_serve(args):
                 reqs.append(r)
                 i += 1
             srv.step()
+            while consumed < len(srv.finished):   # the client takes each result as it completes
+                ex.recycle(srv.finished[consumed])
+                consumed += 1
         makespan = time.perf_counter() - start
         bd = ex.breakdown()
         lat = sorted(r.latency for r in reqs if r.error is None)
@@ -731,6 +791,7 @@ def run_serve(args):
                 "cache_hits": bd.get("cache_hits"), "cache_misses": bd.get("cache_misses"),
                 "cache_evictions": bd.get("cache_evictions"),
                 "cache_peak_gb": bd.get("cache_peak_gb"),
+                "result_buffers": {"prewarmed": prewarmed, "allocated_total": results.allocated},
                 "note": "batch_device_s sums the slots' grouped calls (GEMM + CRT writing C to "
                         "host memory), which overlap on the device; host_scheduling_s is the "
                         "time spent inside Server.step"},
@@ -966,6 +1027,11 @@ def main():
                     help="the batched workload (grouped call) instead of the benchmark")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--err-items", type=int, default=512)
+    ap.add_argument("--n-margin", type=float, default=8.0,
+                    help="batched mode: choose N with calibrated error <= cuBLAS's / margin")
+    ap.add_argument("--calibrate", action="store_true",
+                    help="measure the autotuner's accuracy table against double-double")
+    ap.add_argument("--calibration-out", default=None)
     ap.add_argument("--err-side", type=int, default=48,
                     help="batched mode: rows and columns of each item's error block")
     ap.add_argument("--items-out", default=None,
@@ -1004,6 +1070,9 @@ def main():
         return
     if args.tune_tiles:
         run_tune_tiles(args)
+        return
+    if args.calibrate:
+        run_calibrate(args)
         return
     if args.batched:
         if args.impl == "reference":

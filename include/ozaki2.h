@@ -65,8 +65,9 @@ extern "C" {
 
 /* Options (ozaki2_set_option). */
 #define OZAKI2_OPT_GEMM_VARIANT 1 /* residue-GEMM kernel: one of OZAKI2_GEMM_* (default AUTO) */
-#define OZAKI2_OPT_CHUNK_K 2      /* products accumulated between modular reductions in the residue
-                                     GEMM: a multiple of 64 in [64, 960] (default 960) */
+#define OZAKI2_OPT_CHUNK_K 2      /* most products accumulated between modular reductions in the
+                                     residue GEMM: a multiple of 64 in [64, 960] (default 960); the
+                                     K blocks are spread evenly over the chunks this gives */
 #define OZAKI2_OPT_GRAPH 3        /* 1: ozaki2_dgemm_grouped captures each distinct problem list
                                      once into a CUDA graph and replays it on later calls with
                                      the same list (same pointers and sizes); 0 (default): off.

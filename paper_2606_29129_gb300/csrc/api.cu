@@ -42,6 +42,13 @@ struct ozaki2_context {
     bool pageable_access = false;  // the device can address ordinary (pageable) host memory
     void* in_ws = nullptr;         // device copies of host-resident A and B (ozaki2_dgemm)
     size_t in_ws_bytes = 0;
+    // pinned staging of the tables of ozaki2_encode_operands: a ring, so that a call waits only
+    // for the copy made kEncodeRing calls earlier
+    static constexpr int kEncodeRing = 4;
+    char* enc_stage[kEncodeRing] = {};
+    size_t enc_stage_bytes[kEncodeRing] = {};
+    cudaEvent_t enc_staged[kEncodeRing] = {};
+    int enc_next = 0;
 };
 
 namespace {
@@ -365,6 +372,10 @@ int ozaki2_destroy(ozaki2_handle_t handle) {
     for (auto& e : handle->ev)
         if (e) cudaEventDestroy(e);
     if (handle->staged) cudaEventDestroy(handle->staged);
+    for (int i = 0; i < ozaki2_context::kEncodeRing; ++i) {
+        if (handle->enc_staged[i]) cudaEventDestroy(handle->enc_staged[i]);
+        if (handle->enc_stage[i]) cudaFreeHost(handle->enc_stage[i]);
+    }
     clear_graphs(handle);
     if (handle->capture_stream) cudaStreamDestroy(handle->capture_stream);
     if (handle->stage) cudaFreeHost(handle->stage);
@@ -759,26 +770,31 @@ int ozaki2_encode_operands(ozaki2_handle_t handle, int count, ozaki2_operand* op
         }
     }
     const size_t tb = (size_t)encode_table_bytes(count, ops);
+    // the device copy of the tables lives in the workspace; earlier calls on this stream have
+    // read theirs before this call's copy lands (stream order)
     if ((rc = ensure_workspace(ctx, tb))) return rc;
-    if (!ctx->staged &&
-        cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming) != cudaSuccess)
+    const int slot = ctx->enc_next;
+    ctx->enc_next = (slot + 1) % ozaki2_context::kEncodeRing;
+    cudaEvent_t& ev = ctx->enc_staged[slot];
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
         return OZAKI2_ERROR_CUDA;
-    if (cudaEventSynchronize(ctx->staged) != cudaSuccess) return OZAKI2_ERROR_CUDA;
-    if (ctx->stage_bytes < tb) {
-        if (ctx->stage) cudaFreeHost(ctx->stage);
-        ctx->stage = nullptr;
-        ctx->stage_bytes = 0;
-        if (cudaMallocHost(&ctx->stage, tb) != cudaSuccess) {
+    if (cudaEventSynchronize(ev) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    if (ctx->enc_stage_bytes[slot] < tb) {
+        if (ctx->enc_stage[slot]) cudaFreeHost(ctx->enc_stage[slot]);
+        ctx->enc_stage[slot] = nullptr;
+        ctx->enc_stage_bytes[slot] = 0;
+        if (cudaMallocHost(&ctx->enc_stage[slot], tb) != cudaSuccess) {
             cudaGetLastError();
             return OZAKI2_ERROR_ALLOC;
         }
-        ctx->stage_bytes = tb;
+        ctx->enc_stage_bytes[slot] = tb;
     }
-    build_encode_tables(count, ops, ctx->scaling, ctx->stage);
+    char* host = ctx->enc_stage[slot];
+    build_encode_tables(count, ops, ctx->scaling, host);
     char* tables_dev = static_cast<char*>(ctx->ws);
-    if (cudaMemcpyAsync(tables_dev, ctx->stage, tb, cudaMemcpyHostToDevice, ctx->stream) !=
+    if (cudaMemcpyAsync(tables_dev, host, tb, cudaMemcpyHostToDevice, ctx->stream) !=
             cudaSuccess ||
-        cudaEventRecord(ctx->staged, ctx->stream) != cudaSuccess)
+        cudaEventRecord(ev, ctx->stream) != cudaSuccess)
         return OZAKI2_ERROR_CUDA;
     return launch_encode(count, ops, tables_dev, ctx->d_status, ctx->stream);
 }

@@ -159,9 +159,36 @@ __device__ __forceinline__ bool abs_words(uint32_t (&Y)[W]) {
     return m != 0;
 }
 
-// OutT = double (DGEMM) or float (SGEMM): C'' is rounded to 53 or 24 bits, then scaled.
+// Pair sums v_g = bias_g + sum_{l in g} c_l K_l from the residues of one entry: one multiply-add
+// per residue (the signed product wraps modulo 2^32 to the exact value, in [0, 2^25)).
+template <int N>
+__device__ __forceinline__ void pair_sums(const int (&cres)[N], const CrtTables& t,
+                                          uint32_t (&v)[(N + 1) / 2]) {
+#pragma unroll
+    for (int g = 0; g < (N + 1) / 2; ++g) {
+        v[g] = t.grp_bias[g];
+#pragma unroll
+        for (int l = 2 * g; l < 2 * g + 2 && l < N; ++l) v[g] += (uint32_t)cres[l] * t.K[l];
+    }
+}
+
+// c + K_lo b_lo + K_hi b_hi with K_lo, K_hi the unsigned 16-bit halves of `kpair` and b_lo, b_hi
+// the signed bytes 0, 1 (HI = false) or 2, 3 (HI = true) of `b`: the same pair sum in one
+// instruction (exact: the true value lies in [0, 2^25)).
+template <bool HI>
+__device__ __forceinline__ uint32_t dot2(uint32_t kpair, uint32_t b, uint32_t c) {
+    uint32_t d;
+    if constexpr (HI)
+        asm("dp2a.hi.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(kpair), "r"(b), "r"(c));
+    else
+        asm("dp2a.lo.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(kpair), "r"(b), "r"(c));
+    return d;
+}
+
+// OutT = double (DGEMM) or float (SGEMM): C'' is rounded to 53 or 24 bits, then scaled.  v: the
+// pair sums of the entry (pair_sums).
 template <int N, typename OutT>
-__device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
+__device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int ea, int fb,
                                           const CrtTables& t) {
     constexpr int W = crt_words(N);
     constexpr int G = (N + 1) / 2;
@@ -169,21 +196,16 @@ __device__ __forceinline__ OutT crt_value(const int (&cres)[N], int ea, int fb,
         if constexpr (sizeof(OutT) == 4) return __uint_as_float(0x7FC00000u);
         else return __longlong_as_double(0x7FF8000000000000ll);
     }
-    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^48 X / P (fixed point).  Per pair of
-    // moduli, v_g = bias_g + sum c_l K_l: one multiply-add per residue (the signed product wraps
-    // modulo 2^32 to the exact value, which lies in [0, 2^25)).
+    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^48 X / P (fixed point).
     uint64_t acc[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) acc[j] = 0;
     uint64_t S = 0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        uint32_t v = t.grp_bias[g];
+        S += (uint64_t)v[g] * t.R48[g];
 #pragma unroll
-        for (int l = 2 * g; l < 2 * g + 2 && l < N; ++l) v += (uint32_t)cres[l] * t.K[l];
-        S += (uint64_t)v * t.R48[g];
-#pragma unroll
-        for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.PG[g][j] * v;
+        for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.PG[g][j] * v[g];
     }
     uint32_t X[W];
     fold_columns<W>(acc, X);
@@ -330,19 +352,34 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
         const int i = i0 + il;
         const int ea = i < m ? sa[i] : 0;
         const int8_t* base = res + (int64_t)i * ldr + j0 + jq;
-        uint32_t wd[N];
+        constexpr int G = (N + 1) / 2;
+        // per pair of planes, the residues of the four entries interleaved: lo holds entries 0
+        // and 1 (bytes c_2g, c_2g+1 of each), hi entries 2 and 3
+        uint32_t lo[G], hi[G];
 #pragma unroll
-        for (int l = 0; l < N; ++l)
-            wd[l] = __ldg(reinterpret_cast<const unsigned int*>(base + (int64_t)l * plane));
+        for (int g = 0; g < G; ++g) {
+            const uint32_t w0 =
+                __ldg(reinterpret_cast<const unsigned int*>(base + (int64_t)(2 * g) * plane));
+            const uint32_t w1 =
+                2 * g + 1 < N ? __ldg(reinterpret_cast<const unsigned int*>(
+                                    base + (int64_t)(2 * g + 1) * plane))
+                              : 0u;
+            lo[g] = __byte_perm(w0, w1, 0x5140);
+            hi[g] = __byte_perm(w0, w1, 0x7362);
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = j0 + jq + q;
             OutT y = 0;
             if (i < m && j < n) {
-                int c[N];
+                uint32_t v[G];
 #pragma unroll
-                for (int l = 0; l < N; ++l) c[l] = (int)(int8_t)(uint8_t)(wd[l] >> (8 * q));
-                y = crt_value<N, OutT>(c, ea, sb[j], t);
+                for (int g = 0; g < G; ++g) {
+                    const uint32_t b = q < 2 ? lo[g] : hi[g];
+                    v[g] = (q & 1) ? dot2<true>(t.Kpair[g], b, t.grp_bias[g])
+                                   : dot2<false>(t.Kpair[g], b, t.grp_bias[g]);
+                }
+                y = crt_value<N, OutT>(v, ea, sb[j], t);
             }
             tile[jq + q][il] = y;
         }
@@ -359,7 +396,9 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
                 int c[N];
 #pragma unroll
                 for (int l = 0; l < N; ++l) c[l] = p[(int64_t)l * plane];
-                y = crt_value<N, OutT>(c, sa[i], fb, t);
+                uint32_t v[(N + 1) / 2];
+                pair_sums<N>(c, t, v);
+                y = crt_value<N, OutT>(v, sa[i], fb, t);
             }
             tile[lane][il] = y;
         }

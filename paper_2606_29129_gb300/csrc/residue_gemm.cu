@@ -918,11 +918,16 @@ uint64_t g_attr_grouped = 0, g_attr_aux = 0, g_attr_aux_grouped = 0, g_attr_pair
 
 }  // namespace
 
-static int chunk_blocks_of(int chunk_k) {
+// K blocks (of 64) between modular reductions: at most chunk_k / 64 (and at most 15: <= 960
+// products keep the fp32 accumulator exact), spread evenly over the same number of chunks, so
+// that no chunk is a short remainder (k = 1024: 8 + 8 blocks rather than 15 + 1).
+static int chunk_blocks_of(int chunk_k, int k_blocks) {
     int cb = chunk_k / BK;
     if (cb < 1) cb = 1;
-    if (cb > 15) cb = 15;  // <= 960 products between reductions keeps fp32 exact
-    return cb;
+    if (cb > 15) cb = 15;
+    if (k_blocks <= 0) return cb;
+    const int nchunks = (k_blocks + cb - 1) / cb;
+    return (k_blocks + nchunks - 1) / nchunks;
 }
 
 bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, int k_pad,
@@ -933,7 +938,7 @@ bool make_group_gemm_problem(GroupGemmProblem* g, int N, int m_pad, int n_pad, i
     if (!encode_planes(&g->ta, planes_a, N, geo.rows_a, geo.ld, BM) ||
         !encode_planes(&g->tb, planes_b, N, geo.rows_b, geo.ld, bn))
         return false;
-    const int cb = chunk_blocks_of(chunk_k);
+    const int cb = chunk_blocks_of(chunk_k, k_pad / BK);
     g->out = out;
     g->out_ld = n_pad;
     g->out_plane = (int64_t)m_pad * n_pad;
@@ -957,7 +962,7 @@ int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int to
                          g_attr_grouped) != cudaSuccess)
         return OZAKI2_ERROR_CUDA;
     GemmArgs a = {};
-    a.chunk_blocks = chunk_blocks_of(chunk_k);
+    a.chunk_blocks = 15;  // unused: each problem carries its own chunk
     a.status = status;
     a.limit_ns = limit_ns;
     a.ep = t;
@@ -1045,11 +1050,9 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
                         const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
                         int variant, cudaStream_t stream, unsigned long long limit_ns) {
     if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
-    int cb = chunk_k / BK;
-    if (cb < 1) cb = 1;
-    if (cb > 15) cb = 15;  // <= 960 products between reductions keeps fp32 exact
     GemmArgs a;
     a.k_blocks = k_pad / BK;
+    const int cb = chunk_blocks_of(chunk_k, a.k_blocks);
     a.chunk_blocks = cb;
     a.nchunks = a.k_blocks > 0 ? (a.k_blocks + cb - 1) / cb : 0;
     a.m_rows = m_pad;

@@ -1,13 +1,16 @@
 // scale.cu -- Step 2 scaling of Ozaki scheme II with the scale-invariant formula of Section 4
 // (eq. (proposed-mu)/(proposed-nu), Algorithm 2).
 //
-// Each line (row of op(A) or column of op(B)) gets a_norm = sum_h a_h^2 accumulated in the order
-// h = 0..len-1, one fused multiply-add rounded upward per term (every partial sum is an upper
-// bound, as Algorithm 2 requires), then log2(mu) = floor(w - t) from Algorithm 2.
+// Each line (row of op(A) or column of op(B)) gets a_norm = sum_h a_h^2 rounded upward (Section
+// 4), in a fixed order: blocks of kNormBlock = 256 consecutive terms, each summed from 0 with one
+// fused multiply-add rounded upward per term, then the block sums added in block order with
+// upward rounding.  Every partial sum is an upper bound, as Algorithm 2 requires, and the fixed
+// order keeps the shifts bit-identical to a sequential reference.  Then log2(mu) = floor(w - t)
+// from Algorithm 2.
 //
-// The kernel is bound by HBM reads of the matrix (8 bytes per element) and, on GB300, by the
-// FP64 FMA rate; the fixed summation order keeps the shifts bit-identical to a sequential
-// reference.
+// The kernels are bound by HBM reads of the matrix (8 bytes per element) and, on GB300, by the
+// FP64 FMA rate.  Lines of at most one block run one thread per line; longer lines are split
+// across the warps of a block (scale_split_kernel), each warp summing whole blocks.
 #include <float.h>
 
 #include "ozaki2_internal.h"
@@ -70,12 +73,22 @@ __device__ __forceinline__ int accu_line_exponent(uint64_t mb, unsigned* status)
     return ilogb(__longlong_as_double((long long)mb));
 }
 
-// Running state of one line: the squared norm (proposed and fast modes), the maximum |a| as a
-// double (fast mode) or as bits (accurate mode).
+constexpr int kNormBlock = 256;  // terms per block of the squared-norm sum
+
+// Running state of one line: the squared norm (proposed and fast modes) as the sum of the closed
+// blocks (total) and the open block (s), the maximum |a| as a double (fast mode) or as bits
+// (accurate mode).
 template <int SCALING>
 struct LineAcc {
-    double s = 0.0, mx = 0.0;
+    double s = 0.0, total = 0.0, mx = 0.0;
     uint64_t mb = 0;
+    // closes the open block: total += s, rounded upward (exact for the first block)
+    __device__ __forceinline__ void end_block() {
+        if (SCALING != OZAKI2_SCALING_ACCURATE) {
+            total = __dadd_ru(total, s);
+            s = 0.0;
+        }
+    }
     __device__ __forceinline__ void add(double v) {
         if (SCALING == OZAKI2_SCALING_ACCURATE) {
             const uint64_t b = (uint64_t)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
@@ -87,11 +100,12 @@ struct LineAcc {
     }
     __device__ __forceinline__ int result(float pprime, float delta, unsigned* status) {
         if (SCALING == OZAKI2_SCALING_ACCURATE) return accu_line_exponent(mb, status);
+        end_block();
         if (SCALING == OZAKI2_SCALING_FAST) {
-            if (isnan(s)) mx = s;  // fmax drops NaN; the norm keeps it
-            return alg1_shift(s, mx, pprime, delta, status);
+            if (isnan(total)) mx = total;  // fmax drops NaN; the norm keeps it
+            return alg1_shift(total, mx, pprime, delta, status);
         }
-        return alg2_shift(s, pprime, status);
+        return alg2_shift(total, pprime, status);
     }
 };
 
@@ -99,6 +113,7 @@ struct LineAcc {
 // consecutive doubles per step, so every load is coalesced.  Loads run two batches of 16 ahead
 // of the dependent FMA chain so that enough bytes are in flight with one thread per line.
 constexpr int kBatch = 16;  // loads per batch for doubles (twice as many for floats)
+static_assert(kNormBlock % (2 * kBatch) == 0, "batches must not straddle a norm block");
 
 // T = double (DGEMM) or float (SGEMM: every float is exactly a double, so the sums and the
 // shifts are those of the widened values).
@@ -125,6 +140,7 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
         }
 #pragma unroll
         for (int u = 0; u < kB; ++u) acc.add(to_double(a[u]));
+        if (((h + kB) & (kNormBlock - 1)) == 0) acc.end_block();
         if (!has_b) break;
         if (h + 2 * kB < full) {
 #pragma unroll
@@ -133,8 +149,12 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
         }
 #pragma unroll
         for (int u = 0; u < kB; ++u) acc.add(to_double(b[u]));
+        if (((h + 2 * kB) & (kNormBlock - 1)) == 0) acc.end_block();
     }
-    for (int h = full; h < len; ++h) acc.add(to_double(__ldg(p + (int64_t)h * ld)));
+    for (int h = full; h < len; ++h) {
+        acc.add(to_double(__ldg(p + (int64_t)h * ld)));
+        if (((h + 1) & (kNormBlock - 1)) == 0) acc.end_block();
+    }
     shifts[i] = acc.result(pprime, delta, status);
 }
 
@@ -190,6 +210,8 @@ __device__ __forceinline__ void scale_contiguous_warp(const T* __restrict__ X, i
         if (h0 + TL < len) load(h0 + TL);
         if (lane < nl) {
             for (int u = 0; u < cnt; ++u) acc.add(to_double(t[lane][u]));
+            // tiles start at multiples of TL, which divides kNormBlock
+            if (((h0 + cnt) & (kNormBlock - 1)) == 0) acc.end_block();
         }
         __syncwarp();
     }
@@ -234,6 +256,107 @@ struct ScaleSide {
     int lines;
     int* shifts;
 };
+
+// ---- lines longer than one block: the blocks of 32 lines split across the 8 warps of a block
+constexpr int kSplitWarps = 8;
+
+// Elements per tile row of the split kernel's transposes: 128 bytes.
+template <typename T>
+__host__ __device__ constexpr int split_tile() { return 128 / (int)sizeof(T); }
+
+// One block [hb, he) of the adjacent line i, summed in order into acc.
+template <int SCALING, typename T>
+__device__ __forceinline__ void adjacent_block(const T* __restrict__ X, int64_t ld, int i, int hb,
+                                               int he, LineAcc<SCALING>& acc) {
+    constexpr int kB = kBatch;  // loads in flight per thread (the split kernel has many warps)
+    const T* p = X + i;
+    int h = hb;
+    for (; h + kB <= he; h += kB) {
+        T a[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) a[u] = __ldg(p + (int64_t)(h + u) * ld);
+#pragma unroll
+        for (int u = 0; u < kB; ++u) acc.add(to_double(a[u]));
+    }
+    for (; h < he; ++h) acc.add(to_double(__ldg(p + (int64_t)h * ld)));
+}
+
+// One block [hb, he) of the contiguous lines line0 .. line0 + nl - 1, one line per lane, read in
+// coalesced 128-byte rows and transposed through the warp's tile t.
+template <int SCALING, typename T>
+__device__ __forceinline__ void contiguous_block(const T* __restrict__ X, int64_t ld, int nl,
+                                                 int line0, int hb, int he,
+                                                 T (*t)[split_tile<T>() + 1],
+                                                 LineAcc<SCALING>& acc) {
+    constexpr int TL = split_tile<T>();
+    static_assert(TL == 16 || TL == 32, "tile of 128 bytes");
+    constexpr int RPS = 32 / TL;  // rows copied per step of the warp: lane -> (row, column)
+    const int lane = threadIdx.x & 31;
+    const int rc = lane % TL, rr = lane / TL;
+    for (int h0 = hb; h0 < he; h0 += TL) {
+        const int cnt = min(TL, he - h0);
+#pragma unroll 8
+        for (int r = 0; r < 32; r += RPS) {
+            const int row = r + rr, h = h0 + rc;
+            t[row][rc] = (row < nl && h < he) ? __ldg(X + (int64_t)(line0 + row) * ld + h) : (T)0;
+        }
+        __syncwarp();
+        if (lane < nl)
+            for (int u = 0; u < cnt; ++u) acc.add(to_double(t[lane][u]));
+        __syncwarp();
+    }
+}
+
+// 32 lines of one side per block; warp w sums blocks w, w + 8, ... of every line; after each
+// round of 8 blocks warp 0 adds the block sums to the lines' totals in block order, rounded
+// upward.  The result is the blocked sum of LineAcc, bit for bit.
+template <int SCALING, typename T>
+__global__ void __launch_bounds__(32 * kSplitWarps, 2) scale_split_kernel(ScaleSide a, ScaleSide b,
+                                                                       int groups_a, int len,
+                                                                       float pprime, float delta,
+                                                                       unsigned* status) {
+    static_assert(SCALING != OZAKI2_SCALING_ACCURATE, "accurate mode takes no squared norm");
+    __shared__ T tile[kSplitWarps][32][split_tile<T>() + 1];
+    __shared__ double part[kSplitWarps][32];
+    __shared__ double pmax[kSplitWarps][32];
+    const bool side_b = (int)blockIdx.x >= groups_a;
+    const ScaleSide& S = side_b ? b : a;
+    const T* X = static_cast<const T*>(S.X);
+    const int line0 = ((int)blockIdx.x - (side_b ? groups_a : 0)) * 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nl = min(32, S.lines - line0);
+    const bool adjacent = S.es != 1 || S.ls == 1;
+    const int nblocks = (len + kNormBlock - 1) / kNormBlock;
+    LineAcc<SCALING> run;    // warp 0: the folded total and the line maximum
+    double wmax = 0.0;       // this warp's maximum |a| of the line (fast mode)
+    for (int r0 = 0; r0 < nblocks; r0 += kSplitWarps) {
+        const int blk = r0 + warp;
+        LineAcc<SCALING> acc;
+        if (blk < nblocks) {
+            const int hb = blk * kNormBlock, he = min(hb + kNormBlock, len);
+            if (adjacent) {
+                if (lane < nl) adjacent_block<SCALING, T>(X, S.es, line0 + lane, hb, he, acc);
+            } else {
+                contiguous_block<SCALING, T>(X, S.ls, nl, line0, hb, he, tile[warp], acc);
+            }
+        }
+        part[warp][lane] = acc.s;
+        if (SCALING == OZAKI2_SCALING_FAST) wmax = fmax(wmax, acc.mx);
+        __syncthreads();
+        if (warp == 0) {
+            for (int w = 0; w < kSplitWarps && r0 + w < nblocks; ++w)
+                run.total = __dadd_ru(run.total, part[w][lane]);
+        }
+        __syncthreads();
+    }
+    if (SCALING == OZAKI2_SCALING_FAST) {
+        pmax[warp][lane] = wmax;
+        __syncthreads();
+        if (warp == 0)
+            for (int w = 0; w < kSplitWarps; ++w) run.mx = fmax(run.mx, pmax[w][lane]);
+    }
+    if (warp == 0 && lane < nl) S.shifts[line0 + lane] = run.result(pprime, delta, status);
+}
 
 template <int SCALING, typename T>
 __global__ void __launch_bounds__(128) scale_pair_kernel(ScaleSide a, ScaleSide b, int blocks_a,
@@ -302,6 +425,14 @@ template <int SCALING>
 static void launch_scale_t(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, float pprime, float delta, int* shifts, unsigned* status,
                            cudaStream_t stream) {
+    if (SCALING != OZAKI2_SCALING_ACCURATE && len > kNormBlock) {  // long lines: split
+        const ScaleSide side{X, line_stride, elem_stride, lines, shifts};
+        const ScaleSide none{X, line_stride, elem_stride, 0, shifts};
+        constexpr int kS = SCALING == OZAKI2_SCALING_ACCURATE ? OZAKI2_SCALING_PROPOSED : SCALING;
+        scale_split_kernel<kS, double><<<(lines + 31) / 32, 32 * kSplitWarps, 0, stream>>>(
+            side, none, (lines + 31) / 32, len, pprime, delta, status);
+        return;
+    }
     if (elem_stride != 1 || line_stride == 1) {  // lines adjacent
         scale_adjacent_kernel<SCALING><<<(lines + 31) / 32, 32, 0, stream>>>(
             X, elem_stride, lines, len, pprime, delta, shifts, status);
@@ -333,6 +464,16 @@ template <typename T>
 static void launch_scale_pair_t(const ScaleSide& sa, const ScaleSide& sb, int blocks_a, int grid,
                                 int len, float pprime, float delta, unsigned* status,
                                 cudaStream_t stream, int scaling) {
+    if (scaling != OZAKI2_SCALING_ACCURATE && len > kNormBlock) {  // long lines: split
+        const int ga = (sa.lines + 31) / 32, gb = (sb.lines + 31) / 32;
+        if (scaling == OZAKI2_SCALING_FAST)
+            scale_split_kernel<OZAKI2_SCALING_FAST, T><<<ga + gb, 32 * kSplitWarps, 0, stream>>>(
+                sa, sb, ga, len, pprime, delta, status);
+        else
+            scale_split_kernel<OZAKI2_SCALING_PROPOSED, T>
+                <<<ga + gb, 32 * kSplitWarps, 0, stream>>>(sa, sb, ga, len, pprime, delta, status);
+        return;
+    }
     if (scaling == OZAKI2_SCALING_FAST)
         scale_pair_kernel<OZAKI2_SCALING_FAST, T><<<grid, 128, 0, stream>>>(
             sa, sb, blocks_a, len, pprime, delta, status);

@@ -116,6 +116,7 @@ void build(int N, ModTables& t) {
             const uint64_t cf = prod / (uint64_t)kModuli[l];
             t.crt.K[l] = (uint32_t)(cf * (uint64_t)t.inverses[l] % prod);
         }
+        t.crt.Kpair[g] = t.crt.K[l0] | (l1 - l0 > 1 ? t.crt.K[l0 + 1] << 16 : 0u);
         t.crt.grp_bias[g] = (uint32_t)(256 * prod);  // >= 128 sum K_l: the group sum stays >= 0
         Words PG{1};
         for (int j = 0; j < N; ++j)

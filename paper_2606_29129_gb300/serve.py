@@ -53,6 +53,9 @@ class Request:
     B: object = None              # host column-major storage (n, k) float64
     a_key: object = None          # identity of A for the residue cache (None: not reused)
     b_key: object = None          # identity of B
+    out: object = None            # caller's page-locked host buffer (n, m) float64 for the
+                                  # result, or None (the executor takes one from its pool)
+    buffer: object = None         # the page-locked buffer C lives in
     arrival: float = 0.0
     num_moduli: int = 0
     admitted: float | None = None
@@ -106,6 +109,7 @@ class Server:
             req.arrival = self.clock()
         req.num_moduli = autotune.choose_n(self.calibration, req.k, req.target, self.default_n)
         need = self.ex.workspace_bytes([req])
+        req.dev["ws_bytes"] = need
         too_large = getattr(self.ex, "too_large", None)
         if req.io_bytes > self.io_budget or need > self.ex.slot_workspace or \
                 (too_large is not None and too_large(req)):
@@ -154,11 +158,15 @@ class Server:
                 continue
             batch = []
             work = 0.0
-            while self.admitted and len(batch) < self.max_batch and \
-                    self.ex.workspace_bytes(batch + [self.admitted[0]]) <= self.ex.slot_workspace:
+            ws = 0   # the sum of the requests' own workspaces bounds the batch's from above
+            while self.admitted and len(batch) < self.max_batch:
                 nxt = self.admitted[0]
+                need = nxt.dev.get("ws_bytes") or self.ex.workspace_bytes([nxt])
+                if ws + need > self.ex.slot_workspace:
+                    break
                 if batch and self.max_batch_flops and work + nxt.flops > self.max_batch_flops:
                     break
+                ws += need
                 work += nxt.flops
                 batch.append(self.admitted.popleft())
             if not batch:
@@ -174,6 +182,38 @@ class Server:
         while not self.idle():
             if not self.step() and poll_sleep:
                 time.sleep(poll_sleep)
+
+
+class ResultPool:
+    """Reusable page-locked host buffers for results, in power-of-two buckets of float64
+    elements.  Page-locking host memory costs more than the emulated product of a mid-size
+    request, so a server hands each result buffer back to the pool once the client has consumed
+    the result (GpuExecutor.recycle)."""
+
+    def __init__(self, alloc=None):
+        self.free = collections.defaultdict(list)
+        self.allocated = 0
+        self._alloc = alloc
+
+    @staticmethod
+    def bucket(numel: int) -> int:
+        return 1 << max(0, (max(numel, 1) - 1).bit_length())
+
+    def take(self, numel: int):
+        b = self.bucket(numel)
+        if self.free[b]:
+            return self.free[b].pop()
+        self.allocated += 1
+        return self._alloc(b)
+
+    def give(self, buf, numel: int):
+        self.free[self.bucket(numel)].append(buf)
+
+    def prewarm(self, numel: int, count: int):
+        b = self.bucket(numel)
+        while len(self.free[b]) < count:
+            self.allocated += 1
+            self.free[b].append(self._alloc(b))
 
 
 class CacheEntry:
@@ -256,13 +296,15 @@ class GpuExecutor:
     ozaki2_dgemm_grouped."""
 
     def __init__(self, slots: int = 2, slot_workspace_bytes: int = 8 << 30, device: int = 0,
-                 cache_bytes: int = 0):
+                 cache_bytes: int = 0, result_pool: ResultPool | None = None):
         import torch
 
         from . import ozaki2 as oz
 
         self.oz = oz
         self.torch = torch
+        self.results = result_pool or ResultPool(
+            lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True))
         self.device = torch.device("cuda", device)
         self.slot_workspace = slot_workspace_bytes
         self._slots = []
@@ -332,8 +374,29 @@ class GpuExecutor:
             r.dev["uploaded"] = ev
         self.stats["upload_bytes"] += 8 * (r.m * r.k + r.k * r.n)
         # the result is written by the CRT kernel straight into page-locked host memory
-        r.dev["host_C"] = torch.empty((r.n, r.m), dtype=torch.float64, pin_memory=True)
+        r.dev["host_C"] = self._result_buffer(r)
         return True
+
+    def _result_buffer(self, r: Request):
+        """The caller's page-locked result buffer, else one from the result pool."""
+        torch = self.torch
+        if r.out is not None:
+            if not (isinstance(r.out, torch.Tensor) and r.out.is_pinned() and
+                    r.out.dtype == torch.float64 and r.out.is_contiguous() and
+                    r.out.numel() >= r.m * r.n):
+                raise ValueError("Request.out must be a contiguous page-locked float64 tensor "
+                                 "of at least m * n elements")
+            r.buffer = r.out
+        else:
+            r.buffer = self.results.take(r.m * r.n)
+        return r.buffer
+
+    def recycle(self, r: Request):
+        """Hands a finished request's pool buffer back (its C is no longer valid after this)."""
+        if r.buffer is not None and r.out is None:
+            self.results.give(r.buffer, r.m * r.n)
+        r.buffer = None
+        r.C = None
 
     def _admit_cached(self, r: Request):
         torch, oz, cache = self.torch, self.oz, self.cache
@@ -385,7 +448,7 @@ class GpuExecutor:
                 self.stats["encoded_operands"] += len(fresh)
                 del keep   # the allocator reuses these bytes only after the upload stream's work
         r.dev["enc"] = entries
-        r.dev["host_C"] = torch.empty((r.n, r.m), dtype=torch.float64, pin_memory=True)
+        r.dev["host_C"] = self._result_buffer(r)
         return True
 
     def launch(self, slot: int, reqs):
@@ -440,7 +503,7 @@ class GpuExecutor:
         self.stats["batch_ms"] += start.elapsed_time(end)
         self.stats["batches"] += 1
         for r in reqs:
-            r.C = r.dev["host_C"].numpy()
+            r.C = r.dev["host_C"].view(-1)[: r.m * r.n].view(r.n, r.m).numpy()
             self.stats["result_bytes"] += 8 * r.m * r.n
 
     def release(self, r: Request):

@@ -77,3 +77,15 @@ def test_tune_grouped_tiles_keeps_automatic_when_not_beaten(monkeypatch):
     monkeypatch.setattr(autotune, "_time_ms", lambda call, reps: 1.0 if not h.rules else 2.0)
     res = autotune.tune_grouped_tiles(lambda: None, h)
     assert res["rules"] == [] and h.rules == [] and res["best_ms"] == 1.0
+
+
+def test_choose_n_margin_and_table_file(tmp_path):
+    import json
+
+    table = {3: {"k": 512, "cublas": 1e-11, "N": {13: 5e-10, 14: 2e-11, 15: 9e-12, 16: 1e-14}}}
+    assert autotune.choose_n(table, 500, margin=8.0) == 16     # 9e-12 > 1e-11 / 8
+    assert autotune.choose_n(table, 500, target=1e-13, margin=8.0) == 16
+    path = tmp_path / "cal.json"
+    path.write_text(json.dumps({"table": autotune.table_to_json(table)}))
+    assert autotune.load_calibration(str(path)) == table
+    assert autotune.load_calibration(str(tmp_path / "missing.json")) is None

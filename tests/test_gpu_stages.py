@@ -49,6 +49,29 @@ def test_scale_matches_oracle(oz, orc, trans, shape, phi):
     assert np.array_equal(f_ref, e_ref)
 
 
+@pytest.mark.parametrize("trans", ["N", "T"])
+@pytest.mark.parametrize("shape", [(40, 4097), (70, 6000), (33, 2304)])
+@pytest.mark.parametrize("mode", ["proposed", "fast"])
+def test_scale_long_lines_match_oracle(oz, orc, trans, shape, mode):
+    """Lines of many norm blocks (k > 2048: more than one round of the warps that split a line's
+    blocks), both memory layouts, both scalings that take the squared norm."""
+    lines, k = shape
+    N = 16
+    A = synthetic.paper_matrix(lines, k, 2.0, 7 * k) if trans == "N" else \
+        synthetic.paper_matrix(k, lines, 2.0, 7 * k)
+    h = oz.Handle()
+    omode = orc.PROPOSED_MODE
+    if mode == "fast":
+        h.set_option(oz.OPT_SCALING, oz.SCALING_FAST)
+        omode = orc.FAST_MODE
+    ld = A.shape[-1]
+    e_ref = orc.shifts_mode(A, lines, k, N, omode, side=0, trans=trans, ld=ld)
+    assert np.array_equal(_gpu.shifts_a(oz, A, lines, k, N, trans, ld, handle=h), e_ref)
+    tb = "T" if trans == "N" else "N"
+    f_ref = orc.shifts_mode(A, lines, k, N, omode, side=1, trans=tb, ld=ld)
+    assert np.array_equal(_gpu.shifts_b(oz, A, k, lines, N, tb, ld, handle=h), f_ref)
+
+
 @pytest.mark.parametrize("N", [2, 8, 20])
 @pytest.mark.parametrize("alpha", [2.0**40, 2.0**-40, 3.7e20, 3.7e-20, 1e-160])
 def test_scale_extreme_magnitudes(oz, orc, N, alpha):

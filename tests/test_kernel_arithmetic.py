@@ -87,3 +87,42 @@ def test_crt_pair_groups_exact(N):
             assert -P // 2 <= Y < P // 2
         else:                                              # near a tie: one correction at most
             assert -P <= Y < P
+
+
+def _byte_perm(x, y, s):
+    """The byte permute of the CUDA ISA: result byte i is byte (nibble i of s) of y:x."""
+    src = [(x >> (8 * b)) & 0xFF for b in range(4)] + [(y >> (8 * b)) & 0xFF for b in range(4)]
+    return sum(src[(s >> (4 * i)) & 7] << (8 * i) for i in range(4))
+
+
+def _dp2a(a, b, c, hi):
+    """dp2a.{lo,hi}.u32.s32: c + a.h0 * b.byte(0 or 2) + a.h1 * b.byte(1 or 3), modulo 2^32, with
+    the halves of a unsigned and the bytes of b signed."""
+    sb = [((b >> (8 * i)) & 0xFF) - (256 if (b >> (8 * i)) & 0x80 else 0) for i in range(4)]
+    h0, h1 = a & 0xFFFF, a >> 16
+    k = 2 if hi else 0
+    return (c + h0 * sb[k] + h1 * sb[k + 1]) & 0xFFFFFFFF
+
+
+@pytest.mark.parametrize("N", range(2, 21))
+def test_crt_pair_sums_by_byte_permute_and_dot_product(N):
+    """The reconstruction reads four entries' residues per plane in one 32-bit word, interleaves
+    the words of the two planes of a pair with byte permutes (0x5140: entries 0 and 1, 0x7362:
+    entries 2 and 3) and forms each pair sum with one two-way dot product of the packed
+    constants K_2g | K_2g+1 << 16: the same v_g as the residue-by-residue sum."""
+    ps, P, q, K, tab = pair_tables(N)
+    rng = random.Random(100 + N)
+    for _ in range(200):
+        c = [[rng.randint(-128, 127) for _ in range(4)] for _ in range(N)]  # c[l][entry]
+        words = [sum((c[l][e] & 0xFF) << (8 * e) for e in range(4)) for l in range(N)]
+        for g in tab:
+            ls = g["ls"]
+            assert all(0 <= K[l] < 1 << 16 for l in ls)
+            kpair = K[ls[0]] | ((K[ls[1]] << 16) if len(ls) > 1 else 0)
+            w0 = words[ls[0]]
+            w1 = words[ls[1]] if len(ls) > 1 else 0
+            lo, hi = _byte_perm(w0, w1, 0x5140), _byte_perm(w0, w1, 0x7362)
+            for e in range(4):
+                want = (g["bias"] + sum(c[l][e] * K[l] for l in ls)) & 0xFFFFFFFF
+                got = _dp2a(kpair, lo if e < 2 else hi, g["bias"], e & 1)
+                assert got == want

@@ -215,3 +215,17 @@ def test_batch_work_cap():
         srv.submit(make(i))
     srv.run_until_idle()
     assert [len(b["reqs"]) for b in ex.batches] == [3, 3, 1]
+
+
+def test_result_pool_reuses_buffers_by_bucket():
+    from paper_2606_29129_gb300.serve import ResultPool
+
+    made = []
+    pool = ResultPool(lambda n: made.append(n) or ("buf", len(made), n))
+    a = pool.take(1000)              # bucket 1024
+    assert a[2] == 1024 and pool.allocated == 1
+    pool.give(a, 1000)
+    assert pool.take(900) is a       # same bucket: reused, nothing allocated
+    assert pool.take(1025)[2] == 2048 and pool.allocated == 2
+    pool.prewarm(64, 3)
+    assert len(pool.free[64]) == 3 and pool.allocated == 5
