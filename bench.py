@@ -406,9 +406,10 @@ def run_gpu(args, world, rank, local):
         # flops per second per SM clock: compares runs taken at different power-capped clocks
         roofline["tflops_per_ghz"] = achieved / (clk["sm_mhz"] / 1e3)
     extra = {}
-    if rank == 0:
+    if rank == 0 and not args.profile_step:
         extra = accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np)
-    e2e = measure_e2e(args, oz, h, A, B, m, n, k, N, torch, gemm) if rank == 0 else None
+    e2e = (measure_e2e(args, oz, h, A, B, m, n, k, N, torch, gemm)
+           if rank == 0 and not args.profile_step else None)
     if rank != 0:
         return
     square = m == n == k
@@ -1023,6 +1024,9 @@ def main():
     ap.add_argument("--gemm-traffic", type=float, default=None,
                     help="DRAM bytes per residue-GEMM launch from an ncu capture, if current")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="only the timed steps (no cuBLAS, accuracy, CPU or e2e legs): for "
+                         "launch lists under a profiler")
     ap.add_argument("--batched", action="store_true",
                     help="the batched workload (grouped call) instead of the benchmark")
     ap.add_argument("--batch", type=int, default=512)

@@ -83,6 +83,10 @@ extern "C" {
                                      undefined.  A bound shorter than the kernel needs makes every
                                      call time out; tests use it to exercise that path.  Graphs
                                      of grouped calls are keyed on it. */
+#define OZAKI2_OPT_GROUP_M 6      /* tile order of the single-problem residue GEMM: the number of
+                                     m-tiles that sweep the n-tiles together (so that the CTAs
+                                     running at the same time share A and B panels in L2); 0
+                                     (default) = 16, else 1..1024.  Results do not depend on it. */
 #define OZAKI2_SCALING_PROPOSED 0 /* Algorithm 2 (Section 4): scale-invariant, CRT bound by
                                      construction */
 #define OZAKI2_SCALING_FAST 1     /* Algorithm 1 (Section 2.3): the original fast mode, kept for
@@ -242,7 +246,9 @@ int ozaki2_dgemm_grouped(ozaki2_handle_t handle, int count, const ozaki2_problem
  *
  * side 'A' encodes the rows of op(A) (lines = m), side 'B' the columns of op(B) (lines = n),
  * each of length k; trans, X and ld are as transA, A, lda (or transB, B, ldb) of ozaki2_dgemm
- * (device memory, or host memory the device can address, read in place).  `data` is a
+ * (device memory, or host memory the device can address: like ozaki2_dgemm, the handle first
+ * copies a host-resident X into a device buffer it allocates and keeps, or reads it in place
+ * when a workspace was set with ozaki2_set_workspace).  `data` is a
  * caller-owned device buffer of ozaki2_operand_bytes(side, lines, k, num_moduli) bytes, 256-byte
  * aligned; ozaki2_encode_operands writes it and sets `scaling` to the handle's scaling mode. */
 typedef struct ozaki2_operand {

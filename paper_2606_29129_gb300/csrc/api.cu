@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -19,6 +20,7 @@ struct ozaki2_context {
     bool user_ws = false;
     int chunk_k = 960;             // products accumulated between modular reductions
     int gemm_variant = OZAKI2_GEMM_AUTO;
+    int group_m = 0;               // m-tiles per group of the residue-GEMM tile order (0: 16)
     int scaling = OZAKI2_SCALING_PROPOSED;  // Algorithm 2, or Algorithm 1 (original fast mode)
     unsigned long long wait_limit_ns = ozaki2::kDefaultWaitLimitNs;  // residue-GEMM wait bound
     ozaki2::TileRules tiles;       // grouped calls: tile width and K chunk by size class
@@ -49,6 +51,10 @@ struct ozaki2_context {
     size_t enc_stage_bytes[kEncodeRing] = {};
     cudaEvent_t enc_staged[kEncodeRing] = {};
     int enc_next = 0;
+    // pipelined host-operand path of ozaki2_dgemm: a second stream and its events
+    cudaStream_t side = nullptr;
+    static constexpr int kPipeEvents = 12;
+    cudaEvent_t pipe_ev[kPipeEvents] = {};
 };
 
 namespace {
@@ -165,7 +171,7 @@ int ensure_workspace(ozaki2_context* ctx, size_t bytes) {
 struct Layout {
     int64_t m_pad, n_pad, k_pad;
     PlaneGeom geo;  // stored extent of the residue planes (no padding rows beyond one TMA box)
-    size_t off_e, off_f, off_pa, off_pb, off_res, total;
+    size_t off_e, off_f, off_pa, off_pb, off_res, off_part, total;
 };
 
 Layout make_layout(int m, int n, int k, int N) {
@@ -185,6 +191,7 @@ Layout make_layout(int m, int n, int k, int N) {
     L.off_pa = take((size_t)2 * N * L.geo.rows_a * L.geo.ld);
     L.off_pb = take((size_t)2 * N * L.geo.rows_b * L.geo.ld);
     L.off_res = take((size_t)N * L.m_pad * L.n_pad);
+    L.off_part = take(scale_partials_bytes(m + n, k));  // norm-block sums of long lines
     L.total = off;
     return L;
 }
@@ -243,6 +250,144 @@ int ensure_input_stage(ozaki2_context* ctx, size_t bytes) {
     return OZAKI2_SUCCESS;
 }
 
+// Host-resident operands, pipelined over column blocks of op(B) (proposed or fast scaling, no
+// caller workspace, op(B) = B so that its columns are contiguous, n of at least 2 blocks).
+// Under these scalings a column's shift depends on that column alone (eq. (proposed-nu)), so the
+// columns of op(B) can be scaled, converted and multiplied block by block: stream S (the
+// handle's) stages A, scales and converts it, then per block scales and converts B_j and runs
+// its residue GEMMs; a second stream stages the blocks of B over the link once A is in, and runs
+// each block's reconstruction (which writes C over the link when C is in host memory) while the
+// next block's GEMMs run.  Every step computes what the unblocked path computes, so the result
+// is the same bits.
+constexpr int kPipeMinBlock = 2048;
+
+bool pipeline_applies(const ozaki2_context* ctx, char transB, int n, const void* A,
+                      const void* B, const void* C) {
+    if (ctx->user_ws || ctx->scaling == OZAKI2_SCALING_ACCURATE || !is_notrans(transB))
+        return false;
+    if (n < 2 * kPipeMinBlock) return false;
+    return host_resident(A) || host_resident(B) || host_resident(C);
+}
+
+int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, double alpha,
+                    const void* A, int lda, const void* B, int ldb, double beta, void* C, int ldc,
+                    int N, bool f32, const Layout& L, const ModTables* T) {
+    int rc;
+    cudaStream_t S = ctx->stream;
+    if (!ctx->side &&
+        cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    for (auto& e : ctx->pipe_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+    cudaStream_t S2 = ctx->side;
+    const size_t esz = f32 ? 4 : 8;
+    // column blocks: multiples of 256 columns, at most 4
+    int nb = n / (2 * kPipeMinBlock) >= 2 ? 4 : 2;
+    const int64_t blk = ((int64_t)(n + nb - 1) / nb + 255) / 256 * 256;
+    nb = (int)((n + blk - 1) / blk);
+    if (nb > 4) return OZAKI2_ERROR_CUDA;  // not reached: blk >= n / 4
+
+    // staging buffer: A (when host-resident), then the blocks of B
+    const bool host_a = host_resident(A), host_b = host_resident(B);
+    const int acols = is_notrans(transA) ? k : m, arows = is_notrans(transA) ? m : k;
+    const size_t a_span = ((size_t)lda * (size_t)(acols - 1) + (size_t)arows) * esz;
+    const size_t a_room = host_a ? (size_t)round_up((int64_t)a_span, 256) : 0;
+    size_t b_room = 0;
+    for (int j = 0; j < nb && host_b; ++j) {
+        const int64_t cols = std::min<int64_t>(blk, n - j * blk);
+        b_room += (size_t)round_up((int64_t)(((size_t)ldb * (cols - 1) + k) * esz), 256);
+    }
+    if (a_room + b_room && (rc = ensure_input_stage(ctx, a_room + b_room))) return rc;
+    char* stage = static_cast<char*>(ctx->in_ws);
+    cudaEvent_t ev_start = ctx->pipe_ev[0], ev_a = ctx->pipe_ev[1], ev_done = ctx->pipe_ev[2];
+    cudaEvent_t* ev_b = ctx->pipe_ev + 3;   // B block j staged (j < 4)
+    cudaEvent_t* ev_g = ctx->pipe_ev + 7;   // residue GEMMs of block j done (j < 4)
+
+    char* ws = static_cast<char*>(ctx->ws);
+    int* e = reinterpret_cast<int*>(ws + L.off_e);
+    int* f = reinterpret_cast<int*>(ws + L.off_f);
+    char* pa = ws + L.off_pa;
+    char* pb = ws + L.off_pb;
+    int8_t* res = reinterpret_cast<int8_t*>(ws + L.off_res);
+    double* part = reinterpret_cast<double*>(ws + L.off_part);
+    const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
+
+    // S2 starts after the work already queued on S (earlier calls may still read the buffers)
+    if (cudaEventRecord(ev_start, S) != cudaSuccess || cudaStreamWaitEvent(S2, ev_start, 0) !=
+                                                           cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    // A: staged on S, then scaled and converted
+    if (host_a) {
+        if ((rc = cuda_rc(launch_stage_in(stage, A, a_span, ctx->num_sms, S)))) return rc;
+        A = stage;
+    }
+    if (cudaEventRecord(ev_a, S) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    int64_t als, aes;
+    rows_of_op(transA, lda, &als, &aes);
+    // (the pair launcher with no columns of op(B): it takes FP32 inputs as well)
+    if ((rc = cuda_rc(launch_scale_pair(A, als, aes, m, B, 0, 1, 0, k, pp, T->delta, e, f,
+                                        ctx->d_status, S, ctx->scaling, f32, part))) ||
+        (rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, L.geo.rows_a, L.geo.ld,
+                                     ctx->d_status, S, f32, false))))
+        return rc;
+    // B blocks: staged on S2 once A is in (A goes first over the link)
+    const char* bsrc[4];
+    if (cudaStreamWaitEvent(S2, ev_a, 0) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    {
+        char* p = stage + a_room;
+        for (int j = 0; j < nb; ++j) {
+            const int64_t c0 = j * blk, cols = std::min<int64_t>(blk, n - c0);
+            const char* src = static_cast<const char*>(B) + (size_t)c0 * ldb * esz;
+            if (host_b) {
+                const size_t span = ((size_t)ldb * (cols - 1) + k) * esz;
+                if ((rc = cuda_rc(launch_stage_in(p, src, span, ctx->num_sms, S2)))) return rc;
+                bsrc[j] = p;
+                p += round_up((int64_t)span, 256);
+            } else {
+                bsrc[j] = src;
+            }
+            if (cudaEventRecord(ev_b[j], S2) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        }
+    }
+    // per block: scale and convert B_j, residue GEMMs (S); reconstruction (S2)
+    int64_t pb_off = 0;
+    for (int j = 0; j < nb; ++j) {
+        const int64_t c0 = j * blk, cols = std::min<int64_t>(blk, n - c0);
+        const int cols_pad = (int)round_up(cols, OZAKI2_ROWS_ALIGN_B);
+        const PlaneGeom geo{L.geo.rows_a, (int)std::max<int64_t>(cols, 256), L.geo.ld,
+                            L.geo.out_rows, (int)round_up(cols, 32)};
+        char* pbj = pb + pb_off;   // (2 ld bytes per row: a multiple of 128, as TMA needs)
+        pb_off += (int64_t)2 * N * geo.rows_b * geo.ld;
+        if (cudaStreamWaitEvent(S, ev_b[j], 0) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        // columns of op(B) = B: line stride ldb, elements contiguous
+        if ((rc = cuda_rc(launch_scale_pair(A, 0, 1, 0, bsrc[j], ldb, 1, (int)cols, k, pp,
+                                            T->delta, e, f + c0, ctx->d_status, S, ctx->scaling,
+                                            f32, part))) ||
+            (rc = cuda_rc(launch_convert(bsrc[j], ldb, 1, (int)cols, k, f + c0, T->conv, pbj,
+                                         geo.rows_b, geo.ld, ctx->d_status, S, f32, false))))
+            return rc;
+        if ((rc = launch_residue_gemm(N, (int)L.m_pad, cols_pad, (int)L.k_pad, geo, pa, pbj,
+                                      res + c0, T->epi, ctx->d_status, ctx->num_sms,
+                                      ctx->chunk_k, ctx->gemm_variant, S, ctx->wait_limit_ns,
+                                      L.n_pad, L.m_pad * L.n_pad, ctx->group_m)))
+            return rc;
+        if (cudaEventRecord(ev_g[j], S) != cudaSuccess ||
+            cudaStreamWaitEvent(S2, ev_g[j], 0) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+        char* Cj = static_cast<char*>(C) + (size_t)c0 * ldc * esz;
+        if ((rc = cuda_rc(launch_crt(res + c0, L.n_pad, L.m_pad * L.n_pad, m, (int)cols, e,
+                                     f + c0, alpha, beta, Cj, ldc, *T, ctx->d_status, S2, f32,
+                                     true))))
+            return rc;
+    }
+    // the call completes on S
+    if (cudaEventRecord(ev_done, S2) != cudaSuccess || cudaStreamWaitEvent(S, ev_done, 0) !=
+                                                           cudaSuccess)
+        return OZAKI2_ERROR_CUDA;
+    return OZAKI2_SUCCESS;
+}
+
 int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m, int n, int k,
                double alpha, const void* A, int lda, const void* B, int ldb, double beta,
                void* C, int ldc, int N, bool f32 = false) {
@@ -280,6 +425,10 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     void* pb = ws + L.off_pb;
     int8_t* res = reinterpret_cast<int8_t*>(ws + L.off_res);
     cudaStream_t st = ctx->stream;
+
+    if (!ctx->timing && pipeline_applies(ctx, transB, n, A, B, C))
+        return dgemm_pipelined(ctx, transA, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, N, f32,
+                               L, T);
 
     // Host-resident A or B (page-locked, or pageable on a coherent link) are first copied into
     // device memory by a kernel, so the scaling and the conversion, which each read the inputs,
@@ -320,8 +469,9 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
             return rc;
     } else {
         const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
+        double* part = reinterpret_cast<double*>(ws + L.off_part);
         if ((rc = cuda_rc(launch_scale_pair(A, als, aes, m, B, bls, bes, n, k, pp, T->delta, e,
-                                            f, ctx->d_status, st, ctx->scaling, f32))))
+                                            f, ctx->d_status, st, ctx->scaling, f32, part))))
             return rc;
     }
     mark(1);
@@ -335,7 +485,8 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     mark(2);
     if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, L.geo, pa, pb, res,
                                   T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
-                                  ctx->gemm_variant, st, ctx->wait_limit_ns)))
+                                  ctx->gemm_variant, st, ctx->wait_limit_ns, 0, 0,
+                                  ctx->group_m)))
         return rc;
     mark(3);
     rc = cuda_rc(launch_crt(res, L.n_pad, L.m_pad * L.n_pad, m, n, e, f, alpha, beta, C, ldc, *T,
@@ -372,6 +523,9 @@ int ozaki2_destroy(ozaki2_handle_t handle) {
     for (auto& e : handle->ev)
         if (e) cudaEventDestroy(e);
     if (handle->staged) cudaEventDestroy(handle->staged);
+    for (auto& e : handle->pipe_ev)
+        if (e) cudaEventDestroy(e);
+    if (handle->side) cudaStreamDestroy(handle->side);
     for (int i = 0; i < ozaki2_context::kEncodeRing; ++i) {
         if (handle->enc_staged[i]) cudaEventDestroy(handle->enc_staged[i]);
         if (handle->enc_stage[i]) cudaFreeHost(handle->enc_stage[i]);
@@ -419,6 +573,10 @@ int ozaki2_set_option(ozaki2_handle_t handle, int option, int value) {
         case OZAKI2_OPT_WAIT_LIMIT_NS:
             if (value < 0) return -3;
             ctx->wait_limit_ns = (unsigned long long)value;
+            return OZAKI2_SUCCESS;
+        case OZAKI2_OPT_GROUP_M:
+            if (value < 0 || value > 1024) return -3;
+            ctx->group_m = value;
             return OZAKI2_SUCCESS;
         default:
             return -2;
@@ -769,6 +927,36 @@ int ozaki2_encode_operands(ozaki2_handle_t handle, int count, ozaki2_operand* op
                 return OZAKI2_ERROR_CUDA;
         }
     }
+    // Host-resident matrices (page-locked, or pageable on a coherent link) are first copied into
+    // device memory by a kernel, as ozaki2_dgemm does, so the scaling and the conversion read
+    // them from HBM (the link is crossed once); with a caller workspace they are read in place.
+    std::vector<ozaki2_operand> staged(ops, ops + count);
+    if (!ctx->user_ws) {
+        size_t total = 0;
+        std::vector<size_t> span(count, 0);
+        for (int i = 0; i < count; ++i) {
+            const ozaki2_operand& o = ops[i];
+            if (o.lines <= 0 || o.k <= 0 || !host_resident(o.X)) continue;
+            const bool sa = o.side == 'A' || o.side == 'a', nt = is_notrans(o.trans);
+            const int64_t rows = sa ? (nt ? o.lines : o.k) : (nt ? o.k : o.lines);
+            const int64_t cols = sa ? (nt ? o.k : o.lines) : (nt ? o.lines : o.k);
+            span[i] = (size_t)((int64_t)o.ld * (cols - 1) + rows) * sizeof(double);
+            total += (size_t)round_up((int64_t)span[i], 256);
+        }
+        if (total) {
+            if ((rc = ensure_input_stage(ctx, total))) return rc;
+            char* p = static_cast<char*>(ctx->in_ws);
+            for (int i = 0; i < count; ++i) {
+                if (!span[i]) continue;
+                if ((rc = cuda_rc(launch_stage_in(p, ops[i].X, span[i], ctx->num_sms,
+                                                  ctx->stream))))
+                    return rc;
+                staged[i].X = reinterpret_cast<const double*>(p);
+                p += round_up((int64_t)span[i], 256);
+            }
+        }
+    }
+    ops = staged.data();
     const size_t tb = (size_t)encode_table_bytes(count, ops);
     // the device copy of the tables lives in the workspace; earlier calls on this stream have
     // read theirs before this call's copy lands (stream order)
@@ -823,6 +1011,14 @@ int ozaki2_set_grouped_tiles(ozaki2_handle_t handle, int count, const int* n_max
     return OZAKI2_SUCCESS;
 }
 
+// Scratch for the norm-block sums of lines longer than one block (the handle's workspace), or
+// NULL when none is needed or a caller workspace is too small (then one thread per line).
+static double* partials_scratch(ozaki2_context* ctx, int lines, int len) {
+    const size_t bytes = scale_partials_bytes(lines, len);
+    if (!bytes || ensure_workspace(ctx, bytes) != OZAKI2_SUCCESS) return nullptr;
+    return static_cast<double*>(ctx->ws);
+}
+
 int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const double* A, int lda,
                    int num_moduli, int* shifts) {
     if (!is_trans_char(transA)) return -2;
@@ -842,7 +1038,7 @@ int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const doub
     if (ctx->scaling == OZAKI2_SCALING_ACCURATE) return OZAKI2_ERROR_MODE;
     const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
     return cuda_rc(launch_scale(A, ls, es, m, k, pp, shifts, ctx->d_status, ctx->stream,
-                                ctx->scaling, T->delta));
+                                ctx->scaling, T->delta, partials_scratch(ctx, m, k)));
 }
 
 int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const double* B, int ldb,
@@ -864,7 +1060,7 @@ int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const doub
     if (ctx->scaling == OZAKI2_SCALING_ACCURATE) return OZAKI2_ERROR_MODE;
     const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
     return cuda_rc(launch_scale(B, ls, es, n, k, pp, shifts, ctx->d_status, ctx->stream,
-                                ctx->scaling, T->delta));
+                                ctx->scaling, T->delta, partials_scratch(ctx, n, k)));
 }
 
 int ozaki2_scale_accurate(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
@@ -983,7 +1179,8 @@ int ozaki2_residue_gemm(ozaki2_handle_t handle, int num_moduli, int m_pad, int n
     const PlaneGeom geo{m_pad, n_pad, k_pad, m_pad, n_pad};
     return launch_residue_gemm(num_moduli, m_pad, n_pad, k_pad, geo, planes_a, planes_b, residues,
                                T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
-                               ctx->gemm_variant, ctx->stream, ctx->wait_limit_ns);
+                               ctx->gemm_variant, ctx->stream, ctx->wait_limit_ns, 0, 0,
+                               ctx->group_m);
 }
 
 int ozaki2_crt(ozaki2_handle_t handle, int num_moduli, int m, int n, const int8_t* residues,

@@ -5,7 +5,7 @@
 // reconstruction is exact multi-word integer arithmetic instead of split FP64 constants:
 //   X    = sum_l P_l q_l c_l modulo P, as sum_g PG_g v_g over pairs of moduli (below)
 //          (W 32-bit words, 64-bit column sums)
-//   Q    = round(X / P)                          (48-bit fixed-point estimate of sum_g v_g/prod_g)
+//   Q    = round(X / P)                          (46-bit fixed-point estimate of sum_g v_g/prod_g)
 //   C''  = X - Q P                               (exact; corrected by +-P if the estimate sat
 //                                                 within 2^-10 of a half-integer)
 // X and Q P are formed modulo 2^(32 W) with W just large enough for Y (see crt_words).
@@ -196,26 +196,29 @@ __device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int 
         if constexpr (sizeof(OutT) == 4) return __uint_as_float(0x7FC00000u);
         else return __longlong_as_double(0x7FF8000000000000ll);
     }
-    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^48 X / P (fixed point).
+    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^46 X / P (fixed point).  A pair's
+    // constant round(2^46 / prod_g) is below 2^32, so its term is one 32 x 32 -> 64-bit
+    // multiply-add; a single modulus (odd N) keeps a 64-bit constant.
     uint64_t acc[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) acc[j] = 0;
     uint64_t S = 0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        S += (uint64_t)v[g] * t.R48[g];
+        if (2 * g + 1 < N) S += (uint64_t)v[g] * (uint32_t)t.R46[g];
+        else S += (uint64_t)v[g] * t.R46[g];
 #pragma unroll
         for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.PG[g][j] * v[g];
     }
     uint32_t X[W];
     fold_columns<W>(acc, X);
-    // Q = round(X / P) from the fixed-point estimate; |S/2^48 - X/P| < 2^-20
-    const uint64_t frac = S & ((1ull << 48) - 1);
-    const uint32_t Q = (uint32_t)((S + (1ull << 47)) >> 48);
+    // Q = round(X / P) from the fixed-point estimate; |S/2^46 - X/P| < 2^-18
+    const uint64_t frac = S & ((1ull << 46) - 1);
+    const uint32_t Q = (uint32_t)((S + (1ull << 45)) >> 46);
     uint32_t Y[W];
     add_word_times<W>(X, Q, t.negP, Y);  // Y = X - Q P (mod 2^(32 W))
-    const uint64_t half = 1ull << 47;
-    if ((frac > half ? frac - half : half - frac) < (1ull << 38)) {
+    const uint64_t half = 1ull << 45;
+    if ((frac > half ? frac - half : half - frac) < (1ull << 36)) {
         // The estimate sits within 2^-10 of a half-integer: make -P/2 <= Y < P/2 exactly.
         const bool neg = (Y[W - 1] >> 31) != 0;
         uint32_t mag[W];

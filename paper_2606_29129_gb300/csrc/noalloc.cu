@@ -139,7 +139,8 @@ extern "C" int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int 
     const int64_t off_pa = off_f + up(4 * n_pad, 256);
     const int64_t off_pb = off_pa + up(2 * num_moduli * (int64_t)geo.rows_a * geo.ld, 256);
     const int64_t off_res = off_pb + up(2 * num_moduli * (int64_t)geo.rows_b * geo.ld, 256);
-    const int64_t total = off_res + up(num_moduli * m_pad * n_pad, 256);
+    const int64_t off_part = off_res + up(num_moduli * m_pad * n_pad, 256);
+    const int64_t total = off_part + up((int64_t)scale_partials_bytes(m + n, k), 256);
     if (total > (int64_t)OZAKI2_NOALLOC_SCRATCH_BYTES) return OZAKI2_ERROR_TOO_LARGE;
 
     unsigned* status = reinterpret_cast<unsigned*>(s);
@@ -153,8 +154,13 @@ extern "C" int ozaki2_dgemm_noalloc(char transA, char transB, int m, int n, int 
 
     const int64_t als = notrans(transA) ? 1 : lda, aes = notrans(transA) ? lda : 1;
     const int64_t bls = notrans(transB) ? ldb : 1, bes = notrans(transB) ? 1 : ldb;
-    if (launch_scale(A, als, aes, m, k, T->pprime, e, status, st) != cudaSuccess ||
-        launch_scale(B, bls, bes, n, k, T->pprime, f, status, st) != cudaSuccess ||
+    // norm-block sums of long lines: A's, then B's
+    double* part_a = reinterpret_cast<double*>(s + off_part);
+    double* part_b = part_a + scale_partials_bytes(m, k) / sizeof(double);
+    if (launch_scale(A, als, aes, m, k, T->pprime, e, status, st, OZAKI2_SCALING_PROPOSED, 0.0f,
+                     part_a) != cudaSuccess ||
+        launch_scale(B, bls, bes, n, k, T->pprime, f, status, st, OZAKI2_SCALING_PROPOSED, 0.0f,
+                     part_b) != cudaSuccess ||
         launch_convert(A, als, aes, m, k, e, T->conv, pa, geo.rows_a, geo.ld, status, st) !=
             cudaSuccess ||
         launch_convert(B, bls, bes, n, k, f, T->conv, pb, geo.rows_b, geo.ld, status, st) !=

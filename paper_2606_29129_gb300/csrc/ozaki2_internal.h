@@ -41,7 +41,7 @@ struct CrtTables {
     uint32_t Kpair[(kMaxModuli + 1) / 2];  // K_2g | K_2g+1 << 16 (every K_l < prod_g < 2^16)
     uint32_t grp_bias[(kMaxModuli + 1) / 2];
     uint32_t PG[(kMaxModuli + 1) / 2][kMaxWords];
-    unsigned long long R48[(kMaxModuli + 1) / 2];  // round(2^48 / prod_g)
+    unsigned long long R46[(kMaxModuli + 1) / 2];  // round(2^46 / prod_g); < 2^32 for a pair
 };
 
 struct EpilogueTables {
@@ -252,10 +252,18 @@ const ModTables* mod_tables(int N);
 // Shifts of the rows of op(A) (m lines) and the columns of op(B) (n lines), both of length len,
 // in one launch; strides as for launch_scale.
 // f32: the matrices hold floats (SGEMM), else doubles.
+// partials: NULL, or device scratch of scale_partials_bytes(m + n, len) bytes, which lets lines
+// longer than one norm block split across warps (NULL: one thread per line).
 cudaError_t launch_scale_pair(const void* A, int64_t a_ls, int64_t a_es, int m, const void* B,
                               int64_t b_ls, int64_t b_es, int n, int len, float pprime,
                               float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
-                              int scaling, bool f32 = false);
+                              int scaling, bool f32 = false, double* partials = nullptr);
+// Scratch bytes of the norm-block sums (and maxima) of `lines` lines of length len: 0 when a
+// line fits one block of 256 terms.
+inline size_t scale_partials_bytes(int lines, int len) {
+    const int64_t nblocks = ((int64_t)len + 255) / 256;
+    return nblocks > 1 ? (size_t)(2 * nblocks * (int64_t)lines * 8) : 0;
+}
 
 #ifdef __CUDACC__
 // The double of the same value as a float, built from the bits with integer operations (the
@@ -289,7 +297,7 @@ constexpr int kAccuZeroLine = INT32_MAX;
 cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                          int len, float pprime, int* shifts, unsigned* status,
                          cudaStream_t stream, int scaling = OZAKI2_SCALING_PROPOSED,
-                         float delta = 0.0f);
+                         float delta = 0.0f, double* partials = nullptr);
 
 // f32: X holds floats (SGEMM), else doubles.  accurate: the shifts come from accurate mode,
 // whose a' may need six more bits than the proposed and fast scalings allow.
@@ -303,7 +311,8 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
                         const void* planes_a, const void* planes_b, int8_t* out,
                         const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
                         int variant, cudaStream_t stream,
-                        unsigned long long limit_ns = kDefaultWaitLimitNs);
+                        unsigned long long limit_ns = kDefaultWaitLimitNs, int64_t out_ld = 0,
+                        int64_t out_plane = 0, int group_m = 0);
 
 // f32: C holds floats (SGEMM: C'' rounded to 24 bits, alpha and beta applied in single
 // precision), else doubles.  padded: the residue buffer extends to whole 32 x 32 tiles in every

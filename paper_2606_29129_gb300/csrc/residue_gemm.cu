@@ -43,7 +43,7 @@ constexpr int EPI_WARPS = 8;
 constexpr int EPI_COLS = 128;      // accumulator columns drained by one epilogue warp
 constexpr int NUM_BARRIERS = 2 * STAGES + 5;   // full, empty, acc_full[2], acc_empty[2], drain
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARRIERS * 8 + 16;
-constexpr int GROUP_M = 16;                    // m-tiles per group in the tile order (L2 reuse)
+constexpr int GROUP_M = 16;  // default m-tiles per group in the tile order (L2 reuse)
 
 // Instruction descriptor of tcgen05.mma kind::f16: D fp32 (bits 4-5 = 1), A and B bf16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
@@ -59,6 +59,7 @@ static_assert(idesc_for(BN) == IDESC, "instruction descriptor");
 
 struct GemmArgs {
     int tiles_m, tiles_n, total_tiles, k_blocks, chunk_blocks, nchunks;
+    int group_m;  // m-tiles per group of the tile order
     int m_rows;  // rows of the A planes / product residues (m_pad)
     int m_live, n_live;  // product residues stored: rows below m_live, columns below n_live
     int8_t* out;
@@ -152,10 +153,10 @@ __device__ __forceinline__ void decode_tile(int tile, const GemmArgs& a, int& l,
     const int per_plane = a.tiles_m * a.tiles_n;
     l = tile / per_plane;
     const int idx = tile - l * per_plane;
-    const int per_group = GROUP_M * a.tiles_n;
+    const int per_group = a.group_m * a.tiles_n;
     const int g = idx / per_group;
-    const int first_m = g * GROUP_M;
-    const int gsize = min(a.tiles_m - first_m, GROUP_M);
+    const int first_m = g * a.group_m;
+    const int gsize = min(a.tiles_m - first_m, a.group_m);
     const int r = idx - g * per_group;
     mt = first_m + r % gsize;
     nt = r / gsize;
@@ -175,14 +176,14 @@ struct TileInfo {
 };
 
 __device__ __forceinline__ void decode_local(int idx, int tiles_m, int tiles_n, int& l, int& mt,
-                                             int& nt) {
+                                             int& nt, int group_m = GROUP_M) {
     const int per_plane = tiles_m * tiles_n;
     l = idx / per_plane;
     const int r0 = idx - l * per_plane;
-    const int per_group = GROUP_M * tiles_n;
+    const int per_group = group_m * tiles_n;
     const int g = r0 / per_group;
-    const int first_m = g * GROUP_M;
-    const int gsize = min(tiles_m - first_m, GROUP_M);
+    const int first_m = g * group_m;
+    const int gsize = min(tiles_m - first_m, group_m);
     const int r = r0 - g * per_group;
     mt = first_m + r % gsize;
     nt = r / gsize;
@@ -196,7 +197,7 @@ struct SingleSource {
     const GemmArgs* a;
     __device__ __forceinline__ TileInfo get(int t) const {
         TileInfo ti;
-        decode_local(t, a->tiles_m, a->tiles_n, ti.l, ti.mt, ti.nt);
+        decode_local(t, a->tiles_m, a->tiles_n, ti.l, ti.mt, ti.nt, a->group_m);
         ti.ta = ta;
         ti.tb = tb;
         ti.k_blocks = a->k_blocks;
@@ -988,6 +989,7 @@ int launch_aux_gemm(int m_pad, int n_pad, int k_pad, const PlaneGeom& geo, const
     a.k_blocks = k_pad / BK;
     a.chunk_blocks = kAuxChunkBlocks;
     a.nchunks = (a.k_blocks + kAuxChunkBlocks - 1) / kAuxChunkBlocks;
+    a.group_m = GROUP_M;
     a.m_rows = m_pad;
     a.out = reinterpret_cast<int8_t*>(cmax);
     a.out_ld = m_pad;
@@ -1048,8 +1050,11 @@ int launch_aux_gemm_grouped(const GroupGemmProblem* probs, int count, int total_
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const PlaneGeom& geo,
                         const void* planes_a, const void* planes_b, int8_t* out,
                         const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
-                        int variant, cudaStream_t stream, unsigned long long limit_ns) {
+                        int variant, cudaStream_t stream, unsigned long long limit_ns,
+                        int64_t out_ld, int64_t out_plane, int group_m) {
     if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
+    if (out_ld <= 0) out_ld = n_pad;
+    if (out_plane <= 0) out_plane = (int64_t)m_pad * out_ld;
     GemmArgs a;
     a.k_blocks = k_pad / BK;
     const int cb = chunk_blocks_of(chunk_k, a.k_blocks);
@@ -1059,12 +1064,14 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
     a.m_live = geo.out_rows;
     a.n_live = geo.out_cols;
     a.out = out;
-    a.out_ld = n_pad;
-    a.out_plane = (int64_t)m_pad * n_pad;
+    a.out_ld = out_ld;
+    a.out_plane = out_plane;
+    a.group_m = group_m > 0 ? group_m : GROUP_M;
     a.status = status;
     a.limit_ns = limit_ns;
     a.ep = t;
     if (a.k_blocks == 0) {  // empty inner dimension: every product residue is zero
+        if (out_ld != n_pad || out_plane != (int64_t)m_pad * n_pad) return OZAKI2_ERROR_CUDA;
         cudaError_t e = cudaMemsetAsync(out, 0, (size_t)num_moduli * m_pad * n_pad, stream);
         return e == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
     }

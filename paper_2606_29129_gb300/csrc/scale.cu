@@ -9,8 +9,10 @@
 // from Algorithm 2.
 //
 // The kernels are bound by HBM reads of the matrix (8 bytes per element) and, on GB300, by the
-// FP64 FMA rate.  Lines of at most one block run one thread per line; longer lines are split
-// across the warps of a block (scale_split_kernel), each warp summing whole blocks.
+// FP64 FMA rate.  Lines of at most one block run one thread per line; longer lines, when the
+// caller gives scratch for the block sums, run two kernels: one warp per norm block of 32 lines
+// (scale_partials_kernel), then one thread per line adding its block sums in order
+// (scale_fold_kernel).
 #include <float.h>
 
 #include "ozaki2_internal.h"
@@ -307,55 +309,62 @@ __device__ __forceinline__ void contiguous_block(const T* __restrict__ X, int64_
     }
 }
 
-// 32 lines of one side per block; warp w sums blocks w, w + 8, ... of every line; after each
-// round of 8 blocks warp 0 adds the block sums to the lines' totals in block order, rounded
-// upward.  The result is the blocked sum of LineAcc, bit for bit.
+// Norm-block sums: block (g, c) of the grid takes the 32 lines of group g and warp w sums their
+// norm block c * 8 + w.  part: [nblocks][lines] block sums, then (fast mode) [nblocks][lines]
+// block maxima, per side.
 template <int SCALING, typename T>
-__global__ void __launch_bounds__(32 * kSplitWarps, 2) scale_split_kernel(ScaleSide a, ScaleSide b,
-                                                                       int groups_a, int len,
-                                                                       float pprime, float delta,
-                                                                       unsigned* status) {
+__global__ void __launch_bounds__(32 * kSplitWarps) scale_partials_kernel(
+    ScaleSide a, ScaleSide b, int groups_a, int chunks, int len, double* part_a,
+    double* part_b) {
     static_assert(SCALING != OZAKI2_SCALING_ACCURATE, "accurate mode takes no squared norm");
     __shared__ T tile[kSplitWarps][32][split_tile<T>() + 1];
-    __shared__ double part[kSplitWarps][32];
-    __shared__ double pmax[kSplitWarps][32];
-    const bool side_b = (int)blockIdx.x >= groups_a;
+    const int group = (int)blockIdx.x / chunks, chunk = (int)blockIdx.x % chunks;
+    const bool side_b = group >= groups_a;
     const ScaleSide& S = side_b ? b : a;
+    double* part = side_b ? part_b : part_a;
     const T* X = static_cast<const T*>(S.X);
-    const int line0 = ((int)blockIdx.x - (side_b ? groups_a : 0)) * 32;
+    const int line0 = (group - (side_b ? groups_a : 0)) * 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nl = min(32, S.lines - line0);
-    const bool adjacent = S.es != 1 || S.ls == 1;
     const int nblocks = (len + kNormBlock - 1) / kNormBlock;
-    LineAcc<SCALING> run;    // warp 0: the folded total and the line maximum
-    double wmax = 0.0;       // this warp's maximum |a| of the line (fast mode)
-    for (int r0 = 0; r0 < nblocks; r0 += kSplitWarps) {
-        const int blk = r0 + warp;
-        LineAcc<SCALING> acc;
-        if (blk < nblocks) {
-            const int hb = blk * kNormBlock, he = min(hb + kNormBlock, len);
-            if (adjacent) {
-                if (lane < nl) adjacent_block<SCALING, T>(X, S.es, line0 + lane, hb, he, acc);
-            } else {
-                contiguous_block<SCALING, T>(X, S.ls, nl, line0, hb, he, tile[warp], acc);
-            }
-        }
-        part[warp][lane] = acc.s;
-        if (SCALING == OZAKI2_SCALING_FAST) wmax = fmax(wmax, acc.mx);
-        __syncthreads();
-        if (warp == 0) {
-            for (int w = 0; w < kSplitWarps && r0 + w < nblocks; ++w)
-                run.total = __dadd_ru(run.total, part[w][lane]);
-        }
-        __syncthreads();
+    const int blk = chunk * kSplitWarps + warp;
+    if (blk >= nblocks) return;  // the whole warp: no block barrier follows
+    const int hb = blk * kNormBlock, he = min(hb + kNormBlock, len);
+    LineAcc<SCALING> acc;
+    if (S.es != 1 || S.ls == 1) {
+        if (lane < nl) adjacent_block<SCALING, T>(X, S.es, line0 + lane, hb, he, acc);
+    } else {
+        contiguous_block<SCALING, T>(X, S.ls, nl, line0, hb, he, tile[warp], acc);
     }
-    if (SCALING == OZAKI2_SCALING_FAST) {
-        pmax[warp][lane] = wmax;
-        __syncthreads();
-        if (warp == 0)
-            for (int w = 0; w < kSplitWarps; ++w) run.mx = fmax(run.mx, pmax[w][lane]);
+    if (lane < nl) {
+        part[(int64_t)blk * S.lines + line0 + lane] = acc.s;
+        if (SCALING == OZAKI2_SCALING_FAST)
+            part[(int64_t)(nblocks + blk) * S.lines + line0 + lane] = acc.mx;
     }
-    if (warp == 0 && lane < nl) S.shifts[line0 + lane] = run.result(pprime, delta, status);
+}
+
+// One thread per line: the block sums added in block order, rounded upward (the blocked sum of
+// LineAcc, bit for bit), the maximum of the block maxima, then the shift.
+template <int SCALING>
+__global__ void __launch_bounds__(256) scale_fold_kernel(ScaleSide a, ScaleSide b, int len,
+                                                        const double* __restrict__ part_a,
+                                                        const double* __restrict__ part_b,
+                                                        float pprime, float delta,
+                                                        unsigned* status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool side_b = t >= a.lines;
+    const ScaleSide& S = side_b ? b : a;
+    const int i = side_b ? t - a.lines : t;
+    if (i >= S.lines) return;
+    const double* part = side_b ? part_b : part_a;
+    const int nblocks = (len + kNormBlock - 1) / kNormBlock;
+    LineAcc<SCALING> acc;
+    for (int blk = 0; blk < nblocks; ++blk) {
+        acc.total = __dadd_ru(acc.total, part[(int64_t)blk * S.lines + i]);
+        if (SCALING == OZAKI2_SCALING_FAST)
+            acc.mx = fmax(acc.mx, part[(int64_t)(nblocks + blk) * S.lines + i]);
+    }
+    S.shifts[i] = acc.result(pprime, delta, status);
 }
 
 template <int SCALING, typename T>
@@ -421,17 +430,35 @@ cudaError_t launch_scale_grouped(const GroupProblem* probs, const ScaleWork* wor
     return cudaGetLastError();
 }
 
+// Lines longer than one norm block, with scratch for the block sums: the partial sums of every
+// (32 lines, block), then the ordered fold per line.  Side b may have no lines.
+template <int SCALING, typename T>
+static void launch_split(const ScaleSide& sa, const ScaleSide& sb, int len, float pprime,
+                         float delta, double* partials, unsigned* status, cudaStream_t stream) {
+    const int nblocks = (len + kNormBlock - 1) / kNormBlock;
+    const int chunks = (nblocks + kSplitWarps - 1) / kSplitWarps;
+    const int ga = (sa.lines + 31) / 32, gb = (sb.lines + 31) / 32;
+    double* pa = partials;
+    double* pb = partials + 2 * (int64_t)nblocks * sa.lines;
+    scale_partials_kernel<SCALING, T><<<(ga + gb) * chunks, 32 * kSplitWarps, 0, stream>>>(
+        sa, sb, ga, chunks, len, pa, pb);
+    const int lines = sa.lines + sb.lines;
+    scale_fold_kernel<SCALING><<<(lines + 255) / 256, 256, 0, stream>>>(sa, sb, len, pa, pb,
+                                                                       pprime, delta, status);
+}
+
 template <int SCALING>
 static void launch_scale_t(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, float pprime, float delta, int* shifts, unsigned* status,
-                           cudaStream_t stream) {
-    if (SCALING != OZAKI2_SCALING_ACCURATE && len > kNormBlock) {  // long lines: split
-        const ScaleSide side{X, line_stride, elem_stride, lines, shifts};
-        const ScaleSide none{X, line_stride, elem_stride, 0, shifts};
-        constexpr int kS = SCALING == OZAKI2_SCALING_ACCURATE ? OZAKI2_SCALING_PROPOSED : SCALING;
-        scale_split_kernel<kS, double><<<(lines + 31) / 32, 32 * kSplitWarps, 0, stream>>>(
-            side, none, (lines + 31) / 32, len, pprime, delta, status);
-        return;
+                           cudaStream_t stream, double* partials) {
+    if constexpr (SCALING != OZAKI2_SCALING_ACCURATE) {
+        if (partials && len > kNormBlock) {  // long lines: split across warps
+            const ScaleSide side{X, line_stride, elem_stride, lines, shifts};
+            const ScaleSide none{X, line_stride, elem_stride, 0, shifts};
+            launch_split<SCALING, double>(side, none, len, pprime, delta, partials, status,
+                                          stream);
+            return;
+        }
     }
     if (elem_stride != 1 || line_stride == 1) {  // lines adjacent
         scale_adjacent_kernel<SCALING><<<(lines + 31) / 32, 32, 0, stream>>>(
@@ -446,32 +473,31 @@ static void launch_scale_t(const double* X, int64_t line_stride, int64_t elem_st
 
 cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stride, int lines,
                          int len, float pprime, int* shifts, unsigned* status,
-                         cudaStream_t stream, int scaling, float delta) {
+                         cudaStream_t stream, int scaling, float delta, double* partials) {
     if (lines <= 0) return cudaSuccess;
     if (scaling == OZAKI2_SCALING_FAST)
         launch_scale_t<OZAKI2_SCALING_FAST>(X, line_stride, elem_stride, lines, len, pprime,
-                                            delta, shifts, status, stream);
+                                            delta, shifts, status, stream, partials);
     else if (scaling == OZAKI2_SCALING_ACCURATE)
         launch_scale_t<OZAKI2_SCALING_ACCURATE>(X, line_stride, elem_stride, lines, len, pprime,
-                                                delta, shifts, status, stream);
+                                                delta, shifts, status, stream, partials);
     else
         launch_scale_t<OZAKI2_SCALING_PROPOSED>(X, line_stride, elem_stride, lines, len, pprime,
-                                                delta, shifts, status, stream);
+                                                delta, shifts, status, stream, partials);
     return cudaGetLastError();
 }
 
 template <typename T>
 static void launch_scale_pair_t(const ScaleSide& sa, const ScaleSide& sb, int blocks_a, int grid,
                                 int len, float pprime, float delta, unsigned* status,
-                                cudaStream_t stream, int scaling) {
-    if (scaling != OZAKI2_SCALING_ACCURATE && len > kNormBlock) {  // long lines: split
-        const int ga = (sa.lines + 31) / 32, gb = (sb.lines + 31) / 32;
+                                cudaStream_t stream, int scaling, double* partials) {
+    if (partials && scaling != OZAKI2_SCALING_ACCURATE && len > kNormBlock) {  // long lines
         if (scaling == OZAKI2_SCALING_FAST)
-            scale_split_kernel<OZAKI2_SCALING_FAST, T><<<ga + gb, 32 * kSplitWarps, 0, stream>>>(
-                sa, sb, ga, len, pprime, delta, status);
+            launch_split<OZAKI2_SCALING_FAST, T>(sa, sb, len, pprime, delta, partials, status,
+                                                 stream);
         else
-            scale_split_kernel<OZAKI2_SCALING_PROPOSED, T>
-                <<<ga + gb, 32 * kSplitWarps, 0, stream>>>(sa, sb, ga, len, pprime, delta, status);
+            launch_split<OZAKI2_SCALING_PROPOSED, T>(sa, sb, len, pprime, delta, partials,
+                                                     status, stream);
         return;
     }
     if (scaling == OZAKI2_SCALING_FAST)
@@ -488,17 +514,17 @@ static void launch_scale_pair_t(const ScaleSide& sa, const ScaleSide& sb, int bl
 cudaError_t launch_scale_pair(const void* A, int64_t a_ls, int64_t a_es, int m, const void* B,
                               int64_t b_ls, int64_t b_es, int n, int len, float pprime,
                               float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
-                              int scaling, bool f32) {
+                              int scaling, bool f32, double* partials) {
     const int blocks_a = (m + 127) / 128, blocks_b = (n + 127) / 128;
     if (blocks_a + blocks_b == 0) return cudaSuccess;
     const ScaleSide sa{A, a_ls, a_es, m, e}, sb{B, b_ls, b_es, n, f};
     const int grid = blocks_a + blocks_b;
     if (f32)
         launch_scale_pair_t<float>(sa, sb, blocks_a, grid, len, pprime, delta, status, stream,
-                                   scaling);
+                                   scaling, partials);
     else
         launch_scale_pair_t<double>(sa, sb, blocks_a, grid, len, pprime, delta, status, stream,
-                                    scaling);
+                                    scaling, partials);
     return cudaGetLastError();
 }
 

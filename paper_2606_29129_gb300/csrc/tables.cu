@@ -122,8 +122,8 @@ void build(int N, ModTables& t) {
         for (int j = 0; j < N; ++j)
             if (j < l0 || j >= l1) mul_small(PG, (uint32_t)kModuli[j]);
         for (int w = 0; w < kMaxWords; ++w) t.crt.PG[g][w] = w < (int)PG.size() ? PG[w] : 0u;
-        t.crt.R48[g] = (unsigned long long)(((unsigned __int128)1 << 48) / prod +
-                                            ((((unsigned __int128)1 << 48) % prod) * 2 >= prod));
+        t.crt.R46[g] = (unsigned long long)(((unsigned __int128)1 << 46) / prod +
+                                            ((((unsigned __int128)1 << 46) % prod) * 2 >= prod));
     }
     {   // two's complement of P over kMaxWords words
         uint64_t borrow = 0;

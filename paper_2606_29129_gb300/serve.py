@@ -420,18 +420,20 @@ class GpuExecutor:
                 fresh.append((side, e, X, lines))
             entries[side] = e
         if fresh:
-            # upload the missing operands and encode them, all on the upload stream
+            # encode the missing operands on the upload stream; the library copies each
+            # page-locked host matrix into device memory with a kernel (the link's full rate)
+            # before scaling and converting it
             with torch.cuda.stream(self.upload):
                 ops = []
                 keep = []
                 for side, e, X, lines in fresh:
                     e.buf = torch.empty(e.nbytes, dtype=torch.uint8, device=self.device)
-                    dX = self._pinned(torch, X).to(self.device, non_blocking=True)
-                    keep.append(dX)
+                    hX = self._pinned(torch, X)
+                    keep.append(hX)
                     self.stats["upload_bytes"] += 8 * lines * r.k
                     # A as stored: column-major m x k (ld m); B: k x n (ld k)
                     ld = max(1, r.m if side == "A" else r.k)
-                    ops.append(dict(side=side, trans="N", lines=lines, k=r.k, X=dX, ld=ld,
+                    ops.append(dict(side=side, trans="N", lines=lines, k=r.k, X=hX, ld=ld,
                                     num_moduli=r.num_moduli, data=e.buf))
                 arr = oz.operands_array(ops)
                 t0 = torch.cuda.Event(enable_timing=True)
@@ -446,7 +448,8 @@ class GpuExecutor:
                     e.ready = t1
                 self._encode_events.append((t0, t1))
                 self.stats["encoded_operands"] += len(fresh)
-                del keep   # the allocator reuses these bytes only after the upload stream's work
+                # host matrices that were pinned here must outlive the staging copy
+                r.dev["pinned_inputs"] = keep
         r.dev["enc"] = entries
         r.dev["host_C"] = self._result_buffer(r)
         return True

@@ -9,6 +9,7 @@ X = sum_g (P / prod_g) v_g is congruent to sum_l P_l q_l c_l modulo P, and the 4
 estimate of X / P is within 2^-20."""
 import math
 import random
+from fractions import Fraction
 
 import pytest
 
@@ -60,7 +61,7 @@ def pair_tables(N):
         for l in ls:
             K[l] = (prod // ps[l]) * q[l] % prod
         tab.append(dict(ls=ls, prod=prod, bias=256 * prod, PG=P // prod,
-                        R48=((1 << 48) + prod // 2) // prod))
+                        R46=((1 << 46) + prod // 2) // prod))
     return ps, P, q, K, tab
 
 
@@ -75,15 +76,17 @@ def test_crt_pair_groups_exact(N):
         for g in tab:
             v = (g["bias"] + sum(c[l] * K[l] for l in g["ls"])) & 0xFFFFFFFF  # wraps mod 2^32
             assert 0 <= v < 1 << 25                        # so the wrapped value is exact
-            S += v * g["R48"]
+            if len(g["ls"]) == 2:                          # a pair: a 32-bit constant
+                assert g["R46"] < 1 << 32
+            S += v * g["R46"]
             X += g["PG"] * v
         assert S < 1 << 64
         assert (X - sum(c[l] * (P // ps[l]) * q[l] for l in range(N))) % P == 0
-        assert abs(S / (1 << 48) - X / P) < 2.0 ** -20
-        Q = (S + (1 << 47)) >> 48
+        assert abs(Fraction(S, 1 << 46) - Fraction(X, P)) < Fraction(1, 1 << 18)
+        Q = (S + (1 << 45)) >> 46
         Y = X - Q * P
-        frac = S & ((1 << 48) - 1)
-        if abs(frac - (1 << 47)) >= 1 << 38:               # away from a tie: already reduced
+        frac = S & ((1 << 46) - 1)
+        if abs(frac - (1 << 45)) >= 1 << 36:               # away from a tie: already reduced
             assert -P // 2 <= Y < P // 2
         else:                                              # near a tie: one correction at most
             assert -P <= Y < P
