@@ -278,9 +278,12 @@ def run_tune_tiles(args):
     one SM, or 256 x 256 on an SM pair) and K chunk, for square DGEMMs of each size."""
     from paper_2606_29129_gb300 import autotune
 
-    table = autotune.tune_tiles(sizes=tuple(args.tune_sizes), N=args.moduli)
+    with ClockSampler(0) as clocks:
+        table = autotune.tune_tiles(sizes=tuple(args.tune_sizes), N=args.moduli,
+                                    chunks=tuple(args.tune_chunks),
+                                    groups=tuple(args.tune_groups))
     print(json.dumps({"mode": "tile_tuning", "N": args.moduli,
-                      "table": autotune.tiles_to_json(table),
+                      "table": autotune.tiles_to_json(table), "clocks": clocks.summary(),
                       "variants": {"1": "128 x 256 tiles, one CTA per SM",
                                    "2": "256 x 256 tiles on SM pairs"}}), flush=True)
 
@@ -1060,6 +1063,9 @@ def main():
     ap.add_argument("--tune-tiles", action="store_true",
                     help="time the residue-GEMM kernel variants and K chunks per size class")
     ap.add_argument("--tune-sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192, 16384])
+    ap.add_argument("--tune-chunks", type=int, nargs="+", default=[960, 640, 448, 320])
+    ap.add_argument("--tune-groups", type=int, nargs="+", default=[0],
+                    help="tile-order group sizes to time (0: the library default, 16)")
     ap.add_argument("--scaling-study", action="store_true",
                     help="fast mode (Algorithm 1) against the proposed scaling over alpha = 2^s")
     ap.add_argument("--study-sizes", type=int, nargs="+", default=[1024, 16384])

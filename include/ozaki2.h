@@ -86,7 +86,9 @@ extern "C" {
 #define OZAKI2_OPT_GROUP_M 6      /* tile order of the single-problem residue GEMM: the number of
                                      m-tiles that sweep the n-tiles together (so that the CTAs
                                      running at the same time share A and B panels in L2); 0
-                                     (default) = 16, else 1..1024.  Results do not depend on it. */
+                                     (default) = 32 for OZAKI2_GEMM_SINGLE and 4 for
+                                     OZAKI2_GEMM_PAIR (fastest measured on GB300), else 1..1024.
+                                     Results do not depend on it. */
 #define OZAKI2_SCALING_PROPOSED 0 /* Algorithm 2 (Section 4): scale-invariant, CRT bound by
                                      construction */
 #define OZAKI2_SCALING_FAST 1     /* Algorithm 1 (Section 2.3): the original fast mode, kept for

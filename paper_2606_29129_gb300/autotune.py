@@ -165,9 +165,10 @@ def _time_ms(fn, reps):
 
 
 def tune_tiles(sizes=(1024, 2048, 4096, 8192, 16384), N=16, variants=TILE_VARIANTS,
-               chunks=CHUNKS, reps=3, seed=0, device="cuda"):
-    """Times ozaki2_dgemm on m = n = k = size for every (kernel variant, K chunk) and returns
-    {size_class(size): {"size": size, "ms": {(variant, chunk): ms}, "best": (variant, chunk)}}."""
+               chunks=CHUNKS, reps=3, seed=0, device="cuda", groups=(0,)):
+    """Times ozaki2_dgemm on m = n = k = size for every (kernel variant, K chunk, tile-order
+    group size; 0 = the library's default) and returns {size_class(size): {"size": size,
+    "ms": {(variant, chunk, group): ms}, "best": (variant, chunk, group)}}."""
     import torch
 
     import synthetic
@@ -182,14 +183,16 @@ def tune_tiles(sizes=(1024, 2048, 4096, 8192, 16384), N=16, variants=TILE_VARIAN
         ms = {}
         for variant in variants:
             for chunk in chunks:
-                h.set_option(oz.OPT_GEMM_VARIANT, variant)
-                h.set_option(oz.OPT_CHUNK_K, chunk)
+                for group in groups:
+                    h.set_option(oz.OPT_GEMM_VARIANT, variant)
+                    h.set_option(oz.OPT_CHUNK_K, chunk)
+                    h.set_option(oz.OPT_GROUP_M, group)
 
-                def call():
-                    oz._check("ozaki2_dgemm", oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B, k,
-                                                              0.0, C, m, N, h))
+                    def call():
+                        oz._check("ozaki2_dgemm", oz.ozaki2_dgemm("N", "N", m, n, k, 1.0, A, m, B,
+                                                                  k, 0.0, C, m, N, h))
 
-                ms[(variant, chunk)] = _time_ms(call, reps)
+                    ms[(variant, chunk, group)] = _time_ms(call, reps)
         out[size_class(k)] = {"size": size, "ms": ms, "best": best_config(ms)}
     return out
 
@@ -200,9 +203,10 @@ def apply_tiles(handle, table, k: int) -> bool:
     entry = table.get(size_class(k))
     if entry is None:
         return False
-    variant, chunk = entry["best"]
+    variant, chunk, *group = entry["best"]
     handle.set_option(oz.OPT_GEMM_VARIANT, variant)
     handle.set_option(oz.OPT_CHUNK_K, chunk)
+    handle.set_option(oz.OPT_GROUP_M, group[0] if group else 0)
     return True
 
 
@@ -282,6 +286,12 @@ def tune_grouped_chunk(call, handle, chunks=CHUNKS, reps=3):
 
 
 def tiles_to_json(table):
-    return {str(c): {"size": v["size"], "best": {"variant": v["best"][0], "chunk_k": v["best"][1]},
-                     "ms": {f"{var}/{ch}": t for (var, ch), t in v["ms"].items()}}
+    def best(b):
+        out = {"variant": b[0], "chunk_k": b[1]}
+        if len(b) > 2:
+            out["group_m"] = b[2]
+        return out
+
+    return {str(c): {"size": v["size"], "best": best(v["best"]),
+                     "ms": {"/".join(str(x) for x in key): t for key, t in v["ms"].items()}}
             for c, v in table.items()}

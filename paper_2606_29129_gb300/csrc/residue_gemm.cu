@@ -43,7 +43,10 @@ constexpr int EPI_WARPS = 8;
 constexpr int EPI_COLS = 128;      // accumulator columns drained by one epilogue warp
 constexpr int NUM_BARRIERS = 2 * STAGES + 5;   // full, empty, acc_full[2], acc_empty[2], drain
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + NUM_BARRIERS * 8 + 16;
-constexpr int GROUP_M = 16;  // default m-tiles per group in the tile order (L2 reuse)
+constexpr int GROUP_M = 16;  // m-tiles per group in the tile order of grouped calls (L2 reuse)
+// Defaults of single-problem calls, fastest in a sweep on GB300 (8192^3 and 16384^3, N = 16):
+// 32 m-tiles of 128 rows for the one-SM kernel, 4 m-tiles of 256 rows for the SM-pair kernel.
+constexpr int GROUP_M_SINGLE = 32, GROUP_M_PAIR = 4;
 
 // Instruction descriptor of tcgen05.mma kind::f16: D fp32 (bits 4-5 = 1), A and B bf16
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
@@ -1066,7 +1069,7 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
     a.out = out;
     a.out_ld = out_ld;
     a.out_plane = out_plane;
-    a.group_m = group_m > 0 ? group_m : GROUP_M;
+    a.group_m = group_m;  // 0: the kernel's default, set below
     a.status = status;
     a.limit_ns = limit_ns;
     a.ep = t;
@@ -1089,6 +1092,7 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
         if (ensure_smem_attr((const void*)residue_gemm_pair_kernel, (int)pair::SMEM_BYTES,
                              g_attr_pair) != cudaSuccess)
             return OZAKI2_ERROR_CUDA;
+        if (a.group_m <= 0) a.group_m = GROUP_M_PAIR;
         a.tiles_m = (m_pad + pair::BM - 1) / pair::BM;
         a.tiles_n = n_pad / pair::BN;
         a.total_tiles = a.tiles_m * a.tiles_n * num_moduli;
@@ -1122,6 +1126,7 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
     if (ensure_smem_attr((const void*)residue_gemm_kernel, (int)SMEM_BYTES, g_attr_single) !=
         cudaSuccess)
         return OZAKI2_ERROR_CUDA;
+    if (a.group_m <= 0) a.group_m = GROUP_M_SINGLE;
     a.tiles_m = m_pad / BM;
     a.tiles_n = n_pad / BN;
     a.total_tiles = a.tiles_m * a.tiles_n * num_moduli;

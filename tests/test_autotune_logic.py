@@ -34,7 +34,12 @@ def test_best_config_and_apply():
     table = {autotune.size_class(4096): {"size": 4096, "ms": ms, "best": (oz.GEMM_PAIR, 960)}}
     h = FakeHandle()
     assert autotune.apply_tiles(h, table, 4096)
-    assert h.options == {oz.OPT_GEMM_VARIANT: oz.GEMM_PAIR, oz.OPT_CHUNK_K: 960}
+    assert h.options == {oz.OPT_GEMM_VARIANT: oz.GEMM_PAIR, oz.OPT_CHUNK_K: 960,
+                         oz.OPT_GROUP_M: 0}
+    table3 = {autotune.size_class(4096): {"size": 4096, "ms": {}, "best": (oz.GEMM_SINGLE, 640, 32)}}
+    h3 = FakeHandle()
+    assert autotune.apply_tiles(h3, table3, 4096) and h3.options[oz.OPT_GROUP_M] == 32
+    assert autotune.tiles_to_json(table3)[str(autotune.size_class(4096))]["best"]["group_m"] == 32
     h2 = FakeHandle()
     assert not autotune.apply_tiles(h2, table, 64) and h2.options == {}
     js = autotune.tiles_to_json(table)

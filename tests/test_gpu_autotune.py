@@ -15,9 +15,10 @@ def test_tune_tiles_and_apply(orc):
     from paper_2606_29129_gb300 import autotune
     from paper_2606_29129_gb300 import ozaki2 as oz
 
-    table = autotune.tune_tiles(sizes=(512,), N=14, chunks=(960, 320), reps=1)
+    table = autotune.tune_tiles(sizes=(512,), N=14, chunks=(960, 320), reps=1, groups=(0, 2))
     entry = table[autotune.size_class(512)]
-    assert set(entry["ms"]) == {(v, c) for v in autotune.TILE_VARIANTS for c in (960, 320)}
+    assert set(entry["ms"]) == {(v, c, g) for v in autotune.TILE_VARIANTS for c in (960, 320)
+                                for g in (0, 2)}
     assert entry["best"] in entry["ms"] and all(t > 0 for t in entry["ms"].values())
     m, n, k, N = 300, 520, 512, 14
     A = synthetic.paper_matrix(m, k, 1.0, 61)
@@ -25,10 +26,12 @@ def test_tune_tiles_and_apply(orc):
     ref = _gpu.dgemm(oz, A, B, m, n, k, N)
     for variant in autotune.TILE_VARIANTS:
         for chunk in (960, 320):
-            h = oz.Handle()
-            h.set_option(oz.OPT_GEMM_VARIANT, variant)
-            h.set_option(oz.OPT_CHUNK_K, chunk)
-            assert _gpu.same_bits(_gpu.dgemm(oz, A, B, m, n, k, N, handle=h), ref)
+            for group in (0, 1, 3):
+                h = oz.Handle()
+                h.set_option(oz.OPT_GEMM_VARIANT, variant)
+                h.set_option(oz.OPT_CHUNK_K, chunk)
+                h.set_option(oz.OPT_GROUP_M, group)
+                assert _gpu.same_bits(_gpu.dgemm(oz, A, B, m, n, k, N, handle=h), ref)
     h = oz.Handle()
     assert autotune.apply_tiles(h, table, k)
     assert _gpu.same_bits(_gpu.dgemm(oz, A, B, m, n, k, N, handle=h), ref)
