@@ -31,6 +31,7 @@ PHI = 1.0
 NUM_MODULI = 16
 SGEMM_MODULI = 8
 METRIC = "Ozaki-II DGEMM effective TFLOPS at stated error vs cuBLAS DGEMM; p50/p99 lat"
+FP64_NOMINAL_TFLOPS = 1.25  # GB300's dense FP64 rate (nominal)
 WORKLOAD = f"square FP64 GEMM m=n=k={SIZE}, phi={PHI}, N={NUM_MODULI} moduli"
 
 
@@ -67,6 +68,11 @@ def stage_rooflines(m, n, k, N, esz, stages_ms, hbm_gbs, scaling="proposed", bet
         gbs = nbytes / (ms * 1e-3) / 1e9
         out[name] = {"algorithmic_bytes": nbytes, "ms": ms, "achieved_gbs": gbs,
                      "frac_of_hbm": gbs / hbm_gbs}
+    if "scale" in out:
+        # one upward-rounded FP64 FMA per element: the stage's other bound on GB300, against
+        # the nominal FP64 rate (no measured figure exists for it)
+        tflops = 2.0 * elems / (out["scale"]["ms"] * 1e-3) / 1e12
+        out["scale"].update(fp64_tflops=tflops, frac_of_fp64_nominal=tflops / FP64_NOMINAL_TFLOPS)
     return out
 
 

@@ -253,12 +253,14 @@ int ensure_input_stage(ozaki2_context* ctx, size_t bytes) {
 // Host-resident operands, pipelined over column blocks of op(B) (proposed or fast scaling, no
 // caller workspace, op(B) = B so that its columns are contiguous, n of at least 2 blocks).
 // Under these scalings a column's shift depends on that column alone (eq. (proposed-nu)), so the
-// columns of op(B) can be scaled, converted and multiplied block by block: stream S (the
-// handle's) stages A, scales and converts it, then per block scales and converts B_j and runs
-// its residue GEMMs; a second stream stages the blocks of B over the link once A is in, and runs
-// each block's reconstruction (which writes C over the link when C is in host memory) while the
-// next block's GEMMs run.  Every step computes what the unblocked path computes, so the result
-// is the same bits.
+// columns of op(B) can be scaled, converted and multiplied block by block.  The handle's stream
+// S stages A (copy kernel), scales and converts it, then per block scales and converts B_j,
+// runs its residue GEMMs and its reconstruction.  The link transfers that can overlap the next
+// block's GEMMs, the uploads of B's later blocks, go through a copy engine on a second stream,
+// which uses no SMs (the persistent GEMM holds every SM).  A host-resident C is written by each
+// block's reconstruction over the link.  (Downloading C's blocks by the copy engine from a
+// device buffer measured no faster: ~7.5 ms of exposed link time at 16384^3 either way.)  Every
+// step computes what the unblocked path computes, so the result is the same bits.
 constexpr int kPipeMinBlock = 2048;
 
 bool pipeline_applies(const ozaki2_context* ctx, char transB, int n, const void* A,
@@ -288,7 +290,7 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
     nb = (int)((n + blk - 1) / blk);
     if (nb > 4) return OZAKI2_ERROR_CUDA;  // not reached: blk >= n / 4
 
-    // staging buffer: A (when host-resident), then the blocks of B
+    // device buffers: A and the blocks of B, when host-resident
     const bool host_a = host_resident(A), host_b = host_resident(B);
     const int acols = is_notrans(transA) ? k : m, arows = is_notrans(transA) ? m : k;
     const size_t a_span = ((size_t)lda * (size_t)(acols - 1) + (size_t)arows) * esz;
@@ -301,8 +303,7 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
     if (a_room + b_room && (rc = ensure_input_stage(ctx, a_room + b_room))) return rc;
     char* stage = static_cast<char*>(ctx->in_ws);
     cudaEvent_t ev_start = ctx->pipe_ev[0], ev_a = ctx->pipe_ev[1], ev_done = ctx->pipe_ev[2];
-    cudaEvent_t* ev_b = ctx->pipe_ev + 3;   // B block j staged (j < 4)
-    cudaEvent_t* ev_g = ctx->pipe_ev + 7;   // residue GEMMs of block j done (j < 4)
+    cudaEvent_t* ev_b = ctx->pipe_ev + 3;   // B block j in device memory (j < 4)
 
     char* ws = static_cast<char*>(ctx->ws);
     int* e = reinterpret_cast<int*>(ws + L.off_e);
@@ -331,7 +332,8 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
         (rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, L.geo.rows_a, L.geo.ld,
                                      ctx->d_status, S, f32, false))))
         return rc;
-    // B blocks: staged on S2 once A is in (A goes first over the link)
+    // B blocks on S2 once A is in (A goes first over the link): the first by the copy kernel,
+    // beside A's scaling and conversion; the others by the copy engine, beside the GEMMs
     const char* bsrc[4];
     if (cudaStreamWaitEvent(S2, ev_a, 0) != cudaSuccess) return OZAKI2_ERROR_CUDA;
     {
@@ -341,7 +343,9 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
             const char* src = static_cast<const char*>(B) + (size_t)c0 * ldb * esz;
             if (host_b) {
                 const size_t span = ((size_t)ldb * (cols - 1) + k) * esz;
-                if ((rc = cuda_rc(launch_stage_in(p, src, span, ctx->num_sms, S2)))) return rc;
+                rc = j == 0 ? cuda_rc(launch_stage_in(p, src, span, ctx->num_sms, S2))
+                            : cuda_rc(cudaMemcpyAsync(p, src, span, cudaMemcpyHostToDevice, S2));
+                if (rc) return rc;
                 bsrc[j] = p;
                 p += round_up((int64_t)span, 256);
             } else {
@@ -350,7 +354,7 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
             if (cudaEventRecord(ev_b[j], S2) != cudaSuccess) return OZAKI2_ERROR_CUDA;
         }
     }
-    // per block: scale and convert B_j, residue GEMMs (S); reconstruction (S2)
+    // per block on S: scale and convert B_j, residue GEMMs, reconstruction
     int64_t pb_off = 0;
     for (int j = 0; j < nb; ++j) {
         const int64_t c0 = j * blk, cols = std::min<int64_t>(blk, n - c0);
@@ -372,12 +376,9 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
                                       ctx->chunk_k, ctx->gemm_variant, S, ctx->wait_limit_ns,
                                       L.n_pad, L.m_pad * L.n_pad, ctx->group_m)))
             return rc;
-        if (cudaEventRecord(ev_g[j], S) != cudaSuccess ||
-            cudaStreamWaitEvent(S2, ev_g[j], 0) != cudaSuccess)
-            return OZAKI2_ERROR_CUDA;
         char* Cj = static_cast<char*>(C) + (size_t)c0 * ldc * esz;
         if ((rc = cuda_rc(launch_crt(res + c0, L.n_pad, L.m_pad * L.n_pad, m, (int)cols, e,
-                                     f + c0, alpha, beta, Cj, ldc, *T, ctx->d_status, S2, f32,
+                                     f + c0, alpha, beta, Cj, ldc, *T, ctx->d_status, S, f32,
                                      true))))
             return rc;
     }

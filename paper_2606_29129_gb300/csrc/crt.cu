@@ -440,9 +440,16 @@ __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res
                                                   const int* __restrict__ sb, OutT alpha,
                                                   OutT beta, int ab, OutT* __restrict__ C,
                                                   int64_t ldc, const CrtTables t) {
+    // 32 x 32 tiles of C in row-band order, blocks striding over them (one tile per block when
+    // the grid covers them all; fewer blocks leave room on each SM for another kernel)
     __shared__ OutT tile[TJ][TI + 1];
-    crt_tile<N, OutT, VEC>(res, ldr, plane, m, n, sa, sb, alpha, beta, ab, C, ldc, t,
-                           blockIdx.y * TI, blockIdx.x * TJ, tile);
+    const int tiles_j = (n + TJ - 1) / TJ;
+    const int64_t tiles = (int64_t)tiles_j * ((m + TI - 1) / TI);
+    for (int64_t w = blockIdx.x; w < tiles; w += gridDim.x) {
+        crt_tile<N, OutT, VEC>(res, ldr, plane, m, n, sa, sb, alpha, beta, ab, C, ldc, t,
+                               (int)(w / tiles_j) * TI, (int)(w % tiles_j) * TJ, tile);
+        __syncthreads();  // the tile buffer is written again by the next tile
+    }
 }
 
 // Grouped: each block reconstructs one 32 x 32 tile of one problem's C.
@@ -475,8 +482,11 @@ namespace {
 template <typename OutT, bool VEC>
 cudaError_t launch_crt_typed(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
                              const int* sa, const int* sb, OutT alpha, OutT beta, OutT* C,
-                             int64_t ldc, const ModTables& t, cudaStream_t stream) {
-    dim3 grid((n + TJ - 1) / TJ, (m + TI - 1) / TI);
+                             int64_t ldc, const ModTables& t, cudaStream_t stream,
+                             int max_blocks) {
+    const int64_t tiles = (int64_t)((n + TJ - 1) / TJ) * ((m + TI - 1) / TI);
+    const int64_t cap = max_blocks > 0 ? max_blocks : (int64_t)INT32_MAX;
+    const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
 #define OZAKI2_CRT_CASE(NN)                                                                   \
     case NN:                                                                                  \
         crt_kernel<NN, OutT, VEC><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb,     \
@@ -500,7 +510,7 @@ cudaError_t launch_crt_typed(const int8_t* res, int64_t ldr, int64_t plane, int 
 cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
                        const int* sa, const int* sb, double alpha, double beta, void* C,
                        int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream,
-                       bool f32, bool padded) {
+                       bool f32, bool padded, int max_blocks) {
     (void)status;
     if (m <= 0 || n <= 0) return cudaSuccess;
     // the 32-bit residue loads need 4-byte alignment and planes padded to whole 32 x 32 tiles
@@ -510,15 +520,15 @@ cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int
     if (f32) {
         auto* c = static_cast<float*>(C);
         return vec ? launch_crt_typed<float, true>(res, ldr, plane, m, n, sa, sb, (float)alpha,
-                                                   (float)beta, c, ldc, t, stream)
+                                                   (float)beta, c, ldc, t, stream, max_blocks)
                    : launch_crt_typed<float, false>(res, ldr, plane, m, n, sa, sb, (float)alpha,
-                                                    (float)beta, c, ldc, t, stream);
+                                                    (float)beta, c, ldc, t, stream, max_blocks);
     }
     auto* c = static_cast<double*>(C);
     return vec ? launch_crt_typed<double, true>(res, ldr, plane, m, n, sa, sb, alpha, beta, c, ldc,
-                                                t, stream)
+                                                t, stream, max_blocks)
                : launch_crt_typed<double, false>(res, ldr, plane, m, n, sa, sb, alpha, beta, c,
-                                                 ldc, t, stream);
+                                                 ldc, t, stream, max_blocks);
 }
 
 cudaError_t launch_crt_grouped(int N, const GroupProblem* probs, const CrtWork* work, int blocks,

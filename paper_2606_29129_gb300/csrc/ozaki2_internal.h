@@ -317,16 +317,19 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
 // f32: C holds floats (SGEMM: C'' rounded to 24 bits, alpha and beta applied in single
 // precision), else doubles.  padded: the residue buffer extends to whole 32 x 32 tiles in every
 // plane (true for the library's own layout), which allows 32-bit residue loads.
+// max_blocks > 0: at most that many thread blocks, each striding over the 32 x 32 tiles of C.
 cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int n,
                        const int* sa, const int* sb, double alpha, double beta, void* C,
                        int64_t ldc, const ModTables& t, unsigned* status, cudaStream_t stream,
-                       bool f32 = false, bool padded = false);
+                       bool f32 = false, bool padded = false, int max_blocks = 0);
 
 // Device copy of `bytes` from host memory the device can address (page-locked, or any host
 // memory on a coherent link): a kernel reads the host memory at the link's rate, where a copy-
 // engine upload measured erratic on GB300 after kernels had touched host memory.
+// blocks_per_sm: thread blocks per SM of the copy (default 8; 1 leaves room on every SM for a
+// kernel running beside it).
 cudaError_t launch_stage_in(void* dst, const void* src, size_t bytes, int num_sms,
-                            cudaStream_t stream);
+                            cudaStream_t stream, int blocks_per_sm = 8);
 
 cudaError_t launch_scale_c(int m, int n, double beta, void* C, int64_t ldc,
                            cudaStream_t stream, bool f32 = false);

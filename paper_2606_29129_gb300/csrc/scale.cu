@@ -589,11 +589,11 @@ __global__ void __launch_bounds__(256) stage_in_kernel(Word* __restrict__ dst,
 }  // namespace
 
 cudaError_t launch_stage_in(void* dst, const void* src, size_t bytes, int num_sms,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, int blocks_per_sm) {
     if (bytes == 0) return cudaSuccess;
     const uintptr_t a = reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) |
                         (uintptr_t)bytes;
-    const int grid = 8 * (num_sms > 0 ? num_sms : 1);
+    const int grid = (blocks_per_sm > 0 ? blocks_per_sm : 1) * (num_sms > 0 ? num_sms : 1);
     if ((a & 15) == 0)
         stage_in_kernel<<<grid, 256, 0, stream>>>(static_cast<uint4*>(dst),
                                                   static_cast<const uint4*>(src),

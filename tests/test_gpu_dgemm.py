@@ -307,21 +307,25 @@ def test_host_operands_unaligned_transposed(oz, orc, trans, own_workspace):
 
 
 @pytest.mark.parametrize("case", [
-    # (m, n, k, transA, host A, host B, host C, scaling, dtype)
-    (200, 4700, 600, "N", True, True, True, "proposed", "f64"),
-    (150, 9000, 300, "T", True, True, True, "proposed", "f64"),
-    (96, 8300, 257, "N", False, True, False, "proposed", "f64"),
-    (128, 4100, 1000, "N", False, False, True, "fast", "f64"),
-    (160, 5000, 400, "T", True, True, True, "proposed", "f32"),
+    # (m, n, k, transA, host A, host B, host C, scaling, dtype, beta)
+    (200, 4700, 600, "N", True, True, True, "proposed", "f64", -0.5),
+    (200, 4700, 600, "N", True, True, True, "proposed", "f64", 0.0),
+    (150, 9000, 300, "T", True, True, True, "proposed", "f64", 0.0),
+    (96, 8300, 257, "N", False, True, False, "proposed", "f64", -0.5),
+    (128, 4100, 1000, "N", False, False, True, "fast", "f64", 0.0),
+    (160, 5000, 400, "T", True, True, True, "proposed", "f32", 0.0),
+    (160, 5000, 400, "N", True, False, True, "proposed", "f32", 2.0),
 ])
 def test_host_operands_pipelined_over_column_blocks(oz, orc, case):
     """n >= 4096 with host-resident operands: the call stages A, then pipelines the column blocks
-    of op(B) (staging on a second stream, residue GEMMs per block, each block's reconstruction
-    overlapping the next block's GEMMs).  C is bit-identical to the call on device memory, and
-    to the oracle on a sample that takes columns from every block."""
+    of op(B) (later blocks uploaded by the copy engine on a second stream, residue GEMMs and the
+    reconstruction per block; with beta = 0 a host-resident C's blocks are written to a device
+    buffer and downloaded by the copy engine beside the next block's GEMMs).  C is bit-identical
+    to the call on device memory, and to the oracle on a sample that takes columns from every
+    block."""
     import torch
 
-    m, n, k, tA, ha, hb, hc, scaling, dtype = case
+    m, n, k, tA, ha, hb, hc, scaling, dtype, beta = case
     N = 14
     A, B = make(m, n, k, 1.0, 4 * n + m, tA, "N")
     Cin = synthetic.paper_matrix(m, n, 1.0, 5)
@@ -338,10 +342,10 @@ def test_host_operands_pipelined_over_column_blocks(oz, orc, case):
         return t.pin_memory() if host else t.cuda()
 
     Cd = _gpu.dev(Cin)
-    _gpu.ok(gemm(tA, "N", m, n, k, 0.75, _gpu.dev(A), lda, _gpu.dev(B), ldb, -0.5, Cd, m, N, h),
+    _gpu.ok(gemm(tA, "N", m, n, k, 0.75, _gpu.dev(A), lda, _gpu.dev(B), ldb, beta, Cd, m, N, h),
             "device call")
     Ah, Bh, Ch = dev_or_host(A, ha), dev_or_host(B, hb), dev_or_host(Cin, hc)
-    _gpu.ok(gemm(tA, "N", m, n, k, 0.75, Ah, lda, Bh, ldb, -0.5, Ch, m, N, h), "pipelined call")
+    _gpu.ok(gemm(tA, "N", m, n, k, 0.75, Ah, lda, Bh, ldb, beta, Ch, m, N, h), "pipelined call")
     torch.cuda.synchronize()
     assert h.status() == 0
     got = Ch.cpu().numpy()
@@ -352,12 +356,12 @@ def test_host_operands_pipelined_over_column_blocks(oz, orc, case):
     J = np.unique(J).astype(np.int32)
     mode = orc.FAST_MODE if scaling == "fast" else orc.PROPOSED_MODE
     if f32:
-        want = orc.sgemm_block(A, B, k, N, I, J, tA, "N", 0.75, -0.5,
+        want = orc.sgemm_block(A, B, k, N, I, J, tA, "N", 0.75, beta,
                                np.ascontiguousarray(Cin[np.ix_(J, I)]), lda=lda, ldb=ldb)
     elif mode == orc.PROPOSED_MODE:
-        want = orc.dgemm_block(A, B, m, n, k, N, I, J, tA, "N", 0.75, -0.5,
+        want = orc.dgemm_block(A, B, m, n, k, N, I, J, tA, "N", 0.75, beta,
                                np.ascontiguousarray(Cin[np.ix_(J, I)]), lda=lda, ldb=ldb)
     else:
-        full = orc.dgemm_mode(A, B, m, n, k, N, mode, tA, "N", 0.75, -0.5, Cin, lda, ldb)
+        full = orc.dgemm_mode(A, B, m, n, k, N, mode, tA, "N", 0.75, beta, Cin, lda, ldb)
         want = full[np.ix_(J, I)]
     assert _gpu.same_bits(got[np.ix_(J, I)], want)
