@@ -51,10 +51,6 @@ struct ozaki2_context {
     size_t enc_stage_bytes[kEncodeRing] = {};
     cudaEvent_t enc_staged[kEncodeRing] = {};
     int enc_next = 0;
-    // pipelined host-operand path of ozaki2_dgemm: a second stream and its events
-    cudaStream_t side = nullptr;
-    static constexpr int kPipeEvents = 12;
-    cudaEvent_t pipe_ev[kPipeEvents] = {};
 };
 
 namespace {
@@ -250,17 +246,24 @@ int ensure_input_stage(ozaki2_context* ctx, size_t bytes) {
     return OZAKI2_SUCCESS;
 }
 
-// Host-resident operands, pipelined over column blocks of op(B) (proposed or fast scaling, no
-// caller workspace, op(B) = B so that its columns are contiguous, n of at least 2 blocks).
-// Under these scalings a column's shift depends on that column alone (eq. (proposed-nu)), so the
-// columns of op(B) can be scaled, converted and multiplied block by block.  The handle's stream
-// S stages A (copy kernel), scales and converts it, then per block scales and converts B_j,
-// runs its residue GEMMs and its reconstruction.  The link transfers that can overlap the next
-// block's GEMMs, the uploads of B's later blocks, go through a copy engine on a second stream,
-// which uses no SMs (the persistent GEMM holds every SM).  A host-resident C is written by each
-// block's reconstruction over the link.  (Downloading C's blocks by the copy engine from a
-// device buffer measured no faster: ~7.5 ms of exposed link time at 16384^3 either way.)  Every
-// step computes what the unblocked path computes, so the result is the same bits.
+// Host-resident operands, pipelined (proposed or fast scaling, no caller workspace, op(B) = B so
+// that its columns are contiguous, n of at least two blocks).  Under these scalings a line's
+// shift depends on that line alone (eqs. (proposed-mu), (proposed-nu)), so rows of op(A) and
+// columns of op(B) can be scaled, converted and multiplied block by block.  The blocks of C, in
+// order: the row blocks A_i of a host-resident op(A) against B's first column block B_0 (one row
+// block when A is in device memory, or m is small), then all of A against each later column
+// block B_j.  For each block the handle's stream runs the scaling and conversion of its new
+// operand block, its residue GEMMs, a copy launched to overlap them that uploads the next
+// block's operand block (programmatic dependent launch: the GEMM lets it start once all its
+// CTAs are resident, and it takes the room they leave on each SM), then the reconstruction,
+// which writes a host-resident C over the link.  The first block's operand blocks are uploaded
+// before it at the link's full rate.  Every step computes what the unblocked path computes, so
+// the result is the same bits.
+//
+// Downloads do not overlap the same way: on GB300, device-to-host traffic beside the residue
+// GEMM measured no faster than after it (by a copy kernel or a copy engine; a copy kernel beside
+// a compute-only kernel of the same footprint keeps the link's full ~193 GB/s), so C's blocks
+// are reconstructed straight into host memory.
 constexpr int kPipeMinBlock = 2048;
 
 bool pipeline_applies(const ozaki2_context* ctx, char transB, int n, const void* A,
@@ -271,121 +274,182 @@ bool pipeline_applies(const ozaki2_context* ctx, char transB, int n, const void*
     return host_resident(A) || host_resident(B) || host_resident(C);
 }
 
+// Blocks of `lines` lines: 2 or 4 (4 from 4 kPipeMinBlock lines), multiples of 256 lines.
+struct LineBlocks {
+    int count;
+    int64_t size;
+    int64_t start(int i) const { return i * size; }
+    int64_t lines(int i, int64_t total) const { return std::min<int64_t>(size, total - i * size); }
+};
+LineBlocks line_blocks(int lines) {
+    int cnt = lines / (2 * kPipeMinBlock) >= 2 ? 4 : 2;
+    const int64_t size = ((int64_t)(lines + cnt - 1) / cnt + 255) / 256 * 256;
+    cnt = (int)((lines + size - 1) / size);
+    return {cnt, size};
+}
+
+// The copy of a band of lines of a column-major operand into a compact device buffer at dst:
+// rows [r0, r0 + h) of op(A) (lines_adjacent: op(A) = A) or columns [r0, r0 + h) of a k x n B.
+// The device pitch is a multiple of 16 bytes.
+Copy2D band_copy(void* dst, const void* X, int64_t ld, bool lines_adjacent, int64_t r0,
+                 int64_t h, int k, size_t esz) {
+    Copy2D c;
+    c.dst = dst;
+    if (lines_adjacent) {  // a run per column of A, h elements of it
+        c.src = static_cast<const char*>(X) + (size_t)r0 * esz;
+        c.width = (size_t)h * esz;
+        c.height = (size_t)k;
+    } else {               // a run per line, k elements
+        c.src = static_cast<const char*>(X) + (size_t)r0 * (size_t)ld * esz;
+        c.width = (size_t)k * esz;
+        c.height = (size_t)h;
+    }
+    c.spitch = (size_t)ld * esz;
+    c.dpitch = (c.width + 15) / 16 * 16;
+    return c;
+}
+
 int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, double alpha,
                     const void* A, int lda, const void* B, int ldb, double beta, void* C, int ldc,
                     int N, bool f32, const Layout& L, const ModTables* T) {
     int rc;
     cudaStream_t S = ctx->stream;
-    if (!ctx->side &&
-        cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess)
-        return OZAKI2_ERROR_CUDA;
-    for (auto& e : ctx->pipe_ev)
-        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-            return OZAKI2_ERROR_CUDA;
-    cudaStream_t S2 = ctx->side;
     const size_t esz = f32 ? 4 : 8;
-    // column blocks: multiples of 256 columns, at most 4
-    int nb = n / (2 * kPipeMinBlock) >= 2 ? 4 : 2;
-    const int64_t blk = ((int64_t)(n + nb - 1) / nb + 255) / 256 * 256;
-    nb = (int)((n + blk - 1) / blk);
-    if (nb > 4) return OZAKI2_ERROR_CUDA;  // not reached: blk >= n / 4
-
-    // device buffers: A and the blocks of B, when host-resident
     const bool host_a = host_resident(A), host_b = host_resident(B);
-    const int acols = is_notrans(transA) ? k : m, arows = is_notrans(transA) ? m : k;
-    const size_t a_span = ((size_t)lda * (size_t)(acols - 1) + (size_t)arows) * esz;
-    const size_t a_room = host_a ? (size_t)round_up((int64_t)a_span, 256) : 0;
-    size_t b_room = 0;
-    for (int j = 0; j < nb && host_b; ++j) {
-        const int64_t cols = std::min<int64_t>(blk, n - j * blk);
-        b_room += (size_t)round_up((int64_t)(((size_t)ldb * (cols - 1) + k) * esz), 256);
+    const bool a_adj = is_notrans(transA);  // rows of op(A) adjacent in memory
+    const LineBlocks cb = line_blocks(n);
+    const LineBlocks rb = host_a && m >= 2 * kPipeMinBlock ? line_blocks(m) : LineBlocks{1, m};
+    if (cb.count > 4 || rb.count > 4) return OZAKI2_ERROR_CUDA;  // not reached: size >= lines/4
+    const int nblk = rb.count + cb.count - 1;  // blocks of C
+
+    // block t of C: rows [r0, r0 + h), columns [c0, c0 + cols) of column block j
+    struct Blk {
+        int64_t r0, h, c0, cols;
+        int j;
+    };
+    auto blk = [&](int t) {
+        if (t < rb.count) return Blk{rb.start(t), rb.lines(t, m), 0, cb.lines(0, n), 0};
+        const int j = t - rb.count + 1;
+        return Blk{0, (int64_t)m, cb.start(j), cb.lines(j, n), j};
+    };
+
+    // device memory: copies of A's row blocks and B's column blocks; B's planes per column block
+    // (max(cols, 256) rows each)
+    size_t a_off[4] = {}, b_off[4] = {}, room = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = room;
+        room += (size_t)round_up((int64_t)bytes, 256);
+        return o;
+    };
+    Copy2D ab[4] = {}, bb[4] = {};
+    for (int i = 0; i < rb.count && host_a; ++i) {
+        ab[i] = band_copy(nullptr, A, lda, a_adj, rb.start(i), rb.lines(i, m), k, esz);
+        a_off[i] = take(ab[i].dpitch * ab[i].height);
     }
-    if (a_room + b_room && (rc = ensure_input_stage(ctx, a_room + b_room))) return rc;
+    for (int j = 0; j < cb.count && host_b; ++j) {
+        bb[j] = band_copy(nullptr, B, ldb, false, cb.start(j), cb.lines(j, n), k, esz);
+        b_off[j] = take(bb[j].dpitch * bb[j].height);
+    }
+    if (room && (rc = ensure_input_stage(ctx, room))) return rc;
     char* stage = static_cast<char*>(ctx->in_ws);
-    cudaEvent_t ev_start = ctx->pipe_ev[0], ev_a = ctx->pipe_ev[1], ev_done = ctx->pipe_ev[2];
-    cudaEvent_t* ev_b = ctx->pipe_ev + 3;   // B block j in device memory (j < 4)
+    for (int i = 0; i < rb.count && host_a; ++i) ab[i].dst = stage + a_off[i];
+    for (int j = 0; j < cb.count && host_b; ++j) bb[j].dst = stage + b_off[j];
 
     char* ws = static_cast<char*>(ctx->ws);
     int* e = reinterpret_cast<int*>(ws + L.off_e);
     int* f = reinterpret_cast<int*>(ws + L.off_f);
     char* pa = ws + L.off_pa;
-    char* pb = ws + L.off_pb;
     int8_t* res = reinterpret_cast<int8_t*>(ws + L.off_res);
     double* part = reinterpret_cast<double*>(ws + L.off_part);
     const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
-
-    // S2 starts after the work already queued on S (earlier calls may still read the buffers)
-    if (cudaEventRecord(ev_start, S) != cudaSuccess || cudaStreamWaitEvent(S2, ev_start, 0) !=
-                                                           cudaSuccess)
-        return OZAKI2_ERROR_CUDA;
-    // A: staged on S, then scaled and converted
-    if (host_a) {
-        if ((rc = cuda_rc(launch_stage_in(stage, A, a_span, ctx->num_sms, S)))) return rc;
-        A = stage;
-    }
-    if (cudaEventRecord(ev_a, S) != cudaSuccess) return OZAKI2_ERROR_CUDA;
-    int64_t als, aes;
-    rows_of_op(transA, lda, &als, &aes);
-    // (the pair launcher with no columns of op(B): it takes FP32 inputs as well)
-    if ((rc = cuda_rc(launch_scale_pair(A, als, aes, m, B, 0, 1, 0, k, pp, T->delta, e, f,
-                                        ctx->d_status, S, ctx->scaling, f32, part))) ||
-        (rc = cuda_rc(launch_convert(A, als, aes, m, k, e, T->conv, pa, L.geo.rows_a, L.geo.ld,
-                                     ctx->d_status, S, f32, false))))
-        return rc;
-    // B blocks on S2 once A is in (A goes first over the link): the first by the copy kernel,
-    // beside A's scaling and conversion; the others by the copy engine, beside the GEMMs
-    const char* bsrc[4];
-    if (cudaStreamWaitEvent(S2, ev_a, 0) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+    const int64_t pa_row = (int64_t)2 * L.geo.ld;  // bytes per row of a plane
+    char* pbj[4];
+    int rows_b[4];
     {
-        char* p = stage + a_room;
-        for (int j = 0; j < nb; ++j) {
-            const int64_t c0 = j * blk, cols = std::min<int64_t>(blk, n - c0);
-            const char* src = static_cast<const char*>(B) + (size_t)c0 * ldb * esz;
-            if (host_b) {
-                const size_t span = ((size_t)ldb * (cols - 1) + k) * esz;
-                rc = j == 0 ? cuda_rc(launch_stage_in(p, src, span, ctx->num_sms, S2))
-                            : cuda_rc(cudaMemcpyAsync(p, src, span, cudaMemcpyHostToDevice, S2));
-                if (rc) return rc;
-                bsrc[j] = p;
-                p += round_up((int64_t)span, 256);
-            } else {
-                bsrc[j] = src;
-            }
-            if (cudaEventRecord(ev_b[j], S2) != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        char* p = ws + L.off_pb;
+        for (int j = 0; j < cb.count; ++j) {
+            rows_b[j] = (int)std::max<int64_t>(cb.lines(j, n), 256);
+            pbj[j] = p;
+            p += (int64_t)2 * N * rows_b[j] * L.geo.ld;
         }
     }
-    // per block on S: scale and convert B_j, residue GEMMs, reconstruction
-    int64_t pb_off = 0;
-    for (int j = 0; j < nb; ++j) {
-        const int64_t c0 = j * blk, cols = std::min<int64_t>(blk, n - c0);
-        const int cols_pad = (int)round_up(cols, OZAKI2_ROWS_ALIGN_B);
-        const PlaneGeom geo{L.geo.rows_a, (int)std::max<int64_t>(cols, 256), L.geo.ld,
-                            L.geo.out_rows, (int)round_up(cols, 32)};
-        char* pbj = pb + pb_off;   // (2 ld bytes per row: a multiple of 128, as TMA needs)
-        pb_off += (int64_t)2 * N * geo.rows_b * geo.ld;
-        if (cudaStreamWaitEvent(S, ev_b[j], 0) != cudaSuccess) return OZAKI2_ERROR_CUDA;
-        // columns of op(B) = B: line stride ldb, elements contiguous
-        if ((rc = cuda_rc(launch_scale_pair(A, 0, 1, 0, bsrc[j], ldb, 1, (int)cols, k, pp,
-                                            T->delta, e, f + c0, ctx->d_status, S, ctx->scaling,
-                                            f32, part))) ||
-            (rc = cuda_rc(launch_convert(bsrc[j], ldb, 1, (int)cols, k, f + c0, T->conv, pbj,
-                                         geo.rows_b, geo.ld, ctx->d_status, S, f32, false))))
+    // scaling and conversion of A's row block i (into the same rows of the planes) and of B's
+    // column block j (into its own planes)
+    auto prep_a = [&](int i) -> int {
+        const int64_t r0 = rb.start(i), h = rb.lines(i, m);
+        const void* X = A;
+        int64_t ls, es;
+        rows_of_op(transA, lda, &ls, &es);
+        if (host_a) {
+            X = ab[i].dst;
+            const int64_t w = (int64_t)(ab[i].dpitch / esz);
+            ls = a_adj ? 1 : w;
+            es = a_adj ? w : 1;
+        }
+        const int rows_pad = i + 1 == rb.count ? (int)(L.geo.rows_a - r0) : (int)h;
+        int r;
+        if ((r = cuda_rc(launch_scale_pair(X, ls, es, (int)h, B, 0, 1, 0, k, pp, T->delta,
+                                           e + r0, f, ctx->d_status, S, ctx->scaling, f32,
+                                           part))) ||
+            (r = cuda_rc(launch_convert(X, ls, es, (int)h, k, e + r0, T->conv, pa + r0 * pa_row,
+                                        rows_pad, L.geo.ld, ctx->d_status, S, f32, false,
+                                        L.geo.rows_a))))
+            return r;
+        return OZAKI2_SUCCESS;
+    };
+    auto prep_b = [&](int j) -> int {
+        const int64_t c0 = cb.start(j), cols = cb.lines(j, n);
+        const void* X = static_cast<const char*>(B) + (size_t)c0 * ldb * esz;
+        int64_t ls = ldb;
+        if (host_b) {
+            X = bb[j].dst;
+            ls = (int64_t)(bb[j].dpitch / esz);
+        }
+        int r;
+        if ((r = cuda_rc(launch_scale_pair(A, 0, 1, 0, X, ls, 1, (int)cols, k, pp, T->delta, e,
+                                           f + c0, ctx->d_status, S, ctx->scaling, f32,
+                                           part))) ||
+            (r = cuda_rc(launch_convert(X, ls, 1, (int)cols, k, f + c0, T->conv, pbj[j],
+                                        rows_b[j], L.geo.ld, ctx->d_status, S, f32, false))))
+            return r;
+        return OZAKI2_SUCCESS;
+    };
+
+    // the first block's operand blocks at the link's full rate
+    {
+        Copy2D first[2];
+        int nf = 0;
+        if (host_a) first[nf++] = ab[0];
+        if (host_b) first[nf++] = bb[0];
+        if ((rc = cuda_rc(launch_copies_2d(first, nf, 4 * ctx->num_sms, false, S)))) return rc;
+    }
+    for (int t = 0; t < nblk; ++t) {
+        const Blk b = blk(t);
+        if (t == 0 && ((rc = prep_a(0)) || (rc = prep_b(0)))) return rc;
+        if (t > 0 && (rc = t < rb.count ? prep_a(t) : prep_b(b.j))) return rc;
+        const bool last_row = b.r0 + b.h >= m;
+        const PlaneGeom geo{last_row ? (int)(L.geo.rows_a - b.r0) : (int)b.h, rows_b[b.j],
+                            L.geo.ld, (int)round_up(b.h, 32), (int)round_up(b.cols, 32),
+                            L.geo.rows_a};
+        int8_t* out = res + b.r0 * L.n_pad + b.c0;
+        if ((rc = launch_residue_gemm(N, (int)(last_row ? L.m_pad - b.r0 : b.h),
+                                      (int)round_up(b.cols, OZAKI2_ROWS_ALIGN_B), (int)L.k_pad,
+                                      geo, pa + b.r0 * pa_row, pbj[b.j], out, T->epi,
+                                      ctx->d_status, ctx->num_sms, ctx->chunk_k,
+                                      ctx->gemm_variant, S, ctx->wait_limit_ns, L.n_pad,
+                                      L.m_pad * L.n_pad, ctx->group_m)))
             return rc;
-        if ((rc = launch_residue_gemm(N, (int)L.m_pad, cols_pad, (int)L.k_pad, geo, pa, pbj,
-                                      res + c0, T->epi, ctx->d_status, ctx->num_sms,
-                                      ctx->chunk_k, ctx->gemm_variant, S, ctx->wait_limit_ns,
-                                      L.n_pad, L.m_pad * L.n_pad, ctx->group_m)))
-            return rc;
-        char* Cj = static_cast<char*>(C) + (size_t)c0 * ldc * esz;
-        if ((rc = cuda_rc(launch_crt(res + c0, L.n_pad, L.m_pad * L.n_pad, m, (int)cols, e,
-                                     f + c0, alpha, beta, Cj, ldc, *T, ctx->d_status, S, f32,
-                                     true))))
+        // beside the GEMMs: the next block's operand block in
+        const Copy2D* next = nullptr;
+        if (t + 1 < rb.count && host_a) next = &ab[t + 1];
+        if (t + 1 >= rb.count && t + 1 < nblk && host_b) next = &bb[blk(t + 1).j];
+        if (next && (rc = cuda_rc(launch_copies_2d(next, 1, ctx->num_sms, true, S)))) return rc;
+        char* Cb = static_cast<char*>(C) + ((size_t)b.c0 * ldc + (size_t)b.r0) * esz;
+        if ((rc = cuda_rc(launch_crt(out, L.n_pad, L.m_pad * L.n_pad, (int)b.h, (int)b.cols,
+                                     e + b.r0, f + b.c0, alpha, beta, Cb, ldc, *T,
+                                     ctx->d_status, S, f32, true))))
             return rc;
     }
-    // the call completes on S
-    if (cudaEventRecord(ev_done, S2) != cudaSuccess || cudaStreamWaitEvent(S, ev_done, 0) !=
-                                                           cudaSuccess)
-        return OZAKI2_ERROR_CUDA;
     return OZAKI2_SUCCESS;
 }
 
@@ -524,9 +588,6 @@ int ozaki2_destroy(ozaki2_handle_t handle) {
     for (auto& e : handle->ev)
         if (e) cudaEventDestroy(e);
     if (handle->staged) cudaEventDestroy(handle->staged);
-    for (auto& e : handle->pipe_ev)
-        if (e) cudaEventDestroy(e);
-    if (handle->side) cudaStreamDestroy(handle->side);
     for (int i = 0; i < ozaki2_context::kEncodeRing; ++i) {
         if (handle->enc_staged[i]) cudaEventDestroy(handle->enc_staged[i]);
         if (handle->enc_stage[i]) cudaFreeHost(handle->enc_stage[i]);

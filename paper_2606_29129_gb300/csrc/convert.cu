@@ -234,10 +234,9 @@ __device__ __forceinline__ void load8(const float* src, bool vec, float (&v)[8])
 template <int N, int L, typename T>
 __device__ __forceinline__ void convert_contiguous_item(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
-    const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
+    const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int64_t plane_elems, int k_pad,
     int64_t g, unsigned* status) {
     const int groups = k_pad / 8;
-    const int64_t plane_elems = (int64_t)rows_pad * k_pad;
     constexpr int per16 = 16 / (int)sizeof(T);  // elements per 16 bytes
     const bool vec = (ld % per16 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15u) == 0);
     {
@@ -264,12 +263,12 @@ template <int N, int L, typename T>
 __global__ void __launch_bounds__(256) convert_contiguous_kernel(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
-    unsigned* status) {
+    int64_t plane_elems, unsigned* status) {
     const int64_t total = (int64_t)rows_pad * (k_pad / 8);
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g < total)
-        convert_contiguous_item<N, L, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad, g,
-                                      status);
+        convert_contiguous_item<N, L, T>(X, ld, lines, len, shifts, t, planes, plane_elems,
+                                         k_pad, g, status);
 }
 
 // Lines adjacent (line_stride == 1): a block converts a tile of 64 lines x 64 elements.  The tile
@@ -284,9 +283,8 @@ template <int N, int L, typename T>
 __device__ __forceinline__ void convert_adjacent_tile(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables& t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
-    int64_t tt, T (*tile)[kTileLines + 1], unsigned* status) {
+    int64_t plane_elems, int64_t tt, T (*tile)[kTileLines + 1], unsigned* status) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t plane_elems = (int64_t)rows_pad * k_pad;
     const int tiles_l = (rows_pad + kTileLines - 1) / kTileLines;
     {
         const int tl = (int)(tt % tiles_l);
@@ -329,10 +327,10 @@ template <int N, int L, typename T>
 __global__ void __launch_bounds__(256) convert_adjacent_kernel(
     const T* __restrict__ X, int64_t ld, int lines, int len, const int* __restrict__ shifts,
     const ConvertTables t, __nv_bfloat16* __restrict__ planes, int rows_pad, int k_pad,
-    unsigned* status) {
+    int64_t plane_elems, unsigned* status) {
     __shared__ T tile[kTileK][kTileLines + 1];
     convert_adjacent_tile<N, L, T>(X, ld, lines, len, shifts, t, planes, rows_pad, k_pad,
-                                blockIdx.x, tile, status);  // one tile per block
+                                   plane_elems, blockIdx.x, tile, status);  // one tile per block
 }
 
 // Grouped: each block converts one tile (adjacent lines) or 256 groups of 8 elements
@@ -352,32 +350,33 @@ __global__ void __launch_bounds__(256) convert_grouped_kernel(
     auto* planes = static_cast<__nv_bfloat16*>(w.side ? P.pb : P.pa);
     if (es != 1) {
         convert_adjacent_tile<N, L, double>(X, es, lines, P.k, shifts, t, planes, rows,
-                                            P.geo.ld, w.block, tile, status);
+                                            P.geo.ld, (int64_t)rows * P.geo.ld, w.block, tile,
+                                            status);
     } else {
         const int64_t g = (int64_t)w.block * 256 + threadIdx.x;
         if (g < (int64_t)rows * (P.geo.ld / 8))
-            convert_contiguous_item<N, L, double>(X, ls, lines, P.k, shifts, t, planes, rows,
-                                                  P.geo.ld, g, status);
+            convert_contiguous_item<N, L, double>(X, ls, lines, P.k, shifts, t, planes,
+                                                  (int64_t)rows * P.geo.ld, P.geo.ld, g, status);
     }
 }
 
 template <int N, int L, typename T>
 cudaError_t launch_convert_nl(const T* X, int64_t line_stride, int64_t elem_stride,
                               int lines, int len, const int* shifts, const ConvertTables& t,
-                              __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
-                              cudaStream_t stream) {
+                              __nv_bfloat16* out, int rows_pad, int k_pad, int64_t plane_elems,
+                              unsigned* status, cudaStream_t stream) {
     if (elem_stride != 1) {  // then line_stride == 1: lines adjacent
         const int grid = (int)((int64_t)((rows_pad + kTileLines - 1) / kTileLines) *
                                ((k_pad + kTileK - 1) / kTileK));
         convert_adjacent_kernel<N, L, T><<<grid, 256, 0, stream>>>(X, elem_stride, lines, len,
                                                                 shifts, t, out, rows_pad, k_pad,
-                                                                status);
+                                                                plane_elems, status);
     } else {
         const int64_t total = (int64_t)rows_pad * (k_pad / 8);
         const int grid = (int)((total + 255) / 256);
         convert_contiguous_kernel<N, L, T><<<grid, 256, 0, stream>>>(X, line_stride, lines, len,
                                                                   shifts, t, out, rows_pad,
-                                                                  k_pad, status);
+                                                                  k_pad, plane_elems, status);
     }
     return cudaGetLastError();
 }
@@ -386,16 +385,17 @@ cudaError_t launch_convert_nl(const T* X, int64_t line_stride, int64_t elem_stri
 template <int N, typename T>
 cudaError_t launch_convert_n(const T* X, int64_t line_stride, int64_t elem_stride,
                              int lines, int len, const int* shifts, const ConvertTables& t,
-                             __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
-                             cudaStream_t stream, bool accurate = false) {
+                             __nv_bfloat16* out, int rows_pad, int k_pad, int64_t plane_elems,
+                             unsigned* status, cudaStream_t stream, bool accurate = false) {
     if constexpr (limbs_scaled(N) != limbs_for(N)) {
         if (!accurate)
             return launch_convert_nl<N, limbs_scaled(N), T>(X, line_stride, elem_stride, lines,
                                                             len, shifts, t, out, rows_pad, k_pad,
-                                                            status, stream);
+                                                            plane_elems, status, stream);
     }
     return launch_convert_nl<N, limbs_for(N), T>(X, line_stride, elem_stride, lines, len, shifts,
-                                                 t, out, rows_pad, k_pad, status, stream);
+                                                 t, out, rows_pad, k_pad, plane_elems, status,
+                                                 stream);
 }
 
 }  // namespace
@@ -416,9 +416,11 @@ cudaError_t launch_convert_bar(const void* X, int64_t line_stride, int64_t elem_
     auto* out = static_cast<__nv_bfloat16*>(plane);
     if (f32)
         return launch_convert_n<1>(static_cast<const float*>(X), line_stride, elem_stride, lines,
-                                   len, codes, t, out, rows_pad, k_pad, status, stream);
+                                   len, codes, t, out, rows_pad, k_pad,
+                                   (int64_t)rows_pad * k_pad, status, stream);
     return launch_convert_n<1>(static_cast<const double*>(X), line_stride, elem_stride, lines,
-                               len, codes, t, out, rows_pad, k_pad, status, stream);
+                               len, codes, t, out, rows_pad, k_pad, (int64_t)rows_pad * k_pad,
+                               status, stream);
 }
 
 namespace {
@@ -467,13 +469,14 @@ namespace {
 template <typename T>
 cudaError_t launch_convert_typed(const T* X, int64_t line_stride, int64_t elem_stride, int lines,
                                  int len, const int* shifts, const ConvertTables& t,
-                                 __nv_bfloat16* out, int rows_pad, int k_pad, unsigned* status,
-                                 cudaStream_t stream, bool accurate) {
+                                 __nv_bfloat16* out, int rows_pad, int k_pad,
+                                 int64_t plane_elems, unsigned* status, cudaStream_t stream,
+                                 bool accurate) {
     switch (t.N) {
 #define OZAKI2_CONVERT_CASE(NN)                                                              \
     case NN:                                                                                 \
         return launch_convert_n<NN>(X, line_stride, elem_stride, lines, len, shifts, t, out, \
-                                    rows_pad, k_pad, status, stream, accurate);
+                                    rows_pad, k_pad, plane_elems, status, stream, accurate);
         OZAKI2_CONVERT_CASE(2) OZAKI2_CONVERT_CASE(3) OZAKI2_CONVERT_CASE(4)
         OZAKI2_CONVERT_CASE(5) OZAKI2_CONVERT_CASE(6) OZAKI2_CONVERT_CASE(7)
         OZAKI2_CONVERT_CASE(8) OZAKI2_CONVERT_CASE(9) OZAKI2_CONVERT_CASE(10)
@@ -490,15 +493,19 @@ cudaError_t launch_convert_typed(const T* X, int64_t line_stride, int64_t elem_s
 cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, const int* shifts, const ConvertTables& t, void* planes,
                            int rows_pad, int k_pad, unsigned* status, cudaStream_t stream,
-                           bool f32, bool accurate) {
+                           bool f32, bool accurate, int plane_rows) {
     if (rows_pad <= 0 || k_pad <= 0) return cudaSuccess;
+    if (plane_rows <= 0) plane_rows = rows_pad;
+    if (plane_rows < rows_pad) return cudaErrorInvalidValue;
+    const int64_t plane_elems = (int64_t)plane_rows * k_pad;
     auto* out = static_cast<__nv_bfloat16*>(planes);
     if (f32)
         return launch_convert_typed(static_cast<const float*>(X), line_stride, elem_stride, lines,
-                                    len, shifts, t, out, rows_pad, k_pad, status, stream,
-                                    accurate);
+                                    len, shifts, t, out, rows_pad, k_pad, plane_elems, status,
+                                    stream, accurate);
     return launch_convert_typed(static_cast<const double*>(X), line_stride, elem_stride, lines,
-                                len, shifts, t, out, rows_pad, k_pad, status, stream, accurate);
+                                len, shifts, t, out, rows_pad, k_pad, plane_elems, status, stream,
+                                accurate);
 }
 
 }  // namespace ozaki2

@@ -76,6 +76,9 @@ struct ModTables {
 struct PlaneGeom {
     int rows_a, rows_b, ld;
     int out_rows, out_cols;
+    // rows between consecutive planes of A when the GEMM reads a band of rows out of taller
+    // planes (0: rows_a, the planes are stored back to back)
+    int plane_rows_a = 0;
 };
 // bn: width of the residue-GEMM tiles (rows of op(B) in one TMA box: 256, or 128 or 64 for the
 // narrower tiles of grouped calls).
@@ -302,10 +305,12 @@ cudaError_t launch_scale(const double* X, int64_t line_stride, int64_t elem_stri
 // f32: X holds floats (SGEMM), else doubles.  accurate: the shifts come from accurate mode,
 // whose a' may need six more bits than the proposed and fast scalings allow.
 // Writes planes [N][rows][ld]: rows at or beyond `lines` and K at or beyond `len` as zeros.
+// plane_rows: rows from one plane to the next (0: rows), to convert a band of lines into
+// taller planes (planes pointing at the band's first row).
 cudaError_t launch_convert(const void* X, int64_t line_stride, int64_t elem_stride, int lines,
                            int len, const int* shifts, const ConvertTables& t, void* planes,
                            int rows, int ld, unsigned* status, cudaStream_t stream,
-                           bool f32 = false, bool accurate = false);
+                           bool f32 = false, bool accurate = false, int plane_rows = 0);
 
 int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const PlaneGeom& geo,
                         const void* planes_a, const void* planes_b, int8_t* out,
@@ -330,6 +335,22 @@ cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int
 // kernel running beside it).
 cudaError_t launch_stage_in(void* dst, const void* src, size_t bytes, int num_sms,
                             cudaStream_t stream, int blocks_per_sm = 8);
+
+// A 2-D copy between memories the device can address (device, page-locked or coherent host
+// memory): `height` rows of `width` bytes, from src (rows spitch bytes apart) to dst (dpitch
+// bytes apart).
+struct Copy2D {
+    void* dst;
+    const void* src;
+    size_t dpitch, spitch, width, height;
+};
+// Up to two copies in one launch, each by up to `blocks` thread blocks of 256 threads.
+// overlap_previous: launched with programmatic serialization, so that the copies run beside the
+// kernel before them in the stream once that kernel's blocks have all started (the residue
+// GEMM signals this as it starts); the copy then completes only after that kernel.  The copies
+// must not read what that kernel writes.
+cudaError_t launch_copies_2d(const Copy2D* copies, int count, int blocks, bool overlap_previous,
+                             cudaStream_t stream);
 
 cudaError_t launch_scale_c(int m, int n, double beta, void* C, int64_t ldc,
                            cudaStream_t stream, bool f32 = false);

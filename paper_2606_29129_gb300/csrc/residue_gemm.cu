@@ -590,6 +590,9 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     residue_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                         const __grid_constant__ CUtensorMap tmB, const GemmArgs args) {
+    // a copy launched after this GEMM with programmatic serialization may run beside it (the
+    // pipelined host-operand path); every CTA is resident when it gets here
+    pdl_launch_dependents();
     const SingleSource src{&tmA, &tmB, &args};
     residue_gemm_body(src, args.total_tiles, args);
 }
@@ -639,6 +642,7 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     residue_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
                              const __grid_constant__ CUtensorMap tmB, const GemmArgs args) {
+    pdl_launch_dependents();  // as in residue_gemm_kernel
     extern __shared__ uint8_t smem_raw[];
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
     uint8_t* smem = smem_raw + pad;
@@ -889,11 +893,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // 3-D map over residue planes [N][rows][ld] (bf16, K contiguous), box 64 x box_rows x 1; the
 // boxes of the tile grid that reach beyond rows or ld read zeros.
-bool encode_planes(CUtensorMap* map, const void* base, int N, int rows, int ld, int box_rows) {
+// rows: the rows the GEMM may read from each plane (rows beyond read as zeros); plane_rows: the
+// rows from one plane to the next (0: rows).
+bool encode_planes(CUtensorMap* map, const void* base, int N, int rows, int ld, int box_rows,
+                   int plane_rows = 0) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
+    if (plane_rows <= 0) plane_rows = rows;
+    if (plane_rows < rows) return false;
     cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)rows, (cuuint64_t)N};
-    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * (cuuint64_t)ld * 2};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)plane_rows * (cuuint64_t)ld * 2};
     cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
@@ -1086,7 +1095,8 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
         variant == OZAKI2_GEMM_PAIR || (variant == OZAKI2_GEMM_AUTO && auto_pair);
     CUtensorMap ta, tb;
     if (use_pair) {
-        if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, pair::HALF) ||
+        if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, pair::HALF,
+                           geo.plane_rows_a) ||
             !encode_planes(&tb, planes_b, num_moduli, geo.rows_b, geo.ld, pair::HALF))
             return OZAKI2_ERROR_DRIVER;
         if (ensure_smem_attr((const void*)residue_gemm_pair_kernel, (int)pair::SMEM_BYTES,
@@ -1120,7 +1130,7 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
             return OZAKI2_ERROR_CUDA;
         return cudaGetLastError() == cudaSuccess ? OZAKI2_SUCCESS : OZAKI2_ERROR_CUDA;
     }
-    if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, BM) ||
+    if (!encode_planes(&ta, planes_a, num_moduli, geo.rows_a, geo.ld, BM, geo.plane_rows_a) ||
         !encode_planes(&tb, planes_b, num_moduli, geo.rows_b, geo.ld, BN))
         return OZAKI2_ERROR_DRIVER;
     if (ensure_smem_attr((const void*)residue_gemm_kernel, (int)SMEM_BYTES, g_attr_single) !=

@@ -15,7 +15,10 @@
 // (scale_fold_kernel).
 #include <float.h>
 
+#include <algorithm>
+
 #include "ozaki2_internal.h"
+#include "sm103_ptx.cuh"
 
 namespace ozaki2 {
 namespace {
@@ -586,7 +589,79 @@ __global__ void __launch_bounds__(256) stage_in_kernel(Word* __restrict__ dst,
     for (; i < count; i += stride) dst[i] = src[i];
 }
 
+// 2-D copies: copy c moves c.height rows of c.width bytes (c.width / W words), row r from
+// c.src + r c.spitch to c.dst + r c.dpitch.  Blocks [0, blocks0) take copy 0, the others copy 1;
+// a block copies rows b, b + (its copy's blocks), ..., each thread keeping four words in flight,
+// so one block per SM already covers the host link's latency.  Launched to overlap the grid
+// before it (programmatic serialization), the kernel waits for that grid at its end, so that
+// work launched after the copy also runs after that grid.
+template <typename Word>
+__global__ void __launch_bounds__(256) copy_2d_kernel(const Copy2D c0, const Copy2D c1,
+                                                      int blocks0) {
+    const bool second = (int)blockIdx.x >= blocks0;
+    const Copy2D& c = second ? c1 : c0;
+    const int64_t b = second ? blockIdx.x - blocks0 : blockIdx.x;
+    const int64_t nb = second ? gridDim.x - blocks0 : blocks0;
+    const int64_t words = (int64_t)(c.width / sizeof(Word));
+    for (int64_t r = b; r < (int64_t)c.height; r += nb) {
+        const Word* s = reinterpret_cast<const Word*>(static_cast<const char*>(c.src) +
+                                                      r * (int64_t)c.spitch);
+        Word* d = reinterpret_cast<Word*>(static_cast<char*>(c.dst) + r * (int64_t)c.dpitch);
+        int64_t i = threadIdx.x;
+        for (; i + 3 * 256 < words; i += 4 * 256) {
+            Word w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = s[i + u * 256];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) d[i + u * 256] = w[u];
+        }
+        for (; i < words; i += 256) d[i] = s[i];
+    }
+    pdl_wait_prerequisites();
+}
+
+template <typename Word>
+cudaError_t launch_copy_2d_w(const Copy2D& c0, const Copy2D& c1, int blocks0, int blocks1,
+                             bool overlap_previous, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3((unsigned)(blocks0 + blocks1));
+    cfg.blockDim = dim3(256);
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap_previous ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, copy_2d_kernel<Word>, c0, c1, blocks0);
+}
+
 }  // namespace
+
+cudaError_t launch_copies_2d(const Copy2D* copies, int count, int blocks, bool overlap_previous,
+                             cudaStream_t stream) {
+    Copy2D c[2] = {};
+    int nb[2] = {0, 0}, used = 0;
+    uintptr_t a = 0;
+    for (int i = 0; i < count && i < 2; ++i) {
+        const Copy2D& x = copies[i];
+        if (x.width == 0 || x.height == 0) continue;
+        if (x.dpitch < x.width || x.spitch < x.width) return cudaErrorInvalidValue;
+        a |= reinterpret_cast<uintptr_t>(x.dst) | reinterpret_cast<uintptr_t>(x.src) |
+             (uintptr_t)x.dpitch | (uintptr_t)x.spitch | (uintptr_t)x.width;
+        c[used] = x;
+        nb[used] = (int)std::min<int64_t>(blocks > 0 ? blocks : 1, (int64_t)x.height);
+        ++used;
+    }
+    if (count > 2) return cudaErrorInvalidValue;
+    if (used == 0) return cudaSuccess;
+    if ((a & 15) == 0)
+        return launch_copy_2d_w<uint4>(c[0], c[1], nb[0], nb[1], overlap_previous, stream);
+    if ((a & 7) == 0)
+        return launch_copy_2d_w<uint2>(c[0], c[1], nb[0], nb[1], overlap_previous, stream);
+    if ((a & 3) == 0)
+        return launch_copy_2d_w<unsigned>(c[0], c[1], nb[0], nb[1], overlap_previous, stream);
+    return launch_copy_2d_w<unsigned char>(c[0], c[1], nb[0], nb[1], overlap_previous, stream);
+}
 
 cudaError_t launch_stage_in(void* dst, const void* src, size_t bytes, int num_sms,
                             cudaStream_t stream, int blocks_per_sm) {

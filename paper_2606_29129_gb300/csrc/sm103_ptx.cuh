@@ -110,5 +110,15 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
+// Programmatic dependent launch: lets the next kernel of the stream, when it is launched with
+// programmatic stream serialization, start beside this grid (no effect otherwise).
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Waits until the grids this one was allowed to overlap have completed and their writes are
+// visible (returns at once for a kernel launched without that overlap).
+__device__ __forceinline__ void pdl_wait_prerequisites() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 }  // namespace
 }  // namespace ozaki2

@@ -307,7 +307,7 @@ def test_host_operands_unaligned_transposed(oz, orc, trans, own_workspace):
 
 
 @pytest.mark.parametrize("case", [
-    # (m, n, k, transA, host A, host B, host C, scaling, dtype, beta)
+    # (m, n, k, transA, host A, host B, host C, scaling, dtype, beta[, lda and ldb padding])
     (200, 4700, 600, "N", True, True, True, "proposed", "f64", -0.5),
     (200, 4700, 600, "N", True, True, True, "proposed", "f64", 0.0),
     (150, 9000, 300, "T", True, True, True, "proposed", "f64", 0.0),
@@ -315,19 +315,29 @@ def test_host_operands_unaligned_transposed(oz, orc, trans, own_workspace):
     (128, 4100, 1000, "N", False, False, True, "fast", "f64", 0.0),
     (160, 5000, 400, "T", True, True, True, "proposed", "f32", 0.0),
     (160, 5000, 400, "N", True, False, True, "proposed", "f32", 2.0),
+    # m >= 4096 with host A: A's row blocks within the first column block (ragged last blocks)
+    (4500, 4300, 300, "N", True, True, True, "proposed", "f64", 0.0),
+    (8300, 4200, 200, "T", True, True, True, "proposed", "f64", 0.0, 3),
+    (4200, 8500, 190, "N", True, True, True, "proposed", "f64", 0.0, 5),
+    (4200, 4500, 200, "N", True, False, True, "proposed", "f32", 0.0),
+    (4200, 4500, 200, "T", True, True, False, "proposed", "f64", -0.5),
+    (4200, 4500, 130, "N", True, True, True, "proposed", "f64", 1.5),
 ])
 def test_host_operands_pipelined_over_column_blocks(oz, orc, case):
-    """n >= 4096 with host-resident operands: the call stages A, then pipelines the column blocks
-    of op(B) (later blocks uploaded by the copy engine on a second stream, residue GEMMs and the
-    reconstruction per block; with beta = 0 a host-resident C's blocks are written to a device
-    buffer and downloaded by the copy engine beside the next block's GEMMs).  C is bit-identical
-    to the call on device memory, and to the oracle on a sample that takes columns from every
-    block."""
+    """n >= 4096 with host-resident operands: the call pipelines the column blocks of op(B) and,
+    within the first, the row blocks of a host-resident op(A) with m >= 4096 (each later operand
+    block uploaded by a copy that overlaps the previous block's residue GEMMs; a host-resident C
+    written block by block by the reconstruction).  C is bit-identical to the call on device
+    memory, and to the oracle on a sample that takes rows and columns from every block."""
     import torch
 
-    m, n, k, tA, ha, hb, hc, scaling, dtype, beta = case
+    m, n, k, tA, ha, hb, hc, scaling, dtype, beta = case[:10]
+    pad = case[10] if len(case) > 10 else 0
     N = 14
     A, B = make(m, n, k, 1.0, 4 * n + m, tA, "N")
+    if pad:  # leading dimensions beyond the rows of the stored matrices
+        A = np.pad(A, ((0, 0), (0, pad)))
+        B = np.pad(B, ((0, 0), (0, pad)))
     Cin = synthetic.paper_matrix(m, n, 1.0, 5)
     f32 = dtype == "f32"
     if f32:
@@ -351,7 +361,8 @@ def test_host_operands_pipelined_over_column_blocks(oz, orc, case):
     got = Ch.cpu().numpy()
     assert _gpu.same_bits(got, Cd.cpu().numpy())
     rng = np.random.default_rng(n)
-    I = np.sort(rng.choice(m, size=24, replace=False)).astype(np.int32)
+    I = np.sort(np.concatenate([rng.choice(m, size=24, replace=False), [0, m - 1]]))
+    I = np.unique(I).astype(np.int32)
     J = np.sort(np.concatenate([rng.choice(n, size=40, replace=False), [0, n - 1]]))
     J = np.unique(J).astype(np.int32)
     mode = orc.FAST_MODE if scaling == "fast" else orc.PROPOSED_MODE
