@@ -185,41 +185,23 @@ __device__ __forceinline__ uint32_t dot2(uint32_t kpair, uint32_t b, uint32_t c)
     return d;
 }
 
-// OutT = double (DGEMM) or float (SGEMM): C'' is rounded to 53 or 24 bits, then scaled.  v: the
-// pair sums of the entry (pair_sums).
+// The W words of Y = X - Q P, passed by value to the out-of-line path.
+template <int W>
+struct Words {
+    uint32_t w[W];
+};
+
+// Rounding of C'' = Y (two's complement, |Y| < P) to OutT, scaled by 2^-(ea + fb), for every
+// case the straight-line path of crt_value leaves: an estimate near a half-integer (Y may be off
+// by P), a leading word below the top one, a result outside the normal range.  Out of line, so
+// the common path carries none of it.
 template <int N, typename OutT>
-__device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int ea, int fb,
-                                          const CrtTables& t) {
+__device__ __noinline__ OutT crt_value_rare(Words<crt_words(N)> Yw, bool near_half, int ea,
+                                            int fb, const CrtTables& t) {
     constexpr int W = crt_words(N);
-    constexpr int G = (N + 1) / 2;
-    if (ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE) {
-        if constexpr (sizeof(OutT) == 4) return __uint_as_float(0x7FC00000u);
-        else return __longlong_as_double(0x7FF8000000000000ll);
-    }
-    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^46 X / P (fixed point).  A pair's
-    // constant round(2^46 / prod_g) is below 2^32, so its term is one 32 x 32 -> 64-bit
-    // multiply-add; a single modulus (odd N) keeps a 64-bit constant.
-    uint64_t acc[W];
-#pragma unroll
-    for (int j = 0; j < W; ++j) acc[j] = 0;
-    uint64_t S = 0;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        if (2 * g + 1 < N) S += (uint64_t)v[g] * (uint32_t)t.R46[g];
-        else S += (uint64_t)v[g] * t.R46[g];
-#pragma unroll
-        for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.PG[g][j] * v[g];
-    }
-    uint32_t X[W];
-    fold_columns<W>(acc, X);
-    // Q = round(X / P) from the fixed-point estimate; |S/2^46 - X/P| < 2^-18
-    const uint64_t frac = S & ((1ull << 46) - 1);
-    const uint32_t Q = (uint32_t)((S + (1ull << 45)) >> 46);
-    uint32_t Y[W];
-    add_word_times<W>(X, Q, t.negP, Y);  // Y = X - Q P (mod 2^(32 W))
-    const uint64_t half = 1ull << 45;
-    if ((frac > half ? frac - half : half - frac) < (1ull << 36)) {
-        // The estimate sits within 2^-10 of a half-integer: make -P/2 <= Y < P/2 exactly.
+    uint32_t (&Y)[W] = Yw.w;
+    if (near_half) {
+        // make -P/2 <= Y < P/2 exactly
         const bool neg = (Y[W - 1] >> 31) != 0;
         uint32_t mag[W];
         uint32_t cb = 1;
@@ -253,78 +235,126 @@ __device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int 
             }
         }
     }
-    // |Y| and sign
     const bool neg = abs_words<W>(Y);
-    // leading word and the 96-bit window below the leading bit.  The top word is almost always
-    // the leading one (the shifts make |C''| large against P), so that case is straight-line
-    // code and the search for a lower leading word is a branch.
-    int top = W - 1;
-    uint32_t w0 = Y[W - 1], w1 = W > 1 ? Y[W - 2] : 0u, w2 = W > 2 ? Y[W - 3] : 0u, low_or = 0;
+    int top = -1;
 #pragma unroll
-    for (int j = 0; j < W - 3; ++j) low_or |= Y[j];
-    if (w0 == 0) {
-        top = -1;
+    for (int j = W - 1; j >= 0; --j)
+        if (top < 0 && Y[j] != 0) top = j;
+    if (top < 0) return (OutT)0;
+    uint32_t w0 = 0, w1 = 0, w2 = 0, low_or = 0;
 #pragma unroll
-        for (int j = W - 1; j >= 0; --j)
-            if (top < 0 && Y[j] != 0) top = j;
-        if (top < 0) return (OutT)0;
-        w0 = w1 = w2 = low_or = 0;
-#pragma unroll
-        for (int j = 0; j < W; ++j) {
-            if (j == top) w0 = Y[j];
-            if (j == top - 1) w1 = Y[j];
-            if (j == top - 2) w2 = Y[j];
-            if (j < top - 2) low_or |= Y[j];
-        }
+    for (int j = 0; j < W; ++j) {
+        if (j == top) w0 = Y[j];
+        if (j == top - 1) w1 = Y[j];
+        if (j == top - 2) w2 = Y[j];
+        if (j < top - 2) low_or |= Y[j];
     }
     const int lz = __clz(w0);
-    int msb = 32 * top + 31 - lz;
-    uint64_t win = ((uint64_t)w0 << 32) | w1;
-    bool sticky = low_or != 0;
-    if (lz) {
-        win = (win << lz) | (w2 >> (32 - lz));
-        sticky = sticky || ((w2 << lz) != 0);
-    } else {
-        sticky = sticky || (w2 != 0);
-    }
+    const int msb = 32 * top + 31 - lz;
+    const uint32_t hi = __funnelshift_l(w1, w0, lz), lo = __funnelshift_l(w2, w1, lz);
+    const uint32_t sticky = ((w2 << lz) | low_or) != 0 ? 1u : 0u;
+    const uint64_t win = ((uint64_t)hi << 32) | lo | sticky;
+    const int E = msb - (ea + fb);
     if constexpr (sizeof(OutT) == 4) {
-        // 24 bits, ties to even; then the exponent.  Outside the normal single range the value
-        // x 2^-(e+f) (24 bits, exponent within +-500 for single inputs) is exact in double and
-        // its conversion to float is the one rounding.
-        uint32_t m24 = (uint32_t)(win >> 40);
+        const uint32_t m24 = (uint32_t)(win >> 40);
         const uint64_t rem = win & ((1ull << 40) - 1);
-        if (rem > (1ull << 39) || (rem == (1ull << 39) && (sticky || (m24 & 1)))) {
-            ++m24;
-            if (m24 >> 24) {
-                m24 >>= 1;
-                ++msb;
-            }
-        }
+        const uint32_t m = m24 + (uint32_t)((rem + ((1ull << 39) - 1) + (m24 & 1u)) >> 40);
         const uint32_t sign = neg ? 0x80000000u : 0u;
-        const int E = msb - (ea + fb);
-        if (E >= -126 && E <= 127)
-            return __uint_as_float(sign | ((uint32_t)(E + 127) << 23) | (m24 & 0x7FFFFFu));
-        return double_bits_to_float(((uint64_t)sign << 32) | ((uint64_t)(E + 1023) << 52) |
-                                    ((uint64_t)(m24 & 0x7FFFFFu) << 29));
+        if (E >= -126 && E <= 126)
+            return __uint_as_float(sign | (((uint32_t)(E + 126) << 23) + m));
+        // outside the normal single range: x 2^-(e+f) (24 bits, exponent within +-500 for
+        // single inputs) is exact in double and its conversion to float is the one rounding
+        const uint32_t mr = m >> 24 ? m >> 1 : m;
+        const int Er = m >> 24 ? E + 1 : E;
+        return double_bits_to_float(((uint64_t)sign << 32) | ((uint64_t)(Er + 1023) << 52) |
+                                    ((uint64_t)(mr & 0x7FFFFFu) << 29));
     } else {
-        uint64_t m53 = win >> 11;
-        const uint32_t rem = (uint32_t)(win & 0x7FF);
-        if (rem > 0x400 || (rem == 0x400 && (sticky || (m53 & 1)))) {
-            ++m53;
-            if (m53 >> 53) {
-                m53 >>= 1;
-                ++msb;
-            }
-        }
+        const uint64_t m53 = win >> 11;
+        const uint32_t rem = (uint32_t)win & 0x7FFu;
+        const uint64_t m = m53 + ((rem + 0x3FFu + ((uint32_t)m53 & 1u)) >> 11);
         const uint64_t sign = neg ? (1ull << 63) : 0ull;
-        const int E = msb - (ea + fb);  // unbiased exponent of C'' 2^-(e+f)
-        if (E >= -1022 && E <= 1023)
-            return __longlong_as_double((long long)(sign | ((uint64_t)(E + 1023) << 52) |
-                                                    (m53 & ((1ull << 52) - 1))));
+        if (E >= -1022 && E <= 1022)
+            return __longlong_as_double(
+                (long long)(sign | (((uint64_t)(E + 1022) << 52) + m)));
+        const uint64_t mr = m >> 53 ? m >> 1 : m;
+        const int msbr = m >> 53 ? msb + 1 : msb;
         const double x = __longlong_as_double(
-            (long long)(sign | ((uint64_t)(msb + 1023) << 52) | (m53 & ((1ull << 52) - 1))));
+            (long long)(sign | ((uint64_t)(msbr + 1023) << 52) | (mr & ((1ull << 52) - 1))));
         return scale_pow2_rn(x, -(ea + fb));
     }
+}
+
+// OutT = double (DGEMM) or float (SGEMM): C'' is rounded to 53 or 24 bits, then scaled by
+// 2^-(ea + fb).  v: the pair sums of the entry (pair_sums or dot2).  The shifts must be finite
+// (the caller substitutes 0 for OZAKI2_SHIFT_NONFINITE and selects NaN afterwards).
+template <int N, typename OutT>
+__device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int ea, int fb,
+                                          const CrtTables& t) {
+    constexpr int W = crt_words(N);
+    constexpr int G = (N + 1) / 2;
+    // X = sum_g PG_g v_g (64-bit column sums) and S ~ 2^46 X / P (fixed point).  A pair's
+    // constant round(2^46 / prod_g) is below 2^32, so its term is one 32 x 32 -> 64-bit
+    // multiply-add; a single modulus (odd N) keeps a 64-bit constant.
+    uint64_t acc[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) acc[j] = 0;
+    uint64_t S = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (2 * g + 1 < N) S += (uint64_t)v[g] * (uint32_t)t.R46[g];
+        else S += (uint64_t)v[g] * t.R46[g];
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc[j] += (uint64_t)t.PG[g][j] * v[g];
+    }
+    uint32_t X[W];
+    fold_columns<W>(acc, X);
+    // Q = round(X / P) from the fixed-point estimate (|S/2^46 - X/P| < 2^-18, S < 2^60): adding
+    // 2^45 touches only the high word.  The estimate is within 2^-10 of a half-integer when
+    // (S - 2^45 + 2^36) mod 2^46 < 2^37, i.e. bits 37..45 of that difference are clear; Q may
+    // then be one off, which crt_value_rare settles exactly.
+    const uint32_t s_hi = (uint32_t)(S >> 32);
+    const uint32_t Q = (s_hi + (1u << 13)) >> 14;
+    const bool near_half =
+        ((uint32_t)((S - ((1ull << 45) - (1ull << 36))) >> 32) & 0x3FE0u) == 0;
+    Words<W> Yw;
+    add_word_times<W>(X, Q, t.negP, Yw.w);  // Y = X - Q P (mod 2^(32 W))
+    // The common case, straight-line: |Y| with the top word leading (the shifts make |C''|
+    // large against P) and a result in the normal range.  The 64 bits from the leading one down
+    // come by funnel shifts (a shift of 0 keeps the words), every lower bit folded into bit 0 as
+    // a sticky bit (it lies below every rounding position); rounding to nearest even adds the
+    // remainder, half an ulp less one and the kept part's last bit, and a rounded-up 2^53 (2^24)
+    // carries into the exponent field.
+    uint32_t A[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) A[j] = Yw.w[j];
+    const bool neg = abs_words<W>(A);
+    const uint32_t w0 = A[W - 1], w1 = W > 1 ? A[W - 2] : 0u, w2 = W > 2 ? A[W - 3] : 0u;
+    uint32_t low_or = 0;
+#pragma unroll
+    for (int j = 0; j < W - 3; ++j) low_or |= A[j];
+    const int lz = __clz(w0);  // 32 when the top word is zero: the rare path then
+    const uint32_t hi = __funnelshift_l(w1, w0, lz), lo = __funnelshift_l(w2, w1, lz);
+    const uint32_t sticky = ((w2 << lz) | low_or) != 0 ? 1u : 0u;
+    const uint64_t win = ((uint64_t)hi << 32) | lo | sticky;
+    const int E = 32 * (W - 1) + 31 - lz - (ea + fb);
+    OutT y;
+    bool normal;
+    if constexpr (sizeof(OutT) == 4) {
+        const uint32_t m24 = (uint32_t)(win >> 40);
+        const uint64_t rem = win & ((1ull << 40) - 1);
+        const uint32_t m = m24 + (uint32_t)((rem + ((1ull << 39) - 1) + (m24 & 1u)) >> 40);
+        y = __uint_as_float((neg ? 0x80000000u : 0u) | (((uint32_t)(E + 126) << 23) + m));
+        normal = E >= -126 && E <= 126;
+    } else {
+        const uint64_t m53 = win >> 11;
+        const uint32_t rem = (uint32_t)win & 0x7FFu;
+        const uint64_t m = m53 + ((rem + 0x3FFu + ((uint32_t)m53 & 1u)) >> 11);
+        y = __longlong_as_double(
+            (long long)((neg ? (1ull << 63) : 0ull) | (((uint64_t)(E + 1022) << 52) + m)));
+        normal = E >= -1022 && E <= 1022;
+    }
+    if (near_half || w0 == 0 || !normal) y = crt_value_rare<N, OutT>(Yw, near_half, ea, fb, t);
+    return y;
 }
 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
@@ -342,6 +372,22 @@ __host__ __device__ inline int ab_flags(double alpha, double beta) {
     return (alpha != 1.0 ? 1 : 0) | (beta != 0.0 ? 2 : 0);
 }
 
+template <typename OutT>
+__device__ __forceinline__ OutT quiet_nan() {
+    if constexpr (sizeof(OutT) == 4) return __uint_as_float(0x7FC00000u);
+    else return __longlong_as_double(0x7FF8000000000000ll);
+}
+
+// C'' scaled for one entry, NaN when either line is non-finite (the value is computed with
+// zero shifts then, and replaced).
+template <int N, typename OutT>
+__device__ __forceinline__ OutT crt_entry(const uint32_t (&v)[(N + 1) / 2], int ea, int fb,
+                                          const CrtTables& t) {
+    const bool bad = ea == OZAKI2_SHIFT_NONFINITE || fb == OZAKI2_SHIFT_NONFINITE;
+    const OutT y = crt_value<N, OutT>(v, bad ? 0 : ea, bad ? 0 : fb, t);
+    return bad ? quiet_nan<OutT>() : y;
+}
+
 template <int N, typename OutT, bool VEC>
 __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t ldr,
                                          int64_t plane, int m, int n, const int* __restrict__ sa,
@@ -351,9 +397,24 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
                                          OutT (*tile)[TI + 1]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if constexpr (VEC) {
+        // The padded planes hold every entry of the tile, so entries outside C are computed
+        // (from zero shifts) like the others and only their stores are skipped: no per-entry
+        // bounds test.
         const int il = threadIdx.x >> 3, jq = (threadIdx.x & 7) * 4;
         const int i = i0 + il;
         const int ea = i < m ? sa[i] : 0;
+        int fb[4];
+        const int* sbq = sb + j0 + jq;
+        if (j0 + jq + 4 <= n && (reinterpret_cast<uintptr_t>(sbq) & 15u) == 0) {
+            const int4 f4 = __ldg(reinterpret_cast<const int4*>(sbq));
+            fb[0] = f4.x;
+            fb[1] = f4.y;
+            fb[2] = f4.z;
+            fb[3] = f4.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fb[q] = j0 + jq + q < n ? sbq[q] : 0;
+        }
         const int8_t* base = res + (int64_t)i * ldr + j0 + jq;
         constexpr int G = (N + 1) / 2;
         // per pair of planes, the residues of the four entries interleaved: lo holds entries 0
@@ -372,19 +433,14 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int j = j0 + jq + q;
-            OutT y = 0;
-            if (i < m && j < n) {
-                uint32_t v[G];
+            uint32_t v[G];
 #pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const uint32_t b = q < 2 ? lo[g] : hi[g];
-                    v[g] = (q & 1) ? dot2<true>(t.Kpair[g], b, t.grp_bias[g])
-                                   : dot2<false>(t.Kpair[g], b, t.grp_bias[g]);
-                }
-                y = crt_value<N, OutT>(v, ea, sb[j], t);
+            for (int g = 0; g < G; ++g) {
+                const uint32_t b = q < 2 ? lo[g] : hi[g];
+                v[g] = (q & 1) ? dot2<true>(t.Kpair[g], b, t.grp_bias[g])
+                               : dot2<false>(t.Kpair[g], b, t.grp_bias[g]);
             }
-            tile[jq + q][il] = y;
+            tile[jq + q][il] = crt_entry<N, OutT>(v, ea, fb[q], t);
         }
     } else {
         const int j = j0 + lane;
@@ -401,7 +457,7 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
                 for (int l = 0; l < N; ++l) c[l] = p[(int64_t)l * plane];
                 uint32_t v[(N + 1) / 2];
                 pair_sums<N>(c, t, v);
-                y = crt_value<N, OutT>(v, sa[i], fb, t);
+                y = crt_entry<N, OutT>(v, sa[i], fb, t);
             }
             tile[lane][il] = y;
         }
@@ -441,14 +497,23 @@ __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res
                                                   OutT beta, int ab, OutT* __restrict__ C,
                                                   int64_t ldc, const CrtTables t) {
     // 32 x 32 tiles of C in row-band order, blocks striding over them (one tile per block when
-    // the grid covers them all; fewer blocks leave room on each SM for another kernel)
+    // the grid covers them all; fewer blocks leave room on each SM for another kernel).  The
+    // (band, column) position advances by the stride's quotient and remainder, so the loop
+    // divides nothing.
     __shared__ OutT tile[TJ][TI + 1];
-    const int tiles_j = (n + TJ - 1) / TJ;
-    const int64_t tiles = (int64_t)tiles_j * ((m + TI - 1) / TI);
-    for (int64_t w = blockIdx.x; w < tiles; w += gridDim.x) {
+    const unsigned tiles_j = (unsigned)(n + TJ - 1) / TJ, tiles_i = (unsigned)(m + TI - 1) / TI;
+    const unsigned step_i = gridDim.x / tiles_j, step_j = gridDim.x % tiles_j;
+    unsigned ti = blockIdx.x / tiles_j, tj = blockIdx.x % tiles_j;
+    while (ti < tiles_i) {
         crt_tile<N, OutT, VEC>(res, ldr, plane, m, n, sa, sb, alpha, beta, ab, C, ldc, t,
-                               (int)(w / tiles_j) * TI, (int)(w % tiles_j) * TJ, tile);
+                               (int)(ti * TI), (int)(tj * TJ), tile);
         __syncthreads();  // the tile buffer is written again by the next tile
+        ti += step_i;
+        tj += step_j;
+        if (tj >= tiles_j) {
+            tj -= tiles_j;
+            ++ti;
+        }
     }
 }
 
