@@ -23,7 +23,11 @@
 namespace ozaki2 {
 namespace {
 
-constexpr int TI = 32, TJ = 32;  // tile of the output: 32 rows x 32 columns, 256 threads
+// Tiles of the output, 256 threads each: 32 rows x 64 columns on the padded layout (VEC), where
+// a thread reconstructs eight consecutive entries of one row; 32 x 32 otherwise.
+constexpr int TI = 32, TJ = 32, TJV = 64;
+template <bool VEC>
+__host__ __device__ constexpr int tile_cols() { return VEC ? TJV : TJ; }
 
 // y * 2^s rounded to nearest once, for any s (x is a normal double).  Only results outside the
 // normal range come here; kept out of line so that none of its FP64 multiplies is if-converted
@@ -362,10 +366,6 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
-// One 32 x 32 tile of C (rows i0.., columns j0..); all 256 threads take part.  VEC: the
-// residue planes are padded to whole 32 x 32 tiles and 4-byte aligned (the library's own
-// layout), so thread t reads four consecutive residues of row t/8 per plane with one 32-bit
-// load; otherwise each residue is read on its own.
 // ab: bit 0 set when alpha != 1 (multiply by alpha), bit 1 when beta != 0 (add beta C); the
 // host decides, so the kernel makes no floating-point comparisons.
 __host__ __device__ inline int ab_flags(double alpha, double beta) {
@@ -388,7 +388,15 @@ __device__ __forceinline__ OutT crt_entry(const uint32_t (&v)[(N + 1) / 2], int 
     return bad ? quiet_nan<OutT>() : y;
 }
 
-template <int N, typename OutT, bool VEC>
+// One tile of C (rows i0.., columns j0..; 32 x 64 for VEC, 32 x 32 otherwise); all 256 threads
+// take part.  VEC: the residue planes are padded to whole 32 x 64 tiles and 8-byte aligned (the
+// library's own layout), so thread t reconstructs the eight consecutive entries of row t/8 from
+// column 8 (t % 8), reading them with one 64-bit load per plane (half the loads and address
+// arithmetic per entry of four-entry threads); entries outside C are computed from zero shifts
+// like the others and only their stores are skipped.  A non-finite shift of the row or of a
+// column replaces the entries it touches by NaN after the fact, so the common path computes
+// every entry the same way.  Otherwise each residue is read on its own.
+template <int N, typename OutT, bool VEC, bool AB = true>
 __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t ldr,
                                          int64_t plane, int m, int n, const int* __restrict__ sa,
                                          const int* __restrict__ sb, OutT alpha, OutT beta,
@@ -396,51 +404,51 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
                                          const CrtTables& t, int i0, int j0,
                                          OutT (*tile)[TI + 1]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int COLS = tile_cols<VEC>();
     if constexpr (VEC) {
-        // The padded planes hold every entry of the tile, so entries outside C are computed
-        // (from zero shifts) like the others and only their stores are skipped: no per-entry
-        // bounds test.
-        const int il = threadIdx.x >> 3, jq = (threadIdx.x & 7) * 4;
+        const int il = threadIdx.x >> 3, jq = (threadIdx.x & 7) * 8;
         const int i = i0 + il;
         const int ea = i < m ? sa[i] : 0;
-        int fb[4];
-        const int* sbq = sb + j0 + jq;
-        if (j0 + jq + 4 <= n && (reinterpret_cast<uintptr_t>(sbq) & 15u) == 0) {
-            const int4 f4 = __ldg(reinterpret_cast<const int4*>(sbq));
-            fb[0] = f4.x;
-            fb[1] = f4.y;
-            fb[2] = f4.z;
-            fb[3] = f4.w;
-        } else {
+        int fb[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) fb[q] = j0 + jq + q < n ? sbq[q] : 0;
-        }
+        for (int q = 0; q < 8; ++q) fb[q] = j0 + jq + q < n ? sb[j0 + jq + q] : 0;
+        bool bad = ea == OZAKI2_SHIFT_NONFINITE;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) bad |= fb[q] == OZAKI2_SHIFT_NONFINITE;
+        const int ea_u = ea == OZAKI2_SHIFT_NONFINITE ? 0 : ea;
         const int8_t* base = res + (int64_t)i * ldr + j0 + jq;
         constexpr int G = (N + 1) / 2;
-        // per pair of planes, the residues of the four entries interleaved: lo holds entries 0
-        // and 1 (bytes c_2g, c_2g+1 of each), hi entries 2 and 3
-        uint32_t lo[G], hi[G];
+        // per pair of planes, the residues of the eight entries interleaved two entries to a
+        // word: w[g][h] holds entries 2h and 2h + 1 (bytes c_2g, c_2g+1 of each)
+        uint32_t w[G][4];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            const uint32_t w0 =
-                __ldg(reinterpret_cast<const unsigned int*>(base + (int64_t)(2 * g) * plane));
-            const uint32_t w1 =
-                2 * g + 1 < N ? __ldg(reinterpret_cast<const unsigned int*>(
-                                    base + (int64_t)(2 * g + 1) * plane))
-                              : 0u;
-            lo[g] = __byte_perm(w0, w1, 0x5140);
-            hi[g] = __byte_perm(w0, w1, 0x7362);
+            const uint2 a = __ldg(reinterpret_cast<const uint2*>(base + (int64_t)(2 * g) * plane));
+            const uint2 b = 2 * g + 1 < N ? __ldg(reinterpret_cast<const uint2*>(
+                                                base + (int64_t)(2 * g + 1) * plane))
+                                          : make_uint2(0u, 0u);
+            w[g][0] = __byte_perm(a.x, b.x, 0x5140);
+            w[g][1] = __byte_perm(a.x, b.x, 0x7362);
+            w[g][2] = __byte_perm(a.y, b.y, 0x5140);
+            w[g][3] = __byte_perm(a.y, b.y, 0x7362);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             uint32_t v[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                const uint32_t b = q < 2 ? lo[g] : hi[g];
+                const uint32_t b = w[g][q >> 1];
                 v[g] = (q & 1) ? dot2<true>(t.Kpair[g], b, t.grp_bias[g])
                                : dot2<false>(t.Kpair[g], b, t.grp_bias[g]);
             }
-            tile[jq + q][il] = crt_entry<N, OutT>(v, ea, fb[q], t);
+            const int fbu = fb[q] == OZAKI2_SHIFT_NONFINITE ? 0 : fb[q];
+            tile[jq + q][il] = crt_value<N, OutT>(v, ea_u, fbu, t);
+        }
+        if (bad) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (ea == OZAKI2_SHIFT_NONFINITE || fb[q] == OZAKI2_SHIFT_NONFINITE)
+                    tile[jq + q][il] = quiet_nan<OutT>();
         }
     } else {
         const int j = j0 + lane;
@@ -465,17 +473,18 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
     __syncthreads();
     // Two loops rather than one with selects: a select between the product and the plain value
     // still issues the (predicated-off) floating-point multiply, which for doubles occupies the
-    // narrow FP64 pipe.
-    if (ab == 0) {
+    // narrow FP64 pipe.  AB = false (alpha = 1, beta = 0, decided on the host) compiles only the
+    // plain stores.
+    if (!AB || ab == 0) {
 #pragma unroll
-        for (int r = 0; r < TJ / 8; ++r) {
+        for (int r = 0; r < COLS / 8; ++r) {
             const int jl = warp + 8 * r;
             const int jj = j0 + jl, ii = i0 + lane;
             if (ii < m && jj < n) C[ii + (int64_t)jj * ldc] = tile[jl][lane];
         }
-    } else {
+    } else if constexpr (AB) {
 #pragma unroll 1
-        for (int r = 0; r < TJ / 8; ++r) {
+        for (int r = 0; r < COLS / 8; ++r) {
             const int jl = warp + 8 * r;
             const int jj = j0 + jl, ii = i0 + lane;
             if (ii < m && jj < n) {
@@ -489,24 +498,34 @@ __device__ __forceinline__ void crt_tile(const int8_t* __restrict__ res, int64_t
     }
 }
 
-template <int N, typename OutT, bool VEC>
-__global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res, int64_t ldr,
+// Blocks per SM the register budget is cut for: four (64 registers a thread) where that spills
+// nothing, measured faster at N = 16 than the three that the compiler's own choice leaves room
+// for; three for the five-word N >= 17 and for the grouped kernel from N = 12 on, where four
+// would spill.
+__host__ __device__ constexpr int crt_min_blocks(int N, bool grouped) {
+    return (grouped ? N <= 11 : N <= 16) ? 4 : 3;
+}
+
+// AB = false: alpha = 1 and beta = 0 (the kernel has no alpha/beta code at all).
+template <int N, typename OutT, bool VEC, bool AB>
+__global__ void __launch_bounds__(256, crt_min_blocks(N, false)) crt_kernel(const int8_t* __restrict__ res, int64_t ldr,
                                                   int64_t plane, int m, int n,
                                                   const int* __restrict__ sa,
                                                   const int* __restrict__ sb, OutT alpha,
                                                   OutT beta, int ab, OutT* __restrict__ C,
                                                   int64_t ldc, const CrtTables t) {
-    // 32 x 32 tiles of C in row-band order, blocks striding over them (one tile per block when
+    // tiles of C in row-band order, blocks striding over them (one tile per block when
     // the grid covers them all; fewer blocks leave room on each SM for another kernel).  The
     // (band, column) position advances by the stride's quotient and remainder, so the loop
     // divides nothing.
-    __shared__ OutT tile[TJ][TI + 1];
-    const unsigned tiles_j = (unsigned)(n + TJ - 1) / TJ, tiles_i = (unsigned)(m + TI - 1) / TI;
+    constexpr int COLS = tile_cols<VEC>();
+    __shared__ OutT tile[COLS][TI + 1];
+    const unsigned tiles_j = (unsigned)(n + COLS - 1) / COLS, tiles_i = (unsigned)(m + TI - 1) / TI;
     const unsigned step_i = gridDim.x / tiles_j, step_j = gridDim.x % tiles_j;
     unsigned ti = blockIdx.x / tiles_j, tj = blockIdx.x % tiles_j;
     while (ti < tiles_i) {
-        crt_tile<N, OutT, VEC>(res, ldr, plane, m, n, sa, sb, alpha, beta, ab, C, ldc, t,
-                               (int)(ti * TI), (int)(tj * TJ), tile);
+        crt_tile<N, OutT, VEC, AB>(res, ldr, plane, m, n, sa, sb, alpha, beta, ab, C, ldc, t,
+                               (int)(ti * TI), (int)(tj * COLS), tile);
         __syncthreads();  // the tile buffer is written again by the next tile
         ti += step_i;
         tj += step_j;
@@ -517,12 +536,13 @@ __global__ void __launch_bounds__(256) crt_kernel(const int8_t* __restrict__ res
     }
 }
 
-// Grouped: each block reconstructs one 32 x 32 tile of one problem's C.
+// Grouped: each block reconstructs one 32 x 64 tile of one problem's C (the work list holds
+// their corners; every problem's product residues are padded to whole tiles).
 template <int N>
-__global__ void __launch_bounds__(256) crt_grouped_kernel(const GroupProblem* __restrict__ probs,
+__global__ void __launch_bounds__(256, crt_min_blocks(N, true)) crt_grouped_kernel(const GroupProblem* __restrict__ probs,
                                                           const CrtWork* __restrict__ work,
                                                           const CrtTables t) {
-    __shared__ double tile[TJ][TI + 1];
+    __shared__ double tile[TJV][TI + 1];
     const CrtWork w = work[blockIdx.x];
     const GroupProblem& P = probs[w.problem];
     crt_tile<N, double, true>(P.res, P.n_pad, (int64_t)P.m_pad * P.n_pad, P.m, P.n, P.e, P.f,
@@ -549,15 +569,18 @@ cudaError_t launch_crt_typed(const int8_t* res, int64_t ldr, int64_t plane, int 
                              const int* sa, const int* sb, OutT alpha, OutT beta, OutT* C,
                              int64_t ldc, const ModTables& t, cudaStream_t stream,
                              int max_blocks) {
-    const int64_t tiles = (int64_t)((n + TJ - 1) / TJ) * ((m + TI - 1) / TI);
+    const int64_t tiles = (int64_t)((n + tile_cols<VEC>() - 1) / tile_cols<VEC>()) * ((m + TI - 1) / TI);
     const int64_t cap = max_blocks > 0 ? max_blocks : (int64_t)INT32_MAX;
     const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+    const int ab = ab_flags(alpha, beta);
 #define OZAKI2_CRT_CASE(NN)                                                                   \
     case NN:                                                                                  \
-        crt_kernel<NN, OutT, VEC><<<grid, 256, 0, stream>>>(res, ldr, plane, m, n, sa, sb,     \
-                                                            alpha, beta,                       \
-                                                            ab_flags(alpha, beta), C, ldc,     \
-                                                            t.crt);                            \
+        if (ab)                                                                               \
+            crt_kernel<NN, OutT, VEC, true><<<grid, 256, 0, stream>>>(                         \
+                res, ldr, plane, m, n, sa, sb, alpha, beta, ab, C, ldc, t.crt);                \
+        else                                                                                  \
+            crt_kernel<NN, OutT, VEC, false><<<grid, 256, 0, stream>>>(                        \
+                res, ldr, plane, m, n, sa, sb, alpha, beta, ab, C, ldc, t.crt);                \
         break;
     switch (t.N) {
         OZAKI2_CRT_CASE(2) OZAKI2_CRT_CASE(3) OZAKI2_CRT_CASE(4) OZAKI2_CRT_CASE(5)
@@ -578,9 +601,9 @@ cudaError_t launch_crt(const int8_t* res, int64_t ldr, int64_t plane, int m, int
                        bool f32, bool padded, int max_blocks) {
     (void)status;
     if (m <= 0 || n <= 0) return cudaSuccess;
-    // the 32-bit residue loads need 4-byte alignment and planes padded to whole 32 x 32 tiles
-    const bool vec = padded && (reinterpret_cast<uintptr_t>(res) & 3u) == 0 && ldr % 4 == 0 &&
-                     plane % 4 == 0 && ldr >= (int64_t)(n + TJ - 1) / TJ * TJ &&
+    // the 64-bit residue loads need 8-byte alignment and planes padded to whole 32 x 64 tiles
+    const bool vec = padded && (reinterpret_cast<uintptr_t>(res) & 7u) == 0 && ldr % 8 == 0 &&
+                     plane % 8 == 0 && ldr >= (int64_t)(n + TJV - 1) / TJV * TJV &&
                      plane >= (int64_t)(m + TI - 1) / TI * TI * ldr;
     if (f32) {
         auto* c = static_cast<float*>(C);

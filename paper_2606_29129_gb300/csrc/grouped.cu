@@ -120,7 +120,7 @@ void make_plan(int count, const ozaki2_problem* probs, Plan& P, const TileRules*
         const int64_t bes = notrans(p.transB) ? 1 : p.ldb;
         const int cb = (has_a ? 0 : convert_blocks(p.m, aes, geo.rows_a, geo.ld)) +
                        (has_b ? 0 : convert_blocks(p.n, bes, geo.rows_b, geo.ld));
-        const int rb = ((p.m + 31) / 32) * ((p.n + 31) / 32);
+        const int rb = ((p.m + 31) / 32) * ((p.n + 63) / 64);  // 32 x 64 CRT tiles
         if (p.num_moduli != curN) {
             curN = p.num_moduli;
             P.conv_n.push_back(curN);
@@ -255,7 +255,7 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
             for (int b = 0; b < cb; ++b) cw[nc++] = ConvertWork{(int)a, side, b};
         }
         for (int i0 = 0; i0 < p.m; i0 += 32)
-            for (int j0 = 0; j0 < p.n; j0 += 32) rw[nr++] = CrtWork{(int)a, i0, j0};
+            for (int j0 = 0; j0 < p.n; j0 += 64) rw[nr++] = CrtWork{(int)a, i0, j0};
     }
     return OZAKI2_SUCCESS;
 }

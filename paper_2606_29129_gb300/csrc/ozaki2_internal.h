@@ -137,7 +137,7 @@ struct ScaleWork {       // 128 lines of one side of one problem
 struct ConvertWork {     // block `block` of one side of one problem (adjacent: a 64 x 64 tile,
     int problem, side, block;  // contiguous: 256 groups of 8 elements)
 };
-struct CrtWork {         // one 32 x 32 tile of C
+struct CrtWork {         // one 32 x 64 tile of C
     int problem, i0, j0;
 };
 
