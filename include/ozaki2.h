@@ -296,9 +296,16 @@ size_t ozaki2_grouped_encoded_workspace_size(int count, const ozaki2_problem* pr
 
 /* ---- the stages, one entry point each ------------------------------------------------------ */
 /* Step 2 scaling (Algorithm 2, eq. (proposed-mu)): shifts[i] = log2(mu_i) for the m rows of
- * op(A) (m x k, lda).  The squared norm is accumulated in order h = 1..k with one fused
- * multiply-add rounded upward per term.  A zero row gets 0; a row with a non-finite squared
- * norm gets OZAKI2_SHIFT_NONFINITE and raises OZAKI2_STATUS_NONFINITE.  shifts: device int[m].
+ * op(A) (m x k, lda).  The squared norm (Section 4: single or double precision, rounded upward)
+ * is summed in single precision with every operation rounded upward, on terms rescaled exactly
+ * by powers of two: in blocks of 256 consecutive terms, with E the largest exponent field of
+ * the block's terms so far, each term enters as x = single-up(|a| 2^(1023 - E)) and the
+ * block's sum as f = single-up(x x + f) (a rise of E by d first rescales f to
+ * single-up(f 2^(-2d))); the block values double-up(double-up(f 2^(E-1023)) 2^(E-1023)) are
+ * added in block order, rounded upward.  The result bounds the exact sum from above.  A zero
+ * row gets 0; a row with a non-finite squared norm (an Inf or NaN entry, or a norm beyond the
+ * double range) gets OZAKI2_SHIFT_NONFINITE and raises OZAKI2_STATUS_NONFINITE.
+ * shifts: device int[m].
  * With OZAKI2_OPT_SCALING = OZAKI2_SCALING_FAST the shifts are those of Algorithm 1 instead
  * (eq. (fast-mode-mu): the same norm, plus the row maximum max_h |a_ih|); a row whose norm or
  * maximum is zero gets 0.  In OZAKI2_SCALING_ACCURATE mode the shifts depend on both operands:
@@ -311,6 +318,17 @@ int ozaki2_scale_a(ozaki2_handle_t handle, char transA, int m, int k, const doub
  * (eq. (proposed-nu)).  Same conventions as ozaki2_scale_a. */
 int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const double* B, int ldb,
                    int num_moduli, int* shifts);
+
+/* The shifts of ozaki2_scale_a (side 'A': the rows of op(A), lines x k, X = A, ld = lda) or
+ * ozaki2_scale_b (side 'B': the columns of op(B), k x lines, X = B, ld = ldb), computed by the
+ * kernels ozaki2_dgemm runs, together with the squared norms they come from: norms[i] receives
+ * a_norm of line i exactly as Algorithm 2 takes it (a double; +Inf or NaN for a non-finite
+ * line).  Not in OZAKI2_SCALING_ACCURATE mode (OZAKI2_ERROR_MODE), which takes no norm.
+ * shifts: device int[lines]; norms: device double[lines].
+ * Arguments: handle 1, side 2, trans 3, lines 4, k 5, X 6, ld 7, num_moduli 8, shifts 9,
+ * norms 10. */
+int ozaki2_scale_norms(ozaki2_handle_t handle, char side, char trans, int lines, int k,
+                       const double* X, int ld, int num_moduli, int* shifts, double* norms);
 
 /* Both scalings of accurate mode (Section 2.3), which need A and B together: line maxima,
  * A-bar = ceil(mu' |A|) and B-bar as bf16 planes in the handle's workspace, the auxiliary

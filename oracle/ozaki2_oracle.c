@@ -327,25 +327,83 @@ static int make_consts(int N, orc_consts* c) {
 /* Step 2 scaling: row/column squared norms and Algorithm 2                              */
 /* ------------------------------------------------------------------------------------ */
 
-/* a_norm := sum_h a_h^2 "computed with rounding-up" (Section 4, the input of Algorithm 2).  The
- * paper fixes the rounding direction but no order of the terms.  Reading: the terms in blocks of
- * ORC_NORM_BLOCK consecutive h; within a block one fused multiply-add per term, rounded upward,
- * from 0 in the order h; then the block sums added in block order, each addition rounded
- * upward.  Every operation rounds up and every term is nonnegative, so the result bounds the
- * exact sum from above; a line of at most ORC_NORM_BLOCK terms is the plain sequential sum. */
+/* a_norm := sum_h a_h^2 "computed with rounding-up" (the input of Algorithm 2); Section 4 lets the
+ * sums be evaluated in single or double precision, each with rounding up.  Reading: single
+ * precision on exactly rescaled terms, in blocks of ORC_NORM_BLOCK consecutive h (the paper
+ * gives no order), each block taken in groups of ORC_NORM_GROUP consecutive terms (the last
+ * group of a line may be shorter).  Before a group is added, E, the block's scale, becomes the
+ * largest of E, 1 and the exponent fields of the group's terms (E = 0 at the start of a block);
+ * a rise of E by d rescales the block's single-precision sum to f = single-up(f 2^(-2d)).  Each
+ * term of the group then enters as x = single-up(|a| 2^(1023 - E)), a value in [0, 2), and
+ * f = single-up(x x + f), from f = 0 in the order h.  The block's value is
+ * double-up(double-up(f 2^(E - 1023)) 2^(E - 1023)), which is f 2^(2 (E - 1023)) whenever that is
+ * a normal double; the block values are added in block order, each addition rounded upward.
+ * Every operation rounds up and every rescaling is by a power of two, so a_norm bounds the exact
+ * sum from above.  A block with an infinite term has value +Inf, one with a NaN term NaN (as an
+ * FP64 sum of the squares would have). */
 #define ORC_NORM_BLOCK 256
+#define ORC_NORM_GROUP 16
+
+/* single-up(v 2^k) for a finite v > 0 (v a double, k any integer).  Below 2^-200 the value is
+ * under the least positive single, which single-up gives; otherwise the scaled value is a
+ * normal double (>= 2^-252), computed exactly, then rounded up to single. */
+static float ru_float_pow2(double v, int k) {
+    if (ilogb(v) + k < -200) return 0x1p-149f;
+    return ru_float(ldexp(v, k));
+}
+
+/* The biased exponent field of a finite nonzero double, a subnormal counting as 1. */
+static int exp_field(double v) {
+    uint64_t b;
+    memcpy(&b, &v, sizeof b);
+    int e = (int)((b >> 52) & 0x7FF);
+    return e ? e : 1;
+}
+
 static double line_norm_ru(const double* x, int64_t stride, int64_t len) {
     int old = fegetround();
     fesetround(FE_UPWARD);
     double total = 0.0;
     for (int64_t b0 = 0; b0 < len; b0 += ORC_NORM_BLOCK) {
         const int64_t b1 = b0 + ORC_NORM_BLOCK < len ? b0 + ORC_NORM_BLOCK : len;
-        double s = 0.0;
-        for (int64_t h = b0; h < b1; ++h) {
-            double a = x[h * stride];
-            s = fma(a, a, s);
+        int E = 0;
+        float f = 0.0f;
+        int has_inf = 0, has_nan = 0;
+        for (int64_t g0 = b0; g0 < b1; g0 += ORC_NORM_GROUP) {
+            const int64_t g1 = g0 + ORC_NORM_GROUP < b1 ? g0 + ORC_NORM_GROUP : b1;
+            int En = E > 1 ? E : 1;
+            for (int64_t h = g0; h < g1; ++h) {
+                const double a = fabs(x[h * stride]);
+                if (isnan(a)) has_nan = 1;
+                else if (isinf(a)) has_inf = 1;
+                else if (a != 0.0 && exp_field(a) > En) En = exp_field(a);
+            }
+            if (has_nan || has_inf) continue;   /* the block's value is settled */
+            if (En > E && f != 0.0f) f = ru_float_pow2((double)f, -2 * (En - E));
+            E = En;
+            for (int64_t h = g0; h < g1; ++h) {
+                const double a = fabs(x[h * stride]);
+                if (a == 0.0) continue;        /* x = 0 leaves f unchanged */
+                const float xf = ru_float_pow2(a, 1023 - E);
+                /* x x is exact in double (24-bit operands); the sum rounds up in double, then
+                 * up to single: rounding up twice is rounding up once (every single is a double) */
+                const double sum = (double)xf * (double)xf + (double)f;
+                f = ru_float(sum);
+            }
         }
-        total = total + s;
+        double v;
+        if (has_nan) {
+            v = NAN;
+        } else if (has_inf) {
+            v = INFINITY;
+        } else if (E == 0) {
+            v = 0.0;
+        } else {
+            const double p = ldexp(1.0, E - 1023);   /* exact: E in [1, 2046] */
+            volatile double t = (double)f * p;        /* rounded up */
+            v = t * p;                                /* rounded up */
+        }
+        total = total + v;
     }
     fesetround(old);
     return total;

@@ -1125,6 +1125,40 @@ int ozaki2_scale_b(ozaki2_handle_t handle, char transB, int k, int n, const doub
                                 ctx->scaling, T->delta, partials_scratch(ctx, n, k)));
 }
 
+int ozaki2_scale_norms(ozaki2_handle_t handle, char side, char trans, int lines, int k,
+                       const double* X, int ld, int num_moduli, int* shifts, double* norms) {
+    const bool is_a = side == 'A' || side == 'a';
+    if (!is_a && side != 'B' && side != 'b') return -2;
+    if (!is_trans_char(trans)) return -3;
+    if (lines < 0) return -4;
+    if (k < 0) return -5;
+    if (lines > 0 && k > 0 && !X) return -6;
+    // rows of the stored matrix: op(A) = A is lines x k, op(B) = B is k x lines
+    const int rows = is_a == is_notrans(trans) ? lines : k;
+    if (ld < (rows > 1 ? rows : 1)) return -7;
+    const ModTables* T = mod_tables(num_moduli);
+    if (!T) return -8;
+    if (lines > 0 && !shifts) return -9;
+    if (lines > 0 && !norms) return -10;
+    ozaki2_context* ctx;
+    int rc = resolve(handle, &ctx);
+    if (rc) return rc;
+    if (ctx->scaling == OZAKI2_SCALING_ACCURATE) return OZAKI2_ERROR_MODE;
+    if (lines == 0) return OZAKI2_SUCCESS;
+    int64_t ls, es;
+    if (is_a) rows_of_op(trans, ld, &ls, &es);
+    else cols_of_op(trans, ld, &ls, &es);
+    const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
+    double* part = partials_scratch(ctx, lines, k);
+    if (is_a)
+        return cuda_rc(launch_scale_pair(X, ls, es, lines, nullptr, 0, 1, 0, k, pp, T->delta,
+                                         shifts, nullptr, ctx->d_status, ctx->stream,
+                                         ctx->scaling, false, part, norms, nullptr));
+    return cuda_rc(launch_scale_pair(nullptr, 0, 1, 0, X, ls, es, lines, k, pp, T->delta, nullptr,
+                                     shifts, ctx->d_status, ctx->stream, ctx->scaling, false,
+                                     part, nullptr, norms));
+}
+
 int ozaki2_scale_accurate(ozaki2_handle_t handle, char transA, char transB, int m, int n, int k,
                           const double* A, int lda, const double* B, int ldb, int num_moduli,
                           int* e, int* f, unsigned* cmax) {

@@ -257,10 +257,12 @@ const ModTables* mod_tables(int N);
 // f32: the matrices hold floats (SGEMM), else doubles.
 // partials: NULL, or device scratch of scale_partials_bytes(m + n, len) bytes, which lets lines
 // longer than one norm block split across warps (NULL: one thread per line).
+// norms_a / norms_b: NULL, or device doubles that receive the squared norms the shifts come from.
 cudaError_t launch_scale_pair(const void* A, int64_t a_ls, int64_t a_es, int m, const void* B,
                               int64_t b_ls, int64_t b_es, int n, int len, float pprime,
                               float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
-                              int scaling, bool f32 = false, double* partials = nullptr);
+                              int scaling, bool f32 = false, double* partials = nullptr,
+                              double* norms_a = nullptr, double* norms_b = nullptr);
 // Scratch bytes of the norm-block sums (and maxima) of `lines` lines of length len: 0 when a
 // line fits one block of 256 terms.
 inline size_t scale_partials_bytes(int lines, int len) {

@@ -2,14 +2,15 @@
 // (eq. (proposed-mu)/(proposed-nu), Algorithm 2).
 //
 // Each line (row of op(A) or column of op(B)) gets a_norm = sum_h a_h^2 rounded upward (Section
-// 4), in a fixed order: blocks of kNormBlock = 256 consecutive terms, each summed from 0 with one
-// fused multiply-add rounded upward per term, then the block sums added in block order with
-// upward rounding.  Every partial sum is an upper bound, as Algorithm 2 requires, and the fixed
-// order keeps the shifts bit-identical to a sequential reference.  Then log2(mu) = floor(w - t)
-// from Algorithm 2.
+// 4, which allows single or double precision), in a fixed order: blocks of kNormBlock = 256
+// consecutive terms, each summed in single precision on terms rescaled exactly by a power of two
+// (LineAcc), then the block values added in block order with upward rounding.  Every partial sum
+// is an upper bound, as Algorithm 2 requires, and the fixed order keeps the shifts bit-identical
+// to a sequential reference.  Then log2(mu) = floor(w - t) from Algorithm 2.
 //
-// The kernels are bound by HBM reads of the matrix (8 bytes per element) and, on GB300, by the
-// FP64 FMA rate.  Lines of at most one block run one thread per line; longer lines, when the
+// The kernels are bound by HBM reads of the matrix (8 bytes per element): the per-term work is
+// integer and single-precision arithmetic, with only a few FP64 operations per block of 256
+// terms.  Lines of at most one block run one thread per line; longer lines, when the
 // caller gives scratch for the block sums, run two kernels: one warp per norm block of 32 lines
 // (scale_partials_kernel), then one thread per line adding its block sums in order
 // (scale_fold_kernel).
@@ -80,36 +81,179 @@ __device__ __forceinline__ int accu_line_exponent(uint64_t mb, unsigned* status)
 
 constexpr int kNormBlock = 256;  // terms per block of the squared-norm sum
 
-// Running state of one line: the squared norm (proposed and fast modes) as the sum of the closed
-// blocks (total) and the open block (s), the maximum |a| as a double (fast mode) or as bits
-// (accurate mode).
+// single-up(f 2^-s) for a single f >= 0 and s >= 1, from the bits: a normal result is f with its
+// exponent lowered; a subnormal one is the mantissa shifted right, rounded up on any lost bit
+// (the least positive single when nothing is left).  Taken only when a block's largest exponent
+// rises.
+__device__ __forceinline__ float scale_down_ru(float f, int s) {
+    const uint32_t b = __float_as_uint(f);
+    if (b == 0u) return 0.0f;
+    const int ef = (int)(b >> 23);
+    if (ef > s) return __uint_as_float(b - ((uint32_t)s << 23));
+    const uint32_t m = ef ? ((b & 0x7FFFFFu) | 0x800000u) : b;
+    const int r = s + 1 - (ef ? ef : 1);  // >= 1
+    if (r >= 25) return __uint_as_float(1u);
+    const uint32_t q = m >> r;
+    return __uint_as_float(q + ((m & ((1u << r) - 1u)) != 0u ? 1u : 0u));
+}
+
+// single-up(|v| 2^(1023 - E)) for the bits b of |v| (finite, nonzero) whose exponent field is at
+// most E, when |v| is a subnormal double or the result may be a subnormal single.  With M the
+// integer mantissa, the value is M 2^-sh in units of 2^-149 (the least positive single); a
+// normal single keeps the 24 bits from M's leading one and rounds up on any lower one, a
+// subnormal single is the unit count rounded up (the least positive single when M 2^-sh < 1).
+__device__ __forceinline__ float single_up_rare(uint64_t b, int E) {
+    const int ef = (int)(b >> 52);
+    uint64_t M = b & ((1ull << 52) - 1);
+    int e2 = ef;                              // |v| = M 2^(e2 - 1075)
+    if (ef) M |= 1ull << 52; else e2 = 1;
+    const int sh = E - e2 - 97;               // value = M 2^(e2 - E - 52) = M 2^-sh units
+    const int p = 63 - __clzll((long long)M); // M's leading bit
+    if (p - sh >= 23) {                       // a normal single, exponent p - sh - 149
+        const int ex = p - sh - 149;
+        const uint64_t frac = M ^ (1ull << p);
+        const int drop = p - 23;
+        uint32_t mant;
+        bool lost = false;
+        if (drop >= 0) {
+            mant = (uint32_t)(frac >> drop);
+            lost = (frac & ((1ull << drop) - 1)) != 0;
+        } else {
+            mant = (uint32_t)(frac << -drop);
+        }
+        return __uint_as_float((((uint32_t)(ex + 127)) << 23) + mant + (lost ? 1u : 0u));
+    }
+    if (sh <= 0) return __uint_as_float((uint32_t)(M << -sh));  // exact, below 2^23 units
+    if (sh >= 64) return __uint_as_float(1u);
+    const bool lost = (M & ((1ull << sh) - 1)) != 0;
+    return __uint_as_float((uint32_t)(M >> sh) + (lost ? 1u : 0u));
+}
+
+// Running state of one line.  The squared norm (proposed and fast modes) is summed in single
+// precision with every operation rounded upward (Section 4 allows single or double precision),
+// on terms rescaled exactly: blocks of kNormBlock consecutive terms, taken in groups of
+// kNormGroup.  Before a group, E (0 at a block's start) becomes the largest of E, 1 and the
+// group's exponent fields, and a rise of E by d rescales the block sum to f = single-up(f 2^(-2d));
+// each term then enters as x = single-up(|a| 2^(1023 - E)) in [0, 2) and f = single-up(x x + f).
+// Closing a block adds its value double-up(double-up(f 2^(E - 1023)) 2^(E - 1023)) to `total`,
+// rounded upward.  Every step rounds up and every rescaling is by a power of two, so the norm
+// bounds the exact sum from above; the per-term work is integer and single-precision arithmetic,
+// none on the FP64 pipe that GB300 keeps narrow.  The largest |a| (fast and accurate modes) is
+// kept as bits: for nonnegative doubles the integer order is the value order, and NaN and Inf
+// bits exceed every finite value.
+// T = double (DGEMM) or float (SGEMM: every float is exactly a double, so the sums and the
+// shifts are those of the widened values).
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return widen_exact(x); }
+constexpr int kNormGroup = 16;
+static_assert(kNormBlock % kNormGroup == 0, "groups must not straddle a norm block");
+
 template <int SCALING>
 struct LineAcc {
-    double s = 0.0, total = 0.0, mx = 0.0;
+    float f = 0.0f;
+    int E = 0;       // the open block's scale (0: no group yet)
+    int nf = 0;      // bit 0: an infinite term, bit 1: a NaN term in the open block
+    double total = 0.0;
     uint64_t mb = 0;
-    // closes the open block: total += s, rounded upward (exact for the first block)
+    __device__ __forceinline__ double block_value() const {
+        if (nf) return (nf & 2) ? __longlong_as_double(0x7FF8000000000000ll)
+                                : __longlong_as_double(0x7FF0000000000000ll);
+        if (E == 0) return 0.0;
+        const double pw = __longlong_as_double((long long)E << 52);  // 2^(E - 1023), exact
+        return __dmul_ru(__dmul_ru(widen_exact(f), pw), pw);
+    }
+    // closes the open block: total += its value, rounded upward
     __device__ __forceinline__ void end_block() {
         if (SCALING != OZAKI2_SCALING_ACCURATE) {
-            total = __dadd_ru(total, s);
-            s = 0.0;
+            total = __dadd_ru(total, block_value());
+            f = 0.0f;
+            E = 0;
+            nf = 0;
         }
     }
-    __device__ __forceinline__ void add(double v) {
-        if (SCALING == OZAKI2_SCALING_ACCURATE) {
-            const uint64_t b = (uint64_t)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
-            mb = b > mb ? b : mb;
+    // One group: the first `cnt` of the G values v[] (G <= kNormGroup), the next terms of the
+    // line in order.  The common case runs straight through; a non-finite term (which settles
+    // the block's value), a zero or subnormal term, a term more than 126 binades below E (a
+    // subnormal x) and a rescale into the subnormal range take branches.
+    template <int G, typename T>
+    __device__ __forceinline__ void add_group(const T* v, int cnt) {
+        static_assert(G <= kNormGroup, "one group at a time");
+        // the upper words of |a| (sign cleared): their extremes give the group's largest and
+        // smallest exponent fields; absent terms count as zeros
+        auto word = [&](int u) -> uint32_t {
+            return u < cnt ? (uint32_t)((uint64_t)__double_as_longlong(to_double(v[u])) >> 32) &
+                                 0x7FFFFFFFu
+                           : 0u;
+        };
+        uint32_t wmax = 0u, wmin = 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const uint32_t w = word(u);
+            wmax = max(wmax, w);
+            wmin = min(wmin, w);
+            if (SCALING != OZAKI2_SCALING_PROPOSED) {
+                const uint64_t b = u < cnt ? (uint64_t)__double_as_longlong(to_double(v[u])) &
+                                                 0x7FFFFFFFFFFFFFFFull
+                                           : 0ull;
+                mb = b > mb ? b : mb;
+            }
+        }
+        if (SCALING == OZAKI2_SCALING_ACCURATE) return;
+        const int gmax = max((int)(wmax >> 20), 1), gmin = (int)(wmin >> 20);
+        if (gmax == 0x7FF || nf) {  // an Inf or NaN: the block's value is settled
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const uint64_t b = u < cnt ? (uint64_t)__double_as_longlong(to_double(v[u])) &
+                                                 0x7FFFFFFFFFFFFFFFull
+                                           : 0ull;
+                if ((b >> 52) == 0x7FF) nf |= (b & ((1ull << 52) - 1)) ? 2 : 1;
+            }
+            return;
+        }
+        if (gmax > E) {
+            if (E) f = scale_down_ru(f, 2 * (gmax - E));
+            E = gmax;
+        }
+        if (gmin != 0 && E - gmin <= 126) {
+            // every term a normal double whose x is a normal single: (1 + M/2^52) 2^-t with
+            // exponent -t, the top 23 fraction bits, plus one for any lower bit
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const uint64_t b = (uint64_t)__double_as_longlong(to_double(v[u]));
+                const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+                const int t = E - (int)((hi >> 20) & 0x7FFu);
+                const uint32_t top = __funnelshift_l(lo, hi & 0xFFFFFu, 3);
+                const uint32_t lost = min(lo & 0x1FFFFFFFu, 1u);
+                const float x = __uint_as_float(((uint32_t)(127 - t) << 23) + top + lost);
+                f = __fmaf_ru(x, x, f);
+            }
         } else {
-            s = __fma_ru(v, v, s);
-            if (SCALING == OZAKI2_SCALING_FAST) mx = fmax(mx, fabs(v));
+            // zeros, subnormal doubles, subnormal singles or a short group: term by term
+#pragma unroll 1
+            for (int u = 0; u < cnt && u < G; ++u) {
+                const uint64_t b = (uint64_t)__double_as_longlong(to_double(v[u])) &
+                                   0x7FFFFFFFFFFFFFFFull;
+                const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+                const int ef = (int)(hi >> 20);
+                const int t = E - ef;
+                uint32_t xb;
+                if (ef != 0 && t <= 126) {
+                    const uint32_t top = __funnelshift_l(lo, hi & 0xFFFFFu, 3);
+                    const uint32_t lost = min(lo & 0x1FFFFFFFu, 1u);
+                    xb = ((uint32_t)(127 - t) << 23) + top + lost;
+                } else {
+                    xb = b == 0 ? 0u : __float_as_uint(single_up_rare(b, E));
+                }
+                const float x = __uint_as_float(xb);
+                f = __fmaf_ru(x, x, f);
+            }
         }
     }
     __device__ __forceinline__ int result(float pprime, float delta, unsigned* status) {
         if (SCALING == OZAKI2_SCALING_ACCURATE) return accu_line_exponent(mb, status);
         end_block();
-        if (SCALING == OZAKI2_SCALING_FAST) {
-            if (isnan(total)) mx = total;  // fmax drops NaN; the norm keeps it
-            return alg1_shift(total, mx, pprime, delta, status);
-        }
+        if (SCALING == OZAKI2_SCALING_FAST)
+            return alg1_shift(total, __longlong_as_double((long long)mb), pprime, delta, status);
         return alg2_shift(total, pprime, status);
     }
 };
@@ -122,12 +266,11 @@ static_assert(kNormBlock % (2 * kBatch) == 0, "batches must not straddle a norm 
 
 // T = double (DGEMM) or float (SGEMM: every float is exactly a double, so the sums and the
 // shifts are those of the widened values).
-__device__ __forceinline__ double to_double(double x) { return x; }
-__device__ __forceinline__ double to_double(float x) { return widen_exact(x); }
 template <int SCALING, typename T = double>
 __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int64_t ld,
                                                     int i, int len, float pprime, float delta,
-                                                    int* shifts, unsigned* status) {
+                                                    int* shifts, unsigned* status,
+                                                    double* norms = nullptr) {
     constexpr int kB = kBatch * 8 / (int)sizeof(T);  // 128 bytes per thread in flight
     const T* p = X + i;
     LineAcc<SCALING> acc;
@@ -144,7 +287,7 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
             for (int u = 0; u < kB; ++u) b[u] = __ldg(p + (int64_t)(h + kB + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kB; ++u) acc.add(to_double(a[u]));
+        for (int g = 0; g < kB; g += kNormGroup) acc.template add_group<kNormGroup>(a + g, kNormGroup);
         if (((h + kB) & (kNormBlock - 1)) == 0) acc.end_block();
         if (!has_b) break;
         if (h + 2 * kB < full) {
@@ -153,14 +296,19 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
                 a[u] = __ldg(p + (int64_t)(h + 2 * kB + u) * ld);
         }
 #pragma unroll
-        for (int u = 0; u < kB; ++u) acc.add(to_double(b[u]));
+        for (int g = 0; g < kB; g += kNormGroup) acc.template add_group<kNormGroup>(b + g, kNormGroup);
         if (((h + 2 * kB) & (kNormBlock - 1)) == 0) acc.end_block();
     }
-    for (int h = full; h < len; ++h) {
-        acc.add(to_double(__ldg(p + (int64_t)h * ld)));
-        if (((h + 1) & (kNormBlock - 1)) == 0) acc.end_block();
+    for (int h = full; h < len; h += kNormGroup) {  // the rest, a group at a time
+        const int cnt = min(kNormGroup, len - h);
+        T r[kNormGroup];
+#pragma unroll
+        for (int u = 0; u < kNormGroup; ++u) r[u] = u < cnt ? __ldg(p + (int64_t)(h + u) * ld) : (T)0;
+        acc.template add_group<kNormGroup>(r, cnt);
+        if (((h + cnt) & (kNormBlock - 1)) == 0) acc.end_block();
     }
     shifts[i] = acc.result(pprime, delta, status);
+    if (norms) norms[i] = acc.total;
 }
 
 template <int SCALING>
@@ -189,7 +337,8 @@ __device__ __forceinline__ void scale_contiguous_warp(const T* __restrict__ X, i
                                                       int lines, int len, int line0,
                                                       float pprime, float delta, int* shifts,
                                                       unsigned* status,
-                                                      T (*t)[tile_len<T>() + 1]) {
+                                                      T (*t)[tile_len<T>() + 1],
+                                                      double* norms = nullptr) {
     constexpr int W = 8 / (int)sizeof(T), TL = tile_len<T>();
     const int lane = threadIdx.x & 31;
     const int nl = min(32, lines - line0);
@@ -214,13 +363,18 @@ __device__ __forceinline__ void scale_contiguous_warp(const T* __restrict__ X, i
         __syncwarp();
         if (h0 + TL < len) load(h0 + TL);
         if (lane < nl) {
-            for (int u = 0; u < cnt; ++u) acc.add(to_double(t[lane][u]));
+#pragma unroll
+            for (int g = 0; g < TL; g += kNormGroup)
+                if (g < cnt) acc.template add_group<kNormGroup>(&t[lane][g], cnt - g);
             // tiles start at multiples of TL, which divides kNormBlock
             if (((h0 + cnt) & (kNormBlock - 1)) == 0) acc.end_block();
         }
         __syncwarp();
     }
-    if (lane < nl) shifts[line0 + lane] = acc.result(pprime, delta, status);
+    if (lane < nl) {
+        shifts[line0 + lane] = acc.result(pprime, delta, status);
+        if (norms) norms[line0 + lane] = acc.total;
+    }
 }
 
 template <int SCALING>
@@ -260,6 +414,7 @@ struct ScaleSide {
     int64_t ls, es;
     int lines;
     int* shifts;
+    double* norms = nullptr;  // optional: the squared norms the shifts come from
 };
 
 // ---- lines longer than one block: the blocks of 32 lines split across the 8 warps of a block
@@ -269,25 +424,44 @@ constexpr int kSplitWarps = 8;
 template <typename T>
 __host__ __device__ constexpr int split_tile() { return 128 / (int)sizeof(T); }
 
-// One block [hb, he) of the adjacent line i, summed in order into acc.
+// One block [hb, he) of the adjacent line i, summed in order into acc.  The loads of the next
+// group are issued before the current one is summed, so each thread keeps a group in flight
+// while it computes.
 template <int SCALING, typename T>
 __device__ __forceinline__ void adjacent_block(const T* __restrict__ X, int64_t ld, int i, int hb,
                                                int he, LineAcc<SCALING>& acc) {
-    constexpr int kB = kBatch;  // loads in flight per thread (the split kernel has many warps)
+    constexpr int G = kNormGroup;
     const T* p = X + i;
+    const int full = hb + (he - hb) / G * G;
+    T a[G], b[G];
+    auto load = [&](T (&r)[G], int h) {
+#pragma unroll
+        for (int u = 0; u < G; ++u) r[u] = __ldg(p + (int64_t)(h + u) * ld);
+    };
     int h = hb;
-    for (; h + kB <= he; h += kB) {
-        T a[kB];
-#pragma unroll
-        for (int u = 0; u < kB; ++u) a[u] = __ldg(p + (int64_t)(h + u) * ld);
-#pragma unroll
-        for (int u = 0; u < kB; ++u) acc.add(to_double(a[u]));
+    if (h < full) load(a, h);
+    for (; h < full; h += 2 * G) {
+        const bool more = h + G < full;
+        if (more) load(b, h + G);
+        acc.template add_group<G>(a, G);
+        if (!more) {
+            h += G;
+            break;
+        }
+        if (h + 2 * G < full) load(a, h + 2 * G);
+        acc.template add_group<G>(b, G);
     }
-    for (; h < he; ++h) acc.add(to_double(__ldg(p + (int64_t)h * ld)));
+    if (h < he) {  // the last, shorter group
+        const int cnt = he - h;
+#pragma unroll
+        for (int u = 0; u < G; ++u) a[u] = u < cnt ? __ldg(p + (int64_t)(h + u) * ld) : (T)0;
+        acc.template add_group<G>(a, cnt);
+    }
 }
 
 // One block [hb, he) of the contiguous lines line0 .. line0 + nl - 1, one line per lane, read in
-// coalesced 128-byte rows and transposed through the warp's tile t.
+// coalesced 128-byte rows and transposed through the warp's tile t; the next tile is loaded into
+// registers while the current one is summed.
 template <int SCALING, typename T>
 __device__ __forceinline__ void contiguous_block(const T* __restrict__ X, int64_t ld, int nl,
                                                  int line0, int hb, int he,
@@ -296,18 +470,29 @@ __device__ __forceinline__ void contiguous_block(const T* __restrict__ X, int64_
     constexpr int TL = split_tile<T>();
     static_assert(TL == 16 || TL == 32, "tile of 128 bytes");
     constexpr int RPS = 32 / TL;  // rows copied per step of the warp: lane -> (row, column)
+    constexpr int STEPS = 32 / RPS;
     const int lane = threadIdx.x & 31;
     const int rc = lane % TL, rr = lane / TL;
+    T reg[STEPS];
+    auto load = [&](int h0) {
+#pragma unroll
+        for (int r = 0; r < STEPS; ++r) {
+            const int row = RPS * r + rr, h = h0 + rc;
+            reg[r] = (row < nl && h < he) ? __ldg(X + (int64_t)(line0 + row) * ld + h) : (T)0;
+        }
+    };
+    if (hb < he) load(hb);
     for (int h0 = hb; h0 < he; h0 += TL) {
         const int cnt = min(TL, he - h0);
-#pragma unroll 8
-        for (int r = 0; r < 32; r += RPS) {
-            const int row = r + rr, h = h0 + rc;
-            t[row][rc] = (row < nl && h < he) ? __ldg(X + (int64_t)(line0 + row) * ld + h) : (T)0;
-        }
+#pragma unroll
+        for (int r = 0; r < STEPS; ++r) t[RPS * r + rr][rc] = reg[r];
         __syncwarp();
-        if (lane < nl)
-            for (int u = 0; u < cnt; ++u) acc.add(to_double(t[lane][u]));
+        if (h0 + TL < he) load(h0 + TL);
+        if (lane < nl) {
+#pragma unroll
+            for (int g = 0; g < TL; g += kNormGroup)
+                if (g < cnt) acc.template add_group<kNormGroup>(&t[lane][g], cnt - g);
+        }
         __syncwarp();
     }
 }
@@ -340,9 +525,10 @@ __global__ void __launch_bounds__(32 * kSplitWarps) scale_partials_kernel(
         contiguous_block<SCALING, T>(X, S.ls, nl, line0, hb, he, tile[warp], acc);
     }
     if (lane < nl) {
-        part[(int64_t)blk * S.lines + line0 + lane] = acc.s;
+        part[(int64_t)blk * S.lines + line0 + lane] = acc.block_value();
         if (SCALING == OZAKI2_SCALING_FAST)
-            part[(int64_t)(nblocks + blk) * S.lines + line0 + lane] = acc.mx;
+            part[(int64_t)(nblocks + blk) * S.lines + line0 + lane] =
+                __longlong_as_double((long long)acc.mb);
     }
 }
 
@@ -364,10 +550,14 @@ __global__ void __launch_bounds__(256) scale_fold_kernel(ScaleSide a, ScaleSide 
     LineAcc<SCALING> acc;
     for (int blk = 0; blk < nblocks; ++blk) {
         acc.total = __dadd_ru(acc.total, part[(int64_t)blk * S.lines + i]);
-        if (SCALING == OZAKI2_SCALING_FAST)
-            acc.mx = fmax(acc.mx, part[(int64_t)(nblocks + blk) * S.lines + i]);
+        if (SCALING == OZAKI2_SCALING_FAST) {
+            const uint64_t b = (uint64_t)__double_as_longlong(
+                part[(int64_t)(nblocks + blk) * S.lines + i]);
+            acc.mb = b > acc.mb ? b : acc.mb;
+        }
     }
     S.shifts[i] = acc.result(pprime, delta, status);
+    if (S.norms) S.norms[i] = acc.total;
 }
 
 template <int SCALING, typename T>
@@ -382,13 +572,14 @@ __global__ void __launch_bounds__(128) scale_pair_kernel(ScaleSide a, ScaleSide 
     if (S.es != 1 || S.ls == 1) {
         const int i = line0 + (int)threadIdx.x;
         if (i < S.lines)
-            scale_adjacent_line<SCALING, T>(X, S.es, i, len, pprime, delta, S.shifts, status);
+            scale_adjacent_line<SCALING, T>(X, S.es, i, len, pprime, delta, S.shifts, status,
+                                            S.norms);
     } else {
         const int warp = threadIdx.x >> 5;
         const int l0 = line0 + 32 * warp;
         if (l0 < S.lines)
             scale_contiguous_warp<SCALING, T>(X, S.ls, S.lines, len, l0, pprime, delta, S.shifts,
-                                              status, tile[warp]);
+                                              status, tile[warp], S.norms);
     }
 }
 
@@ -517,10 +708,11 @@ static void launch_scale_pair_t(const ScaleSide& sa, const ScaleSide& sb, int bl
 cudaError_t launch_scale_pair(const void* A, int64_t a_ls, int64_t a_es, int m, const void* B,
                               int64_t b_ls, int64_t b_es, int n, int len, float pprime,
                               float delta, int* e, int* f, unsigned* status, cudaStream_t stream,
-                              int scaling, bool f32, double* partials) {
+                              int scaling, bool f32, double* partials, double* norms_a,
+                              double* norms_b) {
     const int blocks_a = (m + 127) / 128, blocks_b = (n + 127) / 128;
     if (blocks_a + blocks_b == 0) return cudaSuccess;
-    const ScaleSide sa{A, a_ls, a_es, m, e}, sb{B, b_ls, b_es, n, f};
+    const ScaleSide sa{A, a_ls, a_es, m, e, norms_a}, sb{B, b_ls, b_es, n, f, norms_b};
     const int grid = blocks_a + blocks_b;
     if (f32)
         launch_scale_pair_t<float>(sa, sb, blocks_a, grid, len, pprime, delta, status, stream,

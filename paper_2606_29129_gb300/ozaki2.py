@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
                                i32],
             "ozaki2_scale_a": [vp, ch, i32, i32, vp, i32, i32, vp],
             "ozaki2_scale_b": [vp, ch, i32, i32, vp, i32, i32, vp],
+            "ozaki2_scale_norms": [vp, ch, ch, i32, i32, vp, i32, i32, vp, vp],
             "ozaki2_scale_accurate": [vp, ch, ch, i32, i32, i32, vp, i32, vp, i32, i32, vp, vp,
                                       vp],
             "ozaki2_convert_a": [vp, ch, i32, i32, vp, i32, vp, i32, vp, i32, i32],
@@ -328,6 +329,12 @@ def ozaki2_scale_a(transA, m, k, A, lda, num_moduli, shifts, handle=None) -> int
 def ozaki2_scale_b(transB, k, n, B, ldb, num_moduli, shifts, handle=None) -> int:
     return lib().ozaki2_scale_b(_h(handle), _ch(transB), k, n, _ptr(B), ldb, num_moduli,
                                 _ptr(shifts))
+
+
+def ozaki2_scale_norms(side, trans, lines, k, X, ld, num_moduli, shifts, norms,
+                       handle=None) -> int:
+    return lib().ozaki2_scale_norms(_h(handle), _ch(side), _ch(trans), lines, k, _ptr(X), ld,
+                                    num_moduli, _ptr(shifts), _ptr(norms))
 
 
 def ozaki2_scale_accurate(transA, transB, m, n, k, A, lda, B, ldb, num_moduli, e, f, cmax=None,

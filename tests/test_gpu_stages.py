@@ -82,15 +82,34 @@ def test_scale_extreme_magnitudes(oz, orc, N, alpha):
     assert np.array_equal(_gpu.shifts_a(oz, A, m, k, N), e_ref)
 
 
-def test_scale_log2_argument_sweep(oz, orc):
-    """2^23 one-element rows whose squared norms sweep every single-precision mantissa in
-    [1, 2): the GPU's logarithm step and the oracle's agree on all of them."""
+def _log2_sweep_rows():
+    """2^23 rows (1, v_j) whose squared norms are exactly 1 + j 2^-23, j = 0 .. 2^23 - 1, under
+    the single-precision norm: v_j is the least single with v_j^2 > (j - 1) 2^-23, and
+    single-up(1 + v_j^2) = 1 + j 2^-23 because the squares of neighbouring singles below 1 lie
+    closer than 2^-23."""
     m = 1 << 23
-    x = 1.0 + np.arange(m, dtype=np.float64) * 2.0**-23
-    A = np.sqrt(x).reshape(1, m)     # column-major m x 1, lda = m
+    j = np.arange(m, dtype=np.float64)
+    t = (j - 1) * 2.0**-23
+    v = np.sqrt(np.maximum(t, 0)).astype(np.float32)
+    for _ in range(4):
+        up = (v.astype(np.float64) ** 2 <= t) & (j > 0)
+        v = np.where(up, np.nextafter(v, np.float32(np.inf)), v)
+        pv = np.nextafter(v, np.float32(0))
+        v = np.where((pv.astype(np.float64) ** 2 > t) & (pv > 0), pv, v)
+    v[0] = 0.0
+    assert (v.astype(np.float64) ** 2 <= j * 2.0**-23).all()
+    return np.ascontiguousarray(np.stack([np.ones(m), v.astype(np.float64)])), m
+
+
+def test_scale_log2_argument_sweep(oz, orc):
+    """Rows whose squared norms sweep every single-precision mantissa in [1, 2): the GPU's
+    logarithm step and the oracle's agree on all of them."""
+    A, m = _log2_sweep_rows()          # column-major m x 2, lda = m
+    _, nr = orc.shifts_a(A, m, 2, 14)
+    assert np.array_equal(np.asarray(nr), 1.0 + np.arange(m) * 2.0**-23)
     for N in (14, 20):
-        e_ref, _ = orc.shifts_a(A, m, 1, N)
-        assert np.array_equal(_gpu.shifts_a(oz, A, m, 1, N), e_ref)
+        e_ref, _ = orc.shifts_a(A, m, 2, N)
+        assert np.array_equal(_gpu.shifts_a(oz, A, m, 2, N), e_ref)
 
 
 def test_scale_nonfinite_flag(oz, orc):
@@ -268,3 +287,63 @@ def test_crt_extreme_integers_and_exponents(oz, orc, N):
     for i, x in enumerate(xs[:-1]):
         assert C[0, i] == float(x)
     assert np.isnan(C[:, m - 1]).all()
+
+
+def _norm_lines(k):
+    """Rows whose squared norms reach every branch of the single-precision reading: the block
+    maximum rising late, terms far below it (subnormal singles), subnormal doubles, zeros,
+    overflow to +Inf, Inf and NaN entries, and wide random magnitudes; zero-padded to k."""
+    g = np.random.Generator(np.random.PCG64(91))
+    rows = [
+        np.sort(np.abs(g.standard_normal(300))) * 2.0 ** g.integers(-60, 60, 300),
+        g.standard_normal(600) * np.exp(16.0 * g.standard_normal(600)),
+        np.concatenate([g.random(100) * 2.0**-140, [1.5], g.random(100) * 2.0**-75]),
+        g.random(300) * 5e-310,
+        np.concatenate([g.random(50) * 5e-310, g.random(50) * 1e-300, [0.0] * 20]),
+        np.concatenate([g.random(10), [1e200], g.random(10)]),
+        np.concatenate([g.random(10), [np.inf], g.random(10)]),
+        np.concatenate([g.random(300), [np.nan], g.random(10)]),
+        np.concatenate([[2.0**-1000], g.random(5) * 2.0**1000]),
+        g.random(400) * 2.0**-1060,
+        np.zeros(5),
+    ]
+    rows += list(g.standard_normal((40, k)) * np.exp(8.0 * g.standard_normal((40, k))))
+    M = np.zeros((len(rows), k))
+    for i, r in enumerate(rows):
+        M[i, :min(len(r), k)] = r[:k]
+    return M
+
+
+@pytest.mark.parametrize("k", [200, 700, 2048])
+@pytest.mark.parametrize("side", ["A", "B"])
+@pytest.mark.parametrize("trans", ["N", "T"])
+def test_scale_norms_match_oracle(oz, orc, k, side, trans):
+    """The squared norms the product's scaling kernels compute (one thread per line for lines of
+    one block, the split kernels for longer ones, both memory layouts) equal the oracle's bit
+    for bit on lines that reach every branch of the single-precision reading, and so do the
+    shifts."""
+    import torch
+
+    M = _norm_lines(k)                       # lines x k: the mathematical rows of op(A)
+    lines = M.shape[0]
+    if side == "A":
+        # op(A) = M: A is M (trans N) or M^T (trans T), stored column-major
+        store = np.ascontiguousarray(M.T if trans == "N" else M)
+        ld = lines if trans == "N" else k
+        e_ref, nr_ref = orc.shifts_a(store, lines, k, 16, trans=trans, lda=ld)
+    else:
+        # op(B) = M^T (k x lines): B is M^T (trans N) or M (trans T)
+        store = np.ascontiguousarray(M if trans == "N" else M.T)
+        ld = k if trans == "N" else lines
+        e_ref, nr_ref = orc.shifts_b(store, k, lines, 16, trans=trans, ldb=ld)
+    shifts = torch.zeros(lines, dtype=torch.int32, device="cuda")
+    norms = torch.zeros(lines, dtype=torch.float64, device="cuda")
+    _gpu.ok(oz.ozaki2_scale_norms(side, trans, lines, k, _gpu.dev(store), ld, 16, shifts, norms),
+            "scale_norms")
+    torch.cuda.synchronize()
+    got = norms.cpu().numpy()
+    nr_ref = np.asarray(nr_ref)
+    assert np.array_equal(got.view(np.int64)[~np.isnan(got)],
+                          nr_ref.view(np.int64)[~np.isnan(got)])
+    assert np.array_equal(np.isnan(got), np.isnan(nr_ref))
+    assert np.array_equal(shifts.cpu().numpy(), e_ref)

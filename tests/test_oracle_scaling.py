@@ -7,6 +7,7 @@ Section 4 for alpha = 2^s, the effective-bit-width formula of Section 3.1 for no
 alpha, and the all-ones worked example of Section 3.1 in closed form.
 """
 import math
+import struct
 from decimal import Decimal, getcontext
 from fractions import Fraction
 
@@ -39,7 +40,9 @@ def test_norms_round_up_and_are_tight(orc, phi):
     _, nr = orc.shifts_a(A, m, k, 14)
     for i, S in enumerate(exact_sq_norms_rows(A)):
         assert Fraction(float(nr[i])) >= S
-        assert Fraction(float(nr[i])) <= S * (1 + Fraction(k + 2, 2**52))
+        # single-precision terms and sums, each rounded up: at most 2k + 4 relative steps of
+        # 2^-23 in one block (a conversion and an addition per term, the rescalings)
+        assert Fraction(float(nr[i])) <= S * (1 + Fraction(2 * k + 4, 2**23))
 
 
 @pytest.mark.parametrize("N", [2, 8, 14, 17, 20])
@@ -187,29 +190,84 @@ def test_log2_margin_of_proposed_mu(orc, N):
 
 def _ru(x: Fraction) -> float:
     """The smallest double >= x (rounding upward), from exact rational arithmetic."""
-    d = float(x)
+    try:
+        d = float(x)
+    except OverflowError:
+        return math.inf
     return d if Fraction(d) >= x else math.nextafter(d, math.inf)
 
 
-def blocked_norm_ru(line, block=256):
-    """Upward-rounded squared norm in the blocked order, every operation rounded upward from its
-    exact rational value: fma per term within each block of `block` terms, then the block sums
-    added in order."""
+def _ru32(x: Fraction) -> float:
+    """The smallest single >= x >= 0 (rounding upward), from exact rational arithmetic."""
+    if x == 0:
+        return 0.0
+    f = np.float32(float(x)) if x < 2**120 else np.float32(2.0**120)
+    while Fraction(float(f)) < x:
+        f = np.nextafter(f, np.float32(np.inf))
+    while f > 0 and Fraction(float(np.nextafter(f, np.float32(0)))) >= x:
+        f = np.nextafter(f, np.float32(0))
+    return float(f)
+
+
+def _exp_field(a: float) -> int:
+    """Biased exponent field of a finite nonzero double, a subnormal counting as 1."""
+    e = (struct.unpack("<Q", struct.pack("<d", a))[0] >> 52) & 0x7FF
+    return max(int(e), 1)
+
+
+def blocked_norm_ru(line, block=256, group=16):
+    """The squared norm of Section 4 in single precision with rounding up, as the reading
+    defines it, from exact rational arithmetic: blocks of `block` terms in groups of `group`;
+    before a group, E becomes the largest of E, 1 and the group's exponent fields and a rise of E
+    by d rescales f to single-up(f 2^(-2d)); each term then adds x = single-up(|a| 2^(1023 - E))
+    as f = single-up(x^2 + f); the block value is double-up(double-up(f 2^(E - 1023))
+    2^(E - 1023)), and the block values are added in order, rounded up."""
     total = 0.0
     for b0 in range(0, len(line), block):
-        s = 0.0
-        for a in line[b0:b0 + block]:
-            s = _ru(Fraction(float(a)) ** 2 + Fraction(s))
-        total = _ru(Fraction(total) + Fraction(s))
+        blk = [abs(float(a)) for a in line[b0:b0 + block]]
+        E, f = 0, 0.0
+        has_nan = any(math.isnan(a) for a in blk)
+        has_inf = any(math.isinf(a) for a in blk)
+        if not (has_nan or has_inf):
+            for g0 in range(0, len(blk), group):
+                grp = blk[g0:g0 + group]
+                En = max([E, 1] + [_exp_field(a) for a in grp if a != 0.0])
+                if En > E and f:
+                    f = _ru32(Fraction(f) / Fraction(2) ** (2 * (En - E)))
+                E = En
+                for a in grp:
+                    if a != 0.0:
+                        x = _ru32(Fraction(a) * Fraction(2) ** (1023 - E))
+                        f = _ru32(Fraction(x) ** 2 + Fraction(f))
+        if has_nan:
+            v = math.nan
+        elif has_inf:
+            v = math.inf
+        elif E == 0:
+            v = 0.0
+        else:
+            p = Fraction(2) ** (E - 1023)
+            v = _ru(Fraction(_ru(Fraction(f) * p)) * p)
+        if math.isnan(v) or math.isnan(total):
+            total = math.nan
+        elif math.isinf(v) or math.isinf(total):
+            total = math.inf
+        else:
+            total = _ru(Fraction(total) + Fraction(v))
     return total
+
+
+def _same(a: float, b: float) -> bool:
+    return (math.isnan(a) and math.isnan(b)) or a == b
 
 
 @pytest.mark.parametrize("k", [255, 256, 257, 700, 2048])
 def test_blocked_norm_order_and_bound(orc, k):
-    """The squared norm of Section 4 rounds every operation up; with no order given by the paper,
-    the reading sums blocks of 256 terms in order, then the block sums in order.  The oracle
-    matches that sequence of upward roundings bit for bit (against exact rationals), bounds the
-    exact sum from above and stays within (k + blocks + 2) 2^-52 of it."""
+    """The squared norm of Section 4 rounds every operation up, in single or double precision;
+    the reading takes single precision on terms rescaled exactly by a power of two that follows
+    the largest term seen, in blocks of 256 terms taken 16 at a time.  The oracle matches that sequence of upward roundings bit for
+    bit (against exact rationals), bounds the exact sum from above and stays within
+    (2k + 4 blocks) 2^-23 of it."""
     m = 6
     A = synthetic.paper_matrix(m, k, 2.0, 40 + k)
     _, nr = orc.shifts_a(A, m, k, 14)
@@ -218,15 +276,49 @@ def test_blocked_norm_order_and_bound(orc, k):
     for i, S in enumerate(exact_sq_norms_rows(A)):
         assert float(nr[i]) == blocked_norm_ru(M[i]), i
         assert Fraction(float(nr[i])) >= S
-        assert Fraction(float(nr[i])) <= S * (1 + Fraction(k + blocks + 2, 2**52))
+        assert Fraction(float(nr[i])) <= S * (1 + Fraction(2 * k + 4 * blocks, 2**23))
+
+
+def _wide_lines():
+    """Lines that reach every branch of the reading: wide magnitude ranges (the block maximum
+    rising late, terms 2^-140 below it that round to subnormal singles), subnormal doubles, zeros,
+    huge terms whose block value overflows, and non-finite terms."""
+    g = np.random.Generator(np.random.PCG64(77))
+    lines = []
+    lines.append(np.sort(np.abs(g.standard_normal(300))) * 2.0 ** g.integers(-60, 60, 300))
+    lines.append(g.standard_normal(600) * np.exp(16.0 * g.standard_normal(600)))
+    lines.append(np.concatenate([g.random(100) * 2.0**-140, [1.5], g.random(100) * 2.0**-75]))
+    lines.append(g.random(300) * 5e-310)                        # subnormal doubles only
+    lines.append(np.concatenate([g.random(50) * 5e-310, g.random(50) * 1e-300, [0.0] * 20]))
+    z = g.standard_normal(513)
+    z[::7] = 0.0
+    lines.append(z)
+    lines.append(np.concatenate([g.random(10), [1e200], g.random(10)]))   # overflows: +Inf
+    lines.append(np.concatenate([g.random(10), [np.inf], g.random(10)]))
+    lines.append(np.concatenate([g.random(300), [np.nan], g.random(10)]))
+    lines.append(np.concatenate([[2.0**-1000], g.random(5) * 2.0**1000]))  # rises by 2000 binades
+    lines.append(g.random(400) * 2.0**-1060)                    # deep subnormals
+    return lines
+
+
+def test_blocked_norm_wide_ranges_match_definition(orc):
+    """The oracle's norms equal the exact-rational restatement of the reading on lines that reach
+    its rescalings, subnormal singles and doubles, zeros, overflow and non-finite terms; finite
+    ones bound the exact sum from above."""
+    for idx, line in enumerate(_wide_lines()):
+        k = len(line)
+        A = np.ascontiguousarray(line.reshape(k, 1))   # column-major 1 x k, lda = 1
+        _, nr = orc.shifts_a(A, 1, k, 14)
+        want = blocked_norm_ru(line)
+        assert _same(float(nr[0]), want), (idx, float(nr[0]), want)
+        if math.isfinite(want):
+            S = sum(Fraction(float(v)) ** 2 for v in line)
+            assert Fraction(want) >= S, idx
 
 
 def test_blocked_norm_differs_from_sequential_where_it_should():
-    """The blocked and the sequential upward sums are different readings of the same definition:
-    on a line whose first block ends on a large partial sum they differ in the last bit, which the
-    order pin above can tell apart."""
-    line = [1.0] * 256 + [2.0**-30] * 300
-    seq = 0.0
-    for a in line:
-        seq = _ru(Fraction(a) ** 2 + Fraction(seq))
-    assert blocked_norm_ru(line) != seq
+    """The blocked and the one-block upward sums are different readings of the same definition:
+    on a line whose first block ends on a large partial sum they differ, which the order pin
+    above can tell apart."""
+    line = [1.0] * 256 + [2.0**-20] * 300
+    assert blocked_norm_ru(line) != blocked_norm_ru(line, block=len(line))
