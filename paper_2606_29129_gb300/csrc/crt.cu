@@ -55,12 +55,17 @@ __device__ __noinline__ float double_bits_to_float(uint64_t bits) {
 // 32-bit words of the working integers.  X and Q P are only needed modulo 2^(32 W): the result
 // Y = X - Q P satisfies |Y| < P (Q is round(X/P) or one off near a tie), so W words holding
 // bits(P) + 2 bits carry Y exactly in two's complement.
-__host__ __device__ constexpr int crt_words(int N) {
+__host__ __device__ constexpr int crt_pbits(int N) {
     // bits(P) for N = 2..20: 16 24 32 40 48 56 64 72 80 88 95 103 111 118 126 133 141 148 156
     constexpr int b[21] = {0, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80,
                            88, 95, 103, 111, 118, 126, 133, 141, 148, 156};
-    return (b[N] + 2 + 31) / 32;
+    return b[N];
 }
+__host__ __device__ constexpr int crt_words(int N) { return (crt_pbits(N) + 2 + 31) / 32; }
+// The word that holds the leading bit of a large |C''| (< P/2 < 2^(bits(P) - 1)): the top word
+// of the W, except where bits(P) is a multiple of 32 (N = 4, 8, 12), whose extra sign word stays
+// zero for every |C''| < P.
+__host__ __device__ constexpr int crt_top(int N) { return (crt_pbits(N) - 2) / 32; }
 
 // ---- multi-word integer steps with the carry flag: each chain is one asm statement, so nothing
 // the compiler schedules can come between an instruction that sets the carry and the one that
@@ -322,7 +327,7 @@ __device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int 
         ((uint32_t)((S - ((1ull << 45) - (1ull << 36))) >> 32) & 0x3FE0u) == 0;
     Words<W> Yw;
     add_word_times<W>(X, Q, t.negP, Yw.w);  // Y = X - Q P (mod 2^(32 W))
-    // The common case, straight-line: |Y| with the top word leading (the shifts make |C''|
+    // The common case, straight-line: |Y| with its leading bit in word TOP (the shifts make |C''|
     // large against P) and a result in the normal range.  The 64 bits from the leading one down
     // come by funnel shifts (a shift of 0 keeps the words), every lower bit folded into bit 0 as
     // a sticky bit (it lies below every rounding position); rounding to nearest even adds the
@@ -332,15 +337,18 @@ __device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int 
 #pragma unroll
     for (int j = 0; j < W; ++j) A[j] = Yw.w[j];
     const bool neg = abs_words<W>(A);
-    const uint32_t w0 = A[W - 1], w1 = W > 1 ? A[W - 2] : 0u, w2 = W > 2 ? A[W - 3] : 0u;
-    uint32_t low_or = 0;
+    constexpr int TOP = crt_top(N);
+    const uint32_t w0 = A[TOP], w1 = TOP > 0 ? A[TOP - 1] : 0u, w2 = TOP > 1 ? A[TOP - 2] : 0u;
+    uint32_t low_or = 0, high_or = 0;
 #pragma unroll
-    for (int j = 0; j < W - 3; ++j) low_or |= A[j];
-    const int lz = __clz(w0);  // 32 when the top word is zero: the rare path then
+    for (int j = 0; j < TOP - 2; ++j) low_or |= A[j];
+#pragma unroll
+    for (int j = TOP + 1; j < W; ++j) high_or |= A[j];  // zero unless Q was one off
+    const int lz = __clz(w0);  // 32 when that word is zero: the rare path then
     const uint32_t hi = __funnelshift_l(w1, w0, lz), lo = __funnelshift_l(w2, w1, lz);
     const uint32_t sticky = ((w2 << lz) | low_or) != 0 ? 1u : 0u;
     const uint64_t win = ((uint64_t)hi << 32) | lo | sticky;
-    const int E = 32 * (W - 1) + 31 - lz - (ea + fb);
+    const int E = 32 * TOP + 31 - lz - (ea + fb);
     OutT y;
     bool normal;
     if constexpr (sizeof(OutT) == 4) {
@@ -357,7 +365,8 @@ __device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int 
             (long long)((neg ? (1ull << 63) : 0ull) | (((uint64_t)(E + 1022) << 52) + m)));
         normal = E >= -1022 && E <= 1022;
     }
-    if (near_half || w0 == 0 || !normal) y = crt_value_rare<N, OutT>(Yw, near_half, ea, fb, t);
+    if (near_half || w0 == 0 || high_or != 0 || !normal)
+        y = crt_value_rare<N, OutT>(Yw, near_half, ea, fb, t);
     return y;
 }
 

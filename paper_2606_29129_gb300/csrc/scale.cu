@@ -178,6 +178,39 @@ struct LineAcc {
     template <int G, typename T>
     __device__ __forceinline__ void add_group(const T* v, int cnt) {
         static_assert(G <= kNormGroup, "one group at a time");
+        if constexpr (sizeof(T) == 4 && SCALING == OZAKI2_SCALING_PROPOSED) {
+            // Single-precision inputs whose group holds only normal nonzero singles: a single's
+            // exponent field plus 896 is its double's, and its 23 fraction bits are the top ones
+            // of the double's, so x is built from the single's bits with nothing rounded off.
+            uint32_t wmax = 0u, wmin = 0xFFFFFFFFu;
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const uint32_t w = u < cnt ? __float_as_uint(v[u]) & 0x7FFFFFFFu : 0u;
+                wmax = max(wmax, w);
+                wmin = min(wmin, w);
+            }
+            const int fmax = (int)(wmax >> 23), fmin = (int)(wmin >> 23);
+            if (fmin != 0 && fmax != 0xFF && !nf) {
+                const int gmax = fmax + 896;
+                if (gmax > E) {
+                    if (E) f = scale_down_ru(f, 2 * (gmax - E));
+                    E = gmax;
+                }
+                if (E - (fmin + 896) <= 126) {
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        const uint32_t w = __float_as_uint(v[u]) & 0x7FFFFFFFu;
+                        const int t = E - ((int)(w >> 23) + 896);
+                        const float x = __uint_as_float(((uint32_t)(127 - t) << 23) +
+                                                        (w & 0x7FFFFFu));
+                        f = __fmaf_ru(x, x, f);
+                    }
+                    return;
+                }
+                // a term more than 126 binades below the group's largest: the general path
+                // below, whose E is already the group's
+            }
+        }
         // the upper words of |a| (sign cleared): their extremes give the group's largest and
         // smallest exponent fields; absent terms count as zeros
         auto word = [&](int u) -> uint32_t {
