@@ -66,6 +66,12 @@ __host__ __device__ constexpr int crt_words(int N) { return (crt_pbits(N) + 2 + 
 // of the W, except where bits(P) is a multiple of 32 (N = 4, 8, 12), whose extra sign word stays
 // zero for every |C''| < P.
 __host__ __device__ constexpr int crt_top(int N) { return (crt_pbits(N) - 2) / 32; }
+// Where |C''| < P/2 reaches fewer than 12 bits into word TOP (N = 5, 9, 13, 17), an ordinary entry
+// (some bits below the bound) often starts in the word below: the straight-line path then also
+// takes its window one word lower.
+__host__ __device__ constexpr bool crt_window_drops(int N) {
+    return crt_top(N) >= 1 && (crt_pbits(N) - 2) % 32 < 12;
+}
 
 // ---- multi-word integer steps with the carry flag: each chain is one asm statement, so nothing
 // the compiler schedules can come between an instruction that sets the carry and the one that
@@ -338,17 +344,30 @@ __device__ __forceinline__ OutT crt_value(const uint32_t (&v)[(N + 1) / 2], int 
     for (int j = 0; j < W; ++j) A[j] = Yw.w[j];
     const bool neg = abs_words<W>(A);
     constexpr int TOP = crt_top(N);
-    const uint32_t w0 = A[TOP], w1 = TOP > 0 ? A[TOP - 1] : 0u, w2 = TOP > 1 ? A[TOP - 2] : 0u;
+    uint32_t w0 = A[TOP], w1 = TOP > 0 ? A[TOP - 1] : 0u, w2 = TOP > 1 ? A[TOP - 2] : 0u;
     uint32_t low_or = 0, high_or = 0;
 #pragma unroll
-    for (int j = 0; j < TOP - 2; ++j) low_or |= A[j];
+    for (int j = 0; j < TOP - 3; ++j) low_or |= A[j];    // words below TOP - 3
+    const uint32_t w3 = TOP > 2 ? A[TOP - 3] : 0u;
 #pragma unroll
     for (int j = TOP + 1; j < W; ++j) high_or |= A[j];  // zero unless Q was one off
+    int top = TOP;
+    if constexpr (crt_window_drops(N)) {
+        // a zero word TOP: the window one word lower, word TOP - 3 in it rather than sticky
+        const bool down = w0 == 0u;
+        w0 = down ? w1 : w0;
+        w1 = down ? w2 : w1;
+        w2 = down ? w3 : w2;
+        low_or |= down ? 0u : w3;
+        top = down ? TOP - 1 : TOP;
+    } else {
+        low_or |= w3;
+    }
     const int lz = __clz(w0);  // 32 when that word is zero: the rare path then
     const uint32_t hi = __funnelshift_l(w1, w0, lz), lo = __funnelshift_l(w2, w1, lz);
     const uint32_t sticky = ((w2 << lz) | low_or) != 0 ? 1u : 0u;
     const uint64_t win = ((uint64_t)hi << 32) | lo | sticky;
-    const int E = 32 * TOP + 31 - lz - (ea + fb);
+    const int E = 32 * top + 31 - lz - (ea + fb);
     OutT y;
     bool normal;
     if constexpr (sizeof(OutT) == 4) {

@@ -80,9 +80,12 @@ def test_gemm_variants_and_chunks(oz, orc, variant, chunk):
     assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 16))
 
 
-@pytest.mark.parametrize("N", [2, 5, 8, 11, 14, 16, 17, 18, 20])
+@pytest.mark.parametrize("N", list(range(2, 21)))
 @pytest.mark.parametrize("phi", [0.5, 4.0])
 def test_moduli_counts(oz, orc, N, phi):
+    """Every moduli count: the reconstruction's word count, the word its rounding window starts
+    in (one lower for N = 4, 8, 12, whose top word is always zero, and a second choice for
+    N = 5, 9, 13, 17) and its pair grouping (odd N ends on a single modulus) all change with N."""
     m, n, k = 150, 130, 700
     A, B = make(m, n, k, phi, N)
     C = _gpu.dgemm(oz, A, B, m, n, k, N)
