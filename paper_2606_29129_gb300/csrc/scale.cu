@@ -175,9 +175,11 @@ struct LineAcc {
     // line in order.  The common case runs straight through; a non-finite term (which settles
     // the block's value), a zero or subnormal term, a term more than 126 binades below E (a
     // subnormal x) and a rescale into the subnormal range take branches.
+    // v: the group's terms in order, absent ones (past the end of a line) as zeros.
     template <int G, typename T>
-    __device__ __forceinline__ void add_group(const T* v, int cnt) {
-        static_assert(G <= kNormGroup, "one group at a time");
+    __device__ __forceinline__ void add_group(const T (&v)[G]) {
+        static_assert(G == kNormGroup, "one group at a time");
+        constexpr int cnt = G;
         if constexpr (sizeof(T) == 4 && SCALING == OZAKI2_SCALING_PROPOSED) {
             // Single-precision inputs whose group holds only normal nonzero singles: a single's
             // exponent field plus 896 is its double's, and its 23 fraction bits are the top ones
@@ -262,8 +264,8 @@ struct LineAcc {
             }
         } else {
             // zeros, subnormal doubles, subnormal singles or a short group: term by term
-#pragma unroll 1
-            for (int u = 0; u < cnt && u < G; ++u) {
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
                 const uint64_t b = (uint64_t)__double_as_longlong(to_double(v[u])) &
                                    0x7FFFFFFFFFFFFFFFull;
                 const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
@@ -292,10 +294,10 @@ struct LineAcc {
 };
 
 // Lines adjacent in memory (line_stride == 1): thread i walks line i in order; a warp reads 32
-// consecutive doubles per step, so every load is coalesced.  Loads run two batches of 16 ahead
-// of the dependent FMA chain so that enough bytes are in flight with one thread per line.
-constexpr int kBatch = 16;  // loads per batch for doubles (twice as many for floats)
-static_assert(kNormBlock % (2 * kBatch) == 0, "batches must not straddle a norm block");
+// consecutive elements per step, so every load is coalesced.  The loads of the next group of 16
+// are issued before the current group is summed, so that two groups are in flight per thread.
+// Every group is a register array handed over by reference (a pointer into it had put the
+// arrays in local memory).
 
 // T = double (DGEMM) or float (SGEMM: every float is exactly a double, so the sums and the
 // shifts are those of the widened values).
@@ -304,7 +306,7 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
                                                     int i, int len, float pprime, float delta,
                                                     int* shifts, unsigned* status,
                                                     double* norms = nullptr) {
-    constexpr int kB = kBatch * 8 / (int)sizeof(T);  // 128 bytes per thread in flight
+    constexpr int kB = kNormGroup;  // a group per batch, two batches in flight
     const T* p = X + i;
     LineAcc<SCALING> acc;
     const int full = len / kB * kB;
@@ -319,8 +321,7 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
 #pragma unroll
             for (int u = 0; u < kB; ++u) b[u] = __ldg(p + (int64_t)(h + kB + u) * ld);
         }
-#pragma unroll
-        for (int g = 0; g < kB; g += kNormGroup) acc.template add_group<kNormGroup>(a + g, kNormGroup);
+        acc.add_group(a);
         if (((h + kB) & (kNormBlock - 1)) == 0) acc.end_block();
         if (!has_b) break;
         if (h + 2 * kB < full) {
@@ -328,8 +329,7 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
             for (int u = 0; u < kB; ++u)
                 a[u] = __ldg(p + (int64_t)(h + 2 * kB + u) * ld);
         }
-#pragma unroll
-        for (int g = 0; g < kB; g += kNormGroup) acc.template add_group<kNormGroup>(b + g, kNormGroup);
+        acc.add_group(b);
         if (((h + 2 * kB) & (kNormBlock - 1)) == 0) acc.end_block();
     }
     for (int h = full; h < len; h += kNormGroup) {  // the rest, a group at a time
@@ -337,7 +337,7 @@ __device__ __forceinline__ void scale_adjacent_line(const T* __restrict__ X, int
         T r[kNormGroup];
 #pragma unroll
         for (int u = 0; u < kNormGroup; ++u) r[u] = u < cnt ? __ldg(p + (int64_t)(h + u) * ld) : (T)0;
-        acc.template add_group<kNormGroup>(r, cnt);
+        acc.add_group(r);
         if (((h + cnt) & (kNormBlock - 1)) == 0) acc.end_block();
     }
     shifts[i] = acc.result(pprime, delta, status);
@@ -397,8 +397,14 @@ __device__ __forceinline__ void scale_contiguous_warp(const T* __restrict__ X, i
         if (h0 + TL < len) load(h0 + TL);
         if (lane < nl) {
 #pragma unroll
-            for (int g = 0; g < TL; g += kNormGroup)
-                if (g < cnt) acc.template add_group<kNormGroup>(&t[lane][g], cnt - g);
+            for (int g = 0; g < TL; g += kNormGroup) {
+                if (g < cnt) {
+                    T r[kNormGroup];
+#pragma unroll
+                    for (int u = 0; u < kNormGroup; ++u) r[u] = g + u < cnt ? t[lane][g + u] : (T)0;
+                    acc.add_group(r);
+                }
+            }
             // tiles start at multiples of TL, which divides kNormBlock
             if (((h0 + cnt) & (kNormBlock - 1)) == 0) acc.end_block();
         }
@@ -476,19 +482,19 @@ __device__ __forceinline__ void adjacent_block(const T* __restrict__ X, int64_t 
     for (; h < full; h += 2 * G) {
         const bool more = h + G < full;
         if (more) load(b, h + G);
-        acc.template add_group<G>(a, G);
+        acc.add_group(a);
         if (!more) {
             h += G;
             break;
         }
         if (h + 2 * G < full) load(a, h + 2 * G);
-        acc.template add_group<G>(b, G);
+        acc.add_group(b);
     }
     if (h < he) {  // the last, shorter group
         const int cnt = he - h;
 #pragma unroll
         for (int u = 0; u < G; ++u) a[u] = u < cnt ? __ldg(p + (int64_t)(h + u) * ld) : (T)0;
-        acc.template add_group<G>(a, cnt);
+        acc.add_group(a);
     }
 }
 
@@ -523,8 +529,14 @@ __device__ __forceinline__ void contiguous_block(const T* __restrict__ X, int64_
         if (h0 + TL < he) load(h0 + TL);
         if (lane < nl) {
 #pragma unroll
-            for (int g = 0; g < TL; g += kNormGroup)
-                if (g < cnt) acc.template add_group<kNormGroup>(&t[lane][g], cnt - g);
+            for (int g = 0; g < TL; g += kNormGroup) {
+                if (g < cnt) {
+                    T r[kNormGroup];
+#pragma unroll
+                    for (int u = 0; u < kNormGroup; ++u) r[u] = g + u < cnt ? t[lane][g + u] : (T)0;
+                    acc.add_group(r);
+                }
+            }
         }
         __syncwarp();
     }
