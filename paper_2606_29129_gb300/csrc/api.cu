@@ -1046,7 +1046,7 @@ int ozaki2_encode_operands(ozaki2_handle_t handle, int count, ozaki2_operand* op
             cudaSuccess ||
         cudaEventRecord(ev, ctx->stream) != cudaSuccess)
         return OZAKI2_ERROR_CUDA;
-    return launch_encode(count, ops, tables_dev, ctx->d_status, ctx->stream);
+    return launch_encode(count, ops, tables_dev, ctx->d_status, ctx->stream, ctx->scaling);
 }
 
 

@@ -53,6 +53,7 @@ struct Plan {
     // table sections (offsets within the table block)
     int64_t off_gp = 0, off_gg = 0, off_sw = 0, off_cw = 0, off_rw = 0, table_bytes = 0;
     int n_scale = 0, n_conv = 0, n_crt = 0;
+    int n_scale_adj = 0;  // scale work items of adjacent lines (first in the list)
     std::vector<int> conv_n, conv_begin, conv_count;  // per distinct N: blocks in the table
     std::vector<int> crt_begin, crt_count;
     int total_tiles = 0;
@@ -118,6 +119,10 @@ void make_plan(int count, const ozaki2_problem* probs, Plan& P, const TileRules*
         scale += (has_a ? 0 : (p.m + 127) / 128) + (has_b ? 0 : (p.n + 127) / 128);
         const int64_t aes = notrans(p.transA) ? p.lda : 1;
         const int64_t bes = notrans(p.transB) ? 1 : p.ldb;
+        const int64_t als = notrans(p.transA) ? 1 : p.lda;
+        const int64_t bls = notrans(p.transB) ? p.ldb : 1;
+        if (!has_a && scale_lines_adjacent(als, aes)) P.n_scale_adj += (p.m + 127) / 128;
+        if (!has_b && scale_lines_adjacent(bls, bes)) P.n_scale_adj += (p.n + 127) / 128;
         const int cb = (has_a ? 0 : convert_blocks(p.m, aes, geo.rows_a, geo.ld)) +
                        (has_b ? 0 : convert_blocks(p.n, bes, geo.rows_b, geo.ld));
         const int rb = ((p.m + 31) / 32) * ((p.n + 63) / 64);  // 32 x 64 CRT tiles
@@ -179,7 +184,7 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
     auto* sw = reinterpret_cast<ScaleWork*>(host + P.off_sw);
     auto* cw = reinterpret_cast<ConvertWork*>(host + P.off_cw);
     auto* rw = reinterpret_cast<CrtWork*>(host + P.off_rw);
-    int ns = 0, nc = 0, nr = 0, tile_begin = 0;
+    int ns_adj = 0, ns_con = P.n_scale_adj, nc = 0, nr = 0, tile_begin = 0;
     for (size_t a = 0; a < P.idx.size(); ++a) {
         const ozaki2_problem& p = probs[P.idx[a]];
         const ModTables* T = mod_tables(p.num_moduli);
@@ -249,6 +254,10 @@ int build_grouped_tables(int count, const ozaki2_problem* probs, char* ws, char*
         for (int side = 0; side < 2; ++side) {
             if (side ? eb != nullptr : ea != nullptr) continue;  // encoded: nothing to do
             const int lines = side ? p.n : p.m;
+            // adjacent lines' items first, then contiguous lines' (one kernel each)
+            const bool adj = side ? scale_lines_adjacent(g.b_ls, g.b_es)
+                                  : scale_lines_adjacent(g.a_ls, g.a_es);
+            int& ns = adj ? ns_adj : ns_con;
             for (int l0 = 0; l0 < lines; l0 += 128) sw[ns++] = ScaleWork{(int)a, side, l0};
             const int64_t es = side ? g.b_es : g.a_es;
             const int cb = convert_blocks(lines, es, side ? g.geo.rows_b : g.geo.rows_a, g.geo.ld);
@@ -280,7 +289,8 @@ int launch_grouped(int count, const ozaki2_problem* probs, const char* tables_de
     const auto* dsw = reinterpret_cast<const ScaleWork*>(tables_dev + P.off_sw);
     const auto* dcw = reinterpret_cast<const ConvertWork*>(tables_dev + P.off_cw);
     const auto* drw = reinterpret_cast<const CrtWork*>(tables_dev + P.off_rw);
-    if (launch_scale_grouped(dgp, dsw, P.n_scale, status, stream) != cudaSuccess)
+    if (launch_scale_grouped(dgp, dsw, P.n_scale, status, stream, scaling, P.n_scale_adj) !=
+        cudaSuccess)
         return OZAKI2_ERROR_CUDA;
     if (P.accurate) {
         // the first pass wrote the line exponents; A-bar and B-bar, the auxiliary product's
@@ -430,14 +440,14 @@ void build_encode_tables(int count, const ozaki2_operand* ops, int scaling, char
 }
 
 int launch_encode(int count, const ozaki2_operand* ops, const char* tables_dev, unsigned* status,
-                  cudaStream_t stream) {
+                  cudaStream_t stream, int scaling) {
     EncodePlan E;
     make_encode_plan(count, ops, E);
     if (E.order.empty()) return OZAKI2_SUCCESS;
     const auto* dgp = reinterpret_cast<const GroupProblem*>(tables_dev + E.off_gp);
     const auto* dsw = reinterpret_cast<const ScaleWork*>(tables_dev + E.off_sw);
     const auto* dcw = reinterpret_cast<const ConvertWork*>(tables_dev + E.off_cw);
-    if (launch_scale_grouped(dgp, dsw, E.n_scale, status, stream) != cudaSuccess)
+    if (launch_scale_grouped(dgp, dsw, E.n_scale, status, stream, scaling) != cudaSuccess)
         return OZAKI2_ERROR_CUDA;
     for (size_t g = 0; g < E.conv_n.size(); ++g)
         if (launch_convert_grouped(E.conv_n[g], dgp, dcw + E.conv_begin[g], E.conv_count[g],

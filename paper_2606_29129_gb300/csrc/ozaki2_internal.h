@@ -164,8 +164,19 @@ int launch_residue_gemm_grouped(const GroupGemmProblem* probs, int count, int to
                                 int chunk_k, cudaStream_t stream,
                                 unsigned long long limit_ns = kDefaultWaitLimitNs);
 
+// The memory layout of a line of a grouped problem: element h of line i at X[i ls + h es];
+// lines adjacent (one thread per line) unless es == 1 with ls != 1 (lines contiguous, a warp
+// per 32 lines).
+constexpr int kLayoutAny = 0, kLayoutAdjacent = 1, kLayoutContiguous = 2;
+__host__ __device__ inline bool scale_lines_adjacent(int64_t ls, int64_t es) {
+    return es != 1 || ls == 1;
+}
+// scaling: the mode every problem of the call shares (OZAKI2_SCALING_*).  adjacent_blocks >= 0:
+// the work list holds the items of adjacent lines first (that many), then those of contiguous
+// lines, and each group runs in a kernel of its own; < 0: one kernel decides per item.
 cudaError_t launch_scale_grouped(const GroupProblem* probs, const ScaleWork* work, int blocks,
-                                 unsigned* status, cudaStream_t stream);
+                                 unsigned* status, cudaStream_t stream,
+                                 int scaling = OZAKI2_SCALING_PROPOSED, int adjacent_blocks = -1);
 cudaError_t launch_convert_grouped(int N, const GroupProblem* probs, const ConvertWork* work,
                                    int blocks, const ConvertTables& t, unsigned* status,
                                    cudaStream_t stream, bool accurate = false);
@@ -219,7 +230,7 @@ char* grouped_tables_in_workspace(int count, const ozaki2_problem* probs, char* 
 int encode_table_bytes(int count, const ozaki2_operand* ops);
 void build_encode_tables(int count, const ozaki2_operand* ops, int scaling, char* host);
 int launch_encode(int count, const ozaki2_operand* ops, const char* tables_dev, unsigned* status,
-                  cudaStream_t stream);
+                  cudaStream_t stream, int scaling = OZAKI2_SCALING_PROPOSED);
 
 // Accurate mode (scale.cu, convert.cu, residue_gemm.cu).
 // A-bar plane [rows][ld] (bf16, K contiguous) from the exponent codes of the first pass.

@@ -428,12 +428,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) scale_contiguous_kernel(
                                        tile[warp]);
 }
 
-template <int SCALING>
+// LAYOUT: kLayoutAny decides per work item; kLayoutAdjacent / kLayoutContiguous compile one
+// layout only (the host has sorted the work list by layout), which keeps the other's registers
+// out of the kernel.
+template <int SCALING, int LAYOUT>
 __device__ __forceinline__ void scale_grouped_lines(const GroupProblem& P, const ScaleWork& w,
                                                     const double* X, int64_t ls, int64_t es,
                                                     int lines, int* shifts, unsigned* status,
                                                     double (*tile)[32][kTileLen + 1]) {
-    if (es != 1 || ls == 1) {
+    const bool adjacent = LAYOUT == kLayoutAny ? scale_lines_adjacent(ls, es)
+                                               : LAYOUT == kLayoutAdjacent;
+    if (adjacent) {
         const int i = w.line0 + (int)threadIdx.x;
         if (i < lines)
             scale_adjacent_line<SCALING>(X, es, i, P.k, P.pprime, P.delta, shifts, status);
@@ -630,6 +635,10 @@ __global__ void __launch_bounds__(128) scale_pair_kernel(ScaleSide a, ScaleSide 
 
 // Grouped: each block takes 128 lines of one side of one problem (one thread per line for
 // adjacent lines, one warp per 32 lines for contiguous lines).
+// The scaling mode is a template parameter (every problem of a call shares it), and so is the
+// memory layout of the lines when the host has sorted the work list by layout, so each
+// instantiation carries one mode's and one layout's registers only.
+template <int SCALING, int LAYOUT>
 __global__ void __launch_bounds__(128) scale_grouped_kernel(const GroupProblem* __restrict__ probs,
                                                             const ScaleWork* __restrict__ work,
                                                             unsigned* status) {
@@ -640,32 +649,46 @@ __global__ void __launch_bounds__(128) scale_grouped_kernel(const GroupProblem* 
     const int64_t ls = w.side ? P.b_ls : P.a_ls, es = w.side ? P.b_es : P.a_es;
     const int lines = w.side ? P.n : P.m;
     int* shifts = w.side ? P.f : P.e;
-    if (P.scaling == OZAKI2_SCALING_ACCURATE) {
+    if (SCALING == OZAKI2_SCALING_ACCURATE) {
         // clear this block's entries of the C-bar maxima (they live in the product residues)
         uint32_t* cmax = reinterpret_cast<uint32_t*>(P.res);
         const int i = w.line0 + (int)threadIdx.x;
         if (i < lines) cmax[(w.side ? P.m_pad : 0) + i] = 0u;
     }
-    switch (P.scaling) {
-        case OZAKI2_SCALING_FAST:
-            scale_grouped_lines<OZAKI2_SCALING_FAST>(P, w, X, ls, es, lines, shifts, status, tile);
-            break;
-        case OZAKI2_SCALING_ACCURATE:
-            scale_grouped_lines<OZAKI2_SCALING_ACCURATE>(P, w, X, ls, es, lines, shifts, status,
-                                                         tile);
-            break;
-        default:
-            scale_grouped_lines<OZAKI2_SCALING_PROPOSED>(P, w, X, ls, es, lines, shifts, status,
-                                                         tile);
-    }
+    scale_grouped_lines<SCALING, LAYOUT>(P, w, X, ls, es, lines, shifts, status, tile);
 }
 
 }  // namespace
 
+template <int LAYOUT>
+static void launch_scale_grouped_l(const GroupProblem* probs, const ScaleWork* work, int blocks,
+                                   unsigned* status, cudaStream_t stream, int scaling) {
+    if (scaling == OZAKI2_SCALING_FAST)
+        scale_grouped_kernel<OZAKI2_SCALING_FAST, LAYOUT><<<blocks, 128, 0, stream>>>(probs, work,
+                                                                                     status);
+    else if (scaling == OZAKI2_SCALING_ACCURATE)
+        scale_grouped_kernel<OZAKI2_SCALING_ACCURATE, LAYOUT><<<blocks, 128, 0, stream>>>(
+            probs, work, status);
+    else
+        scale_grouped_kernel<OZAKI2_SCALING_PROPOSED, LAYOUT><<<blocks, 128, 0, stream>>>(
+            probs, work, status);
+}
+
 cudaError_t launch_scale_grouped(const GroupProblem* probs, const ScaleWork* work, int blocks,
-                                 unsigned* status, cudaStream_t stream) {
+                                 unsigned* status, cudaStream_t stream, int scaling,
+                                 int adjacent_blocks) {
     if (blocks <= 0) return cudaSuccess;
-    scale_grouped_kernel<<<blocks, 128, 0, stream>>>(probs, work, status);
+    if (adjacent_blocks < 0) {
+        launch_scale_grouped_l<kLayoutAny>(probs, work, blocks, status, stream, scaling);
+    } else {
+        if (adjacent_blocks > 0)
+            launch_scale_grouped_l<kLayoutAdjacent>(probs, work, adjacent_blocks, status, stream,
+                                                    scaling);
+        if (blocks > adjacent_blocks)
+            launch_scale_grouped_l<kLayoutContiguous>(probs, work + adjacent_blocks,
+                                                      blocks - adjacent_blocks, status, stream,
+                                                      scaling);
+    }
     return cudaGetLastError();
 }
 
