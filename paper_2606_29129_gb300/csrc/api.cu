@@ -274,18 +274,50 @@ bool pipeline_applies(const ozaki2_context* ctx, char transB, int n, const void*
     return host_resident(A) || host_resident(B) || host_resident(C);
 }
 
-// Blocks of `lines` lines: 2 or 4 (4 from 4 kPipeMinBlock lines), multiples of 256 lines.
+// Consecutive blocks of lines: block i is [s[i], s[i + 1]); every boundary but the last is a
+// multiple of 256 lines.
+constexpr int kMaxPipeBlocks = 8;
 struct LineBlocks {
-    int count;
-    int64_t size;
-    int64_t start(int i) const { return i * size; }
-    int64_t lines(int i, int64_t total) const { return std::min<int64_t>(size, total - i * size); }
+    int count = 0;
+    int64_t s[kMaxPipeBlocks + 1] = {};
+    int64_t start(int i) const { return s[i]; }
+    int64_t lines(int i, int64_t) const { return s[i + 1] - s[i]; }
+    void add(int64_t len) { s[count + 1] = s[count] + len; ++count; }
 };
+// `parts` near-equal blocks of the remaining lines, multiples of 256 lines but the last.
+void split_even(LineBlocks& b, int64_t total, int parts) {
+    const int64_t left = total - b.s[b.count];
+    const int64_t size = (left + parts - 1) / parts;
+    const int64_t sz = (size + 255) / 256 * 256;
+    const int first = b.count;
+    while (b.s[b.count] < total) b.add(std::min<int64_t>(sz, total - b.s[b.count]));
+    // no sliver at the end: a last block under 256 lines joins the one before it
+    if (b.count - first >= 2 && b.s[b.count] - b.s[b.count - 1] < 256) {
+        b.s[b.count - 1] = b.s[b.count];
+        --b.count;
+    }
+}
+// Column blocks of B: 2 or 4 (4 from 4 kPipeMinBlock lines).
 LineBlocks line_blocks(int lines) {
-    int cnt = lines / (2 * kPipeMinBlock) >= 2 ? 4 : 2;
-    const int64_t size = ((int64_t)(lines + cnt - 1) / cnt + 255) / 256 * 256;
-    cnt = (int)((lines + size - 1) / size);
-    return {cnt, size};
+    LineBlocks b;
+    split_even(b, lines, lines / (2 * kPipeMinBlock) >= 2 ? 4 : 2);
+    return b;
+}
+// Row blocks of a host-resident op(A): 1024 rows, then twice as many while that stays below a
+// quarter of the rows, then the rest in near-equal blocks of about a quarter.  The pipeline
+// cannot start before the first row block and B's first column block are uploaded, and each
+// later row block is uploaded beside the residue GEMMs of the one before, which take about
+// twice as long per row as its upload: small first blocks growing by two shorten the fill.
+LineBlocks row_blocks(int lines) {
+    LineBlocks b;
+    const int64_t cap = ((int64_t)lines / 4 + 255) / 256 * 256;
+    for (int64_t size = 1024; size < cap && lines - b.s[b.count] > 2 * size; size *= 2)
+        b.add(size);
+    const int64_t left = lines - b.s[b.count];
+    const int parts = (int)std::min<int64_t>(kMaxPipeBlocks - b.count,
+                                             std::max<int64_t>(1, (left + cap - 1) / cap));
+    split_even(b, lines, parts);
+    return b;
 }
 
 // The copy of a band of lines of a column-major operand into a compact device buffer at dst:
@@ -318,8 +350,10 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
     const bool host_a = host_resident(A), host_b = host_resident(B);
     const bool a_adj = is_notrans(transA);  // rows of op(A) adjacent in memory
     const LineBlocks cb = line_blocks(n);
-    const LineBlocks rb = host_a && m >= 2 * kPipeMinBlock ? line_blocks(m) : LineBlocks{1, m};
-    if (cb.count > 4 || rb.count > 4) return OZAKI2_ERROR_CUDA;  // not reached: size >= lines/4
+    LineBlocks rb;
+    if (host_a && m >= 2 * kPipeMinBlock) rb = row_blocks(m);
+    else rb.add(m);
+    if (cb.count > kMaxPipeBlocks || rb.count > kMaxPipeBlocks) return OZAKI2_ERROR_CUDA;
     const int nblk = rb.count + cb.count - 1;  // blocks of C
 
     // block t of C: rows [r0, r0 + h), columns [c0, c0 + cols) of column block j
@@ -335,13 +369,13 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
 
     // device memory: copies of A's row blocks and B's column blocks; B's planes per column block
     // (max(cols, 256) rows each)
-    size_t a_off[4] = {}, b_off[4] = {}, room = 0;
+    size_t a_off[kMaxPipeBlocks] = {}, b_off[kMaxPipeBlocks] = {}, room = 0;
     auto take = [&](size_t bytes) {
         const size_t o = room;
         room += (size_t)round_up((int64_t)bytes, 256);
         return o;
     };
-    Copy2D ab[4] = {}, bb[4] = {};
+    Copy2D ab[kMaxPipeBlocks] = {}, bb[kMaxPipeBlocks] = {};
     for (int i = 0; i < rb.count && host_a; ++i) {
         ab[i] = band_copy(nullptr, A, lda, a_adj, rb.start(i), rb.lines(i, m), k, esz);
         a_off[i] = take(ab[i].dpitch * ab[i].height);
@@ -363,8 +397,8 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
     double* part = reinterpret_cast<double*>(ws + L.off_part);
     const float pp = ctx->scaling == OZAKI2_SCALING_FAST ? T->pprime_fast : T->pprime;
     const int64_t pa_row = (int64_t)2 * L.geo.ld;  // bytes per row of a plane
-    char* pbj[4];
-    int rows_b[4];
+    char* pbj[kMaxPipeBlocks];
+    int rows_b[kMaxPipeBlocks];
     {
         char* p = ws + L.off_pb;
         for (int j = 0; j < cb.count; ++j) {

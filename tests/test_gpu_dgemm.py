@@ -325,6 +325,8 @@ def test_host_operands_unaligned_transposed(oz, orc, trans, own_workspace):
     (4200, 4500, 200, "N", True, False, True, "proposed", "f32", 0.0),
     (4200, 4500, 200, "T", True, True, False, "proposed", "f64", -0.5),
     (4200, 4500, 130, "N", True, True, True, "proposed", "f64", 1.5),
+    # row blocks growing from 1024 (1024, 2048, then near-equal quarters, the last ragged)
+    (12345, 4500, 190, "N", True, True, True, "proposed", "f64", 0.0),
 ])
 def test_host_operands_pipelined_over_column_blocks(oz, orc, case):
     """n >= 4096 with host-resident operands: the call pipelines the column blocks of op(B) and,
