@@ -89,6 +89,13 @@ extern "C" {
                                      (default) = 32 for OZAKI2_GEMM_SINGLE and 4 for
                                      OZAKI2_GEMM_PAIR (fastest measured on GB300), else 1..1024.
                                      Results do not depend on it. */
+#define OZAKI2_OPT_L2_HINTS 7     /* L2 eviction priority of the single-problem residue GEMM's
+                                     tile loads: bits 0-1 for the A tiles, bits 2-3 for the B
+                                     tiles, each 0 (the default policy), 1 (evict last) or 2
+                                     (evict first).  Default 1: the A tiles, reused by the waves
+                                     of tiles that sweep the n-tiles of a raster group, evict
+                                     last (measured 2% faster at 16384^3 on GB300).  Results do
+                                     not depend on it. */
 #define OZAKI2_SCALING_PROPOSED 0 /* Algorithm 2 (Section 4): scale-invariant, CRT bound by
                                      construction */
 #define OZAKI2_SCALING_FAST 1     /* Algorithm 1 (Section 2.3): the original fast mode, kept for

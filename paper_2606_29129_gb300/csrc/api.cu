@@ -21,6 +21,7 @@ struct ozaki2_context {
     int chunk_k = 960;             // products accumulated between modular reductions
     int gemm_variant = OZAKI2_GEMM_AUTO;
     int group_m = 0;               // m-tiles per group of the residue-GEMM tile order (0: 16)
+    int l2_hints = 1;              // OZAKI2_OPT_L2_HINTS (A tiles evict last: measured faster)
     int scaling = OZAKI2_SCALING_PROPOSED;  // Algorithm 2, or Algorithm 1 (original fast mode)
     unsigned long long wait_limit_ns = ozaki2::kDefaultWaitLimitNs;  // residue-GEMM wait bound
     ozaki2::TileRules tiles;       // grouped calls: tile width and K chunk by size class
@@ -471,7 +472,7 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
                                       geo, pa + b.r0 * pa_row, pbj[b.j], out, T->epi,
                                       ctx->d_status, ctx->num_sms, ctx->chunk_k,
                                       ctx->gemm_variant, S, ctx->wait_limit_ns, L.n_pad,
-                                      L.m_pad * L.n_pad, ctx->group_m)))
+                                      L.m_pad * L.n_pad, ctx->group_m, ctx->l2_hints)))
             return rc;
         // beside the GEMMs: the next block's operand block in
         const Copy2D* next = nullptr;
@@ -585,7 +586,7 @@ int dgemm_impl(ozaki2_context* ctx, int argbase, char transA, char transB, int m
     if ((rc = launch_residue_gemm(N, (int)L.m_pad, (int)L.n_pad, (int)L.k_pad, L.geo, pa, pb, res,
                                   T->epi, ctx->d_status, ctx->num_sms, ctx->chunk_k,
                                   ctx->gemm_variant, st, ctx->wait_limit_ns, 0, 0,
-                                  ctx->group_m)))
+                                  ctx->group_m, ctx->l2_hints)))
         return rc;
     mark(3);
     rc = cuda_rc(launch_crt(res, L.n_pad, L.m_pad * L.n_pad, m, n, e, f, alpha, beta, C, ldc, *T,
@@ -669,6 +670,10 @@ int ozaki2_set_option(ozaki2_handle_t handle, int option, int value) {
         case OZAKI2_OPT_WAIT_LIMIT_NS:
             if (value < 0) return -3;
             ctx->wait_limit_ns = (unsigned long long)value;
+            return OZAKI2_SUCCESS;
+        case OZAKI2_OPT_L2_HINTS:
+            if (value < 0 || value > 15 || (value & 3) == 3 || (value >> 2) == 3) return -3;
+            ctx->l2_hints = value;
             return OZAKI2_SUCCESS;
         case OZAKI2_OPT_GROUP_M:
             if (value < 0 || value > 1024) return -3;

@@ -330,7 +330,7 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
                         const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
                         int variant, cudaStream_t stream,
                         unsigned long long limit_ns = kDefaultWaitLimitNs, int64_t out_ld = 0,
-                        int64_t out_plane = 0, int group_m = 0);
+                        int64_t out_plane = 0, int group_m = 0, int l2_hints = 0);
 
 // f32: C holds floats (SGEMM: C'' rounded to 24 bits, alpha and beta applied in single
 // precision), else doubles.  padded: the residue buffer extends to whole 32 x 32 tiles in every

@@ -63,6 +63,7 @@ static_assert(idesc_for(BN) == IDESC, "instruction descriptor");
 struct GemmArgs {
     int tiles_m, tiles_n, total_tiles, k_blocks, chunk_blocks, nchunks;
     int group_m;  // m-tiles per group of the tile order
+    int l2_hints;  // OZAKI2_L2_*: eviction priorities of the A and B tile loads in L2
     int m_rows;  // rows of the A planes / product residues (m_pad)
     int m_live, n_live;  // product residues stored: rows below m_live, columns below n_live
     int8_t* out;
@@ -73,6 +74,25 @@ struct GemmArgs {
 };
 
 // ---------------------------------------------------------------- PTX wrappers (GEMM only)
+// L2 eviction policies for the tile loads (createpolicy): 0 keeps the default.
+__device__ __forceinline__ uint64_t l2_policy(int kind) {
+    uint64_t p = 0;
+    if (kind == 1)
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else if (kind == 2)
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// A tile load with an L2 eviction policy (policy 0: none).
+__device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                                 int x, int y, int z, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)),
+        "l"(policy)
+        : "memory");
+}
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y, int z) {
     asm volatile(
@@ -381,6 +401,8 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
         // ------------------------------------------------------------ TMA producer
         int stage = 0;
         uint32_t phase = 0;
+        // eviction priorities: A policy in bits 0-1, B policy in bits 2-3 of l2_hints
+        const uint64_t pol_a = l2_policy(args.l2_hints & 3), pol_b = l2_policy(args.l2_hints >> 2);
         uint32_t armed_parity[STAGES];
         bool armed[STAGES];
         for (int s = 0; s < STAGES; ++s) armed[s] = false, armed_parity[s] = 0;
@@ -407,10 +429,17 @@ __device__ __forceinline__ void residue_gemm_body(Src src, int total_tiles,
                             break;
                         }
                         mbar_arrive_expect_tx(&full[stage], A_BYTES + ti[s].bn * (BK * 2));
-                        tma_load_3d(sA + stage * A_BYTES, ti[s].ta, &full[stage], kb * BK,
-                                    ti[s].mt * BM, ti[s].l);
-                        tma_load_3d(sB + stage * B_BYTES, ti[s].tb, &full[stage], kb * BK,
-                                    ti[s].nt * ti[s].bn, ti[s].l);
+                        if (pol_a | pol_b) {
+                            tma_load_3d_hint(sA + stage * A_BYTES, ti[s].ta, &full[stage],
+                                             kb * BK, ti[s].mt * BM, ti[s].l, pol_a);
+                            tma_load_3d_hint(sB + stage * B_BYTES, ti[s].tb, &full[stage],
+                                             kb * BK, ti[s].nt * ti[s].bn, ti[s].l, pol_b);
+                        } else {
+                            tma_load_3d(sA + stage * A_BYTES, ti[s].ta, &full[stage], kb * BK,
+                                        ti[s].mt * BM, ti[s].l);
+                            tma_load_3d(sB + stage * B_BYTES, ti[s].tb, &full[stage], kb * BK,
+                                        ti[s].nt * ti[s].bn, ti[s].l);
+                        }
                         armed[stage] = true;
                         armed_parity[stage] = phase;
                         if (++stage == STAGES) {
@@ -1063,11 +1092,12 @@ int launch_residue_gemm(int num_moduli, int m_pad, int n_pad, int k_pad, const P
                         const void* planes_a, const void* planes_b, int8_t* out,
                         const EpilogueTables& t, unsigned* status, int num_sms, int chunk_k,
                         int variant, cudaStream_t stream, unsigned long long limit_ns,
-                        int64_t out_ld, int64_t out_plane, int group_m) {
+                        int64_t out_ld, int64_t out_plane, int group_m, int l2_hints) {
     if (m_pad == 0 || n_pad == 0) return OZAKI2_SUCCESS;
     if (out_ld <= 0) out_ld = n_pad;
     if (out_plane <= 0) out_plane = (int64_t)m_pad * out_ld;
-    GemmArgs a;
+    GemmArgs a = {};
+    a.l2_hints = l2_hints;
     a.k_blocks = k_pad / BK;
     const int cb = chunk_blocks_of(chunk_k, a.k_blocks);
     a.chunk_blocks = cb;
