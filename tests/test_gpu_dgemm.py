@@ -80,6 +80,23 @@ def test_gemm_variants_and_chunks(oz, orc, variant, chunk):
     assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 16))
 
 
+@pytest.mark.parametrize("hints", [0, 1, 2, 4, 8, 1 | (2 << 2)])
+def test_l2_hints_change_nothing(oz, orc, hints):
+    """The L2 eviction policies of the residue GEMM's tile loads change the timing only."""
+    m, n, k = 260, 530, 1100
+    A, B = make(m, n, k, 1.0, 67)
+    h = oz.Handle()
+    h.set_option(oz.OPT_L2_HINTS, hints)
+    C = _gpu.dgemm(oz, A, B, m, n, k, 15, handle=h, variant=1)
+    assert _gpu.same_bits(C, orc.dgemm(A, B, m, n, k, 15))
+
+
+def test_l2_hints_option_checks(oz):
+    h = oz.Handle()
+    for bad in (-1, 3, 12, 16):
+        assert oz.lib().ozaki2_set_option(h.h, oz.OPT_L2_HINTS, bad) == -3
+
+
 @pytest.mark.parametrize("N", list(range(2, 21)))
 @pytest.mark.parametrize("phi", [0.5, 4.0])
 def test_moduli_counts(oz, orc, N, phi):
