@@ -512,10 +512,10 @@ def accuracy_and_baselines(args, A, B, C, m, n, k, N, torch, np):
 
 def measure_e2e(args, oz, h, A, B, m, n, k, N, torch, gemm=None):
     """The same metric through the public API with host buffers: each step passes page-locked
-    host A, B and C to the call, which copies A and B into device memory with a kernel (the
-    link's rate, where a copy-engine upload measured erratic on this part after kernels had
-    touched host memory) and whose reconstruction kernel writes C straight into the host buffer.
-    Every byte in and out crosses the host link inside the timed region."""
+    host A, B and C to the call, which by default copies A and B into device memory with a
+    kernel and whose reconstruction kernel writes C straight into the host buffer
+    (--host-copies 1: copy engines both ways, whose rate measured erratic on this part).  Every
+    byte in and out crosses the host link inside the timed region."""
     gemm = gemm or oz.ozaki2_dgemm
     A_h = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
     B_h = torch.empty(B.shape, dtype=B.dtype, pin_memory=True)
@@ -529,21 +529,32 @@ def measure_e2e(args, oz, h, A, B, m, n, k, N, torch, gemm=None):
         if rc:
             raise oz.Ozaki2Error(gemm.__name__, rc)
 
+    if args.host_copies is not None:
+        h.set_option(oz.OPT_HOST_COPIES, args.host_copies)
     step()
     step()
     torch.cuda.synchronize()
     reps = max(4, min(args.steps, 10))
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
     t0 = time.perf_counter()
-    for _ in range(reps):
+    ev[0].record(stream)
+    for i in range(reps):
         step()
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / reps
     h.set_timing(True)
+    copies = args.host_copies if args.host_copies is not None else 0
+    path = ("host A, B, C (page-locked) passed to the call: inputs staged into HBM by a kernel, "
+            "the result written into host memory by the reconstruction" if copies == 0 else
+            "host A, B, C (page-locked) passed to the call: inputs uploaded by a copy engine, "
+            "the result reconstructed in HBM and downloaded by a copy engine")
     return {"value": 2.0 * m * n * k / (ms * 1e-3) / 1e12, "unit": "TFLOPS",
             "h2d_bytes_per_step": (A.numel() + B.numel()) * A.element_size(),
             "d2h_bytes_per_step": m * n * A.element_size(), "ms_per_step": ms, "steps": reps,
-            "path": "host A, B, C (page-locked) passed to the call: inputs staged into HBM by a "
-                    "kernel, the result written into host memory by the reconstruction",
+            "step_ms": [ev[i].elapsed_time(ev[i + 1]) for i in range(reps)],
+            "host_copies": copies, "path": path,
             "clock": "host wall clock around the steps, synchronised on both sides"}
 
 
@@ -1041,6 +1052,9 @@ def main():
     ap.add_argument("--gemm-traffic", type=float, default=None,
                     help="DRAM bytes per residue-GEMM launch from an ncu capture, if current")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-copies", type=int, choices=[0, 1], default=None,
+                    help="e2e leg: how the call moves host data (OZAKI2_OPT_HOST_COPIES: 0 "
+                         "kernels, the default; 1 copy engines)")
     ap.add_argument("--profile-step", action="store_true",
                     help="only the timed steps (no cuBLAS, accuracy, CPU or e2e legs): for "
                          "launch lists under a profiler")

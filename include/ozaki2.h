@@ -96,6 +96,19 @@ extern "C" {
                                      of tiles that sweep the n-tiles of a raster group, evict
                                      last (measured 2% faster at 16384^3 on GB300).  Results do
                                      not depend on it. */
+#define OZAKI2_OPT_HOST_COPIES 8  /* how ozaki2_dgemm / ozaki2_sgemm move host-resident
+                                     operands when the call pipelines over blocks of C (host
+                                     operands, n >= 4096, op(B) = B): 0 (default) = kernels:
+                                     each next operand block is uploaded by a copy kernel beside
+                                     the residue GEMMs, and the reconstruction writes host C
+                                     directly; 1 = copy engines (when every host operand is
+                                     page-locked; else as 0): the uploads run on a copy stream
+                                     from the start, and C's blocks are reconstructed in device
+                                     memory and downloaded while the next blocks compute.  On
+                                     GB300 at 16384^3, 1 finished some calls in 88 ms against a
+                                     steady 100 ms for 0, but its copy engines' rate is erratic
+                                     (other calls took 115-270 ms).  Results do not depend on
+                                     it. */
 #define OZAKI2_SCALING_PROPOSED 0 /* Algorithm 2 (Section 4): scale-invariant, CRT bound by
                                      construction */
 #define OZAKI2_SCALING_FAST 1     /* Algorithm 1 (Section 2.3): the original fast mode, kept for

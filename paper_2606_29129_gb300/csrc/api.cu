@@ -22,6 +22,7 @@ struct ozaki2_context {
     int gemm_variant = OZAKI2_GEMM_AUTO;
     int group_m = 0;               // m-tiles per group of the residue-GEMM tile order (0: 16)
     int l2_hints = 1;              // OZAKI2_OPT_L2_HINTS (A tiles evict last: measured faster)
+    int host_copies = 0;           // OZAKI2_OPT_HOST_COPIES (kernels: measured steadier)
     int scaling = OZAKI2_SCALING_PROPOSED;  // Algorithm 2, or Algorithm 1 (original fast mode)
     unsigned long long wait_limit_ns = ozaki2::kDefaultWaitLimitNs;  // residue-GEMM wait bound
     ozaki2::TileRules tiles;       // grouped calls: tile width and K chunk by size class
@@ -45,6 +46,13 @@ struct ozaki2_context {
     bool pageable_access = false;  // the device can address ordinary (pageable) host memory
     void* in_ws = nullptr;         // device copies of host-resident A and B (ozaki2_dgemm)
     size_t in_ws_bytes = 0;
+    void* out_ws = nullptr;        // device copies of host C's blocks (pipelined ozaki2_dgemm)
+    size_t out_ws_bytes = 0;
+    // copy-engine transfers of a pipelined ozaki2_dgemm: uploads on up_stream, downloads on
+    // down_stream, ordered against the handle's stream by events
+    cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    static constexpr int kCopyEvents = 40;
+    cudaEvent_t copy_ev[kCopyEvents] = {};
     // pinned staging of the tables of ozaki2_encode_operands: a ring, so that a call waits only
     // for the copy made kEncodeRing calls earlier
     static constexpr int kEncodeRing = 4;
@@ -114,6 +122,16 @@ bool addressable(const ozaki2_context* ctx, const void* p) {
         return ctx->pageable_access;
     }
     return a.type != cudaMemoryTypeUnregistered || ctx->pageable_access;
+}
+
+// True if p is page-locked host memory (allocated so, or registered).
+bool page_locked(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
 }
 
 // True if p is host memory (page-locked, or pageable on a coherent link) rather than device or
@@ -247,6 +265,40 @@ int ensure_input_stage(ozaki2_context* ctx, size_t bytes) {
     return OZAKI2_SUCCESS;
 }
 
+// The streams and events of copy-engine transfers.
+int ensure_copy_streams(ozaki2_context* ctx) {
+    if (ctx->up_stream) return OZAKI2_SUCCESS;
+    for (cudaEvent_t& e : ctx->copy_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            e = nullptr;
+            return OZAKI2_ERROR_CUDA;
+        }
+    if (cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
+        ctx->down_stream = ctx->up_stream = nullptr;
+        return OZAKI2_ERROR_CUDA;
+    }
+    return OZAKI2_SUCCESS;
+}
+
+// The device buffers of C's blocks, `bytes` in all.
+int ensure_output_stage(ozaki2_context* ctx, size_t bytes) {
+    if (ctx->out_ws_bytes >= bytes) return OZAKI2_SUCCESS;
+    if (ctx->out_ws) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return OZAKI2_ERROR_CUDA;
+        cudaFree(ctx->out_ws);
+        ctx->out_ws = nullptr;
+        ctx->out_ws_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->out_ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return OZAKI2_ERROR_ALLOC;
+    }
+    ctx->out_ws_bytes = bytes;
+    return OZAKI2_SUCCESS;
+}
+
 // Host-resident operands, pipelined (proposed or fast scaling, no caller workspace, op(B) = B so
 // that its columns are contiguous, n of at least two blocks).  Under these scalings a line's
 // shift depends on that line alone (eqs. (proposed-mu), (proposed-nu)), so rows of op(A) and
@@ -257,14 +309,18 @@ int ensure_input_stage(ozaki2_context* ctx, size_t bytes) {
 // operand block, its residue GEMMs, a copy launched to overlap them that uploads the next
 // block's operand block (programmatic dependent launch: the GEMM lets it start once all its
 // CTAs are resident, and it takes the room they leave on each SM), then the reconstruction,
-// which writes a host-resident C over the link.  The first block's operand blocks are uploaded
-// before it at the link's full rate.  Every step computes what the unblocked path computes, so
-// the result is the same bits.
+// which writes C's block.  The first block's operand blocks are uploaded before it at the link's
+// full rate.  Every step computes what the unblocked path computes, so the result is the same
+// bits.
 //
-// Downloads do not overlap the same way: on GB300, device-to-host traffic beside the residue
-// GEMM measured no faster than after it (by a copy kernel or a copy engine; a copy kernel beside
-// a compute-only kernel of the same footprint keeps the link's full ~193 GB/s), so C's blocks
-// are reconstructed straight into host memory.
+// Copy engines instead (OZAKI2_OPT_HOST_COPIES = 1, every host operand page-locked): all host
+// operand blocks are queued for upload on one copy stream at the start, each awaited by the
+// handle's stream where it is first needed; with a host C every block of C is reconstructed
+// into a device buffer of its own (uploaded first when beta != 0) and downloaded on a second
+// copy stream while the next blocks compute, the last block made small.  No kernel then touches
+// host memory.  On GB300 this hides nearly all of the link's traffic when the copy engines run
+// at their usual rate, but their rate is erratic (a call now and then takes several times as
+// long), so kernels are the default.
 constexpr int kPipeMinBlock = 2048;
 
 bool pipeline_applies(const ozaki2_context* ctx, char transB, int n, const void* A,
@@ -298,10 +354,19 @@ void split_even(LineBlocks& b, int64_t total, int parts) {
         --b.count;
     }
 }
-// Column blocks of B: 2 or 4 (4 from 4 kPipeMinBlock lines).
-LineBlocks line_blocks(int lines) {
+// Column blocks of B: 2 or 4 (4 from 4 kPipeMinBlock lines).  small_tail: the same over all but
+// a last block of about lines / 16 (256 to 1024 lines, and what rounding the others to multiples
+// of 256 leaves).
+LineBlocks line_blocks(int lines, bool small_tail) {
     LineBlocks b;
-    split_even(b, lines, lines / (2 * kPipeMinBlock) >= 2 ? 4 : 2);
+    int64_t body = lines;
+    if (small_tail) {
+        const int64_t want = ((int64_t)lines / 16 + 255) / 256 * 256;
+        const int64_t tail = std::min<int64_t>(1024, std::max<int64_t>(256, want));
+        body = (lines - tail) / 256 * 256;
+    }
+    split_even(b, body, body / (2 * kPipeMinBlock) >= 2 ? 4 : 2);
+    if (body < lines) b.add(lines - body);
     return b;
 }
 // Row blocks of a host-resident op(A): 1024 rows, then twice as many while that stays below a
@@ -350,7 +415,12 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
     const size_t esz = f32 ? 4 : 8;
     const bool host_a = host_resident(A), host_b = host_resident(B);
     const bool a_adj = is_notrans(transA);  // rows of op(A) adjacent in memory
-    const LineBlocks cb = line_blocks(n);
+    const bool host_c = host_resident(C);
+    // copy engines move the host data when every host operand is page-locked
+    const bool ce = ctx->host_copies == 1 && (!host_a || page_locked(A)) &&
+                    (!host_b || page_locked(B)) && (!host_c || page_locked(C));
+    const bool stage_c = ce && host_c;  // C's blocks reconstructed in device memory
+    const LineBlocks cb = line_blocks(n, stage_c);
     LineBlocks rb;
     if (host_a && m >= 2 * kPipeMinBlock) rb = row_blocks(m);
     else rb.add(m);
@@ -387,6 +457,15 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
     }
     if (room && (rc = ensure_input_stage(ctx, room))) return rc;
     char* stage = static_cast<char*>(ctx->in_ws);
+    // a device buffer for each block of C, so that no reconstruction waits for a download
+    size_t c_off[2 * kMaxPipeBlocks] = {}, c_room = 0;
+    for (int t = 0; stage_c && t < nblk; ++t) {
+        const Blk b = blk(t);
+        c_off[t] = c_room;
+        c_room += (size_t)round_up(b.h * b.cols * (int64_t)esz, 256);
+    }
+    if (stage_c && (rc = ensure_output_stage(ctx, c_room))) return rc;
+    if (ce && (rc = ensure_copy_streams(ctx))) return rc;
     for (int i = 0; i < rb.count && host_a; ++i) ab[i].dst = stage + a_off[i];
     for (int j = 0; j < cb.count && host_b; ++j) bb[j].dst = stage + b_off[j];
 
@@ -450,16 +529,72 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
         return OZAKI2_SUCCESS;
     };
 
-    // the first block's operand blocks at the link's full rate
-    {
+    // block t of C in host memory, and its device buffer (stage_c)
+    auto c_host = [&](const Blk& b) {
+        return static_cast<char*>(C) + ((size_t)b.c0 * ldc + (size_t)b.r0) * esz;
+    };
+    auto c_copy = [&](int t, bool down) {
+        const Blk b = blk(t);
+        char* h = c_host(b);
+        char* d = static_cast<char*>(ctx->out_ws) + c_off[t];
+        const size_t hp = (size_t)ldc * esz, dp = (size_t)b.h * esz;
+        return down ? Copy2D{h, d, hp, dp, dp, (size_t)b.cols}
+                    : Copy2D{d, h, dp, hp, dp, (size_t)b.cols};
+    };
+
+    // copy engines: every upload queued now, after the work already on the handle's stream
+    // (which may still read the staging buffers); events 0-3 order the streams, 4.. the uploads
+    cudaEvent_t* ev = ctx->copy_ev;
+    int up_ev[2 * kMaxPipeBlocks][3];  // per block: operand uploads and C's, -1 for none
+    for (auto& u : up_ev) u[0] = u[1] = u[2] = -1;
+    // on every return, the handle's stream waits for both copy streams
+    struct JoinCopies {
+        ozaki2_context* ctx;
+        bool armed = false;
+        ~JoinCopies() {
+            if (!armed) return;
+            if (cudaEventRecord(ctx->copy_ev[1], ctx->down_stream) == cudaSuccess)
+                cudaStreamWaitEvent(ctx->stream, ctx->copy_ev[1], 0);
+            if (cudaEventRecord(ctx->copy_ev[2], ctx->up_stream) == cudaSuccess)
+                cudaStreamWaitEvent(ctx->stream, ctx->copy_ev[2], 0);
+        }
+    } join{ctx};
+    if (ce) {
+        if (cudaEventRecord(ev[0], S) != cudaSuccess ||
+            cudaStreamWaitEvent(ctx->up_stream, ev[0], 0) != cudaSuccess ||
+            cudaStreamWaitEvent(ctx->down_stream, ev[0], 0) != cudaSuccess)
+            return OZAKI2_ERROR_CUDA;
+        join.armed = true;
+        int u = 4;
+        auto up = [&](const Copy2D& c) -> int {
+            if (u >= ozaki2_context::kCopyEvents ||
+                cudaMemcpy2DAsync(c.dst, c.dpitch, c.src, c.spitch, c.width, c.height,
+                                  cudaMemcpyHostToDevice, ctx->up_stream) != cudaSuccess ||
+                cudaEventRecord(ev[u], ctx->up_stream) != cudaSuccess)
+                return -1;
+            return u++;
+        };
+        for (int t = 0; t < nblk; ++t) {
+            if (t < rb.count && host_a && (up_ev[t][0] = up(ab[t])) < 0) return OZAKI2_ERROR_CUDA;
+            if ((t == 0 || t >= rb.count) && host_b && (up_ev[t][1] = up(bb[blk(t).j])) < 0)
+                return OZAKI2_ERROR_CUDA;
+            if (stage_c && beta != 0.0 && (up_ev[t][2] = up(c_copy(t, false))) < 0)
+                return OZAKI2_ERROR_CUDA;
+        }
+    } else {
+        // the first block's operand blocks at the link's full rate
         Copy2D first[2];
         int nf = 0;
         if (host_a) first[nf++] = ab[0];
         if (host_b) first[nf++] = bb[0];
         if ((rc = cuda_rc(launch_copies_2d(first, nf, 4 * ctx->num_sms, false, S)))) return rc;
     }
+    auto await = [&](int u) {
+        return u < 0 || cudaStreamWaitEvent(S, ev[u], 0) == cudaSuccess;
+    };
     for (int t = 0; t < nblk; ++t) {
         const Blk b = blk(t);
+        if (!await(up_ev[t][0]) || !await(up_ev[t][1])) return OZAKI2_ERROR_CUDA;
         if (t == 0 && ((rc = prep_a(0)) || (rc = prep_b(0)))) return rc;
         if (t > 0 && (rc = t < rb.count ? prep_a(t) : prep_b(b.j))) return rc;
         const bool last_row = b.r0 + b.h >= m;
@@ -474,16 +609,29 @@ int dgemm_pipelined(ozaki2_context* ctx, char transA, int m, int n, int k, doubl
                                       ctx->gemm_variant, S, ctx->wait_limit_ns, L.n_pad,
                                       L.m_pad * L.n_pad, ctx->group_m, ctx->l2_hints)))
             return rc;
-        // beside the GEMMs: the next block's operand block in
-        const Copy2D* next = nullptr;
-        if (t + 1 < rb.count && host_a) next = &ab[t + 1];
-        if (t + 1 >= rb.count && t + 1 < nblk && host_b) next = &bb[blk(t + 1).j];
-        if (next && (rc = cuda_rc(launch_copies_2d(next, 1, ctx->num_sms, true, S)))) return rc;
-        char* Cb = static_cast<char*>(C) + ((size_t)b.c0 * ldc + (size_t)b.r0) * esz;
+        if (!ce) {
+            // beside the GEMMs: the next block's operand block in
+            const Copy2D* next = nullptr;
+            if (t + 1 < rb.count && host_a) next = &ab[t + 1];
+            if (t + 1 >= rb.count && t + 1 < nblk && host_b) next = &bb[blk(t + 1).j];
+            if (next && (rc = cuda_rc(launch_copies_2d(next, 1, ctx->num_sms, true, S))))
+                return rc;
+        }
+        char* Cd = stage_c ? static_cast<char*>(ctx->out_ws) + c_off[t] : c_host(b);
+        const int64_t ldd = stage_c ? b.h : ldc;
+        if (!await(up_ev[t][2])) return OZAKI2_ERROR_CUDA;
         if ((rc = cuda_rc(launch_crt(out, L.n_pad, L.m_pad * L.n_pad, (int)b.h, (int)b.cols,
-                                     e + b.r0, f + b.c0, alpha, beta, Cb, ldc, *T,
+                                     e + b.r0, f + b.c0, alpha, beta, Cd, ldd, *T,
                                      ctx->d_status, S, f32, true))))
             return rc;
+        if (stage_c) {
+            const Copy2D c = c_copy(t, true);
+            if (cudaEventRecord(ev[3], S) != cudaSuccess ||
+                cudaStreamWaitEvent(ctx->down_stream, ev[3], 0) != cudaSuccess ||
+                cudaMemcpy2DAsync(c.dst, c.dpitch, c.src, c.spitch, c.width, c.height,
+                                  cudaMemcpyDeviceToHost, ctx->down_stream) != cudaSuccess)
+                return OZAKI2_ERROR_CUDA;
+        }
     }
     return OZAKI2_SUCCESS;
 }
@@ -619,6 +767,14 @@ int ozaki2_destroy(ozaki2_handle_t handle) {
     cudaStreamSynchronize(handle->stream);
     if (handle->ws && !handle->user_ws) cudaFree(handle->ws);
     if (handle->in_ws) cudaFree(handle->in_ws);
+    if (handle->out_ws) cudaFree(handle->out_ws);
+    for (cudaStream_t st : {handle->up_stream, handle->down_stream})
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
+    for (cudaEvent_t e : handle->copy_ev)
+        if (e) cudaEventDestroy(e);
     if (handle->d_status) cudaFree(handle->d_status);
     for (auto& e : handle->ev)
         if (e) cudaEventDestroy(e);
@@ -674,6 +830,10 @@ int ozaki2_set_option(ozaki2_handle_t handle, int option, int value) {
         case OZAKI2_OPT_L2_HINTS:
             if (value < 0 || value > 15 || (value & 3) == 3 || (value >> 2) == 3) return -3;
             ctx->l2_hints = value;
+            return OZAKI2_SUCCESS;
+        case OZAKI2_OPT_HOST_COPIES:
+            if (value != 0 && value != 1) return -3;
+            ctx->host_copies = value;
             return OZAKI2_SUCCESS;
         case OZAKI2_OPT_GROUP_M:
             if (value < 0 || value > 1024) return -3;

@@ -34,6 +34,7 @@ OPT_SCALING = 4
 OPT_WAIT_LIMIT_NS = 5
 OPT_GROUP_M = 6
 OPT_L2_HINTS = 7
+OPT_HOST_COPIES = 8
 SCALING_PROPOSED, SCALING_FAST, SCALING_ACCURATE = 0, 1, 2
 GEMM_AUTO, GEMM_SINGLE, GEMM_PAIR = 0, 1, 2
 NOALLOC_SCRATCH_BYTES = 8 << 20

@@ -95,6 +95,8 @@ def test_l2_hints_option_checks(oz):
     h = oz.Handle()
     for bad in (-1, 3, 12, 16):
         assert oz.lib().ozaki2_set_option(h.h, oz.OPT_L2_HINTS, bad) == -3
+    for bad in (-1, 2):
+        assert oz.lib().ozaki2_set_option(h.h, oz.OPT_HOST_COPIES, bad) == -3
 
 
 @pytest.mark.parametrize("N", list(range(2, 21)))
@@ -345,12 +347,15 @@ def test_host_operands_unaligned_transposed(oz, orc, trans, own_workspace):
     # row blocks growing from 1024 (1024, 2048, then near-equal quarters, the last ragged)
     (12345, 4500, 190, "N", True, True, True, "proposed", "f64", 0.0),
 ])
-def test_host_operands_pipelined_over_column_blocks(oz, orc, case):
+@pytest.mark.parametrize("copies", [0, 1])
+def test_host_operands_pipelined_over_column_blocks(oz, orc, case, copies):
     """n >= 4096 with host-resident operands: the call pipelines the column blocks of op(B) and,
     within the first, the row blocks of a host-resident op(A) with m >= 4096 (each later operand
     block uploaded by a copy that overlaps the previous block's residue GEMMs; a host-resident C
-    written block by block by the reconstruction).  C is bit-identical to the call on device
-    memory, and to the oracle on a sample that takes rows and columns from every block."""
+    written block by block by the reconstruction), or with copy engines (copies = 1: uploads
+    queued on a copy stream, C's blocks reconstructed in device memory and downloaded on
+    another).  C is bit-identical to the call on device memory, and to the oracle on a sample
+    that takes rows and columns from every block."""
     import torch
 
     m, n, k, tA, ha, hb, hc, scaling, dtype, beta = case[:10]
@@ -368,6 +373,7 @@ def test_host_operands_pipelined_over_column_blocks(oz, orc, case):
     gemm = oz.ozaki2_sgemm if f32 else oz.ozaki2_dgemm
     h = oz.Handle()
     h.set_option(oz.OPT_SCALING, oz.SCALING_FAST if scaling == "fast" else oz.SCALING_PROPOSED)
+    h.set_option(oz.OPT_HOST_COPIES, copies)
 
     def dev_or_host(x, host):
         t = torch.from_numpy(np.ascontiguousarray(x))
