@@ -268,18 +268,29 @@ int ensure_input_stage(ozaki2_context* ctx, size_t bytes) {
 // The streams and events of copy-engine transfers.
 int ensure_copy_streams(ozaki2_context* ctx) {
     if (ctx->up_stream) return OZAKI2_SUCCESS;
-    for (cudaEvent_t& e : ctx->copy_ev)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            e = nullptr;
-            return OZAKI2_ERROR_CUDA;
+    bool ok = true;
+    for (cudaStream_t* st : {&ctx->down_stream, &ctx->up_stream})
+        if (ok && cudaStreamCreateWithFlags(st, cudaStreamNonBlocking) != cudaSuccess) {
+            *st = nullptr;
+            ok = false;
         }
-    if (cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
-        ctx->down_stream = ctx->up_stream = nullptr;
-        return OZAKI2_ERROR_CUDA;
+    for (cudaEvent_t& e : ctx->copy_ev)
+        if (ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            e = nullptr;
+            ok = false;
+        }
+    if (ok) return OZAKI2_SUCCESS;
+    // all or nothing: the next call starts again from scratch
+    cudaGetLastError();
+    for (cudaStream_t* st : {&ctx->down_stream, &ctx->up_stream}) {
+        if (*st) cudaStreamDestroy(*st);
+        *st = nullptr;
     }
-    return OZAKI2_SUCCESS;
+    for (cudaEvent_t& e : ctx->copy_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    return OZAKI2_ERROR_CUDA;
 }
 
 // The device buffers of C's blocks, `bytes` in all.
