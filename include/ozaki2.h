@@ -89,13 +89,15 @@ extern "C" {
                                      (default) = 32 for OZAKI2_GEMM_SINGLE and 4 for
                                      OZAKI2_GEMM_PAIR (fastest measured on GB300), else 1..1024.
                                      Results do not depend on it. */
-#define OZAKI2_OPT_L2_HINTS 7     /* L2 eviction priority of the single-problem residue GEMM's
-                                     tile loads: bits 0-1 for the A tiles, bits 2-3 for the B
-                                     tiles, each 0 (the default policy), 1 (evict last) or 2
-                                     (evict first).  Default 1: the A tiles, reused by the waves
-                                     of tiles that sweep the n-tiles of a raster group, evict
-                                     last (measured 2% faster at 16384^3 on GB300).  Results do
-                                     not depend on it. */
+#define OZAKI2_OPT_L2_HINTS 7     /* L2 eviction priority of the tile loads of the one-SM
+                                     residue-GEMM kernel (OZAKI2_GEMM_SINGLE): bits 0-1 for the
+                                     A tiles, bits 2-3 for the B tiles, each 0 (the default
+                                     policy), 1 (evict last) or 2 (evict first).  Default 1: the
+                                     A tiles, reused by the waves of tiles that sweep the n-tiles
+                                     of a raster group, evict last (measured 0-2% faster at
+                                     16384^3 on GB300).  The SM-pair kernel takes no hints
+                                     (evict-last A measured 5% slower there at 8192^3).  Results
+                                     do not depend on it. */
 #define OZAKI2_OPT_HOST_COPIES 8  /* how ozaki2_dgemm / ozaki2_sgemm move host-resident
                                      operands when the call pipelines over blocks of C (host
                                      operands, n >= 4096, op(B) = B): 0 (default) = kernels:
